@@ -1,0 +1,97 @@
+"""Snapshot windows and output aggregation in float64 (test infrastructure).
+
+Methods, "Streaming IaaS": a stream sampled at f_s is processed in fixed
+length snapshots; each request carries floor(f_s / r) = S strictly new
+samples, and the snapshot state moves forward by S, so snapshot k (k = 0, 1,
+...) is the window of the last W samples ending at time (k+1) S:
+
+    window_k = x[(k+1) S - W, (k+1) S)     (zero before the stream starts).
+
+Methods, "Data aggregation" and "Aggregation latency": a model whose output
+is itself a W-sample series returns, per snapshot, S samples of cleaned
+data.  With aggregation latency delta (in samples) the samples emitted at
+snapshot k are the times
+
+    [k S - delta, k S + S - delta).
+
+* LATEST(delta): the newest window's prediction on those times, i.e. the
+  slice pred_k[W - S - delta, W - delta).  delta = 0 is the paper's
+  "fully-online" / causal scheme (keep the most recent S samples).
+* AVERAGE(delta): the mean, over every window j <= k already pushed (j >= 0)
+  that covers a time, of that window's prediction there -- the overlapping
+  predictions the paper says could be aggregated.  delta = W - S averages
+  each sample over all W / S windows that cover it (full overlap-add).
+
+Cleaned strain is strain minus the aggregated prediction (Sec. 1, DeepClean
+predicts and subtracts noise); strain before time 0 is taken as zero.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LATEST = 0
+AVERAGE = 1
+
+
+def window(x_total, W, S, k):
+    """Snapshot window k of a (C, N) stream -> (C, W), zero-filled before t=0."""
+    x_total = np.asarray(x_total, np.float64)
+    C = x_total.shape[0]
+    end = (k + 1) * S
+    out = np.zeros((C, W))
+    lo = end - W
+    src_lo = max(lo, 0)
+    out[:, src_lo - lo:] = x_total[:, src_lo:end]
+    return out
+
+
+def emit_times(k, S, delta):
+    return np.arange(k * S - delta, k * S + S - delta)
+
+
+def aggregate(preds, W, S, mode, delta):
+    """Aggregated predictions per snapshot: preds (n, W) -> (n, S)."""
+    preds = np.asarray(preds, np.float64)
+    n = preds.shape[0]
+    assert 0 <= delta <= W - S
+    out = np.zeros((n, S))
+    for k in range(n):
+        if mode == LATEST:
+            out[k] = preds[k, W - S - delta:W - delta]
+            continue
+        for i, tau in enumerate(emit_times(k, S, delta)):
+            vals = []
+            for j in range(0, k + 1):  # windows already pushed, in order
+                start = (j + 1) * S - W
+                if start <= tau < start + W:
+                    vals.append(preds[j, tau - start])
+            out[k, i] = np.mean(vals)
+    return out
+
+
+def clean(strain_total, agg, S, delta):
+    """cleaned = strain - aggregated prediction on the emitted times (n, S)."""
+    strain_total = np.asarray(strain_total, np.float64)
+    n = agg.shape[0]
+    out = np.zeros((n, S))
+    for k in range(n):
+        t = emit_times(k, S, delta)
+        s = np.where(t >= 0, strain_total[np.clip(t, 0, None)], 0.0)
+        out[k] = s - agg[k]
+    return out
+
+
+def run_deepclean_stream(forward, witness_total, strain_total, W, S, n_snap,
+                         mode, delta, snaps=None):
+    """Push n_snap snapshots; returns (predictions (n, W), cleaned (n, S)).
+
+    ``forward`` maps a (B, C, W) batch of windows to (B, W) predictions.
+    ``snaps`` restricts the windows evaluated (others are not needed by
+    LATEST); by default every snapshot is evaluated.
+    """
+    ks = range(n_snap) if snaps is None else snaps
+    wins = np.stack([window(witness_total, W, S, k) for k in ks])
+    preds = np.zeros((n_snap, W))
+    preds[list(ks)] = forward(wins)
+    agg = aggregate(preds, W, S, mode, delta)
+    return preds, clean(strain_total, agg, S, delta)
