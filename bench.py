@@ -1,0 +1,460 @@
+"""Streaming DeepClean benchmark on one GB300 (or N independent replicas).
+
+Workload: DeepClean-shaped streaming inference, windows of 21 x 32768 samples
+(8 s at 4096 Hz), stride 256 samples per snapshot, 64 snapshots per batch,
+full overlap-add aggregation (each cleaned sample averaged over the 128
+windows that cover it).  One step = one push of 64 new snapshots through the
+whole streaming path: device ring update, DeepClean on the 64 windows, and
+the fused subtract + overlap-add that emits 64 x 256 cleaned samples.
+
+Metric: snapshots/s (whole job), with p50/p99 step latency, for the BF16
+tensor-core path and the plain FP32 path (value = the BF16 path when built).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gw|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the path
+has no cross-stream exchange); the timed region is bracketed by barriers and
+the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W, S, B, C = 32768, 256, 64, 21
+METRIC = "streaming snapshots/s and p50/p99 latency, BF16 vs FP32 path at stated error, 1 GB300"
+WORKLOAD = "DeepClean streaming: 21x32768 windows (8 s @ 4096 Hz), stride 256, batch 64, overlap-add"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def dc_flops_per_window(L=W):
+    """Algorithmic FLOPs of one DeepClean window (2 per MAC, valid outputs only)."""
+    from paper_2108_12430_gb300 import synth
+    f, lin = 0, L
+    for kind, cin, cout, k, s, pl, pr, op, bn, act in synth.DEEPCLEAN_LAYERS:
+        if kind == "conv":
+            lout = (lin + pl + pr - k) // s + 1
+            f += 2 * cout * cin * k * lout
+        else:
+            lout = (lin - 1) * s - pl - pr + k + op
+            f += 2 * cout * cin * k * lin
+        lin = lout
+    return f
+
+
+def dc_layer_flops(L=W):
+    from paper_2108_12430_gb300 import synth
+    out, lin = [], L
+    for kind, cin, cout, k, s, pl, pr, op, bn, act in synth.DEEPCLEAN_LAYERS:
+        if kind == "conv":
+            lout = (lin + pl + pr - k) // s + 1
+            out.append(2 * cout * cin * k * lout)
+        else:
+            lout = (lin - 1) * s - pl - pr + k + op
+            out.append(2 * cout * cin * k * lin)
+        lin = lout
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def make_stream_inputs(n_samples, seed=1234):
+    from paper_2108_12430_gb300 import synth
+    wit = synth.witness_channels(seed, C, n_samples)
+    strain = synth.coupled_strain(seed, wit)
+    return wit.astype(np.float32), strain.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_path(G, torch, precision, steps, warmup, wit_d, str_d, flush, dev_index):
+    """Time `steps` device-resident pushes; returns per-step ms and profile."""
+    from paper_2108_12430_gb300 import synth
+    ctx = G.gw_ctx_create(dev_index, 0)
+    params = synth.flatten_params(synth.deepclean_params(1234))
+    m = G.gw_model_create(ctx, G.GW_MODEL_DEEPCLEAN, precision, C, params)
+    s = G.gw_stream_create(ctx, [m], 1, C, W, S, B, G.GW_AGG_AVERAGE, W - S)
+    out = torch.zeros(B * S, device="cuda")
+    st = torch.cuda.current_stream()
+    h = st.cuda_stream
+    n_step = B * S
+
+    def push(i):
+        o = i * n_step
+        G.gw_stream_push(s, B, wit_d[:, o:o + n_step].contiguous().data_ptr(),
+                         str_d[o:o + n_step].contiguous().data_ptr(), out.data_ptr(), G.GW_MEM_DEVICE, h)
+
+    # pre-slice inputs so the timed region holds only the library's work
+    slices = [(wit_d[:, i * n_step:(i + 1) * n_step].contiguous(), str_d[i * n_step:(i + 1) * n_step].contiguous())
+              for i in range(warmup + steps)]
+
+    def push_pre(i):
+        w_, s_ = slices[i]
+        G.gw_stream_push(s, B, w_.data_ptr(), s_.data_ptr(), out.data_ptr(), G.GW_MEM_DEVICE, h)
+
+    for i in range(warmup):
+        push_pre(i)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = G.gw_launch_count()
+    for i in range(steps):
+        flush.zero_()  # evict L2 between timed steps (outside the events)
+        evs[i][0].record(st)
+        push_pre(warmup + i)
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    launches = G.gw_launch_count() - l0
+    ms = [a.elapsed_time(b) for a, b in evs]
+    res = {"ms": ms, "launches_per_step": launches / steps}
+    return ctx, m, s, res, push_pre
+
+
+def profile_pass(G, torch, push_fn, first, steps, flush):
+    G.gw_profile_enable(True)
+    for i in range(steps):
+        flush.zero_()
+        push_fn(first + i)
+    torch.cuda.synchronize()
+    prof = G.gw_profile_read()
+    G.gw_profile_enable(False)
+    return prof
+
+
+def accuracy(G, torch, precision, dev_index):
+    """rel-L2 of two full 21 x 32768 windows against the FP64 oracle."""
+    from oracle import nets
+    from paper_2108_12430_gb300 import synth
+    ctx = G.gw_ctx_create(dev_index, 0)
+    params = synth.deepclean_params(1234)
+    m = G.gw_model_create(ctx, G.GW_MODEL_DEEPCLEAN, precision, C, synth.flatten_params(params))
+    x = synth.witness_channels(77, C, W + S)
+    y = torch.zeros(2, W, device="cuda")
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    G.gw_deepclean_forward(m, xd.data_ptr(), W + S, S, 2, W, y.data_ptr())
+    torch.cuda.synchronize()
+    wins = np.stack([x[:, :W], x[:, S:S + W]]).astype(np.float32).astype(np.float64)
+    ref = nets.deepclean_forward(wins, params, synth.DEEPCLEAN_LAYERS)
+    got = y.cpu().numpy().astype(np.float64)
+    err = max(float(np.linalg.norm(got[i] - ref[i]) / np.linalg.norm(ref[i])) for i in range(2))
+    G.gw_model_destroy(m)
+    G.gw_ctx_destroy(ctx)
+    return err
+
+
+def e2e_pass(G, torch, s, wit_h, str_h, first, steps):
+    """Host-buffer pushes through the public API: H2D + compute + D2H per step."""
+    n_step = B * S
+    out = torch.empty(B * S, dtype=torch.float32).pin_memory()
+    lat = []
+    lib = G.lib()
+    h = torch.cuda.current_stream().cuda_stream
+    for i in range(steps):
+        w_, s_ = wit_h[first + i], str_h[first + i]
+        t0 = time.perf_counter()
+        rc = lib.gw_stream_push(s, B, w_.data_ptr(), s_.data_ptr(), out.data_ptr(), G.GW_MEM_HOST, h)
+        lat.append((time.perf_counter() - t0) * 1e3)
+        if rc < 0:
+            raise G.GwError(rc, lib.gw_last_error().decode())
+    return lat
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2108_12430_gb300 import build as Bld
+    Bld.build()
+    from paper_2108_12430_gb300 import gwstream as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev_index = torch.cuda.current_device()
+    K, Wm = args.steps, args.warmup
+    n_total = (Wm + K + 8) * B * S
+    wit, strain = make_stream_inputs(n_total, seed=1234 + rank)
+    wit_d = torch.from_numpy(wit).cuda()
+    str_d = torch.from_numpy(strain).cuda()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    pk, pk_src = peaks()
+
+    paths = {}
+    precisions = [("bf16", G.GW_BF16), ("fp32", G.GW_FP32)]
+    headline = None
+    clocks = None
+    for name, prec in precisions:
+        try:
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            with ClockSampler(dev_index) as cs:
+                ctx, m, s, res, push_fn = run_path(G, torch, prec, K, Wm, wit_d, str_d, flush, dev_index)
+            if world > 1:
+                dist.barrier()
+        except G.GwError as e:
+            if e.code == G.GW_ENOTIMPL:
+                paths[name] = {"unavailable": str(e)}
+                continue
+            raise
+        ms = np.array(res["ms"])
+        tot = float(ms.sum())
+        if world > 1:
+            t = torch.tensor([tot], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        prof = profile_pass(G, torch, push_fn, Wm, min(K, 8), flush)
+        # host-buffer e2e: pinned host copies of the next steps' inputs
+        n_step = B * S
+        first = Wm + K
+        ne2e = min(K, 8)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        wit_h = {first + i: pin(wit[:, (first + i) * n_step:(first + i + 1) * n_step])
+                 for i in range(ne2e)}
+        str_h = {first + i: pin(strain[(first + i) * n_step:(first + i + 1) * n_step]) for i in range(ne2e)}
+        # re-align the stream head is not needed: pushes continue the same stream
+        lat = e2e_pass(G, torch, s, wit_h, str_h, first, ne2e)
+        err = accuracy(G, torch, prec, dev_index) if rank == 0 else None
+        G.gw_stream_destroy(s)
+        G.gw_model_destroy(m)
+        G.gw_ctx_destroy(ctx)
+        conv_keys = [k for k in prof if k.startswith("conv")]
+        conv_ms = sum(prof[k][0] for k in conv_keys)
+        conv_n = sum(prof[k][1] for k in conv_keys)
+        prof_steps = min(K, 8)
+        conv_flops = dc_flops_per_window() * B * prof_steps
+        paths[name] = {
+            "value": B * K * world / (tot / 1e3),
+            "ms_per_step": tot / K,
+            "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)),
+            "rel_l2_vs_fp64_oracle": err,
+            "e2e_value": B * ne2e * world / (sum(lat) / 1e3),
+            "e2e_p50_ms": float(np.percentile(lat, 50)),
+            "e2e_p99_ms": float(np.percentile(lat, 99)),
+            "gpu_launches_per_step": res["launches_per_step"],
+            "conv_tflops": conv_flops / (conv_ms / 1e3) / 1e12 if conv_ms else None,
+            "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+            "clocks": cs.summary(),
+        }
+        if headline is None:
+            headline = name
+            clocks = paths[name]["clocks"]
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    hp = paths[headline]
+    kernels = hp["kernels"]
+    # dominant kernel family: the conv layers (same kernel, different shapes)
+    conv_ms_step = sum(v["ms_per_step"] for k, v in kernels.items() if k.startswith("conv"))
+    achieved = dc_flops_per_window() * B / (conv_ms_step / 1e3) / 1e12
+    if headline == "bf16":
+        peak = pk["bf16_tflops"]
+        bound = "tensor"
+        peak_note = f"dense bf16 burst, {pk_src}"
+    else:
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound = "alu"
+        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
+    traffic = None
+    cpu = cpu_baseline(budget_s=args.cpu_seconds)
+    line = {
+        "metric": METRIC,
+        "value": hp["value"],
+        "unit": "snapshots/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": hp["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16" if headline == "bf16" else "f32",
+        "data": "synthetic (seeded witness noise + coloured aLIGO-like strain with 60 Hz coupling)",
+        "config": {"workload": WORKLOAD, "window": W, "stride": S, "batch": B, "channels": C,
+                   "aggregation": "AVERAGE, delay W-S", "path": headline,
+                   "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "p50_ms": hp["p50_ms"],
+        "p99_ms": hp["p99_ms"],
+        "rel_l2_vs_fp64_oracle": hp["rel_l2_vs_fp64_oracle"],
+        "e2e": {"value": hp["e2e_value"], "unit": "snapshots/s", "p50_ms": hp["e2e_p50_ms"],
+                "p99_ms": hp["e2e_p99_ms"],
+                "h2d_bytes_per_step": (C + 1) * B * S * 4, "d2h_bytes_per_step": B * S * 4},
+        "gpu_launches": int(round(hp["gpu_launches_per_step"] * K)),
+        "roofline": {"bound": bound, "kernel": "conv layers (8 launches per step)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_note,
+                     "per_unit": f"{dc_flops_per_window()} flop per window x {B} windows per step"},
+        "paths": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in paths.items()},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_snapshot_seconds(n_windows, seed=4321):
+    """Time the FP64 oracle on n_windows consecutive snapshots of the workload."""
+    from oracle import nets, stream as ostream
+    from paper_2108_12430_gb300 import synth
+    params = synth.deepclean_params(1234)
+    wit = synth.witness_channels(seed, C, W + (n_windows - 1) * S)
+    strain = synth.coupled_strain(seed, wit)
+    t0 = time.perf_counter()
+    wins = np.stack([wit[:, j * S:j * S + W] for j in range(n_windows)])
+    preds = nets.deepclean_forward(wins, params, synth.DEEPCLEAN_LAYERS)
+    agg = ostream.aggregate(preds, W, S, ostream.AVERAGE, 0)
+    ostream.clean(strain, agg, S, 0)
+    return time.perf_counter() - t0
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(budget_s=15.0):
+    t1 = oracle_snapshot_seconds(1)
+    n = int(max(1, min(64, budget_s / max(t1, 1e-3))))
+    t = oracle_snapshot_seconds(n)
+    return {"value": n / t, "unit": "snapshots/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"{n} consecutive 21x32768 windows (stride 256) through the FP64 numpy oracle "
+                      f"DeepClean + aggregation, {t:.1f} s"}
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle_snapshot_seconds(1)
+    for _ in range(args.warmup):
+        oracle_snapshot_seconds(1)
+    ts = [oracle_snapshot_seconds(1) for _ in range(args.steps)]
+    tot = sum(ts)
+    v = args.steps / tot
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "snapshots/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "window": W, "stride": S, "batch": B,
+                                        "reference_sample": "1 snapshot (one window) per step"},
+        "p50_ms": float(np.percentile(ts, 50) * 1e3), "p99_ms": float(np.percentile(ts, 99) * 1e3),
+        "cpu_baseline": {"value": v, "unit": "snapshots/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": "1 window of 21x32768 per step through the FP64 numpy oracle"},
+        "e2e": {"value": v, "unit": "snapshots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gw", "reference"], default="gw")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * gwstream.h -- C ABI of the GB300 streaming inference library for detector
+ * time series (DeepClean-shaped noise regression -> subtraction -> resample
+ * -> whitening -> BBHnet-shaped detection), after arXiv 2108.12430.
+ *
+ * Conventions for every entry point
+ *  - Returns GW_OK (0) or a negative GW_E* code; gw_last_error() gives a
+ *    thread-local message for the last failure on the calling thread.
+ *    No C++ exception crosses this boundary.
+ *  - "device" pointers are CUDA device memory on the context's device (for
+ *    example a torch CUDA tensor's data_ptr()); "host" pointers are CPU memory
+ *    (pinned memory makes the copies asynchronous-capable but is not
+ *    required).  The caller owns every buffer it passes; the library owns the
+ *    objects it creates and all device memory behind them (weights, stream
+ *    state, workspaces) until the matching *_destroy.
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device-pointer entry points are stream-ordered and return
+ *    before the GPU finishes; host-pointer entry points return after their
+ *    outputs have been written to host memory.
+ *  - Sample layouts are row-major, time innermost: [batch][channel][time].
+ *  - Layers whose input size fails the checks stated below return GW_EINVAL
+ *    and launch nothing.
+ */
+#ifndef GWSTREAM_H
+#define GWSTREAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GW_OK          0
+#define GW_EINVAL     -1  /* bad argument: null pointer, size or mode out of range */
+#define GW_EBUDGET    -2  /* the object would exceed the context's HBM budget */
+#define GW_ENOMEM     -3  /* cudaMalloc failed */
+#define GW_ECUDA      -4  /* a CUDA runtime call or kernel launch failed */
+#define GW_ETIMEOUT   -5  /* a bounded wait ran out (host or device side) */
+#define GW_ESTATE     -6  /* object in the wrong state (e.g. destroyed, or faulted) */
+#define GW_ENOTIMPL   -7  /* combination not implemented (e.g. a precision for a model kind) */
+#define GW_ENONFINITE -8  /* NaN or Inf found in an input snapshot */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum gw_precision { GW_FP32 = 0, GW_BF16 = 1, GW_FP8 = 2 };
+enum gw_model_kind { GW_MODEL_DEEPCLEAN = 0, GW_MODEL_BBHNET = 1 };
+enum gw_agg_mode { GW_AGG_LATEST = 0, GW_AGG_AVERAGE = 1 };
+enum gw_mem { GW_MEM_HOST = 0, GW_MEM_DEVICE = 1 };
+
+typedef struct gw_ctx* gw_ctx_t;
+typedef struct gw_model* gw_model_t;
+typedef struct gw_fir* gw_fir_t;
+typedef struct gw_stream* gw_stream_t;
+
+const char* gw_last_error(void);
+const char* gw_version(void);
+
+/* ---- context ------------------------------------------------------------
+ * One context per GPU.  `hbm_budget_bytes` caps the device memory of every
+ * object created under the context (0 = no cap); a create that would exceed
+ * it returns GW_EBUDGET and allocates nothing.
+ */
+int gw_ctx_create(int device, size_t hbm_budget_bytes, gw_ctx_t* out);
+int gw_ctx_destroy(gw_ctx_t ctx);
+size_t gw_ctx_bytes_in_use(gw_ctx_t ctx);
+
+/* ---- models -------------------------------------------------------------
+ * DeepClean-shaped autoencoder (Sec. 1, "DeepClean"): 21 -> 8 (k7 s1),
+ * 8 -> 16 -> 32 -> 64 (k7 s2 p3), transposed 64 -> 32 -> 16 -> 8 (k7 s2 p3,
+ * output padding 1), each with eval BatchNorm + tanh; output conv 8 -> 1 (k7
+ * p3).  BBHnet-shaped classifier (Sec. 1, "BBHnet"): stem 2 -> 32 (k16, pad
+ * 7/8) + BN + ReLU, 4 residual blocks (32, 64, 128, 256 channels; conv k7 s2,
+ * conv k7 s1, shortcut k1 s2, BN after each), global average pool, linear
+ * 256 -> 1.
+ *
+ * `params` (host, FP32) holds the raw, unfolded parameters in canonical
+ * order: per layer w (PyTorch layout: conv [C_out][C_in][K], transposed conv
+ * [C_in][C_out][K]), b [C_out], then BatchNorm gamma, beta, running mean,
+ * running var [C_out] each; BBHnet appends the head w [256], b [1].  Its
+ * length must equal gw_model_param_count(kind, n_in).  BatchNorm (eps 1e-5)
+ * is folded into the weights in FP64 on the host at create time, then the
+ * weights are cast to the model's precision and copied to the device.
+ * `in_mean` / `in_std` (host, n_in floats, may be NULL) standardise the
+ * input per channel, (x - mean) / std, inside the first kernel.
+ * `act_scales` (FP8 only; host, one per conv layer, may be NULL): static
+ * per-tensor scale of each layer's input activations.
+ */
+typedef struct gw_model_desc {
+  int kind;               /* enum gw_model_kind */
+  int precision;          /* enum gw_precision */
+  int n_in;               /* input channels: 21 for DeepClean, 2 for BBHnet */
+  const float* params;    /* host */
+  size_t n_params;
+  const float* in_mean;   /* host [n_in] or NULL */
+  const float* in_std;    /* host [n_in] or NULL */
+  const float* act_scales;/* host [n_layers] or NULL */
+  int n_act_scales;
+} gw_model_desc;
+
+size_t gw_model_param_count(int kind, int n_in);
+int gw_model_create(gw_ctx_t ctx, const gw_model_desc* desc, gw_model_t* out);
+int gw_model_destroy(gw_model_t m);
+
+/* DeepClean forward over B windows of L samples (L a multiple of 8).
+ * x: device FP32; channel c of window b is the L samples starting at
+ *    x + c * ld + b * window_stride, so B consecutive snapshots of one stream
+ *    are overlapping views of one [C][ld] buffer (window_stride = stride S).
+ * y: device FP32 [B][L], the predicted noise.
+ * Output per window: the network of gw_model_create applied to that window
+ * alone, zero padding at its edges (Methods, "Streaming IaaS": every
+ * snapshot goes through the static model on its own). */
+int gw_deepclean_forward(gw_model_t m, const float* x, int64_t ld, int64_t window_stride,
+                         int B, int L, float* y, void* cuda_stream);
+
+/* BBHnet logits.  x: device FP32 [B][2][L] whitened strain (L a multiple of
+ * 16, L >= 16); logits: device FP32 [B]. */
+int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, void* cuda_stream);
+
+/* ---- whitening FIR --------------------------------------------------------
+ * Linear-phase whitening filter designed in FP64 on the host from a
+ * one-sided PSD sampled on f_j = j fs / nfft, j = 0 .. nfft/2 (n_psd =
+ * nfft/2 + 1, nfft even): target amplitude sqrt(2 / (fs S_j)) (unit-variance
+ * output), zero-phase inverse DFT, centred, truncated to `ntaps` (odd,
+ * <= nfft) and Hann-windowed.  `precision` selects FP32 SIMT or BF16
+ * tensor-core application. */
+int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps,
+                            int precision, gw_fir_t* out);
+int gw_fir_destroy(gw_fir_t f);
+int gw_fir_ntaps(gw_fir_t f);
+/* Host copy of the FP64 taps (ntaps doubles). */
+int gw_fir_taps(gw_fir_t f, double* taps_out);
+/* Valid-mode filtering y[b][c][n] = sum_k h[k] x[b][c][n + k],
+ * n < L_in - ntaps + 1.  x: device FP32 [B][C][L_in]; y: device FP32
+ * [B][C][L_in - ntaps + 1]. */
+int gw_whiten(gw_fir_t f, const float* x, int B, int C, int L_in, float* y, void* cuda_stream);
+
+/* ---- streams ---------------------------------------------------------------
+ * A stream keeps the snapshot state of one or two detectors on the device
+ * (Methods, "Streaming IaaS": the state holds the previous snapshot and each
+ * request brings only floor(f_s / r) = stride new samples).  Snapshot k is
+ * the last `window` samples ending after push k; before the stream has
+ * `window` samples the missing past is zero.  Each push of n_snap snapshots
+ * runs DeepClean on the n_snap windows (one batch), subtracts the aggregated
+ * prediction from strain and returns stride cleaned samples per snapshot
+ * (Methods, "Data aggregation" and "Aggregation latency"):
+ *   emitted times of snapshot k: [k*stride - agg_delay, (k+1)*stride - agg_delay)
+ *   GW_AGG_LATEST : the newest window's prediction on those times;
+ *   GW_AGG_AVERAGE: the mean over every window pushed so far that covers a
+ *                   time, summed in window order (agg_delay = window - stride
+ *                   gives full overlap-add over window/stride windows).
+ * Strain before time 0 counts as zero.  Constraints: stride a multiple of 8,
+ * window a multiple of 8 and of stride, 0 <= agg_delay <= window - stride,
+ * 1 <= n_snap <= max_batch. */
+typedef struct gw_stream_desc {
+  int n_det;       /* detectors, 1 or 2; one DeepClean model each (may be the same object) */
+  int n_witness;   /* witness channels per detector (the model's n_in) */
+  int window;      /* W samples per snapshot */
+  int stride;      /* S new samples per snapshot */
+  int max_batch;   /* largest n_snap of one push */
+  int agg_mode;    /* enum gw_agg_mode */
+  int agg_delay;   /* aggregation latency in samples */
+} gw_stream_desc;
+
+int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* desc, const gw_model_t* deepclean,
+                     gw_stream_t* out);
+int gw_stream_destroy(gw_stream_t s);
+/* Push n_snap snapshots.
+ * witness: [n_det][n_witness][n_snap*stride]; strain: [n_det][n_snap*stride];
+ * clean_out: [n_det][n_snap*stride] (snapshot-major within each detector).
+ * mem = GW_MEM_HOST: host pointers; the call copies in, runs, copies out and
+ *   returns when clean_out is written.
+ * mem = GW_MEM_DEVICE: device pointers; stream-ordered on cuda_stream.
+ * Non-finite input samples are rejected with GW_ENONFINITE before the state
+ * changes (host mode; device mode checks on the device and reports through
+ * gw_stream_status). */
+int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float* strain,
+                   float* clean_out, int mem, void* cuda_stream);
+/* Samples pushed so far per detector. */
+int64_t gw_stream_head(gw_stream_t s);
+/* Device-side status of the stream: GW_OK or GW_ENONFINITE (sticky until reset). */
+int gw_stream_status(gw_stream_t s, void* cuda_stream);
+
+/* ---- instrumentation ---------------------------------------------------------
+ * Process-wide, for benchmarks.  gw_profile_enable(1) clears the record and
+ * brackets every kernel launch the library makes with a pair of CUDA events on
+ * the launching stream (adds a little host overhead per launch);
+ * gw_profile_read synchronises those events and writes, per kernel name, the
+ * summed device time and the launch count.  `names` receives up to
+ * `names_len` bytes of '\n'-separated names in the order of the other two
+ * arrays (at most `max_entries` each).  Returns the number of names, or a
+ * negative code.  gw_launch_count returns the number of kernels launched by
+ * the library since load (always counted). */
+int gw_profile_enable(int on);
+int gw_profile_read(char* names, size_t names_len, double* total_ms, int64_t* launches, int max_entries);
+int64_t gw_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWSTREAM_H */

@@ -1,0 +1,747 @@
+// Host runtime behind the C ABI: contexts, models (FP64 BatchNorm fold and
+// packing), whitening FIR design (FP64), offline forwards and streams.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <atomic>
+#include <map>
+#include <mutex>
+
+#include "gw_internal.h"
+
+namespace gw {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// ---- instrumentation ---------------------------------------------------------
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::atomic<int64_t> g_launches{0};
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof;
+
+Prof::Prof(const char* name, cudaStream_t s) : slot(-1), st(s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRec r;
+  r.name = name;
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+  cudaEventRecord(r.a, st);
+  g_prof.push_back(r);
+  slot = (int)g_prof.size() - 1;
+}
+
+Prof::~Prof() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(g_prof[slot].b, st);
+}
+
+static void prof_clear() {
+  for (auto& r : g_prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+}
+
+// ---- device memory with a per-context budget ------------------------------
+static std::mutex g_alloc_mu;
+
+void* dev_alloc(gw_ctx* ctx, size_t bytes, size_t* counter) {
+  if (bytes == 0) return nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+      throw Error(GW_EBUDGET, "HBM budget exceeded: " + std::to_string(ctx->in_use + bytes) + " > " +
+                                  std::to_string(ctx->budget) + " bytes");
+    ctx->in_use += bytes;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    ctx->in_use -= bytes;
+    throw Error(GW_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  if (counter) *counter += bytes;
+  return p;
+}
+
+void dev_free(gw_ctx* ctx, void* p, size_t bytes, size_t* counter) {
+  if (!p) return;
+  cudaFree(p);
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  ctx->in_use -= bytes;
+  if (counter) *counter -= bytes;
+}
+
+// ---- layer tables ----------------------------------------------------------
+std::vector<LayerSpec> deepclean_specs(int n_in) {
+  std::vector<LayerSpec> v;
+  v.push_back({false, n_in, 8, 7, 1, 3, 3, 0, true, ACT_TANH});
+  v.push_back({false, 8, 16, 7, 2, 3, 3, 0, true, ACT_TANH});
+  v.push_back({false, 16, 32, 7, 2, 3, 3, 0, true, ACT_TANH});
+  v.push_back({false, 32, 64, 7, 2, 3, 3, 0, true, ACT_TANH});
+  v.push_back({true, 64, 32, 7, 2, 3, 3, 1, true, ACT_TANH});
+  v.push_back({true, 32, 16, 7, 2, 3, 3, 1, true, ACT_TANH});
+  v.push_back({true, 16, 8, 7, 2, 3, 3, 1, true, ACT_TANH});
+  v.push_back({false, 8, 1, 7, 1, 3, 3, 0, false, ACT_NONE});
+  return v;
+}
+
+std::vector<LayerSpec> bbhnet_specs(int n_in) {
+  std::vector<LayerSpec> v;
+  v.push_back({false, n_in, 32, 16, 1, 7, 8, 0, true, ACT_RELU});
+  int cin = 32;
+  for (int cout : {32, 64, 128, 256}) {
+    v.push_back({false, cin, cout, 7, 2, 3, 3, 0, true, ACT_RELU});
+    v.push_back({false, cout, cout, 7, 1, 3, 3, 0, true, ACT_NONE});
+    v.push_back({false, cin, cout, 1, 2, 0, 0, 0, true, ACT_NONE});
+    cin = cout;
+  }
+  return v;
+}
+
+static size_t layer_param_count(const LayerSpec& s) {
+  return (size_t)s.cin * s.cout * s.k + s.cout + (s.bn ? 4 * (size_t)s.cout : 0);
+}
+
+static std::vector<LayerSpec> specs_for(int kind, int n_in) {
+  if (kind == GW_MODEL_DEEPCLEAN) return deepclean_specs(n_in);
+  if (kind == GW_MODEL_BBHNET) return bbhnet_specs(n_in);
+  throw Error(GW_EINVAL, "unknown model kind");
+}
+
+// FP64 BatchNorm fold (eval statistics, eps = 1e-5):
+//   a = gamma / sqrt(var + eps); w' = w a (per output channel); b' = (b - mean) a + beta.
+// The folded weights come back in [C_out][C_in][K] order for both conv kinds.
+static void fold_layer(const LayerSpec& s, const float* p, std::vector<double>& w, std::vector<double>& b) {
+  const size_t nw = (size_t)s.cin * s.cout * s.k;
+  const float* pw = p;
+  const float* pb = p + nw;
+  w.assign(nw, 0.0);
+  b.assign(s.cout, 0.0);
+  std::vector<double> a(s.cout, 1.0), shift(s.cout, 0.0);
+  if (s.bn) {
+    const float* g = pb + s.cout;
+    const float* be = g + s.cout;
+    const float* mu = be + s.cout;
+    const float* var = mu + s.cout;
+    for (int o = 0; o < s.cout; ++o) {
+      a[o] = (double)g[o] / std::sqrt((double)var[o] + 1e-5);
+      b[o] = ((double)pb[o] - (double)mu[o]) * a[o] + (double)be[o];
+    }
+  } else {
+    for (int o = 0; o < s.cout; ++o) b[o] = pb[o];
+  }
+  for (int o = 0; o < s.cout; ++o)
+    for (int i = 0; i < s.cin; ++i)
+      for (int k = 0; k < s.k; ++k) {
+        const double raw = s.transposed ? pw[((size_t)i * s.cout + o) * s.k + k] : pw[((size_t)o * s.cin + i) * s.k + k];
+        w[((size_t)o * s.cin + i) * s.k + k] = raw * a[o];
+      }
+}
+
+template <typename T>
+static T* upload(gw_model* m, const std::vector<T>& host) {
+  T* d = (T*)dev_alloc(m->ctx, host.size() * sizeof(T), &m->bytes);
+  m->allocs.push_back(d);
+  GW_CUDA(cudaMemcpy(d, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return d;
+}
+
+static void model_free(gw_model* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  for (void* p : m->allocs) cudaFree(p);
+  if (m->ws) cudaFree(m->ws);
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    m->ctx->in_use -= m->bytes + m->ws_bytes;
+  }
+  delete m;
+}
+
+static void* model_workspace(gw_model* m, size_t bytes) {
+  if (bytes <= m->ws_bytes) return m->ws;
+  GW_CUDA(cudaDeviceSynchronize());
+  if (m->ws) dev_free(m->ctx, m->ws, m->ws_bytes, nullptr);
+  m->ws = nullptr;
+  m->ws_bytes = 0;
+  m->ws = dev_alloc(m->ctx, bytes, nullptr);
+  m->ws_bytes = bytes;
+  return m->ws;
+}
+
+// ---- FIR design (FP64) -----------------------------------------------------
+// Zero-phase inverse real DFT of the amplitude A_j = sqrt(2 / (fs S_j)),
+// centred on tap (ntaps-1)/2, truncated and Hann-windowed:
+//   h0[n] = (A_0 + A_{N/2} cos(pi n) + 2 sum_{j=1}^{N/2-1} A_j cos(2 pi j n / N)) / N.
+static std::vector<double> design_whitening(const double* psd, int n_psd, double fs, int ntaps) {
+  const int N = 2 * (n_psd - 1);
+  std::vector<double> A(n_psd), ctab(N);
+  for (int j = 0; j < n_psd; ++j) A[j] = std::sqrt(2.0 / (fs * psd[j]));
+  for (int m = 0; m < N; ++m) ctab[m] = std::cos(2.0 * M_PI * (double)m / (double)N);
+  const int c = (ntaps - 1) / 2;
+  std::vector<double> h(ntaps);
+  for (int n = 0; n <= c; ++n) {
+    double s = A[0] + A[N / 2] * ((n & 1) ? -1.0 : 1.0);
+    double acc = 0.0;
+    long long jn = 0;
+    for (int j = 1; j < N / 2; ++j) {
+      jn += n;
+      if (jn >= N) jn -= N;
+      acc += A[j] * ctab[jn];
+    }
+    const double h0 = (s + 2.0 * acc) / (double)N;
+    const int k1 = c + n, k2 = c - n;
+    h[k1] = h0 * 0.5 * (1.0 - std::cos(2.0 * M_PI * k1 / (ntaps - 1)));
+    h[k2] = h0 * 0.5 * (1.0 - std::cos(2.0 * M_PI * k2 / (ntaps - 1)));
+  }
+  return h;
+}
+
+// ---- forward runners ---------------------------------------------------------
+static const char* kDcNames[8] = {"conv_f32.enc1", "conv_f32.enc2", "conv_f32.enc3", "conv_f32.enc4",
+                                  "conv_f32.dec1", "conv_f32.dec2", "conv_f32.dec3", "conv_f32.out"};
+// DeepClean on B windows in FP32.  Input element (b, c, t) at
+// x + b*xb + c*xc + t; the first layer standardises when mean != null.
+static void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
+                          float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st) {
+  const auto& Ls = m->layers;
+  const float* in = x;
+  int64_t ib = xb, ic = xc;
+  int lin = L;
+  float* bufs[2] = {buf0, buf1};
+  for (size_t li = 0; li < Ls.size(); ++li) {
+    const LayerSpec& s = Ls[li].s;
+    const int lout = s.lout(lin);
+    ConvF32Args a{};
+    a.x = in; a.xb = ib; a.xc = ic;
+    const bool last = (li + 1 == Ls.size());
+    if (last) {
+      a.y = y; a.yb = y_ld; a.yc = 0;
+    } else {
+      a.y = bufs[li & 1]; a.yb = (int64_t)s.cout * lout; a.yc = lout;
+    }
+    a.res = nullptr;
+    a.w = Ls[li].w; a.bias = Ls[li].b;
+    a.in_mean = (li == 0 && standardise) ? m->in_mean : nullptr;
+    a.in_istd = (li == 0 && standardise) ? m->in_istd : nullptr;
+    a.B = B; a.lin = lin; a.lout = lout; a.s = s;
+    {
+      Prof p(kDcNames[li], st);
+      launch_conv_f32(a, st);
+    }
+    in = a.y; ib = a.yb; ic = a.yc;
+    lin = lout;
+  }
+}
+
+static void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st) {
+  const auto& Ls = m->layers;
+  const size_t per = (size_t)B * 32 * L;
+  float* buf[3] = {ws, ws + per, ws + 2 * per};
+  auto conv = [&](const LayerDev& Ld, const float* in, int64_t ib, int64_t ic, int lin, float* out,
+                  const float* res, int act) {
+    LayerSpec s = Ld.s;
+    s.act = act;
+    const int lout = s.lout(lin);
+    ConvF32Args a{};
+    a.x = in; a.xb = ib; a.xc = ic;
+    a.y = out; a.yb = (int64_t)s.cout * lout; a.yc = lout;
+    a.res = res; a.rb = a.yb; a.rc = a.yc;
+    a.w = Ld.w; a.bias = Ld.b;
+    a.B = B; a.lin = lin; a.lout = lout; a.s = s;
+    Prof p("conv_f32.bbhnet", st);
+    launch_conv_f32(a, st);
+    return lout;
+  };
+  int l = conv(Ls[0], x, 2LL * L, L, L, buf[0], nullptr, ACT_RELU);
+  int cin = 32, h = 0;
+  for (int blk = 0; blk < 4; ++blk) {
+    const LayerDev& c1 = Ls[1 + 3 * blk];
+    const LayerDev& c2 = Ls[2 + 3 * blk];
+    const LayerDev& sc = Ls[3 + 3 * blk];
+    const int cout = c1.s.cout;
+    const int a_i = (h + 1) % 3, o_i = (h + 2) % 3;
+    const int64_t hb = (int64_t)cin * l, hc = l;
+    const int l2 = conv(c1, buf[h], hb, hc, l, buf[a_i], nullptr, ACT_RELU);
+    conv(sc, buf[h], hb, hc, l, buf[o_i], nullptr, ACT_NONE);
+    conv(c2, buf[a_i], (int64_t)cout * l2, l2, l2, buf[o_i], buf[o_i], ACT_RELU);
+    h = o_i;
+    l = l2;
+    cin = cout;
+  }
+  Prof p("gap_linear_f32", st);
+  launch_gap_linear_f32(buf[h], (int64_t)cin * l, l, B, cin, l, m->head_w, m->head_b, logits, st);
+}
+
+}  // namespace gw
+
+// ---- stream object ------------------------------------------------------------
+struct gw_stream {
+  gw_ctx* ctx = nullptr;
+  gw_stream_desc d{};
+  gw_model* dc[2] = {nullptr, nullptr};
+  int64_t R = 0;
+  int64_t head = 0;
+  float* ring_f32[2] = {nullptr, nullptr};
+  __nv_bfloat16* ring_bf16[2] = {nullptr, nullptr};
+  float* strain[2] = {nullptr, nullptr};
+  float* acc[2] = {nullptr, nullptr};
+  float* pred = nullptr;
+  void* act0 = nullptr;
+  void* act1 = nullptr;
+  float* stage_in = nullptr;
+  float* stage_out = nullptr;
+  int* status = nullptr;
+  int* err = nullptr;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+namespace gw {
+
+static void stream_free(gw_stream* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  for (void* p : s->allocs) cudaFree(p);
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    s->ctx->in_use -= s->bytes;
+  }
+  delete s;
+}
+
+template <typename T>
+static T* salloc(gw_stream* s, size_t count) {
+  T* p = (T*)dev_alloc(s->ctx, count * sizeof(T), &s->bytes);
+  s->allocs.push_back(p);
+  GW_CUDA(cudaMemset(p, 0, count * sizeof(T)));
+  return p;
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+#define GW_API_BEGIN try {
+#define GW_API_END                                                  \
+  }                                                                 \
+  catch (const gw::Error& e) {                                      \
+    gw::set_last_error(e.what());                                   \
+    return e.code;                                                  \
+  }                                                                 \
+  catch (const std::bad_alloc&) {                                   \
+    gw::set_last_error("host allocation failed");                   \
+    return GW_ENOMEM;                                               \
+  }                                                                 \
+  catch (const std::exception& e) {                                 \
+    gw::set_last_error(e.what());                                   \
+    return GW_EINVAL;                                               \
+  }                                                                 \
+  return GW_OK;
+
+extern "C" {
+
+const char* gw_last_error(void) { return gw::g_last_error.c_str(); }
+const char* gw_version(void) { return "gwstream 0.1 (sm_103a)"; }
+
+int gw_profile_enable(int on) {
+  GW_API_BEGIN
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_clear();
+  g_prof_on = on != 0;
+  GW_API_END
+}
+
+int gw_profile_read(char* names, size_t names_len, double* total_ms, int64_t* launches, int max_entries) {
+  try {
+    GW_CHECK_ARG(names && total_ms && launches && max_entries > 0, "NULL argument");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::map<std::string, std::pair<double, int64_t>> agg;
+    for (auto& r : g_prof) {
+      GW_CUDA(cudaEventSynchronize(r.b));
+      float ms = 0.f;
+      GW_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      auto& e = agg[r.name];
+      e.first += ms;
+      e.second += 1;
+    }
+    std::string buf;
+    int n = 0;
+    for (auto& kv : agg) {
+      if (n >= max_entries) break;
+      total_ms[n] = kv.second.first;
+      launches[n] = kv.second.second;
+      buf += kv.first + "\n";
+      ++n;
+    }
+    GW_CHECK_ARG(buf.size() < names_len, "names buffer too small");
+    memcpy(names, buf.c_str(), buf.size() + 1);
+    return n;
+  } catch (const gw::Error& e) {
+    gw::set_last_error(e.what());
+    return e.code;
+  }
+}
+
+int64_t gw_launch_count(void) { return g_launches.load(); }
+
+int gw_ctx_create(int device, size_t hbm_budget_bytes, gw_ctx_t* out) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(out, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  GW_CUDA(cudaGetDeviceCount(&n));
+  GW_CHECK_ARG(device >= 0 && device < n, "device index out of range");
+  GW_CUDA(cudaSetDevice(device));
+  auto* c = new gw_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  *out = c;
+  GW_API_END
+}
+
+int gw_ctx_destroy(gw_ctx_t ctx) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx, "ctx is NULL");
+  delete ctx;
+  GW_API_END
+}
+
+size_t gw_ctx_bytes_in_use(gw_ctx_t ctx) { return ctx ? ctx->in_use : 0; }
+
+size_t gw_model_param_count(int kind, int n_in) {
+  if (n_in <= 0) return 0;
+  if (kind != GW_MODEL_DEEPCLEAN && kind != GW_MODEL_BBHNET) return 0;
+  size_t n = 0;
+  for (const auto& s : specs_for(kind, n_in)) n += layer_param_count(s);
+  if (kind == GW_MODEL_BBHNET) n += 257;
+  return n;
+}
+
+int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
+  gw_model* m = nullptr;
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && d && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(d->kind == GW_MODEL_DEEPCLEAN || d->kind == GW_MODEL_BBHNET, "unknown model kind");
+  GW_CHECK_ARG(d->precision >= GW_FP32 && d->precision <= GW_FP8, "unknown precision");
+  GW_CHECK_ARG(d->n_in >= 1 && d->n_in <= 256, "n_in out of range");
+  GW_CHECK_ARG(d->params, "params is NULL");
+  GW_CHECK_ARG(d->n_params == gw_model_param_count(d->kind, d->n_in), "n_params does not match the layer table");
+  if (d->precision == GW_FP8 && d->kind != GW_MODEL_BBHNET)
+    throw Error(GW_ENOTIMPL, "FP8 is implemented for the BBHnet model only");
+  if (d->precision != GW_FP32 && !tc_supported())
+    throw Error(GW_ENOTIMPL, "tensor-core path needs an sm_103 device");
+  GW_CUDA(cudaSetDevice(ctx->device));
+  m = new gw_model();
+  try {
+  m->ctx = ctx;
+  m->kind = d->kind;
+  m->precision = d->precision;
+  m->n_in = d->n_in;
+  const auto specs = specs_for(d->kind, d->n_in);
+  const float* p = d->params;
+  for (size_t li = 0; li < specs.size(); ++li) {
+    const LayerSpec& s = specs[li];
+    std::vector<double> wf, bf;
+    fold_layer(s, p, wf, bf);
+    p += layer_param_count(s);
+    LayerDev L;
+    L.s = s;
+    std::vector<float> w32(wf.begin(), wf.end()), b32(bf.begin(), bf.end());
+    L.w = upload(m, w32);
+    L.b = upload(m, b32);
+    if (d->precision != GW_FP32) {
+      if (d->precision == GW_FP8) {
+        GW_CHECK_ARG(d->act_scales == nullptr || d->n_act_scales == (int)specs.size(),
+                     "act_scales must have one entry per conv layer");
+        L.act_scale = d->act_scales ? d->act_scales[li] : 1.0f;
+      }
+      tc_pack_layer(L, wf, d->precision, ctx, &m->bytes, m->allocs);
+    }
+    m->layers.push_back(L);
+  }
+  if (d->kind == GW_MODEL_BBHNET) {
+    std::vector<float> hw(p, p + 256), hb(p + 256, p + 257);
+    m->head_w = upload(m, hw);
+    m->head_b = upload(m, hb);
+  }
+  std::vector<float> mean(d->n_in, 0.f), istd(d->n_in, 1.f);
+  for (int c = 0; c < d->n_in; ++c) {
+    if (d->in_mean) mean[c] = d->in_mean[c];
+    if (d->in_std) {
+      GW_CHECK_ARG(d->in_std[c] > 0.f, "in_std must be positive");
+      istd[c] = 1.0f / d->in_std[c];
+    }
+  }
+  m->in_mean = upload(m, mean);
+  m->in_istd = upload(m, istd);
+  } catch (...) {
+    model_free(m);
+    m = nullptr;
+    throw;
+  }
+  *out = m;
+  m = nullptr;
+  GW_API_END
+}
+
+int gw_model_destroy(gw_model_t m) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(m, "model is NULL");
+  model_free(m);
+  GW_API_END
+}
+
+int gw_deepclean_forward(gw_model_t m, const float* x, int64_t ld, int64_t window_stride, int B, int L, float* y,
+                         void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(m && x && y, "NULL argument");
+  GW_CHECK_ARG(m->kind == GW_MODEL_DEEPCLEAN, "model is not a DeepClean model");
+  GW_CHECK_ARG(B >= 1 && L >= 8 && L % 8 == 0, "need B >= 1 and L a positive multiple of 8");
+  GW_CHECK_ARG(ld >= L && window_stride >= 0, "bad ld / window_stride");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (m->precision == GW_FP32) {
+    const size_t per = (size_t)B * 8 * L;
+    float* ws = (float*)model_workspace(m, 2 * per * sizeof(float));
+    deepclean_f32(m, x, window_stride, ld, true, B, L, y, L, ws, ws + per, st);
+  } else {
+    throw Error(GW_ENOTIMPL, "DeepClean BF16 offline path not built yet");
+  }
+  GW_API_END
+}
+
+int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(m && x && logits, "NULL argument");
+  GW_CHECK_ARG(m->kind == GW_MODEL_BBHNET, "model is not a BBHnet model");
+  GW_CHECK_ARG(B >= 1 && L >= 16 && L % 16 == 0, "need B >= 1 and L a positive multiple of 16");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (m->precision == GW_FP32) {
+    float* ws = (float*)model_workspace(m, 3 * (size_t)B * 32 * L * sizeof(float));
+    bbhnet_f32(m, x, B, L, logits, ws, st);
+  } else {
+    throw Error(GW_ENOTIMPL, "BBHnet tensor-core path not built yet");
+  }
+  GW_API_END
+}
+
+int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps, int precision,
+                            gw_fir_t* out) {
+  gw_fir* f = nullptr;
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && psd && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(n_psd >= 3 && fs > 0, "bad PSD grid");
+  const int N = 2 * (n_psd - 1);
+  GW_CHECK_ARG(ntaps >= 1 && (ntaps & 1) && ntaps <= N, "ntaps must be odd and <= nfft");
+  GW_CHECK_ARG(precision == GW_FP32 || precision == GW_BF16, "FIR precision must be FP32 or BF16");
+  for (int j = 0; j < n_psd; ++j) GW_CHECK_ARG(psd[j] > 0 && std::isfinite(psd[j]), "PSD must be positive and finite");
+  GW_CUDA(cudaSetDevice(ctx->device));
+  f = new gw_fir();
+  f->ctx = ctx;
+  f->ntaps = ntaps;
+  f->precision = precision;
+  f->taps = design_whitening(psd, n_psd, fs, ntaps);
+  std::vector<float> t32(f->taps.begin(), f->taps.end());
+  try {
+    f->d_taps = (float*)dev_alloc(ctx, t32.size() * 4, &f->bytes);
+    GW_CUDA(cudaMemcpy(f->d_taps, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice));
+  } catch (...) {
+    gw_fir_destroy(f);
+    f = nullptr;
+    throw;
+  }
+  *out = f;
+  f = nullptr;
+  GW_API_END
+}
+
+int gw_fir_destroy(gw_fir_t f) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(f, "fir is NULL");
+  cudaDeviceSynchronize();
+  if (f->d_taps) cudaFree(f->d_taps);
+  if (f->d_toeplitz) cudaFree(f->d_toeplitz);
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    f->ctx->in_use -= f->bytes;
+  }
+  delete f;
+  GW_API_END
+}
+
+int gw_fir_ntaps(gw_fir_t f) { return f ? f->ntaps : GW_EINVAL; }
+
+int gw_fir_taps(gw_fir_t f, double* taps_out) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(f && taps_out, "NULL argument");
+  memcpy(taps_out, f->taps.data(), f->taps.size() * sizeof(double));
+  GW_API_END
+}
+
+int gw_whiten(gw_fir_t f, const float* x, int B, int C, int L_in, float* y, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(f && x && y, "NULL argument");
+  GW_CHECK_ARG(B >= 1 && C >= 1 && L_in >= f->ntaps, "need B, C >= 1 and L_in >= ntaps");
+  const int lout = L_in - f->ntaps + 1;
+  Prof p("fir_f32", (cudaStream_t)cuda_stream);
+  launch_fir_f32(x, L_in, y, lout, B * C, f->d_taps, f->ntaps, lout, (cudaStream_t)cuda_stream);
+  GW_API_END
+}
+
+int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* deepclean, gw_stream_t* out) {
+  gw_stream* s = nullptr;
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && d && deepclean && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(d->n_det == 1 || d->n_det == 2, "n_det must be 1 or 2");
+  GW_CHECK_ARG(d->stride >= 8 && d->stride % 8 == 0, "stride must be a positive multiple of 8");
+  GW_CHECK_ARG(d->window >= d->stride && d->window % d->stride == 0 && d->window % 8 == 0,
+               "window must be a multiple of stride and of 8");
+  GW_CHECK_ARG(d->max_batch >= 1 && d->max_batch <= 4096, "max_batch out of range");
+  GW_CHECK_ARG(d->agg_mode == GW_AGG_LATEST || d->agg_mode == GW_AGG_AVERAGE, "unknown aggregation mode");
+  GW_CHECK_ARG(d->agg_delay >= 0 && d->agg_delay <= d->window - d->stride, "agg_delay out of range");
+  for (int i = 0; i < d->n_det; ++i) {
+    GW_CHECK_ARG(deepclean[i] && deepclean[i]->kind == GW_MODEL_DEEPCLEAN, "need one DeepClean model per detector");
+    GW_CHECK_ARG(deepclean[i]->n_in == d->n_witness, "model n_in != n_witness");
+    GW_CHECK_ARG(deepclean[i]->precision == deepclean[0]->precision, "detectors must share a precision");
+  }
+  GW_CUDA(cudaSetDevice(ctx->device));
+  s = new gw_stream();
+  s->ctx = ctx;
+  s->d = *d;
+  const int prec = deepclean[0]->precision;
+  for (int i = 0; i < d->n_det; ++i) s->dc[i] = deepclean[i];
+  const int64_t W = d->window, S = d->stride, nb = d->max_batch, C = d->n_witness;
+  s->R = W + (nb - 1) * S;
+  s->R = (s->R + 7) / 8 * 8;
+  const int G = (int)((C + 7) / 8);
+  try {
+    for (int i = 0; i < d->n_det; ++i) {
+      if (prec == GW_FP32)
+        s->ring_f32[i] = salloc<float>(s, (size_t)C * 2 * s->R);
+      else
+        s->ring_bf16[i] = salloc<__nv_bfloat16>(s, (size_t)G * 2 * s->R * 8);
+      s->strain[i] = salloc<float>(s, (size_t)s->R);
+      s->acc[i] = salloc<float>(s, (size_t)s->R);
+    }
+    s->pred = salloc<float>(s, (size_t)nb * W);
+    const size_t act_elems = (size_t)nb * 8 * W;
+    const size_t esz = prec == GW_FP32 ? 4 : 2;
+    s->act0 = salloc<char>(s, act_elems * esz);
+    s->act1 = salloc<char>(s, act_elems * esz);
+    s->stage_in = salloc<float>(s, (size_t)d->n_det * (C + 1) * nb * S);
+    s->stage_out = salloc<float>(s, (size_t)d->n_det * nb * S);
+    s->status = salloc<int>(s, 2);
+    s->err = s->status + 1;
+  } catch (...) {
+    stream_free(s);
+    s = nullptr;
+    throw;
+  }
+  *out = s;
+  s = nullptr;
+  GW_API_END
+}
+
+int gw_stream_destroy(gw_stream_t s) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(s, "stream is NULL");
+  stream_free(s);
+  GW_API_END
+}
+
+int64_t gw_stream_head(gw_stream_t s) { return s ? s->head : GW_EINVAL; }
+
+int gw_stream_status(gw_stream_t s, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(s, "stream is NULL");
+  int h[2] = {0, 0};
+  GW_CUDA(cudaMemcpyAsync(h, s->status, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream));
+  GW_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  if (h[0]) return h[0];
+  if (h[1]) return GW_ETIMEOUT;
+  GW_API_END
+}
+
+int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float* strain, float* clean_out, int mem,
+                   void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(s && witness && strain && clean_out, "NULL argument");
+  GW_CHECK_ARG(n_snap >= 1 && n_snap <= s->d.max_batch, "n_snap out of range [1, max_batch]");
+  GW_CHECK_ARG(mem == GW_MEM_HOST || mem == GW_MEM_DEVICE, "mem must be GW_MEM_HOST or GW_MEM_DEVICE");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int C = s->d.n_witness, S = s->d.stride, W = s->d.window, nd = s->d.n_det;
+  const int64_t n = (int64_t)n_snap * S;
+  const float* wit = witness;
+  const float* str = strain;
+  float* out = clean_out;
+  if (mem == GW_MEM_HOST) {
+    const size_t nw = (size_t)nd * C * n, ns = (size_t)nd * n;
+    for (size_t i = 0; i < nw; ++i)
+      if (!std::isfinite(witness[i])) throw Error(GW_ENONFINITE, "non-finite witness sample");
+    for (size_t i = 0; i < ns; ++i)
+      if (!std::isfinite(strain[i])) throw Error(GW_ENONFINITE, "non-finite strain sample");
+    GW_CUDA(cudaMemcpyAsync(s->stage_in, witness, nw * 4, cudaMemcpyHostToDevice, st));
+    GW_CUDA(cudaMemcpyAsync(s->stage_in + nw, strain, ns * 4, cudaMemcpyHostToDevice, st));
+    wit = s->stage_in;
+    str = s->stage_in + nw;
+    out = s->stage_out;
+  }
+  const int64_t R = s->R, head = s->head;
+  const int G = (C + 7) / 8;
+  for (int d = 0; d < nd; ++d) {
+    gw_model* m = s->dc[d];
+    const float* wd = wit + (size_t)d * C * n;
+    {
+      Prof p("ring_push", st);
+      if (m->precision == GW_FP32)
+        launch_ring_push_f32(wd, n, C, (int)n, s->ring_f32[d], R, head, m->in_mean, m->in_istd, s->status, st);
+      else
+        launch_ring_push_bf16(wd, n, C, G, (int)n, s->ring_bf16[d], R, head, m->in_mean, m->in_istd, s->status,
+                              st);
+    }
+    {
+      Prof p("strain_push", st);
+      launch_strain_push(str + (size_t)d * n, (int)n, s->strain[d], R, head, s->status, st);
+    }
+    // window j of this batch ends at head + (j+1) S; in the double-mapped ring
+    // the batch's windows are views at uniform stride S from p0.
+    int64_t p0 = (head + S - W) % R;
+    if (p0 < 0) p0 += R;
+    if (m->precision == GW_FP32) {
+      const size_t per = (size_t)n_snap * 8 * W;
+      deepclean_f32(m, s->ring_f32[d] + p0, S, 2 * R, false, n_snap, W, s->pred, W, (float*)s->act0,
+                    (float*)s->act1, st);
+      (void)per;
+    } else {
+      throw Error(GW_ENOTIMPL, "BF16 stream path not built yet");
+    }
+    {
+      Prof p("sub_ola", st);
+      launch_sub_ola(s->pred, W, n_snap, S, W, R, head, s->d.agg_mode, s->d.agg_delay, s->acc[d], s->strain[d],
+                     out + (size_t)d * n, st);
+    }
+  }
+  s->head += n;
+  if (mem == GW_MEM_HOST) {
+    GW_CUDA(cudaMemcpyAsync(clean_out, s->stage_out, (size_t)nd * n * 4, cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaStreamSynchronize(st));
+  }
+  GW_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/gwstream.h"
+
+namespace gw {
+
+// ---- errors ---------------------------------------------------------------
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+void set_last_error(const std::string& msg);
+
+#define GW_CHECK_ARG(cond, msg) \
+  do { if (!(cond)) throw ::gw::Error(GW_EINVAL, msg); } while (0)
+#define GW_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw ::gw::Error(GW_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define GW_LAUNCH_CHECK() GW_CUDA(cudaGetLastError())
+
+// ---- layer description ----------------------------------------------------
+enum Act { ACT_NONE = 0, ACT_TANH = 1, ACT_RELU = 2 };
+
+struct LayerSpec {
+  bool transposed;
+  int cin, cout, k, stride, pad_l, pad_r, out_pad;
+  bool bn;
+  int act;
+  int lout(int lin) const {
+    return transposed ? (lin - 1) * stride - pad_l - pad_r + k + out_pad
+                      : (lin + pad_l + pad_r - k) / stride + 1;
+  }
+};
+
+std::vector<LayerSpec> deepclean_specs(int n_in);
+std::vector<LayerSpec> bbhnet_specs(int n_in);
+
+// Weights of one layer on the device after the BatchNorm fold.
+struct LayerDev {
+  LayerSpec s;
+  float* w = nullptr;      // FP32 [C_out][C_in][K] (transposed convs re-indexed to this order)
+  float* b = nullptr;      // FP32 [C_out]
+  // tensor-core path (BF16 / FP8): packed operand image and per-K-step table
+  void* wq = nullptr;      // packed B operand image (bf16 or e4m3)
+  uint32_t* table = nullptr;
+  float* wscale = nullptr; // FP8: per-output-channel dequant scale (weight scale * act scale)
+  int n_steps = 0;         // K-steps (MMA instructions per M sub-tile)
+  int npad = 0;            // N (output channels) padded for the MMA
+  int gin = 0;             // input channel groups of 8 (or 16 for FP8)
+  float act_scale = 1.f;   // FP8: scale of this layer's input activations
+  float out_scale = 1.f;   // FP8: scale applied to the outputs for the next layer
+};
+
+}  // namespace gw
+
+// ---- public object structs --------------------------------------------------
+struct gw_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t in_use = 0;
+  bool alive = true;
+};
+
+struct gw_model {
+  gw_ctx* ctx = nullptr;
+  int kind = 0, precision = 0, n_in = 0;
+  std::vector<gw::LayerDev> layers;
+  float* head_w = nullptr;   // BBHnet linear head [256]
+  float* head_b = nullptr;   // [1]
+  float* in_mean = nullptr;  // [n_in]
+  float* in_istd = nullptr;  // [n_in] 1/std
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // workspace for offline forwards (grown on demand)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+struct gw_fir {
+  gw_ctx* ctx = nullptr;
+  int ntaps = 0, precision = 0;
+  std::vector<double> taps;
+  float* d_taps = nullptr;
+  void* d_toeplitz = nullptr;  // BF16 tensor-core operand image
+  size_t bytes = 0;
+};
+
+namespace gw {
+
+// ---- instrumentation -------------------------------------------------------
+// Every launch site opens a Prof scope: it counts the launch and, when
+// profiling is on, records CUDA events around it on the launching stream.
+struct Prof {
+  Prof(const char* name, cudaStream_t st);
+  ~Prof();
+  int slot;
+  cudaStream_t st;
+};
+
+// ---- device memory accounting --------------------------------------------
+void* dev_alloc(gw_ctx* ctx, size_t bytes, size_t* counter);
+void dev_free(gw_ctx* ctx, void* p, size_t bytes, size_t* counter);
+
+// ---- FP32 SIMT kernels (k_f32.cu) --------------------------------------------
+struct ConvF32Args {
+  const float* x; int64_t xb, xc;     // input element (b, c, t) at x + b*xb + c*xc + t
+  float* y; int64_t yb, yc;           // output element (b, c, t)
+  const float* res; int64_t rb, rc;   // optional residual added before the activation
+  const float* w; const float* bias;  // folded weights [C_out][C_in][K], bias [C_out]
+  const float* in_mean; const float* in_istd;  // optional input standardisation
+  int B, lin, lout;
+  LayerSpec s;
+};
+void launch_conv_f32(const ConvF32Args& a, cudaStream_t st);
+void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int rows,
+                    const float* taps, int ntaps, int lout, cudaStream_t st);
+void launch_gap_linear_f32(const float* h, int64_t hb, int64_t hc, int B, int C, int L,
+                           const float* w, const float* b, float* out, cudaStream_t st);
+
+// ---- stream kernels (k_stream.cu) -------------------------------------------
+void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring,
+                          int64_t R, int64_t head, const float* mean, const float* istd,
+                          int* status, cudaStream_t st);
+void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n,
+                           __nv_bfloat16* ring, int64_t R, int64_t head, const float* mean,
+                           const float* istd, int* status, cudaStream_t st);
+void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head,
+                        int* status, cudaStream_t st);
+void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R,
+                    int64_t head, int mode, int delta, float* acc, const float* strain_ring,
+                    float* out, cudaStream_t st);
+
+// ---- tensor-core conv path (k_tc.cu) ---------------------------------------------
+// Activation layout of the tensor-core path: [B][G][P][Lp][8] bf16, with G
+// groups of 8 channels, P phase planes (the consumer's stride) and
+// Lp = L / P positions per plane; channel c of position t sits at
+// [c / 8][t % P][t / P][c % 8].
+struct TcAct {
+  const __nv_bfloat16* p; int64_t bstride;  // elements between batch items
+  int64_t gstride;                          // elements between channel groups
+  int64_t off0;                             // element offset of position 0 of item b=0 (ring windows)
+  int64_t boff;                             // extra per-item offset in positions (ring windows: S)
+  int P; int64_t pstride;                   // phases and elements between phase planes
+  int L;                                    // logical length
+};
+struct TcOut {
+  void* p; int64_t bstride, gstride, pstride; int P;
+  int fp32_single;   // 1: write channel 0 as FP32 [B][L] (prediction output)
+  const __nv_bfloat16* res; int64_t rbstride, rgstride, rpstride; int rP;  // residual (same layout rules)
+};
+int tc_supported();
+void tc_pack_layer(LayerDev& L, const std::vector<double>& wfold, int precision, gw_ctx* ctx,
+                   size_t* counter, std::vector<void*>& allocs);
+void launch_conv_tc(const LayerDev& L, const TcAct& in, int lout, const TcOut& out, int B,
+                    int* err_flag, cudaStream_t st);
+
+}  // namespace gw

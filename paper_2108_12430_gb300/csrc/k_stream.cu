@@ -1,0 +1,170 @@
+// Streaming kernels: snapshot-state update (device rings) and the fused
+// subtract + aggregate step.
+//
+// Snapshot state (Methods, "Streaming IaaS"): the last samples of every
+// channel live in a device ring of capacity R >= W + (max_batch - 1) S.  The
+// witness ring is double-mapped -- sample t is stored at t mod R and at
+// t mod R + R -- so every window [t - W, t) is one contiguous run starting at
+// (t - W) mod R, which the first conv layer reads in place.
+#include "gw_internal.h"
+
+namespace gw {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int64_t pmod(int64_t a, int64_t m) {
+  int64_t r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+__device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t b) {
+  return (a >= 0) ? a / b : -((-a + b - 1) / b);
+}
+
+// src [C][src_ld] (n new samples per channel) -> ring [C][2R], standardised.
+__global__ void ring_push_f32_kernel(const float* __restrict__ src, int64_t src_ld, int C, int n,
+                                     float* __restrict__ ring, int64_t R, int64_t head,
+                                     const float* __restrict__ mean, const float* __restrict__ istd,
+                                     int* status) {
+  const int64_t total = (int64_t)C * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n), i = (int)(e % n);
+    float v = src[(int64_t)c * src_ld + i];
+    if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
+    if (mean) v = (v - mean[c]) * istd[c];
+    const int64_t q = pmod(head + i, R);
+    float* row = ring + (int64_t)c * 2 * R;
+    row[q] = v;
+    row[q + R] = v;
+  }
+}
+
+// src [C][src_ld] -> ring [G][2R][8] bf16 (channel-group blocked), standardised.
+// One thread writes the 8 channels of one (group, time) as a 16-byte store.
+__global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src_ld, int C, int G, int n,
+                                      __nv_bfloat16* __restrict__ ring, int64_t R, int64_t head,
+                                      const float* __restrict__ mean, const float* __restrict__ istd,
+                                      int* status) {
+  const int64_t total = (int64_t)G * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(e / n), i = (int)(e % n);
+    __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = g * 8 + j;
+      float v = 0.f;
+      if (c < C) {
+        v = src[(int64_t)c * src_ld + i];
+        if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
+        if (mean) v = (v - mean[c]) * istd[c];
+      }
+      v8[j] = __float2bfloat16_rn(v);
+    }
+    const int64_t q = pmod(head + i, R);
+    uint4 val = *reinterpret_cast<const uint4*>(v8);
+    uint4* row = reinterpret_cast<uint4*>(ring + (int64_t)g * 2 * R * 8);
+    row[q] = val;
+    row[q + R] = val;
+  }
+}
+
+__global__ void strain_push_kernel(const float* __restrict__ src, int n, float* __restrict__ ring, int64_t R,
+                                   int64_t head, int* status) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float v = src[i];
+    if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
+    ring[pmod(head + i, R)] = v;
+  }
+}
+
+// Fused subtract + aggregate over one batch of n windows (Methods, "Data
+// aggregation", "Aggregation latency").  Window j of the batch covers times
+// [head + (j+1) S - W, head + (j+1) S).  One thread per time tau of the
+// union of the batch's windows:
+//   AVERAGE: sum = acc[tau] (windows of earlier batches, zero for new times)
+//            + pred_j(tau) for covering j in ascending order; the emitted
+//            value of snapshot k(tau) = floor((tau + delta) / S) is the
+//            partial sum up to window k(tau) over the number of windows
+//            (j >= 0) it contains; acc[tau] keeps the full sum.
+//   LATEST:  the emitted value is pred_{k(tau)}(tau).
+// cleaned = strain(tau) - value, written to out[tau - head + delta].
+__global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, int n, int S, int W,
+                               int64_t R, int64_t head, int mode, int delta, float* __restrict__ acc,
+                               const float* __restrict__ strain_ring, float* __restrict__ out) {
+  const int64_t lo = head + S - W;
+  const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
+  const int64_t k0 = head / S;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tau = lo + e;
+    const int64_t r = tau - head;
+    const int64_t k_emit = floordiv64(tau + delta, S);         // global snapshot emitting tau
+    const bool emits = (tau >= head - delta) && (tau < head + (int64_t)n * S - delta);
+    const int jlo = (int)imax64(0, floordiv64(r, S));
+    const int jhi = (int)imin64(n - 1, floordiv64(r + W, S) - 1);
+    const float s_tau = (tau >= 0) ? strain_ring[pmod(tau, R)] : 0.f;
+    if (mode == GW_AGG_LATEST) {
+      if (!emits) continue;
+      const int j = (int)(k_emit - k0);
+      const int64_t start = head + (int64_t)(j + 1) * S - W;
+      out[tau - head + delta] = s_tau - pred[(int64_t)j * pred_ld + (tau - start)];
+      continue;
+    }
+    float sum = (tau < head) ? acc[pmod(tau, R)] : 0.f;
+    for (int j = jlo; j <= jhi; ++j) {
+      const int64_t start = head + (int64_t)(j + 1) * S - W;
+      sum += pred[(int64_t)j * pred_ld + (tau - start)];
+      if (emits && k0 + j == k_emit) {
+        const int64_t first = imax64(0, floordiv64(tau, S));
+        const float cnt = (float)(k_emit - first + 1);
+        out[tau - head + delta] = s_tau - sum / cnt;
+      }
+    }
+    acc[pmod(tau, R)] = sum;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
+}
+
+}  // namespace
+
+void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring, int64_t R,
+                          int64_t head, const float* mean, const float* istd, int* status, cudaStream_t st) {
+  ring_push_f32_kernel<<<grid_for((int64_t)C * n), kThreads, 0, st>>>(src, src_ld, C, n, ring, R, head, mean,
+                                                                       istd, status);
+  GW_LAUNCH_CHECK();
+}
+
+void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n, __nv_bfloat16* ring,
+                           int64_t R, int64_t head, const float* mean, const float* istd, int* status,
+                           cudaStream_t st) {
+  ring_push_bf16_kernel<<<grid_for((int64_t)G * n), kThreads, 0, st>>>(src, src_ld, C, G, n, ring, R, head,
+                                                                        mean, istd, status);
+  GW_LAUNCH_CHECK();
+}
+
+void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head, int* status,
+                        cudaStream_t st) {
+  strain_push_kernel<<<grid_for(n), kThreads, 0, st>>>(src, n, ring, R, head, status);
+  GW_LAUNCH_CHECK();
+}
+
+void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R, int64_t head, int mode,
+                    int delta, float* acc, const float* strain_ring, float* out, cudaStream_t st) {
+  const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
+  sub_ola_kernel<<<grid_for(count), kThreads, 0, st>>>(pred, pred_ld, n, S, W, R, head, mode, delta, acc,
+                                                        strain_ring, out);
+  GW_LAUNCH_CHECK();
+}
+
+}  // namespace gw

@@ -1,0 +1,250 @@
+"""Thin ctypes binding of ``libgwstream.so`` (include/gwstream.h).
+
+Argument marshalling only: every function keeps the C name, converts Python
+ints/arrays to C types, raises ``GwError`` on a negative status and returns
+out-parameters.  No compute happens here.  Device buffers are passed as
+integer addresses (e.g. ``torch.Tensor.data_ptr()``), CUDA streams as the
+integer handle ``torch.cuda.Stream.cuda_stream`` (0 = default stream).
+
+The library must have been built (``paper_2108_12430_gb300.build.build()``,
+which ``__graft_entry__.build()`` calls); there is no fallback if it is
+missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgwstream.so")
+
+GW_OK, GW_EINVAL, GW_EBUDGET, GW_ENOMEM, GW_ECUDA, GW_ETIMEOUT, GW_ESTATE, GW_ENOTIMPL, GW_ENONFINITE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+GW_FP32, GW_BF16, GW_FP8 = 0, 1, 2
+GW_MODEL_DEEPCLEAN, GW_MODEL_BBHNET = 0, 1
+GW_AGG_LATEST, GW_AGG_AVERAGE = 0, 1
+GW_MEM_HOST, GW_MEM_DEVICE = 0, 1
+
+ERROR_NAMES = {GW_EINVAL: "GW_EINVAL", GW_EBUDGET: "GW_EBUDGET", GW_ENOMEM: "GW_ENOMEM", GW_ECUDA: "GW_ECUDA",
+               GW_ETIMEOUT: "GW_ETIMEOUT", GW_ESTATE: "GW_ESTATE", GW_ENOTIMPL: "GW_ENOTIMPL",
+               GW_ENONFINITE: "GW_ENONFINITE"}
+
+# Every symbol include/gwstream.h declares (checked by the CPU tests).
+EXPORTS = (
+    "gw_last_error", "gw_version", "gw_ctx_create", "gw_ctx_destroy", "gw_ctx_bytes_in_use",
+    "gw_model_param_count", "gw_model_create", "gw_model_destroy", "gw_deepclean_forward", "gw_bbhnet_score",
+    "gw_fir_create_whitening", "gw_fir_destroy", "gw_fir_ntaps", "gw_fir_taps", "gw_whiten",
+    "gw_stream_create", "gw_stream_destroy", "gw_stream_push", "gw_stream_head", "gw_stream_status",
+    "gw_profile_enable", "gw_profile_read", "gw_launch_count",
+)
+
+
+class GwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class gw_model_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("precision", C.c_int), ("n_in", C.c_int),
+                ("params", C.POINTER(C.c_float)), ("n_params", C.c_size_t),
+                ("in_mean", C.POINTER(C.c_float)), ("in_std", C.POINTER(C.c_float)),
+                ("act_scales", C.POINTER(C.c_float)), ("n_act_scales", C.c_int)]
+
+
+class gw_stream_desc(C.Structure):
+    _fields_ = [("n_det", C.c_int), ("n_witness", C.c_int), ("window", C.c_int), ("stride", C.c_int),
+                ("max_batch", C.c_int), ("agg_mode", C.c_int), ("agg_delay", C.c_int)]
+
+
+_lib = None
+P = C.c_void_p
+I = C.c_int
+I64 = C.c_int64
+SZ = C.c_size_t
+
+
+def _declare(lib):
+    sig = {
+        "gw_last_error": (C.c_char_p, []),
+        "gw_version": (C.c_char_p, []),
+        "gw_ctx_create": (I, [I, SZ, C.POINTER(P)]),
+        "gw_ctx_destroy": (I, [P]),
+        "gw_ctx_bytes_in_use": (SZ, [P]),
+        "gw_model_param_count": (SZ, [I, I]),
+        "gw_model_create": (I, [P, C.POINTER(gw_model_desc), C.POINTER(P)]),
+        "gw_model_destroy": (I, [P]),
+        "gw_deepclean_forward": (I, [P, P, I64, I64, I, I, P, P]),
+        "gw_bbhnet_score": (I, [P, P, I, I, P, P]),
+        "gw_fir_create_whitening": (I, [P, C.POINTER(C.c_double), I, C.c_double, I, I, C.POINTER(P)]),
+        "gw_fir_destroy": (I, [P]),
+        "gw_fir_ntaps": (I, [P]),
+        "gw_fir_taps": (I, [P, C.POINTER(C.c_double)]),
+        "gw_whiten": (I, [P, P, I, I, I, P, P]),
+        "gw_stream_create": (I, [P, C.POINTER(gw_stream_desc), C.POINTER(P), C.POINTER(P)]),
+        "gw_stream_destroy": (I, [P]),
+        "gw_stream_push": (I, [P, I, P, P, P, I, P]),
+        "gw_stream_head": (I64, [P]),
+        "gw_stream_status": (I, [P, P]),
+        "gw_profile_enable": (I, [I]),
+        "gw_profile_read": (I, [C.c_char_p, SZ, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
+        "gw_launch_count": (I64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def lib():
+    """Load the library (built in-tree); raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2108_12430_gb300.build.build() first")
+        l = C.CDLL(LIB_PATH)
+        _declare(l)
+        _lib = l
+    return _lib
+
+
+def _check(rc):
+    if rc < 0:
+        raise GwError(rc, lib().gw_last_error().decode())
+    return rc
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float)) if a is not None else None
+
+
+# ---- C-ABI mirrors -----------------------------------------------------------
+
+def gw_version():
+    return lib().gw_version().decode()
+
+
+def gw_ctx_create(device=0, hbm_budget_bytes=0):
+    h = P()
+    _check(lib().gw_ctx_create(device, hbm_budget_bytes, C.byref(h)))
+    return h
+
+
+def gw_ctx_destroy(ctx):
+    _check(lib().gw_ctx_destroy(ctx))
+
+
+def gw_ctx_bytes_in_use(ctx):
+    return lib().gw_ctx_bytes_in_use(ctx)
+
+
+def gw_model_param_count(kind, n_in):
+    return lib().gw_model_param_count(kind, n_in)
+
+
+def gw_model_create(ctx, kind, precision, n_in, params, in_mean=None, in_std=None, act_scales=None):
+    params = np.ascontiguousarray(params, np.float32)
+    keep = [params]
+    d = gw_model_desc()
+    d.kind, d.precision, d.n_in = kind, precision, n_in
+    d.params, d.n_params = _fptr(params), params.size
+    if in_mean is not None:
+        in_mean = np.ascontiguousarray(in_mean, np.float32); keep.append(in_mean)
+    if in_std is not None:
+        in_std = np.ascontiguousarray(in_std, np.float32); keep.append(in_std)
+    d.in_mean, d.in_std = _fptr(in_mean), _fptr(in_std)
+    if act_scales is not None:
+        act_scales = np.ascontiguousarray(act_scales, np.float32); keep.append(act_scales)
+        d.act_scales, d.n_act_scales = _fptr(act_scales), act_scales.size
+    h = P()
+    _check(lib().gw_model_create(ctx, C.byref(d), C.byref(h)))
+    return h
+
+
+def gw_model_destroy(m):
+    _check(lib().gw_model_destroy(m))
+
+
+def gw_deepclean_forward(m, x_ptr, ld, window_stride, B, L, y_ptr, stream=0):
+    _check(lib().gw_deepclean_forward(m, x_ptr, ld, window_stride, B, L, y_ptr, stream or None))
+
+
+def gw_bbhnet_score(m, x_ptr, B, L, logits_ptr, stream=0):
+    _check(lib().gw_bbhnet_score(m, x_ptr, B, L, logits_ptr, stream or None))
+
+
+def gw_fir_create_whitening(ctx, psd, fs, ntaps, precision=GW_FP32):
+    psd = np.ascontiguousarray(psd, np.float64)
+    h = P()
+    _check(lib().gw_fir_create_whitening(ctx, psd.ctypes.data_as(C.POINTER(C.c_double)), psd.size, fs, ntaps,
+                                         precision, C.byref(h)))
+    return h
+
+
+def gw_fir_destroy(f):
+    _check(lib().gw_fir_destroy(f))
+
+
+def gw_fir_ntaps(f):
+    return _check(lib().gw_fir_ntaps(f))
+
+
+def gw_fir_taps(f):
+    out = np.zeros(gw_fir_ntaps(f), np.float64)
+    _check(lib().gw_fir_taps(f, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def gw_whiten(f, x_ptr, B, Cc, L_in, y_ptr, stream=0):
+    _check(lib().gw_whiten(f, x_ptr, B, Cc, L_in, y_ptr, stream or None))
+
+
+def gw_stream_create(ctx, models, n_det, n_witness, window, stride, max_batch, agg_mode, agg_delay):
+    d = gw_stream_desc(n_det, n_witness, window, stride, max_batch, agg_mode, agg_delay)
+    arr = (P * 2)(*(list(models) + [None] * (2 - len(models))))
+    h = P()
+    _check(lib().gw_stream_create(ctx, C.byref(d), arr, C.byref(h)))
+    return h
+
+
+def gw_stream_destroy(s):
+    _check(lib().gw_stream_destroy(s))
+
+
+def gw_stream_push(s, n_snap, witness, strain, clean_out, mem=GW_MEM_HOST, stream=0):
+    """Host mode: numpy float32 arrays; device mode: integer device addresses."""
+    if mem == GW_MEM_HOST:
+        for a in (witness, strain, clean_out):
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+        args = (witness.ctypes.data, strain.ctypes.data, clean_out.ctypes.data)
+    else:
+        args = (witness, strain, clean_out)
+    _check(lib().gw_stream_push(s, n_snap, args[0], args[1], args[2], mem, stream or None))
+
+
+def gw_stream_head(s):
+    return lib().gw_stream_head(s)
+
+
+def gw_stream_status(s, stream=0):
+    return lib().gw_stream_status(s, stream or None)
+
+
+def gw_profile_enable(on=True):
+    _check(lib().gw_profile_enable(1 if on else 0))
+
+
+def gw_profile_read(max_entries=64):
+    """{kernel name: (total_ms, launches)} since the last gw_profile_enable."""
+    names = C.create_string_buffer(1 << 16)
+    ms = (C.c_double * max_entries)()
+    cnt = (C.c_int64 * max_entries)()
+    n = _check(lib().gw_profile_read(names, len(names), ms, cnt, max_entries))
+    keys = names.value.decode().split("\n")[:n]
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(keys)}
+
+
+def gw_launch_count():
+    return lib().gw_launch_count()
