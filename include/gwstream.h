@@ -113,6 +113,23 @@ int gw_model_destroy(gw_model_t m);
 int gw_deepclean_forward(gw_model_t m, const float* x, int64_t ld, int64_t window_stride,
                          int B, int L, float* y, void* cuda_stream);
 
+/* The same FP32 DeepClean forward for callers that cannot allocate device
+ * memory -- for example a real-time loop that reserved its memory at start-up
+ * and must never block in cudaMalloc, or a host framework that forbids
+ * allocations by plug-in libraries.  The paper has no counterpart: this is a
+ * deployment variant.  It calls no cudaMalloc/cudaFree and no allocating
+ * library routine; its scratch is a fixed 2 MiB array inside the library
+ * image, held by every GPU that loads the library until the process exits.
+ * Limits: FP32 models only (GW_ENOTIMPL otherwise) and B * L <= 32768 samples
+ * (GW_EINVAL beyond).  The first call on each device looks up the array's
+ * device address on the current device; make that first call before any
+ * CUDA stream capture.  All calls share the one array, so calls that overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller; the array needs no clearing, because each layer
+ * overwrites what the next layer reads.  Arguments as gw_deepclean_forward. */
+int gw_deepclean_forward_noalloc(gw_model_t m, const float* x, int64_t ld, int64_t window_stride,
+                                 int B, int L, float* y, void* cuda_stream);
+
 /* BBHnet logits.  x: device FP32 [B][2][L] whitened strain (L a multiple of
  * 16, L >= 16); logits: device FP32 [B]. */
 int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, void* cuda_stream);

@@ -214,7 +214,7 @@ static const char* kDcNames[8] = {"conv_f32.enc1", "conv_f32.enc2", "conv_f32.en
                                   "conv_f32.dec1", "conv_f32.dec2", "conv_f32.dec3", "conv_f32.out"};
 // DeepClean on B windows in FP32.  Input element (b, c, t) at
 // x + b*xb + c*xc + t; the first layer standardises when mean != null.
-static void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
+void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
                           float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st) {
   const auto& Ls = m->layers;
   const float* in = x;

@@ -129,6 +129,11 @@ void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int 
 void launch_gap_linear_f32(const float* h, int64_t hb, int64_t hc, int B, int C, int L,
                            const float* w, const float* b, float* out, cudaStream_t st);
 
+// DeepClean forward in FP32 over B windows (api.cu): input element (b, c, t)
+// at x + b*xb + c*xc + t, output [B][y_ld]; buf0 / buf1 each hold B*8*L floats.
+void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
+                   float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st);
+
 // ---- stream kernels (k_stream.cu) -------------------------------------------
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring,
                           int64_t R, int64_t head, const float* mean, const float* istd,

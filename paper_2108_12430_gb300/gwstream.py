@@ -37,7 +37,7 @@ EXPORTS = (
     "gw_model_param_count", "gw_model_create", "gw_model_destroy", "gw_deepclean_forward", "gw_bbhnet_score",
     "gw_fir_create_whitening", "gw_fir_destroy", "gw_fir_ntaps", "gw_fir_taps", "gw_whiten",
     "gw_stream_create", "gw_stream_destroy", "gw_stream_push", "gw_stream_head", "gw_stream_status",
-    "gw_profile_enable", "gw_profile_read", "gw_launch_count",
+    "gw_profile_enable", "gw_profile_read", "gw_launch_count", "gw_deepclean_forward_noalloc",
 )
 
 
@@ -91,6 +91,7 @@ def _declare(lib):
         "gw_profile_enable": (I, [I]),
         "gw_profile_read": (I, [C.c_char_p, SZ, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
         "gw_launch_count": (I64, []),
+        "gw_deepclean_forward_noalloc": (I, [P, P, I64, I64, I, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -169,6 +170,10 @@ def gw_model_destroy(m):
 
 def gw_deepclean_forward(m, x_ptr, ld, window_stride, B, L, y_ptr, stream=0):
     _check(lib().gw_deepclean_forward(m, x_ptr, ld, window_stride, B, L, y_ptr, stream or None))
+
+
+def gw_deepclean_forward_noalloc(m, x_ptr, ld, window_stride, B, L, y_ptr, stream=0):
+    _check(lib().gw_deepclean_forward_noalloc(m, x_ptr, ld, window_stride, B, L, y_ptr, stream or None))
 
 
 def gw_bbhnet_score(m, x_ptr, B, L, logits_ptr, stream=0):
