@@ -101,6 +101,9 @@ typedef struct gw_model_desc {
 size_t gw_model_param_count(int kind, int n_in);
 int gw_model_create(gw_ctx_t ctx, const gw_model_desc* desc, gw_model_t* out);
 int gw_model_destroy(gw_model_t m);
+/* Synchronises cuda_stream and reports whether a tensor-core kernel of this
+ * model gave up a bounded device-side wait (GW_ETIMEOUT) since creation. */
+int gw_model_status(gw_model_t m, void* cuda_stream);
 
 /* DeepClean forward over B windows of L samples (L a multiple of 8).
  * x: device FP32; channel c of window b is the L samples starting at
@@ -208,6 +211,18 @@ int gw_stream_status(gw_stream_t s, void* cuda_stream);
  * arrays (at most `max_entries` each).  Returns the number of names, or a
  * negative code.  gw_launch_count returns the number of kernels launched by
  * the library since load (always counted). */
+/* Host-only inspection of how the tensor-core path lowers one conv layer
+ * (no GPU is touched): `spec` = {transposed, c_in, c_out, k, stride, pad_left,
+ * pad_right, out_pad}; `wfold` = folded weights [c_out][c_in][k] (FP64);
+ * `lin` = input length; in_P / out_P = phase planes of input and output.
+ * Writes the packed B-operand image (per K-step: 2 K-halves x npad rows x 16
+ * bytes), the 2-word-per-step table and 20 ints of meta: n_steps, npad,
+ * groups, in phases, chains, tap span, min tap shift, M sub-tiles per CTA,
+ * rows per plane, A bytes, steps per stage, stages, step bytes, TMEM
+ * columns, grid x, valid m of chain 0 and 1, instruction descriptor, dynamic
+ * shared memory bytes, output length. */
+int gw_tc_inspect(const int* spec, int precision, const double* wfold, int lin, int in_P, int out_P,
+                  void* img_out, size_t img_cap, uint32_t* table_out, int table_cap, int* meta_out);
 int gw_profile_enable(int on);
 int gw_profile_read(char* names, size_t names_len, double* total_ms, int64_t* launches, int max_entries);
 int64_t gw_launch_count(void);

@@ -285,6 +285,116 @@ static void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits,
   launch_gap_linear_f32(buf[h], (int64_t)cin * l, l, B, cin, l, m->head_w, m->head_b, logits, st);
 }
 
+// ---- tensor-core runners -------------------------------------------------------
+// Blocked activation of `cout` channels x `lout` positions in P phase planes
+// (element strides; rows of 8 bf16 channels).
+static TcOut blocked_out(void* buf, int cout, int lout, int P) {
+  TcOut o{};
+  const int G = (cout + 7) / 8;
+  const int64_t Lp = (lout + P - 1) / P;
+  o.p = buf;
+  o.pstride = Lp * 8;
+  o.gstride = (int64_t)P * Lp * 8;
+  o.bstride = (int64_t)G * o.gstride;
+  o.P = P;
+  return o;
+}
+
+static TcIn as_input(const TcOut& o, int lout) {
+  TcIn i{};
+  i.p = o.p;
+  i.bstride = o.bstride;
+  i.gstride = o.gstride;
+  i.pstride = o.pstride;
+  i.P = o.P;
+  i.L = lout;
+  return i;
+}
+
+static const char* kDcTcNames[8] = {"conv_tc.enc1", "conv_tc.enc2", "conv_tc.enc3", "conv_tc.enc4",
+                                    "conv_tc.dec1", "conv_tc.dec2", "conv_tc.dec3", "conv_tc.out"};
+
+// Per-item elements of the largest inter-layer activation of a DeepClean window.
+static int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 64; }
+
+// DeepClean on B windows through the tensor-core kernels.  `in` is the
+// blocked BF16 input (ring windows or a converted batch); y gets FP32 [B][y_ld].
+static void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1,
+                         int* err, cudaStream_t st) {
+  const auto& Ls = m->layers;
+  void* bufs[2] = {buf0, buf1};
+  int lin = L;
+  for (size_t li = 0; li < Ls.size(); ++li) {
+    const LayerSpec& s = Ls[li].s;
+    const int lout = s.lout(lin);
+    TcOut o{};
+    if (li + 1 == Ls.size()) {
+      o.p = y;
+      o.bstride = y_ld;
+      o.P = 1;
+      o.fp32_single = 1;
+    } else {
+      o = blocked_out(bufs[li & 1], s.cout, lout, Ls[li + 1].pin);
+      GW_CHECK_ARG(o.bstride <= deepclean_tc_act_elems(L), "activation buffer too small");
+    }
+    {
+      Prof p(kDcTcNames[li], st);
+      launch_conv_tc(Ls[li], in, lout, o, B, err, st);
+    }
+    in = as_input(o, lout);
+    lin = lout;
+  }
+}
+
+// BBHnet on B items of [2][L] FP32 through the tensor-core kernels.
+static void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st) {
+  const auto& Ls = m->layers;
+  const int64_t per = (int64_t)B * 32 * L;  // elements of the largest activation
+  void* in0 = ws;
+  void* buf[3] = {ws + (size_t)B * 8 * L * 2, ws + (size_t)B * 8 * L * 2 + per * 2,
+                  ws + (size_t)B * 8 * L * 2 + 2 * per * 2};
+  TcOut xin = blocked_out(in0, m->n_in, L, Ls[0].pin);
+  {
+    Prof p("to_blocked", st);
+    launch_to_blocked(x, (int64_t)m->n_in * L, L, B, m->n_in, L, nullptr, nullptr, 1.f, xin, 0, st);
+  }
+  int l = Ls[0].s.lout(L);
+  TcOut h = blocked_out(buf[0], Ls[0].s.cout, l, Ls[1].pin);
+  {
+    Prof p("conv_tc.bbhnet", st);
+    launch_conv_tc(Ls[0], as_input(xin, L), l, h, B, m->err, st);
+  }
+  int hi = 0;
+  for (int blk = 0; blk < 4; ++blk) {
+    const LayerDev& c1 = Ls[1 + 3 * blk];
+    LayerDev c2 = Ls[2 + 3 * blk];
+    const LayerDev& sc = Ls[3 + 3 * blk];
+    c2.s.act = ACT_RELU;  // relu(conv2 + shortcut)
+    const int a_i = (hi + 1) % 3, o_i = (hi + 2) % 3;
+    const int l2 = c1.s.lout(l);
+    const int next_P = blk < 3 ? Ls[1 + 3 * (blk + 1)].pin : 1;
+    TcOut a = blocked_out(buf[a_i], c1.s.cout, l2, c2.pin);
+    TcOut o = blocked_out(buf[o_i], c2.s.cout, l2, next_P);
+    Prof p("conv_tc.bbhnet", st);
+    launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
+    launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
+    TcOut o2 = o;
+    o2.res = o.p;
+    o2.rbstride = o.bstride;
+    o2.rgstride = o.gstride;
+    o2.rpstride = o.pstride;
+    o2.rP = o.P;
+    launch_conv_tc(c2, as_input(a, l2), l2, o2, B, m->err, st);
+    h = o;
+    hi = o_i;
+    l = l2;
+  }
+  Prof p("gap_linear_tc", st);
+  launch_gap_linear_blocked(as_input(h, l), Ls.back().s.cout, 0, 1.f, m->head_w, m->head_b, logits, B, st);
+}
+
+static size_t bbhnet_tc_ws_bytes(int B, int L) { return (size_t)B * 8 * L * 2 + 3 * (size_t)B * 32 * L * 2; }
+
 }  // namespace gw
 
 // ---- stream object ------------------------------------------------------------
@@ -488,6 +598,7 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
   }
   m->in_mean = upload(m, mean);
   m->in_istd = upload(m, istd);
+  m->err = upload(m, std::vector<int>(1, 0));
   } catch (...) {
     model_free(m);
     m = nullptr;
@@ -518,8 +629,28 @@ int gw_deepclean_forward(gw_model_t m, const float* x, int64_t ld, int64_t windo
     float* ws = (float*)model_workspace(m, 2 * per * sizeof(float));
     deepclean_f32(m, x, window_stride, ld, true, B, L, y, L, ws, ws + per, st);
   } else {
-    throw Error(GW_ENOTIMPL, "DeepClean BF16 offline path not built yet");
+    // standardise + cast the windows into the blocked BF16 layout, then run
+    const int G = (m->n_in + 7) / 8;
+    const size_t in_elems = (size_t)B * G * L * 8;
+    const size_t act = (size_t)B * deepclean_tc_act_elems(L);
+    char* ws = (char*)model_workspace(m, (in_elems + 2 * act) * 2);
+    TcOut xin = blocked_out(ws, m->n_in, L, 1);
+    {
+      Prof p("to_blocked", st);
+      launch_to_blocked(x, window_stride, ld, B, m->n_in, L, m->in_mean, m->in_istd, 1.f, xin, 0, st);
+    }
+    deepclean_tc(m, as_input(xin, L), B, L, y, L, ws + in_elems * 2, ws + (in_elems + act) * 2, m->err, st);
   }
+  GW_API_END
+}
+
+int gw_model_status(gw_model_t m, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(m, "model is NULL");
+  int h = 0;
+  GW_CUDA(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream));
+  GW_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  if (h) throw Error(GW_ETIMEOUT, "a tensor-core kernel gave up a bounded wait (flag " + std::to_string(h) + ")");
   GW_API_END
 }
 
@@ -532,8 +663,11 @@ int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, v
   if (m->precision == GW_FP32) {
     float* ws = (float*)model_workspace(m, 3 * (size_t)B * 32 * L * sizeof(float));
     bbhnet_f32(m, x, B, L, logits, ws, st);
+  } else if (m->precision == GW_BF16) {
+    char* ws = (char*)model_workspace(m, bbhnet_tc_ws_bytes(B, L));
+    bbhnet_tc(m, x, B, L, logits, ws, st);
   } else {
-    throw Error(GW_ENOTIMPL, "BBHnet tensor-core path not built yet");
+    throw Error(GW_ENOTIMPL, "BBHnet FP8 path not built yet");
   }
   GW_API_END
 }
@@ -639,7 +773,7 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
       s->acc[i] = salloc<float>(s, (size_t)s->R);
     }
     s->pred = salloc<float>(s, (size_t)nb * W);
-    const size_t act_elems = (size_t)nb * 8 * W;
+    const size_t act_elems = (size_t)nb * deepclean_tc_act_elems((int)W);
     const size_t esz = prec == GW_FP32 ? 4 : 2;
     s->act0 = salloc<char>(s, act_elems * esz);
     s->act1 = salloc<char>(s, act_elems * esz);
@@ -723,12 +857,20 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
     int64_t p0 = (head + S - W) % R;
     if (p0 < 0) p0 += R;
     if (m->precision == GW_FP32) {
-      const size_t per = (size_t)n_snap * 8 * W;
       deepclean_f32(m, s->ring_f32[d] + p0, S, 2 * R, false, n_snap, W, s->pred, W, (float*)s->act0,
                     (float*)s->act1, st);
-      (void)per;
     } else {
-      throw Error(GW_ENOTIMPL, "BF16 stream path not built yet");
+      // the first layer reads the windows in place from the blocked BF16 ring
+      TcIn in{};
+      in.p = s->ring_bf16[d];
+      in.off0 = p0 * 8;
+      in.bstride = 0;
+      in.boff = S;
+      in.gstride = 2 * R * 8;
+      in.pstride = 0;
+      in.P = 1;
+      in.L = W;
+      deepclean_tc(m, in, n_snap, W, s->pred, W, s->act0, s->act1, s->err, st);
     }
     {
       Prof p("sub_ola", st);

@@ -59,6 +59,10 @@ struct LayerDev {
   int n_steps = 0;         // K-steps (MMA instructions per M sub-tile)
   int npad = 0;            // N (output channels) padded for the MMA
   int gin = 0;             // input channel groups of 8 (or 16 for FP8)
+  int pin = 1;             // input phase planes the layer reads
+  int n_chains = 1;        // output phases computed per tile (2 for transposed convs)
+  int dspan = 0;           // extra input rows per plane (tap shift range)
+  int dmin = 0;            // smallest tap row shift
   float act_scale = 1.f;   // FP8: scale of this layer's input activations
   float out_scale = 1.f;   // FP8: scale applied to the outputs for the next layer
 };
@@ -86,6 +90,7 @@ struct gw_model {
   // workspace for offline forwards (grown on demand)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  int* err = nullptr;        // device error flag of the tensor-core kernels (bounded waits)
 };
 
 struct gw_fir {
@@ -148,27 +153,38 @@ void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int
                     float* out, cudaStream_t st);
 
 // ---- tensor-core conv path (k_tc.cu) ---------------------------------------------
-// Activation layout of the tensor-core path: [B][G][P][Lp][8] bf16, with G
-// groups of 8 channels, P phase planes (the consumer's stride) and
-// Lp = L / P positions per plane; channel c of position t sits at
-// [c / 8][t % P][t / P][c % 8].
-struct TcAct {
-  const __nv_bfloat16* p; int64_t bstride;  // elements between batch items
-  int64_t gstride;                          // elements between channel groups
-  int64_t off0;                             // element offset of position 0 of item b=0 (ring windows)
-  int64_t boff;                             // extra per-item offset in positions (ring windows: S)
-  int P; int64_t pstride;                   // phases and elements between phase planes
-  int L;                                    // logical length
+// Activation layout of the tensor-core path ("blocked"): channels in groups of
+// 8 (bf16) or 16 (e4m3) so that one position of one group is a 16-byte row;
+// rows of a group are split into P phase planes (P = the stride of the layer
+// that consumes them), so a stride-2 conv reads each tap as a plain row
+// offset.  Element (b, c, t) sits at
+//   base + off0 + b*bstride + (c / cg)*gstride + (t % P)*pstride + (t / P + b*boff)*cg + c % cg
+// with cg = 8 (bf16) or 16 (e4m3).  boff lets B overlapping ring windows be
+// views of one buffer.
+struct TcIn {
+  const void* p;
+  int64_t off0, bstride, boff, gstride, pstride;
+  int P, L;
 };
 struct TcOut {
-  void* p; int64_t bstride, gstride, pstride; int P;
-  int fp32_single;   // 1: write channel 0 as FP32 [B][L] (prediction output)
-  const __nv_bfloat16* res; int64_t rbstride, rgstride, rpstride; int rP;  // residual (same layout rules)
+  void* p;               // blocked activations, or FP32 [B][bstride] when fp32_single
+  int64_t bstride, gstride, pstride;
+  int P;
+  int fp32_single;       // write channel 0 as FP32 (the DeepClean prediction)
+  const void* res;       // optional residual in blocked layout, added before the activation
+  int64_t rbstride, rgstride, rpstride;
+  int rP;
+  int fp8_out;           // write e4m3 (scaled by out_scale) instead of bf16
 };
 int tc_supported();
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wfold, int precision, gw_ctx* ctx,
                    size_t* counter, std::vector<void*>& allocs);
-void launch_conv_tc(const LayerDev& L, const TcAct& in, int lout, const TcOut& out, int B,
-                    int* err_flag, cudaStream_t st);
-
+void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err_flag,
+                    cudaStream_t st);
+// FP32 [B][C][x_ld] (item b at x + b*xb) -> blocked bf16 / e4m3, optionally standardised.
+void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,
+                       const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st);
+// Global average pool over a blocked activation + linear head -> FP32 logits.
+void launch_gap_linear_blocked(const TcIn& in, int C, int fp8, float in_scale, const float* w,
+                               const float* b, float* out, int B, cudaStream_t st);
 }  // namespace gw

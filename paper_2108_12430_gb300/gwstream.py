@@ -38,6 +38,7 @@ EXPORTS = (
     "gw_fir_create_whitening", "gw_fir_destroy", "gw_fir_ntaps", "gw_fir_taps", "gw_whiten",
     "gw_stream_create", "gw_stream_destroy", "gw_stream_push", "gw_stream_head", "gw_stream_status",
     "gw_profile_enable", "gw_profile_read", "gw_launch_count", "gw_deepclean_forward_noalloc",
+    "gw_model_status", "gw_tc_inspect",
 )
 
 
@@ -92,6 +93,9 @@ def _declare(lib):
         "gw_profile_read": (I, [C.c_char_p, SZ, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
         "gw_launch_count": (I64, []),
         "gw_deepclean_forward_noalloc": (I, [P, P, I64, I64, I, I, P, P]),
+        "gw_model_status": (I, [P, P]),
+        "gw_tc_inspect": (I, [C.POINTER(C.c_int), I, C.POINTER(C.c_double), I, I, I, P, SZ,
+                              C.POINTER(C.c_uint32), I, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -166,6 +170,10 @@ def gw_model_create(ctx, kind, precision, n_in, params, in_mean=None, in_std=Non
 
 def gw_model_destroy(m):
     _check(lib().gw_model_destroy(m))
+
+
+def gw_model_status(m, stream=0):
+    _check(lib().gw_model_status(m, stream or None))
 
 
 def gw_deepclean_forward(m, x_ptr, ld, window_stride, B, L, y_ptr, stream=0):
@@ -253,3 +261,22 @@ def gw_profile_read(max_entries=64):
 
 def gw_launch_count():
     return lib().gw_launch_count()
+
+
+TC_META = ("n_steps", "npad", "groups", "in_P", "chains", "dspan", "dmin", "MT", "rows", "a_bytes", "sps", "nst",
+           "step_bytes", "ncols", "grid_x", "mout0", "mout1", "idesc", "smem", "lout")
+
+
+def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P):
+    """Host-only lowering of one layer: (image bytes, table uint32, meta dict)."""
+    spec_a = (C.c_int * 8)(*spec)
+    wf = np.ascontiguousarray(wfold, np.float64)
+    cap = 1 << 24
+    img = np.zeros(cap, np.uint8)
+    table = np.zeros(1 << 14, np.uint32)
+    meta = (C.c_int * 20)()
+    _check(lib().gw_tc_inspect(spec_a, precision, wf.ctypes.data_as(C.POINTER(C.c_double)), lin, in_P, out_P,
+                               img.ctypes.data, cap, table.ctypes.data_as(C.POINTER(C.c_uint32)), table.size, meta))
+    md = dict(zip(TC_META, list(meta)))
+    md["idesc"] &= 0xFFFFFFFF
+    return img[:md["n_steps"] * md["step_bytes"]].copy(), table[:2 * md["n_steps"]].copy(), md

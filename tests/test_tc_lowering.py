@@ -1,0 +1,139 @@
+"""Host-logic test of the tensor-core conv lowering (CPU only).
+
+gw_tc_inspect returns the packed B-operand image, the K-step table and the
+launch plan that the tcgen05 kernel uses.  This test replays the kernel's
+data path in numpy -- input tile rows per (group, phase) plane with zero
+padding, A and B operands gathered through the shared-memory descriptor
+address rule (16-byte rows, 8-row core matrices, SBO = 128 B between
+8-row groups, LBO between the two K-halves), accumulator chains, epilogue
+position mapping -- and compares the result with the oracle's Conv1d /
+ConvTranspose1d on the same bf16-rounded inputs.  Every address is checked
+against its buffer, so an index slip fails here before the kernel runs.
+"""
+import numpy as np
+import pytest
+
+from oracle import layers as Lyr
+from oracle.quant import to_bf16
+from paper_2108_12430_gb300 import gwstream as G
+
+rng = np.random.default_rng(2024)
+
+
+def bf16_bits_to_f64(u16):
+    return (u16.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def f64_to_bf16_bits(x):
+    # inputs are already bf16-representable: truncation is exact
+    return (np.asarray(x, np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+def emulate(spec, x, img, table, md):
+    transposed, cin, cout, k, stride, pl, pr, op = spec
+    Gn, P, rows, MT, dmin, npad = md["groups"], md["in_P"], md["rows"], md["MT"], md["dmin"], md["npad"]
+    chains, step_bytes, a_bytes = md["chains"], md["step_bytes"], md["a_bytes"]
+    chainP = 2 if transposed else 1
+    lin = x.shape[1]
+    lout = md["lout"]
+    assert rows * 16 * Gn * P <= a_bytes
+    assert md["smem"] <= 227 * 1024 and md["ncols"] <= 512
+    assert chains * MT * npad <= md["ncols"]
+    xb = np.zeros((Gn * 8, lin))
+    xb[:cin] = x
+    imgh = img.view(np.uint16)
+    out = np.zeros((cout, lout))
+    written = np.zeros(lout, bool)
+    r_idx = np.arange(128)[:, None]
+    k_idx = np.arange(16)[None, :]
+    for tile in range(md["grid_x"]):
+        m0 = tile * 128 * MT
+        A = np.zeros(a_bytes // 2, np.uint16)
+        for plane in range(Gn * P):
+            g, phi = plane // P, plane % P
+            Lp = (lin - phi + P - 1) // P
+            r0 = max(0, -m0 - dmin)
+            r1 = max(r0, min(rows, Lp - m0 - dmin))
+            for r in range(r0, r1):
+                j = m0 + dmin + r
+                assert 0 <= j < Lp
+                base = (plane * rows + r) * 8
+                A[base:base + 8] = f64_to_bf16_bits(xb[g * 8:(g + 1) * 8, P * j + phi])
+        D = np.zeros((chains, MT, 128, npad))
+        for s in range(md["n_steps"]):
+            w0, w1 = int(table[2 * s]), int(table[2 * s + 1])
+            chain, first = w1 & 15, (w1 >> 4) & 1
+
+            def off(code):
+                g, phi, dd = code & 0xFF, (code >> 8) & 3, (code >> 10) & 63
+                return ((g * P + phi) * rows + dd) * 16
+
+            o0, o1 = off(w0 & 0xFFFF), off(w0 >> 16)
+            lbo = o1 - o0
+            assert lbo >= 0
+            # B operand: rows n, K-halves at LBO = npad * 16, 8-row groups at SBO = 128
+            n_idx = np.arange(npad)[:, None]
+            baddr = s * step_bytes + (n_idx // 8) * 128 + (n_idx % 8) * 16 + (k_idx // 8) * (npad * 16) + (k_idx % 8) * 2
+            assert baddr.max() + 2 <= (s + 1) * step_bytes
+            Bm = bf16_bits_to_f64(imgh[baddr // 2])
+            for mt in range(MT):
+                start = o0 + mt * 2048
+                aaddr = start + (r_idx // 8) * 128 + (r_idx % 8) * 16 + (k_idx // 8) * lbo + (k_idx % 8) * 2
+                assert aaddr.min() >= 0 and aaddr.max() + 2 <= a_bytes
+                Am = bf16_bits_to_f64(A[aaddr // 2])
+                acc = Am @ Bm.T
+                D[chain, mt] = acc if first else D[chain, mt] + acc
+        for c in range(chains):
+            mout = md["mout1"] if c else md["mout0"]
+            for mt in range(MT):
+                m = m0 + mt * 128 + np.arange(128)
+                ok = m < mout
+                u = chainP * m[ok] + c
+                assert u.max(initial=-1) < lout
+                out[:, u] = D[c, mt][ok][:, :cout].T
+                written[u] = True
+    assert written.all()
+    return out
+
+
+CASES = [
+    # DeepClean layers (transposed, cin, cout, k, stride, pad_l, pad_r, out_pad), input length
+    ((0, 21, 8, 7, 1, 3, 3, 0), 2100, 1, 2),
+    ((0, 8, 16, 7, 2, 3, 3, 0), 2102, 2, 2),
+    ((0, 16, 32, 7, 2, 3, 3, 0), 1030, 2, 2),
+    ((0, 32, 64, 7, 2, 3, 3, 0), 530, 2, 1),
+    ((1, 64, 32, 7, 2, 3, 3, 1), 262, 1, 1),
+    ((1, 32, 16, 7, 2, 3, 3, 1), 524, 1, 1),
+    ((1, 16, 8, 7, 2, 3, 3, 1), 1048, 1, 1),
+    ((0, 8, 1, 7, 1, 3, 3, 0), 2096, 1, 1),
+    # BBHnet layers
+    ((0, 2, 32, 16, 1, 7, 8, 0), 600, 1, 2),
+    ((0, 32, 64, 7, 2, 3, 3, 0), 300, 2, 1),
+    ((0, 64, 64, 7, 1, 3, 3, 0), 150, 1, 2),
+    ((0, 128, 256, 1, 2, 0, 0, 0), 300, 2, 1),
+    ((0, 256, 256, 7, 1, 3, 3, 0), 140, 1, 1),
+]
+
+
+@pytest.mark.parametrize("spec,lin,in_P,out_P", CASES)
+def test_tc_lowering_matches_oracle(spec, lin, in_P, out_P):
+    transposed, cin, cout, k, stride, pl, pr, op = spec
+    w = to_bf16(rng.standard_normal((cout, cin, k)) * 0.2)
+    x = to_bf16(rng.standard_normal((cin, lin)))
+    img, table, md = G.gw_tc_inspect(spec, G.GW_BF16, w, lin, in_P, out_P)
+    assert md["in_P"] == in_P
+    got = emulate(spec, x, img, table, md)
+    if transposed:
+        ref = Lyr.conv_transpose1d(x[None], np.transpose(w, (1, 0, 2)), np.zeros(cout), stride, pl, op)[0]
+    else:
+        ref = Lyr.conv1d(x[None], w, np.zeros(cout), stride, pl, pr)[0]
+    assert got.shape == ref.shape
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_tc_instruction_descriptor_fields():
+    # kind::f16: D=F32 (bit 4), A=B=BF16 (bits 7, 10), K-major, N>>3 at 17, M>>4 at 24
+    _, _, md = G.gw_tc_inspect((0, 32, 64, 7, 2, 3, 3, 0), G.GW_BF16, np.zeros((64, 32, 7)), 256, 2, 1)
+    d = md["idesc"]
+    assert (d >> 4) & 3 == 1 and (d >> 7) & 7 == 1 and (d >> 10) & 7 == 1
+    assert (d >> 15) & 3 == 0 and (d >> 17) & 63 == 64 >> 3 and (d >> 24) & 31 == 128 >> 4
