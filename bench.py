@@ -260,6 +260,8 @@ def gpu_arm(args):
 
     paths = {}
     precisions = [("bf16", G.GW_BF16), ("fp32", G.GW_FP32)]
+    if args.only:
+        precisions = [p for p in precisions if p[0] == args.only]
     headline = None
     clocks = None
     for name, prec in precisions:
@@ -282,8 +284,16 @@ def gpu_arm(args):
             t = torch.tensor([tot], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             tot = float(t.item())
+        if args.lite:
+            # profiling runs: only the device-resident timed pushes above
+            G.gw_stream_destroy(s)
+            G.gw_model_destroy(m)
+            G.gw_ctx_destroy(ctx)
+            paths[name] = {"ms_per_step": float(np.mean(res["ms"]))}
+            continue
         prof = profile_pass(G, torch, push_fn, Wm, min(K, 8), flush)
-        # host-buffer e2e: pinned host copies of the next steps' inputs
+        # host-buffer e2e: pinned host copies of the next steps' inputs (the
+        # pushes continue the same stream)
         n_step = B * S
         first = Wm + K
         ne2e = min(K, 8)
@@ -291,7 +301,6 @@ def gpu_arm(args):
         wit_h = {first + i: pin(wit[:, (first + i) * n_step:(first + i + 1) * n_step])
                  for i in range(ne2e)}
         str_h = {first + i: pin(strain[(first + i) * n_step:(first + i + 1) * n_step]) for i in range(ne2e)}
-        # re-align the stream head is not needed: pushes continue the same stream
         lat = e2e_pass(G, torch, s, wit_h, str_h, first, ne2e)
         err = accuracy(G, torch, prec, dev_index) if rank == 0 else None
         G.gw_stream_destroy(s)
@@ -321,7 +330,9 @@ def gpu_arm(args):
             headline = name
             clocks = paths[name]["clocks"]
 
-    if rank != 0:
+    if rank != 0 or args.lite:
+        if args.lite and rank == 0:
+            print(json.dumps({"lite": True, "paths": paths}))
         if world > 1:
             dist.destroy_process_group()
         return
@@ -408,12 +419,15 @@ def cpu_threads():
 
 
 def cpu_baseline(budget_s=15.0):
-    t1 = oracle_snapshot_seconds(1)
-    n = int(max(1, min(64, budget_s / max(t1, 1e-3))))
-    t = oracle_snapshot_seconds(n)
+    oracle_snapshot_seconds(1)
+    n, t, seed = 0, 0.0, 4321
+    while t < budget_s and n < 1024:
+        t += oracle_snapshot_seconds(32, seed=seed)
+        n += 32
+        seed += 1
     return {"value": n / t, "unit": "snapshots/s", "cores": cpu_threads(), "kind": "oracle",
-            "sample": f"{n} consecutive 21x32768 windows (stride 256) through the FP64 numpy oracle "
-                      f"DeepClean + aggregation, {t:.1f} s"}
+            "sample": f"{n} consecutive 21x32768 windows (stride 256, batches of 32) through the FP64 numpy "
+                      f"oracle DeepClean + aggregation, {t:.1f} s"}
 
 
 def reference_arm(args):
@@ -447,6 +461,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gw", "reference"], default="gw")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--only", choices=["bf16", "fp32"], default=None,
+                    help="time one path only (profiling)")
+    ap.add_argument("--lite", action="store_true",
+                    help="timed device pushes only: no e2e, accuracy, CPU baseline or JSON contract line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

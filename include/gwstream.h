@@ -214,14 +214,16 @@ int gw_stream_status(gw_stream_t s, void* cuda_stream);
 /* Host-only inspection of how the tensor-core path lowers one conv layer
  * (no GPU is touched): `spec` = {transposed, c_in, c_out, k, stride, pad_left,
  * pad_right, out_pad}; `wfold` = folded weights [c_out][c_in][k] (FP64);
- * `lin` = input length; in_P / out_P = phase planes of input and output.
+ * `lin` = input length; in_P / out_P = phase planes of input (0 = the
+ * layer's own) and output; `batch` = items the launch plan is made for.
  * Writes the packed B-operand image (per K-step: 2 K-halves x npad rows x 16
  * bytes), the 2-word-per-step table and 20 ints of meta: n_steps, npad,
- * groups, in phases, chains, tap span, min tap shift, M sub-tiles per CTA,
- * rows per plane, A bytes, steps per stage, stages, step bytes, TMEM
- * columns, grid x, valid m of chain 0 and 1, instruction descriptor, dynamic
- * shared memory bytes, output length. */
-int gw_tc_inspect(const int* spec, int precision, const double* wfold, int lin, int in_P, int out_P,
+ * groups, input phases, output positions per row (Q), tap span, min tap
+ * shift, M sub-tiles per tile, rows per plane, A stage bytes, steps per
+ * weight stage, weight stages, step bytes, TMEM columns, tiles per item,
+ * valid rows, channels per position, instruction descriptor, dynamic shared
+ * memory bytes, output length. */
+int gw_tc_inspect(const int* spec, int precision, const double* wfold, int lin, int in_P, int out_P, int batch,
                   void* img_out, size_t img_cap, uint32_t* table_out, int table_cap, int* meta_out);
 int gw_profile_enable(int on);
 int gw_profile_read(char* names, size_t names_len, double* total_ms, int64_t* launches, int max_entries);

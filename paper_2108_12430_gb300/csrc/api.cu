@@ -315,7 +315,7 @@ static const char* kDcTcNames[8] = {"conv_tc.enc1", "conv_tc.enc2", "conv_tc.enc
                                     "conv_tc.dec1", "conv_tc.dec2", "conv_tc.dec3", "conv_tc.out"};
 
 // Per-item elements of the largest inter-layer activation of a DeepClean window.
-static int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 64; }
+static int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 2048; }
 
 // DeepClean on B windows through the tensor-core kernels.  `in` is the
 // blocked BF16 input (ring windows or a converted batch); y gets FP32 [B][y_ld].
@@ -370,6 +370,7 @@ static void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, 
     LayerDev c2 = Ls[2 + 3 * blk];
     const LayerDev& sc = Ls[3 + 3 * blk];
     c2.s.act = ACT_RELU;  // relu(conv2 + shortcut)
+    GW_CHECK_ARG(c1.pin == sc.pin, "block convs must read the same input layout");
     const int a_i = (hi + 1) % 3, o_i = (hi + 2) % 3;
     const int l2 = c1.s.lout(l);
     const int next_P = blk < 3 ? Ls[1 + 3 * (blk + 1)].pin : 1;
@@ -630,11 +631,11 @@ int gw_deepclean_forward(gw_model_t m, const float* x, int64_t ld, int64_t windo
     deepclean_f32(m, x, window_stride, ld, true, B, L, y, L, ws, ws + per, st);
   } else {
     // standardise + cast the windows into the blocked BF16 layout, then run
-    const int G = (m->n_in + 7) / 8;
-    const size_t in_elems = (size_t)B * G * L * 8;
+    TcOut xin = blocked_out(nullptr, m->n_in, L, m->layers[0].pin);
+    const size_t in_elems = (size_t)B * xin.bstride;
     const size_t act = (size_t)B * deepclean_tc_act_elems(L);
     char* ws = (char*)model_workspace(m, (in_elems + 2 * act) * 2);
-    TcOut xin = blocked_out(ws, m->n_in, L, 1);
+    xin.p = ws;
     {
       Prof p("to_blocked", st);
       launch_to_blocked(x, window_stride, ld, B, m->n_in, L, m->in_mean, m->in_istd, 1.f, xin, 0, st);
@@ -761,7 +762,7 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
   for (int i = 0; i < d->n_det; ++i) s->dc[i] = deepclean[i];
   const int64_t W = d->window, S = d->stride, nb = d->max_batch, C = d->n_witness;
   s->R = W + (nb - 1) * S;
-  s->R = (s->R + 7) / 8 * 8;
+  s->R = (s->R + 15) / 16 * 16;  // whole rows in every phase plane of the ring
   const int G = (int)((C + 7) / 8);
   try {
     for (int i = 0; i < d->n_det; ++i) {
@@ -845,8 +846,8 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
       if (m->precision == GW_FP32)
         launch_ring_push_f32(wd, n, C, (int)n, s->ring_f32[d], R, head, m->in_mean, m->in_istd, s->status, st);
       else
-        launch_ring_push_bf16(wd, n, C, G, (int)n, s->ring_bf16[d], R, head, m->in_mean, m->in_istd, s->status,
-                              st);
+        launch_ring_push_bf16(wd, n, C, G, (int)n, s->ring_bf16[d], R, head, m->layers[0].pin, m->in_mean,
+                              m->in_istd, s->status, st);
     }
     {
       Prof p("strain_push", st);
@@ -860,15 +861,20 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
       deepclean_f32(m, s->ring_f32[d] + p0, S, 2 * R, false, n_snap, W, s->pred, W, (float*)s->act0,
                     (float*)s->act1, st);
     } else {
-      // the first layer reads the windows in place from the blocked BF16 ring
+      // the first layer reads the windows in place from the blocked BF16 ring,
+      // stored in the P phase planes the layer consumes (window starts are
+      // multiples of P because S and W are)
+      const int P = m->layers[0].pin;
+      GW_CHECK_ARG(S % P == 0 && W % P == 0 && p0 % P == 0 && R % P == 0,
+                   "stride and window must be multiples of the first layer's phase count");
       TcIn in{};
       in.p = s->ring_bf16[d];
-      in.off0 = p0 * 8;
+      in.off0 = (p0 / P) * 8;
       in.bstride = 0;
-      in.boff = S;
+      in.boff = S / P;
       in.gstride = 2 * R * 8;
-      in.pstride = 0;
-      in.P = 1;
+      in.pstride = (2 * R / P) * 8;
+      in.P = P;
       in.L = W;
       deepclean_tc(m, in, n_snap, W, s->pred, W, s->act0, s->act1, s->err, st);
     }

@@ -60,7 +60,8 @@ struct LayerDev {
   int npad = 0;            // N (output channels) padded for the MMA
   int gin = 0;             // input channel groups of 8 (or 16 for FP8)
   int pin = 1;             // input phase planes the layer reads
-  int n_chains = 1;        // output phases computed per tile (2 for transposed convs)
+  int n_chains = 1;        // output positions folded into one MMA row (Q)
+  int coutp = 8;           // output channels per position in the MMA columns
   int dspan = 0;           // extra input rows per plane (tap shift range)
   int dmin = 0;            // smallest tap row shift
   float act_scale = 1.f;   // FP8: scale of this layer's input activations
@@ -143,8 +144,10 @@ void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool sta
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring,
                           int64_t R, int64_t head, const float* mean, const float* istd,
                           int* status, cudaStream_t st);
+// Blocked BF16 ring [G][P][2R / P][8]: ring position q (0 <= q < 2R) of
+// channel group g sits in plane q % P, row q / P.
 void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n,
-                           __nv_bfloat16* ring, int64_t R, int64_t head, const float* mean,
+                           __nv_bfloat16* ring, int64_t R, int64_t head, int P, const float* mean,
                            const float* istd, int* status, cudaStream_t st);
 void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head,
                         int* status, cudaStream_t st);

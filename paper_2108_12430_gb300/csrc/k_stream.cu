@@ -45,12 +45,14 @@ __global__ void ring_push_f32_kernel(const float* __restrict__ src, int64_t src_
   }
 }
 
-// src [C][src_ld] -> ring [G][2R][8] bf16 (channel-group blocked), standardised.
-// One thread writes the 8 channels of one (group, time) as a 16-byte store.
+// src [C][src_ld] -> ring [G][P][2R / P][8] bf16 (channel-group blocked,
+// P phase planes), standardised.  One thread writes the 8 channels of one
+// (group, time) as a 16-byte store; R is a multiple of P.
 __global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src_ld, int C, int G, int n,
-                                      __nv_bfloat16* __restrict__ ring, int64_t R, int64_t head,
+                                      __nv_bfloat16* __restrict__ ring, int64_t R, int64_t head, int P,
                                       const float* __restrict__ mean, const float* __restrict__ istd,
                                       int* status) {
+  const int64_t plane_rows = 2 * R / P;
   const int64_t total = (int64_t)G * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -69,9 +71,9 @@ __global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src
     }
     const int64_t q = pmod(head + i, R);
     uint4 val = *reinterpret_cast<const uint4*>(v8);
-    uint4* row = reinterpret_cast<uint4*>(ring + (int64_t)g * 2 * R * 8);
-    row[q] = val;
-    row[q + R] = val;
+    uint4* grp = reinterpret_cast<uint4*>(ring + (int64_t)g * 2 * R * 8);
+    grp[(q % P) * plane_rows + q / P] = val;
+    grp[((q + R) % P) * plane_rows + (q + R) / P] = val;
   }
 }
 
@@ -146,9 +148,10 @@ void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float*
 }
 
 void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n, __nv_bfloat16* ring,
-                           int64_t R, int64_t head, const float* mean, const float* istd, int* status,
+                           int64_t R, int64_t head, int P, const float* mean, const float* istd, int* status,
                            cudaStream_t st) {
-  ring_push_bf16_kernel<<<grid_for((int64_t)G * n), kThreads, 0, st>>>(src, src_ld, C, G, n, ring, R, head,
+  GW_CHECK_ARG(P >= 1 && R % P == 0, "ring capacity must be a multiple of the phase count");
+  ring_push_bf16_kernel<<<grid_for((int64_t)G * n), kThreads, 0, st>>>(src, src_ld, C, G, n, ring, R, head, P,
                                                                         mean, istd, status);
   GW_LAUNCH_CHECK();
 }

@@ -1,31 +1,42 @@
 // Tensor-core (tcgen05) implicit-GEMM convolution for sm_103a.
 //
 // Every Conv1d / ConvTranspose1d layer of the two networks runs here as
-//   D[m][n] = sum_steps A_step[m][16 k] * B_step[n][16 k]
-// with M = 128 output positions per MMA (one TMEM lane each), N = output
-// channels (padded to a multiple of 16) and K-steps of 16 BF16 (or 32 e4m3)
-// inputs.  A K-step is made of two 16-byte "slices": 8 (16) input channels of
-// one tap, read from an input phase plane at a row shift.  Because the input
-// tile sits in shared memory in the no-swizzle K-major core-matrix layout
-// (16-byte rows, 8-row core matrices), a tap is only a different descriptor
-// start address: the im2col matrix is never formed.
-//   conv, stride s:  output t, tap k reads input s t + k - p = phase
-//                    (k - p) mod s, row t + floor((k - p) / s);
-//   convT, stride 2: output u = 2 m + psi gathers taps k with psi + p - k
-//                    even from input row m + (psi + p - k) / 2 (two output
-//                    phases = two accumulator chains).
-// The BatchNorm is folded into the weights (FP64, host); bias, activation
-// and an optional residual are applied in the epilogue from TMEM.
+//   D[r][n] = sum_steps A_step[r][16 k] * B_step[n][16 k]
+// with M = 128 "rows" r per MMA (one TMEM lane each), N output columns and
+// K-steps of 16 BF16 (or 32 e4m3) inputs.
 //
-// Data movement: the input tile (all channel groups and phases, plus the tap
-// halo) arrives by one bulk TMA copy per plane; the weight image streams
-// through a ring of stages by bulk TMA; one thread issues the MMAs; all four
-// warps drain TMEM with tcgen05.ld.  Every wait is bounded (1 s) and reports
-// through an error flag instead of hanging.
+// Rows and columns.  A row r stands for Q consecutive output positions
+// u = Q r + sigma (sigma < Q); column n = sigma * C' + o holds output channel o
+// (C' = C_out rounded up to 8, or 1 for the single-channel prediction) of
+// position sigma.  Q = J for a conv and Q = 2 J for a transposed conv: folding
+// J output positions (and both phases of a stride-2 transposed conv) into N
+// makes N >= 64 for the small channel counts of DeepClean instead of 8 or 16,
+// which cuts the shared-memory operand traffic per useful MAC.
+//
+// K slices.  The layer's input is stored in P phase planes (P = stride x J for
+// a conv, J for a transposed conv): input position x = P i + phi sits in plane
+// phi, row i.  Output row r then reads, for every (tap, sigma), input row
+// r + d of plane phi -- a fixed shift.  The distinct (phi, d) over all taps
+// and sigma, times the channel groups of 8 (16 for e4m3), are the K "slices";
+// two slices form a K-step.  Each slice is one 16-byte row per M row, so in
+// the no-swizzle K-major core-matrix layout (16-byte rows, 8-row core
+// matrices, SBO = 128 B) a slice is just a descriptor start address and the
+// two slices of a step are LBO apart: the im2col matrix is never formed.
+// B holds the folded weights arranged per (sigma, o) column and slice.
+//
+// Kernel.  Persistent and warp-specialised: warp 0 stages input tiles by bulk
+// TMA into a 2-deep ring (zero rows for the padding at the edges), warp 1
+// issues the MMAs from one thread into a double-buffered TMEM accumulator,
+// warps 2-5 drain TMEM with tcgen05.ld, add bias (and a residual), apply the
+// activation and store the consumer's layout.  Weights stay resident in shared
+// memory when they fit, else stream per tile through a ring of stages.  The
+// BatchNorm is folded into the weights on the host in FP64.  Every wait is
+// bounded (1 s): on timeout the kernel records an error flag and unwinds.
 #include <cuda_fp8.h>
 #include <string.h>
 
 #include <algorithm>
+#include <set>
 
 #include "gw_internal.h"
 
@@ -33,18 +44,18 @@ namespace gw {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
-constexpr int kErrWaitA = 1, kErrWaitB = 2, kErrWaitEmpty = 4, kErrWaitDone = 8;
+constexpr int kThreads = 192;  // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr long long kWaitCycles = 2000000000ll;
+constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
 
 struct TcParams {
   const char* in;
   int64_t in_off0, in_b, in_boff, in_g, in_p;  // bytes (boff in 16-byte rows)
   int in_P, in_L, G;
-  int MT, rows, dmin, n_chains, chainP, mout0, mout1, lout;
+  int MT, rows, dmin, Q, coutp, mout, lout, tiles_per_item, n_tiles;
   const char* wimg;
   const uint32_t* table;
-  int n_steps, npad, sps, nst, step_bytes, a_bytes, ncols;
+  int n_steps, npad, sps, nst, step_bytes, a_bytes, ncols, resident;
   uint32_t idesc;
   int fp8;
   const float* bias;
@@ -59,6 +70,8 @@ struct TcParams {
   int res_P, res_fp8;
   float res_scale;
   int* err;
+  int coutp_log, out_P_log, res_P_log;  // power-of-two shifts for the epilogue addressing
+  int min_plen;                          // rows of the shortest input plane
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -81,17 +94,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Waits for the barrier phase with a time limit; on timeout records `code`.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+// Bounded wait for a barrier phase.  Gives up when another role has aborted,
+// or after kWaitCycles SM clocks (about 1 s at the GB300's clocks; then it
+// records `code` and raises the abort flag itself).  The limit uses the
+// SM-local cycle counter: it is cheap to read, so a waiting thread reacts to
+// the phase flip at once.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag, int* err, int code) {
   if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
+  const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > kWaitNs) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1u;
       atomicOr(err, code);
       return false;
     }
@@ -144,236 +158,314 @@ __device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// 32 consecutive accumulator columns of this thread's TMEM lane, one wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
       "tcgen05.wait::ld.sync.aligned;\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr)
       : "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The tensor-core path stores activations in bf16 (relative step 2^-8), so
+// the hardware tanh approximation (relative error about 2^-11) is used; the
+// FP32 path keeps tanhf.
+__device__ __forceinline__ float tanh_fast(float v) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
 }
 
 __device__ __forceinline__ float act_fn(float v, int act) {
-  if (act == ACT_TANH) return tanhf(v);
+  if (act == ACT_TANH) return tanh_fast(v);
   if (act == ACT_RELU) return fmaxf(v, 0.f);
   return v;
 }
 
-// Byte offset (for M sub-tile 0) of the 16-byte slice coded as g | phi << 8 | dd << 10.
+// Byte offset (M sub-tile 0) of the slice coded g | phi << 6 | dd << 11 in a
+// tile of P planes per group, `rows` 16-byte rows per plane.
 __device__ __forceinline__ uint32_t slice_off(uint32_t code, int P, int rows) {
-  const uint32_t g = code & 0xFFu, phi = (code >> 8) & 3u, dd = (code >> 10) & 63u;
+  const uint32_t g = code & 63u, phi = (code >> 6) & 31u, dd = (code >> 11) & 31u;
   return ((g * (uint32_t)P + phi) * (uint32_t)rows + dd) * 16u;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  const uint32_t sA = smem_u32(smem);
-  const uint32_t sB = sA + (uint32_t)p.a_bytes;
+  const uint32_t sA = smem_u32(smem);  // 2 stages of a_bytes
+  const uint32_t sW = sA + 2u * (uint32_t)p.a_bytes;
   const uint32_t stage_bytes = (uint32_t)(p.sps * p.step_bytes);
-  uint64_t* bars = (uint64_t*)(smem + p.a_bytes + p.nst * stage_bytes);
-  uint32_t* tslot = (uint32_t*)(bars + 2 + 2 * p.nst);
-  volatile uint32_t* abort_flag = tslot + 1;
-  uint32_t* s_table = tslot + 2;
+  const uint32_t w_bytes = p.resident ? (uint32_t)(p.n_steps * p.step_bytes) : (uint32_t)p.nst * stage_bytes;
+  const int planes = p.G * p.in_P;
+  uint64_t* bars = (uint64_t*)(smem + 2 * p.a_bytes + ((w_bytes + 127u) & ~127u));
+  // barrier slots: a_full[2], a_empty[2], acc_full[2], acc_empty[2], drain, w_full[nst], w_empty[nst]
+  uint64_t* s_adesc = bars + 9 + 2 * p.nst;                 // [n_steps] A descriptor (stage 0, sub-tile 0)
+  uint64_t* s_bdesc = s_adesc + p.n_steps;                  // [n_steps] B descriptor (stage 0)
+  int64_t* s_poff = reinterpret_cast<int64_t*>(s_bdesc + p.n_steps);  // [planes] byte offset of each plane
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(s_poff + planes);
+  uint32_t* tslot = (uint32_t*)(abort_flag + 1);
+  float* s_bias = reinterpret_cast<float*>(tslot + 2);     // [npad] bias, then [npad] FP8 scales
+  float* s_scale = s_bias + p.npad;
+  int* s_plen = reinterpret_cast<int*>(s_scale + p.npad);  // [planes] valid rows of each plane
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+  const int a_full = 0, a_empty = 2, acc_full = 4, acc_empty = 6, drain = 8, w_full = 9, w_empty = 9 + p.nst;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t barA = smem_u32(&bars[0]);
-  const uint32_t barD = smem_u32(&bars[1 + 2 * p.nst]);
-  const int m0 = blockIdx.x * 128 * p.MT;
-  const int b = blockIdx.y;
-
   if (tid == 0) {
-    mbar_init(barA, 1);
-    for (int i = 0; i < p.nst; ++i) {
-      mbar_init(smem_u32(&bars[1 + i]), 1);
-      mbar_init(smem_u32(&bars[1 + p.nst + i]), 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(a_full + i), 1);
+      mbar_init(bar(a_empty + i), 1);
+      mbar_init(bar(acc_full + i), 1);
+      mbar_init(bar(acc_empty + i), 4);  // one arrival per epilogue warp
     }
-    mbar_init(barD, 1);
-    *abort_flag = 0;
+    mbar_init(bar(drain), 1);
+    for (int i = 0; i < p.nst; ++i) {
+      mbar_init(bar(w_full + i), 1);
+      mbar_init(bar(w_empty + i), 1);
+    }
+    *abort_flag = 0u;
     fence_barrier_init();
   }
-  for (int i = tid; i < 2 * p.n_steps; i += kThreads) s_table[i] = p.table[i];
-  if (warp == 0) tmem_alloc(smem_u32(tslot), (uint32_t)p.ncols);
-
-  // Rows of the input tile outside the layer's input are its zero padding.
-  const int planes = p.G * p.in_P;
-  for (int plane = 0; plane < planes; ++plane) {
-    const int phi = plane % p.in_P;
-    const int Lp = (p.in_L - phi + p.in_P - 1) / p.in_P;
-    const int r0 = max(0, -m0 - p.dmin);
-    const int r1 = max(r0, min(p.rows, Lp - m0 - p.dmin));
-    for (int r = tid; r < p.rows; r += kThreads)
-      if (r < r0 || r >= r1) st_shared_zero16(sA + (uint32_t)(plane * p.rows + r) * 16u);
+  // per-CTA tables: MMA descriptors of every K-step (so the issue loop only
+  // adds stage offsets), plane offsets and lengths, bias and scales
+  const uint32_t stage_b = p.resident ? 0u : (uint32_t)p.sps;
+  for (int i = tid; i < p.n_steps; i += kThreads) {
+    const uint32_t w0 = p.table[2 * i];
+    const uint32_t o0 = slice_off(w0 & 0xFFFFu, p.in_P, p.rows), o1 = slice_off(w0 >> 16, p.in_P, p.rows);
+    s_adesc[i] = make_desc(sA + o0, o1 - o0, 128u);
+    const uint32_t pos = p.resident ? (uint32_t)i : (uint32_t)i % stage_b;
+    s_bdesc[i] = make_desc(sW + pos * (uint32_t)p.step_bytes, (uint32_t)p.npad * 16u, 128u);
   }
-  fence_proxy_async();
+  for (int i = tid; i < planes; i += kThreads) {
+    const int g = i / p.in_P, phi = i % p.in_P;
+    s_poff[i] = (int64_t)g * p.in_g + (int64_t)phi * p.in_p;
+    s_plen[i] = (p.in_L - phi + p.in_P - 1) / p.in_P;
+  }
+  for (int i = tid; i < p.npad; i += kThreads) {
+    s_bias[i] = i < p.cout ? p.bias[i] : 0.f;
+    s_scale[i] = (p.wscale && i < p.cout) ? p.wscale[i] : 1.f;
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tslot), (uint32_t)p.ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const int n_chunks = p.resident ? 1 : (p.n_steps + p.sps - 1) / p.sps;
 
-  if (tid == 0) {
-    // input tile: one bulk copy per (channel group, phase) plane
-    uint32_t total = 0;
-    for (int plane = 0; plane < planes; ++plane) {
-      const int phi = plane % p.in_P;
-      const int Lp = (p.in_L - phi + p.in_P - 1) / p.in_P;
-      const int r0 = max(0, -m0 - p.dmin);
-      const int r1 = max(r0, min(p.rows, Lp - m0 - p.dmin));
-      total += (uint32_t)(r1 - r0) * 16u;
+  if (warp == 0) {
+    // ---------------- producer: input tiles (and weights) by bulk TMA ----------------
+    if (p.resident && lane == 0) {
+      mbar_expect_tx(bar(w_full), (uint32_t)(p.n_steps * p.step_bytes));
+      bulk_g2s(sW, p.wimg, (uint32_t)(p.n_steps * p.step_bytes), bar(w_full));
     }
-    if (total) {
-      mbar_expect_tx(barA, total);
-      for (int plane = 0; plane < planes; ++plane) {
-        const int g = plane / p.in_P, phi = plane % p.in_P;
-        const int Lp = (p.in_L - phi + p.in_P - 1) / p.in_P;
-        const int r0 = max(0, -m0 - p.dmin);
-        const int r1 = max(r0, min(p.rows, Lp - m0 - p.dmin));
-        if (r1 <= r0) continue;
-        const char* src = p.in + p.in_off0 + (int64_t)b * p.in_b + (int64_t)g * p.in_g + (int64_t)phi * p.in_p +
-                          ((int64_t)(m0 + p.dmin + r0) + (int64_t)b * p.in_boff) * 16;
-        bulk_g2s(sA + (uint32_t)(plane * p.rows + r0) * 16u, src, (uint32_t)(r1 - r0) * 16u, barA);
-      }
-    } else {
-      mbar_arrive(barA);
-    }
-  }
-
-  const int n_chunks = (p.n_steps + p.sps - 1) / p.sps;
-  if (tid == 32) {
-    // weight producer: chunks of sps K-steps through nst stages
-    for (int c = 0; c < n_chunks; ++c) {
-      const int st = c % p.nst;
-      if (c >= p.nst &&
-          !mbar_wait(smem_u32(&bars[1 + p.nst + st]), (uint32_t)((c / p.nst) - 1) & 1u, p.err, kErrWaitEmpty))
-        break;
-      const int s0 = c * p.sps, s1 = min(p.n_steps, s0 + p.sps);
-      const uint32_t bytes = (uint32_t)((s1 - s0) * p.step_bytes);
-      const uint32_t full = smem_u32(&bars[1 + st]);
-      mbar_expect_tx(full, bytes);
-      bulk_g2s(sB + (uint32_t)st * stage_bytes, p.wimg + (int64_t)s0 * p.step_bytes, bytes, full);
-    }
-  }
-
-  if (tid == 0) {
-    // single-thread MMA issue
-    bool ok = mbar_wait(barA, 0, p.err, kErrWaitA);
-    tc_fence_after();
-    const uint32_t sbo = 128u, b_lbo = (uint32_t)p.npad * 16u;
-    for (int c = 0; ok && c < n_chunks; ++c) {
-      const int st = c % p.nst;
-      if (!mbar_wait(smem_u32(&bars[1 + st]), (uint32_t)(c / p.nst) & 1u, p.err, kErrWaitB)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const int s0 = c * p.sps, s1 = min(p.n_steps, s0 + p.sps);
-      for (int s = s0; s < s1; ++s) {
-        const uint32_t w0 = s_table[2 * s], w1 = s_table[2 * s + 1];
-        const uint32_t chain = w1 & 15u, acc = ((w1 >> 4) & 1u) ? 0u : 1u;
-        const uint32_t o0 = slice_off(w0 & 0xFFFFu, p.in_P, p.rows);
-        const uint32_t o1 = slice_off(w0 >> 16, p.in_P, p.rows);
-        const uint64_t bdesc = make_desc(sB + (uint32_t)st * stage_bytes + (uint32_t)(s - s0) * p.step_bytes, b_lbo, sbo);
-        for (int mt = 0; mt < p.MT; ++mt) {
-          const uint64_t adesc = make_desc(sA + o0 + (uint32_t)mt * 2048u, o1 - o0, sbo);
-          const uint32_t d = tmem + (chain * (uint32_t)p.MT + (uint32_t)mt) * (uint32_t)p.npad;
-          if (p.fp8)
-            mma_f8(d, adesc, bdesc, p.idesc, acc);
+    int i = 0;
+    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
+      const int s = i & 1, k = i >> 1;
+      if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
+      const int b = t / p.tiles_per_item;
+      const int m0 = (t - b * p.tiles_per_item) * 128 * p.MT;
+      const int base = m0 + p.dmin;
+      const uint32_t sAs = sA + (uint32_t)s * (uint32_t)p.a_bytes;
+      const char* src0 = p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)base + (int64_t)b * p.in_boff) * 16;
+      if (base >= 0 && base + p.rows <= p.min_plen) {
+        // interior tile: every plane is one full run of rows
+        if (lane == 0) mbar_expect_tx(bar(a_full + s), (uint32_t)(planes * p.rows) * 16u);
+        __syncwarp();
+        for (int plane = lane; plane < planes; plane += 32)
+          bulk_g2s(sAs + (uint32_t)(plane * p.rows) * 16u, src0 + s_poff[plane], (uint32_t)p.rows * 16u,
+                   bar(a_full + s));
+      } else {
+        // edge tile: rows outside a plane are the layer's zero padding, written
+        // here and made visible to the tensor core before the barrier fires
+        uint32_t total = 0;
+        for (int plane = 0; plane < planes; ++plane) {
+          const int r0 = max(0, -base), r1 = max(r0, min(p.rows, s_plen[plane] - base));
+          for (int r = lane; r < r0; r += 32) st_shared_zero16(sAs + (uint32_t)(plane * p.rows + r) * 16u);
+          for (int r = r1 + lane; r < p.rows; r += 32) st_shared_zero16(sAs + (uint32_t)(plane * p.rows + r) * 16u);
+          total += (uint32_t)(r1 - r0) * 16u;
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          if (total)
+            mbar_expect_tx(bar(a_full + s), total);
           else
-            mma_f16(d, adesc, bdesc, p.idesc, acc);
+            mbar_arrive(bar(a_full + s));
+        }
+        __syncwarp();
+        for (int plane = lane; plane < planes; plane += 32) {
+          const int r0 = max(0, -base), r1 = max(r0, min(p.rows, s_plen[plane] - base));
+          if (r1 > r0)
+            bulk_g2s(sAs + (uint32_t)(plane * p.rows + r0) * 16u, src0 + s_poff[plane] + (int64_t)r0 * 16,
+                     (uint32_t)(r1 - r0) * 16u, bar(a_full + s));
         }
       }
-      mma_commit(smem_u32(&bars[1 + p.nst + st]));
+      if (lane == 0) {
+        if (!p.resident) {
+          for (int c = 0; c < n_chunks; ++c) {
+            const int gc = i * n_chunks + c, st = gc % p.nst, use = gc / p.nst;
+            if (use >= 1 && !mbar_wait(bar(w_empty + st), (uint32_t)(use - 1) & 1u, abort_flag, p.err, kErrWaitEmpty))
+              break;
+            const int s0 = c * p.sps, s1 = min(p.n_steps, s0 + p.sps);
+            const uint32_t bytes = (uint32_t)((s1 - s0) * p.step_bytes);
+            mbar_expect_tx(bar(w_full + st), bytes);
+            bulk_g2s(sW + (uint32_t)st * stage_bytes, p.wimg + (int64_t)s0 * p.step_bytes, bytes, bar(w_full + st));
+          }
+        }
+      }
+      __syncwarp();
+      if (*abort_flag) break;
     }
-    if (!ok) *abort_flag = 1u;
-    mma_commit(barD);
-  }
-  __syncthreads();
-
-  // epilogue: TMEM -> registers -> bias / residual / activation -> global
-  const bool done = mbar_wait(barD, 0, p.err, kErrWaitDone);
-  __syncwarp();
-  tc_fence_after();
-  if (done && *abort_flag == 0u) {
-    const int row = warp * 32 + lane;
-    for (int c = 0; c < p.n_chains; ++c) {
-      const int mout = c ? p.mout1 : p.mout0;
+  } else if (warp == 1) {
+    // ---------------- MMA issue: one thread ----------------
+    if (lane == 0) {
+      bool ok = !p.resident || mbar_wait(bar(w_full), 0u, abort_flag, p.err, kErrWaitW);
+      int i = 0;
+      for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x, ++i) {
+        const int s = i & 1, k = i >> 1;
+        if (!mbar_wait(bar(a_full + s), (uint32_t)k & 1u, abort_flag, p.err, kErrWaitA)) break;
+        if (k >= 1 && !mbar_wait(bar(acc_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitAcc)) break;
+        tc_fence_after();
+        // descriptor start addresses count 16-byte units in their low bits
+        const uint64_t a_stage = (uint64_t)(((uint32_t)s * (uint32_t)p.a_bytes) >> 4);
+        const uint32_t d0 = tmem + (uint32_t)(s * p.MT * p.npad);
+        for (int c = 0; c < n_chunks; ++c) {
+          uint64_t b_stage = 0;
+          int st = 0;
+          if (!p.resident) {
+            const int gc = i * n_chunks + c, use = gc / p.nst;
+            st = gc - use * p.nst;
+            if (!mbar_wait(bar(w_full + st), (uint32_t)use & 1u, abort_flag, p.err, kErrWaitW)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            b_stage = (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
+          }
+          const int s0 = p.resident ? 0 : c * p.sps, s1 = p.resident ? p.n_steps : min(p.n_steps, s0 + p.sps);
+#pragma unroll 4
+          for (int sidx = s0; sidx < s1; ++sidx) {
+            const uint64_t bdesc = s_bdesc[sidx] + b_stage;
+            const uint64_t adesc = s_adesc[sidx] + a_stage;
+            const uint32_t acc = sidx == 0 ? 0u : 1u;
+            for (int mt = 0; mt < p.MT; ++mt) {
+              // M sub-tile mt starts 128 rows (2048 bytes) further
+              if (p.fp8)
+                mma_f8(d0 + (uint32_t)(mt * p.npad), adesc + (uint64_t)(mt * 128), bdesc, p.idesc, acc);
+              else
+                mma_f16(d0 + (uint32_t)(mt * p.npad), adesc + (uint64_t)(mt * 128), bdesc, p.idesc, acc);
+            }
+          }
+          if (!p.resident) mma_commit(bar(w_empty + st));
+        }
+        if (!ok) break;
+        mma_commit(bar(a_empty + s));
+        mma_commit(bar(acc_full + s));
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(bar(drain));
+      mbar_wait(bar(drain), 0u, abort_flag, p.err, kErrDrain);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: TMEM -> bias/residual/activation -> global ----------------
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int i = 0;
+    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
+      const int s = i & 1, k = i >> 1;
+      if (!mbar_wait(bar(acc_full + s), (uint32_t)k & 1u, abort_flag, p.err, kErrWaitAcc)) break;
+      __syncwarp();
+      tc_fence_after();
+      const int b = t / p.tiles_per_item;
+      const int m0 = (t - b * p.tiles_per_item) * 128 * p.MT;
+      char* const outb = p.out + (int64_t)b * p.out_b;
+      const char* const resb = p.res ? p.res + (int64_t)b * p.res_b : nullptr;
+      const int out_mask = p.out_P - 1, res_mask = p.res_P - 1;
       for (int mt = 0; mt < p.MT; ++mt) {
         const int m = m0 + mt * 128 + row;
-        const bool valid = m < mout;
-        const int u = p.chainP * m + c;
-        for (int j = 0; j < p.npad / 16; ++j) {
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((c * p.MT + mt) * p.npad + j * 16), v);
+        const bool valid = m < p.mout;
+        for (int j = 0; j < p.npad / 32; ++j) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((s * p.MT + mt) * p.npad + j * 32), v);
           if (!valid) continue;
+          if (p.fp32_single) {
+            // column n = sigma: output position Q m + sigma, channel 0
+            float* y = reinterpret_cast<float*>(outb);
+            const float bias = s_bias[0];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int n0 = j * 16 + h * 8;
-            if (n0 >= p.cout) continue;
+            for (int e = 0; e < 32; ++e) {
+              const int sg = j * 32 + e;
+              const int u = p.Q * m + sg;
+              if (sg < p.Q && u < p.lout) y[u] = act_fn(v[e] + bias, p.act);
+            }
+            continue;
+          }
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int n0 = j * 32 + h * 8;
+            const int sg = n0 >> p.coutp_log, o0 = n0 & (p.coutp - 1);
+            const int u = p.Q * m + sg;
+            if (sg >= p.Q || o0 >= p.cout || u >= p.lout) continue;
             float x[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int n = n0 + i;
-              float a = v[h * 8 + i];
-              if (n < p.cout) {
-                if (p.wscale) a *= p.wscale[n];
-                a += p.bias[n];
-              } else {
-                a = 0.f;
-              }
-              x[i] = a;
+            for (int e = 0; e < 8; ++e) {
+              const int o = o0 + e;
+              x[e] = o < p.cout ? fmaf(v[h * 8 + e], s_scale[o], s_bias[o]) : 0.f;
             }
-            if (p.res) {
+            if (resb) {
               if (p.res_fp8) {
-                const int go = n0 / 16;
-                const char* rp = p.res + (int64_t)b * p.res_b + (int64_t)go * p.res_g + (int64_t)(u % p.res_P) * p.res_p +
-                                 (int64_t)(u / p.res_P) * 16 + (n0 % 16);
+                const char* rp = resb + (int64_t)(o0 >> 4) * p.res_g + (int64_t)(u & res_mask) * p.res_p +
+                                 (int64_t)(u >> p.res_P_log) * 16 + (o0 & 15);
                 const uint2 rv = *reinterpret_cast<const uint2*>(rp);
                 const __nv_fp8_e4m3* r8 = reinterpret_cast<const __nv_fp8_e4m3*>(&rv);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) x[i] += float(r8[i]) * p.res_scale;
+                for (int e = 0; e < 8; ++e) x[e] += float(r8[e]) * p.res_scale;
               } else {
-                const int go = n0 / 8;
-                const char* rp = p.res + (int64_t)b * p.res_b + (int64_t)go * p.res_g + (int64_t)(u % p.res_P) * p.res_p +
-                                 (int64_t)(u / p.res_P) * 16;
+                const char* rp = resb + (int64_t)(o0 >> 3) * p.res_g + (int64_t)(u & res_mask) * p.res_p +
+                                 (int64_t)(u >> p.res_P_log) * 16;
                 const uint4 rv = *reinterpret_cast<const uint4*>(rp);
                 const __nv_bfloat16* r16 = reinterpret_cast<const __nv_bfloat16*>(&rv);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) x[i] += __bfloat162float(r16[i]);
+                for (int e = 0; e < 8; ++e) x[e] += __bfloat162float(r16[e]);
               }
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = act_fn(x[i], p.act);
-            if (p.fp32_single) {
-              if (n0 == 0) reinterpret_cast<float*>(p.out + (int64_t)b * p.out_b)[u] = x[0];
-            } else if (p.fp8_out) {
-              const int go = n0 / 16;
+            for (int e = 0; e < 8; ++e) x[e] = act_fn(x[e], p.act);
+            if (p.fp8_out) {
               __align__(8) __nv_fp8_e4m3 o8[8];
 #pragma unroll
-              for (int i = 0; i < 8; ++i) o8[i] = __nv_fp8_e4m3(x[i] * p.out_scale);
-              char* op = p.out + (int64_t)b * p.out_b + (int64_t)go * p.out_g + (int64_t)(u % p.out_P) * p.out_p +
-                         (int64_t)(u / p.out_P) * 16 + (n0 % 16);
+              for (int e = 0; e < 8; ++e) o8[e] = __nv_fp8_e4m3(x[e] * p.out_scale);
+              char* op = outb + (int64_t)(o0 >> 4) * p.out_g + (int64_t)(u & out_mask) * p.out_p +
+                         (int64_t)(u >> p.out_P_log) * 16 + (o0 & 15);
               *reinterpret_cast<uint2*>(op) = *reinterpret_cast<const uint2*>(o8);
             } else {
-              const int go = n0 / 8;
               __align__(16) __nv_bfloat16 o16[8];
 #pragma unroll
-              for (int i = 0; i < 8; ++i) o16[i] = __float2bfloat16_rn(x[i]);
-              char* op = p.out + (int64_t)b * p.out_b + (int64_t)go * p.out_g + (int64_t)(u % p.out_P) * p.out_p +
-                         (int64_t)(u / p.out_P) * 16;
+              for (int e = 0; e < 8; ++e) o16[e] = __float2bfloat16_rn(x[e]);
+              char* op = outb + (int64_t)(o0 >> 3) * p.out_g + (int64_t)(u & out_mask) * p.out_p +
+                         (int64_t)(u >> p.out_P_log) * 16;
               *reinterpret_cast<uint4*>(op) = *reinterpret_cast<const uint4*>(o16);
             }
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(acc_empty + s));
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, (uint32_t)p.ncols);
+  if (warp == 1) tmem_dealloc(tmem, (uint32_t)p.ncols);
 }
 
 // FP32 [B][C][*] -> blocked layout (bf16 rows of 8 channels, or e4m3 rows of 16).
@@ -442,6 +534,14 @@ __global__ void gap_linear_blocked_kernel(const char* __restrict__ in, int64_t i
 }
 
 inline int pmod_i(int a, int m) { return ((a % m) + m) % m; }
+inline int floordiv_i(int a, int b) { return (a - pmod_i(a, b)) / b; }
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 152;
+  return n > 0 ? n : 152;
+}
 
 }  // namespace
 
@@ -453,74 +553,79 @@ int tc_supported() {
   return major == 10 && minor == 3;
 }
 
-// Lowers one folded layer to K-steps of two 16-byte slices and packs the B
-// operand image: per step [2 K-halves][npad rows][16 bytes], K-major core
-// matrices with LBO = npad * 16 bytes and SBO = 128 bytes.
-// Host only; fills L's lowering fields and returns the image, table and (FP8)
-// per-channel weight scales.
+// Output positions folded into one M row (J): enough to make N reach 64
+// columns for small channel counts, bounded so the tap halo stays small.
+static int choose_j(const LayerSpec& s) {
+  if (s.cout == 1) return 16;
+  const int coutp = (s.cout + 7) / 8 * 8;
+  const int per_j = s.transposed ? 2 * coutp : coutp;
+  int J = std::max(1, 64 / per_j);
+  J = std::min(J, s.transposed ? 4 : (s.stride == 1 ? 8 : 4));
+  return J;
+}
+
+// Lowers one folded layer: K slices, K-steps and the packed B image (per step
+// [2 K-halves][npad rows][16 bytes]: LBO = npad * 16 bytes, SBO = 128 bytes).
 static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, std::vector<uint8_t>& img,
                         std::vector<uint32_t>& table, std::vector<float>& wscale) {
   const LayerSpec& s = L.s;
   const int cg = fp8 ? 16 : 8;
   const int G = (s.cin + cg - 1) / cg;
-  const int pin = s.transposed ? 1 : s.stride;
-  int npad = std::max(16, (s.cout + 15) / 16 * 16);
-  GW_CHECK_ARG(npad <= 256, "C_out above 256 is not supported by the tensor-core path");
-  GW_CHECK_ARG(G <= 255, "too many input channels");
-  struct Tap { int k, phi, d; };
-  std::vector<std::vector<Tap>> chains;
-  if (!s.transposed) {
-    std::vector<Tap> ch;
-    for (int k = 0; k < s.k; ++k) {
-      const int phi = pmod_i(k - s.pad_l, pin);
-      ch.push_back({k, phi, (k - s.pad_l - phi) / pin});
-    }
-    chains.push_back(ch);
-  } else {
+  const int J = choose_j(s);
+  const int Q = s.transposed ? 2 * J : J;
+  const int P = s.transposed ? J : s.stride * J;
+  const int coutp = s.cout == 1 ? 1 : (s.cout + 7) / 8 * 8;
+  // N padded to a multiple of 32 (the epilogue drains 32 columns per load)
+  const int npad = std::max(32, (Q * coutp + 31) / 32 * 32);
+  GW_CHECK_ARG(npad <= 256, "output columns above 256 are not supported by the tensor-core path");
+  GW_CHECK_ARG(G <= 63 && P <= 31, "layer too wide for the tensor-core path");
+  if (s.transposed)
     GW_CHECK_ARG(s.stride == 2 && s.pad_l == s.pad_r, "transposed conv must have stride 2 and symmetric padding");
-    for (int psi = 0; psi < 2; ++psi) {
-      std::vector<Tap> ch;
-      for (int k = 0; k < s.k; ++k)
-        if (pmod_i(psi + s.pad_l - k, 2) == 0) ch.push_back({k, 0, (psi + s.pad_l - k) / 2});
-      chains.push_back(ch);
-    }
-  }
-  int dmin = 1 << 30, dmax = -(1 << 30);
-  for (auto& ch : chains)
-    for (auto& t : ch) {
-      dmin = std::min(dmin, t.d);
-      dmax = std::max(dmax, t.d);
-    }
-  GW_CHECK_ARG(dmax - dmin < 64, "tap span too large");
-  struct Slice { int g, phi, dd, k; bool dummy; };
-  auto key = [](const Slice& a) { return (a.g * 4 + a.phi) * 64 + a.dd; };
-  struct Step { Slice a, b; int chain; bool first; };
-  std::vector<Step> steps;
-  for (size_t ci = 0; ci < chains.size(); ++ci) {
-    std::vector<std::pair<Slice, Slice>> st;
-    std::vector<Slice> left;
-    for (auto& t : chains[ci]) {
-      int g = 0;
-      for (; g + 1 < G; g += 2)
-        st.push_back({{g, t.phi, t.d - dmin, t.k, false}, {g + 1, t.phi, t.d - dmin, t.k, false}});
-      if (g < G) left.push_back({g, t.phi, t.d - dmin, t.k, false});
-    }
-    std::sort(left.begin(), left.end(), [&](const Slice& a, const Slice& b) { return key(a) < key(b); });
-    for (size_t i = 0; i < left.size(); i += 2) {
-      if (i + 1 < left.size()) {
-        st.push_back({left[i], left[i + 1]});
+  // contributions (sigma, tap) -> input (phi, d)
+  struct Contrib { int sigma, k, phi, d; };
+  std::vector<Contrib> cons;
+  for (int sg = 0; sg < Q; ++sg)
+    for (int k = 0; k < s.k; ++k) {
+      int q;
+      if (!s.transposed) {
+        q = s.stride * sg + k - s.pad_l;
       } else {
-        Slice d = left[i];
-        d.dummy = true;
-        st.push_back({left[i], d});
+        const int j = sg / 2, psi = sg % 2;
+        if (pmod_i(psi + s.pad_l - k, 2) != 0) continue;
+        q = j + (psi + s.pad_l - k) / 2;
       }
+      cons.push_back({sg, k, pmod_i(q, P), floordiv_i(q, P)});
     }
-    for (size_t i = 0; i < st.size(); ++i) {
-      Slice a = st[i].first, b = st[i].second;
-      if (key(b) < key(a)) std::swap(a, b);
-      steps.push_back({a, b, (int)ci, i == 0});
+  int dmin = 1 << 30, dmax = -(1 << 30);
+  std::set<std::pair<int, int>> pos;
+  for (auto& c : cons) {
+    dmin = std::min(dmin, c.d);
+    dmax = std::max(dmax, c.d);
+    pos.insert({c.phi, c.d});
+  }
+  GW_CHECK_ARG(dmax - dmin < 32, "tap span too large");
+  struct Slice { int g, phi, dd; bool dummy; };
+  auto key = [](const Slice& a) { return (a.g * 32 + a.phi) * 32 + a.dd; };
+  std::vector<std::pair<Slice, Slice>> steps;
+  std::vector<Slice> left;
+  for (auto& ps : pos) {
+    int g = 0;
+    for (; g + 1 < G; g += 2)
+      steps.push_back({{g, ps.first, ps.second - dmin, false}, {g + 1, ps.first, ps.second - dmin, false}});
+    if (g < G) left.push_back({g, ps.first, ps.second - dmin, false});
+  }
+  std::sort(left.begin(), left.end(), [&](const Slice& a, const Slice& b) { return key(a) < key(b); });
+  for (size_t i = 0; i < left.size(); i += 2) {
+    if (i + 1 < left.size()) {
+      steps.push_back({left[i], left[i + 1]});
+    } else {
+      Slice d = left[i];
+      d.dummy = true;
+      steps.push_back({left[i], d});
     }
   }
+  for (auto& st : steps)
+    if (key(st.second) < key(st.first)) std::swap(st.first, st.second);
   GW_CHECK_ARG(steps.size() <= 4096, "too many K-steps");
   const int n_steps = (int)steps.size();
   const size_t step_bytes = 32 * (size_t)npad;
@@ -535,36 +640,45 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
       wscale[o] = mx > 0 ? (float)(mx / 448.0) : 1.f;
     }
   }
+  // weight of column (sigma, o), slice (g, phi, d), channel c: the tap k
+  // that maps (sigma, k) to (phi, d), if any
+  std::vector<int> tap_of((size_t)Q * P * 32, -1);
+  for (auto& c : cons) tap_of[((size_t)c.sigma * P + c.phi) * 32 + (c.d - dmin)] = c.k;
   for (int si = 0; si < n_steps; ++si) {
-    const Step& st = steps[si];
     for (int half = 0; half < 2; ++half) {
-      const Slice& sl = half ? st.b : st.a;
-      for (int n = 0; n < npad; ++n)
+      const Slice& sl = half ? steps[si].second : steps[si].first;
+      for (int n = 0; n < npad; ++n) {
+        const int sg = n / coutp, o = n % coutp;
+        if (sl.dummy || sg >= Q || o >= s.cout) continue;
+        const int k = tap_of[((size_t)sg * P + sl.phi) * 32 + sl.dd];
+        if (k < 0) continue;
+        uint8_t* dst = img.data() + si * step_bytes + ((size_t)half * npad + n) * 16;
         for (int kk = 0; kk < cg; ++kk) {
           const int c = sl.g * cg + kk;
-          double v = 0.0;
-          if (!sl.dummy && n < s.cout && c < s.cin) v = wf[((size_t)n * s.cin + c) * s.k + sl.k];
-          uint8_t* dst = img.data() + si * step_bytes + ((size_t)half * npad + n) * 16;
+          if (c >= s.cin) continue;
+          const double v = wf[((size_t)o * s.cin + c) * s.k + k];
           if (fp8) {
-            __nv_fp8_e4m3 q((float)(v / wscale[n < s.cout ? n : 0]));
+            __nv_fp8_e4m3 q((float)(v / wscale[o]));
             memcpy(dst + kk, &q, 1);
           } else {
             __nv_bfloat16 q = __float2bfloat16_rn((float)v);
             memcpy(dst + kk * 2, &q, 2);
           }
         }
+      }
     }
-    auto code = [](const Slice& a) { return (uint32_t)a.g | ((uint32_t)a.phi << 8) | ((uint32_t)a.dd << 10); };
-    table[2 * si] = code(st.a) | (code(st.b) << 16);
-    table[2 * si + 1] = (uint32_t)st.chain | ((st.first ? 1u : 0u) << 4);
+    auto code = [](const Slice& a) { return (uint32_t)a.g | ((uint32_t)a.phi << 6) | ((uint32_t)a.dd << 11); };
+    table[2 * si] = code(steps[si].first) | (code(steps[si].second) << 16);
+    table[2 * si + 1] = si == 0 ? 16u : 0u;
   }
   L.n_steps = n_steps;
   L.npad = npad;
   L.gin = G;
-  L.pin = pin;
-  L.n_chains = (int)chains.size();
+  L.pin = P;
+  L.n_chains = Q;      // output positions per M row
   L.dspan = dmax - dmin;
   L.dmin = dmin;
+  L.coutp = coutp;
 }
 
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wf, int precision, gw_ctx* ctx, size_t* counter,
@@ -594,12 +708,14 @@ void tc_pack_layer(LayerDev& L, const std::vector<double>& wf, int precision, gw
   L.table = d_tab;
 }
 
-// Host-side launch plan (tile size, staging, TMEM columns, descriptors' idesc).
+// Host-side launch plan: tile size, weight residency or staging, TMEM columns,
+// persistent grid, instruction descriptor.
 static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& in, int lout, const TcOut& out,
-                         int* err, size_t* smem_out, dim3* grid_out, int B) {
+                         int* err, size_t* smem_out, dim3* grid_out, int B, int sms) {
   const LayerSpec& s = L.s;
   const int esz = fp8 ? 1 : 2;
   GW_CHECK_ARG(in.P == L.pin, "input phase count does not match the layer");
+  GW_CHECK_ARG(out.fp32_single == (s.cout == 1 ? 1 : 0), "single-channel layers write FP32 predictions");
   q = TcParams{};
   q.in = (const char*)in.p;
   q.in_off0 = in.off0 * esz;
@@ -610,41 +726,56 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.in_P = in.P;
   q.in_L = in.L;
   q.G = L.gin;
-  q.n_chains = L.n_chains;
-  q.chainP = s.transposed ? 2 : 1;
-  q.mout0 = (lout + q.chainP - 1) / q.chainP;
-  q.mout1 = s.transposed ? lout / 2 : 0;
+  q.Q = L.n_chains;
+  q.coutp = L.coutp;
   q.lout = lout;
+  q.mout = (lout + q.Q - 1) / q.Q;
   q.dmin = L.dmin;
-  const int cols_per_mt = L.n_chains * L.npad;
-  int MT = std::max(1, std::min(8, 128 / cols_per_mt));
-  const int tiles_needed = (q.mout0 + 127) / 128;
-  MT = std::min(MT, std::max(1, tiles_needed));
-  auto a_bytes_for = [&](int mt) { return (size_t)L.gin * L.pin * (128 * mt + L.dspan) * 16; };
-  while (MT > 1 && a_bytes_for(MT) > 96 * 1024) --MT;
-  q.MT = MT;
-  q.rows = 128 * MT + L.dspan;
-  q.a_bytes = (int)((a_bytes_for(MT) + 127) / 128 * 128);
   q.step_bytes = 32 * L.npad;
-  const size_t wbytes = (size_t)L.n_steps * q.step_bytes;
-  const size_t budget = 200 * 1024;
-  if (q.a_bytes + wbytes <= budget - 4096) {
-    q.sps = L.n_steps;
-    q.nst = 1;
-  } else {
-    q.sps = std::max(1, 32768 / q.step_bytes);
-    const int n_chunks = (L.n_steps + q.sps - 1) / q.sps;
-    q.nst = std::min(4, n_chunks);
-    while (q.nst > 1 && q.a_bytes + (size_t)q.nst * q.sps * q.step_bytes > budget - 4096) --q.nst;
-  }
-  q.wimg = (const char*)L.wq;
-  q.table = L.table;
   q.n_steps = L.n_steps;
   q.npad = L.npad;
+  const size_t wbytes = (size_t)L.n_steps * q.step_bytes;
+  auto a_bytes_for = [&](int mt) { return ((size_t)L.gin * L.pin * (128 * mt + L.dspan) * 16 + 127) / 128 * 128; };
+  const size_t budget = 220 * 1024;
+  const size_t planes = (size_t)L.gin * L.pin;
+  const size_t fixed = 128 + 8 * 32 + 16 + 16 * (size_t)L.n_steps + 12 * planes + 8 * (size_t)L.npad + 16;
+  int MT = 4;
+  const int tiles_needed = (q.mout + 127) / 128;
+  // prefer small tiles while there are fewer than 8 tiles per SM: the
+  // persistent pipeline overlaps tiles, and more tiles balance the SMs
+  while (MT > 1 && (2 * MT * L.npad > 512 || MT > tiles_needed ||
+                    (int64_t)((q.mout + 128 * MT - 1) / (128 * MT)) * B < 8LL * sms))
+    MT /= 2;
+  q.resident = 0;
+  q.sps = 1;
+  q.nst = 1;
+  for (;; MT /= 2) {
+    const size_t a2 = 2 * a_bytes_for(MT);
+    if (a2 + wbytes + fixed <= budget) {
+      q.resident = 1;
+      q.sps = L.n_steps;
+      q.nst = 1;
+      break;
+    }
+    const int sps = std::max(1, (int)(16384 / q.step_bytes));
+    int nst = std::min(3, (L.n_steps + sps - 1) / sps);
+    while (nst > 1 && a2 + (size_t)nst * sps * q.step_bytes + fixed > budget) --nst;
+    if (a2 + (size_t)nst * sps * q.step_bytes + fixed <= budget) {
+      q.sps = sps;
+      q.nst = std::max(1, nst);
+      break;
+    }
+    GW_CHECK_ARG(MT > 1, "shared memory plan too large");
+  }
+  q.MT = MT;
+  q.rows = 128 * MT + L.dspan;
+  q.a_bytes = (int)a_bytes_for(MT);
   int ncols = 32;
-  while (ncols < cols_per_mt * MT) ncols *= 2;
+  while (ncols < 2 * MT * L.npad) ncols *= 2;
   GW_CHECK_ARG(ncols <= 512, "accumulators exceed tensor memory");
   q.ncols = ncols;
+  q.tiles_per_item = (q.mout + 128 * MT - 1) / (128 * MT);
+  q.n_tiles = q.tiles_per_item * B;
   // instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3 (kind::f8f6f4),
   // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
   q.idesc = (1u << 4) | (fp8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(L.npad >> 3) << 17) |
@@ -672,20 +803,34 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.res_fp8 = fp8 ? 1 : 0;
   q.res_scale = fp8 ? 1.0f / L.out_scale : 1.0f;
   q.err = err;
-  const size_t smem = 128 + (size_t)q.a_bytes + (size_t)q.nst * q.sps * q.step_bytes + 8 * (2 + 2 * q.nst) + 8 +
-                      8 * (size_t)L.n_steps + 16;
+  auto log2_exact = [](int v, const char* what) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    GW_CHECK_ARG((1 << l) == v, std::string(what) + " must be a power of two");
+    return l;
+  };
+  q.coutp_log = log2_exact(q.coutp, "channels per output position");
+  q.out_P_log = log2_exact(std::max(1, out.P), "output phase count");
+  q.res_P_log = log2_exact(q.res_P, "residual phase count");
+  q.min_plen = in.L / in.P;
+  q.wimg = (const char*)L.wq;
+  q.table = L.table;
+  const size_t wsm = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
+  const size_t smem = 128 + 2 * (size_t)q.a_bytes + (wsm + 127) / 128 * 128 + 8 * (9 + 2 * q.nst) +
+                      16 * (size_t)L.n_steps + 12 * planes + 16 + 8 * (size_t)L.npad + 16;
   GW_CHECK_ARG(smem <= 227 * 1024, "shared memory plan too large");
   *smem_out = smem;
-  *grid_out = dim3((q.mout0 + 128 * MT - 1) / (128 * MT), B);
+  const int per_sm = (smem <= 113 * 1024 && ncols <= 256) ? 2 : 1;
+  *grid_out = dim3(std::min(q.n_tiles, sms * per_sm));
 }
 
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err, cudaStream_t st) {
   TcParams q;
   size_t smem = 0;
   dim3 grid;
-  plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B);
-  q.wimg = (const char*)L.wq;
-  q.table = L.table;
+  static int sms = 0;
+  if (!sms) sms = sm_count();
+  plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B, sms);
   static bool attr = false;
   if (!attr) {
     GW_CUDA(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -694,51 +839,6 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
   conv_tc_kernel<<<grid, kThreads, smem, st>>>(q);
   GW_LAUNCH_CHECK();
 }
-
-}  // namespace gw
-
-// Host-only inspection of the lowering and launch plan of one layer (no GPU).
-extern "C" int gw_tc_inspect(const int* spec, int precision, const double* wfold, int lin, int in_P, int out_P,
-                             void* img_out, size_t img_cap, uint32_t* table_out, int table_cap, int* meta_out) {
-  using namespace gw;
-  try {
-    GW_CHECK_ARG(spec && wfold && img_out && table_out && meta_out, "NULL argument");
-    GW_CHECK_ARG(precision == GW_BF16 || precision == GW_FP8, "precision must be BF16 or FP8");
-    LayerDev L;
-    L.s = LayerSpec{spec[0] != 0, spec[1], spec[2], spec[3], spec[4], spec[5], spec[6], spec[7], true, ACT_NONE};
-    const LayerSpec& s = L.s;
-    GW_CHECK_ARG(s.cin >= 1 && s.cout >= 1 && s.k >= 1 && s.stride >= 1 && lin >= 1, "bad layer spec");
-    std::vector<double> wf(wfold, wfold + (size_t)s.cout * s.cin * s.k);
-    std::vector<uint8_t> img;
-    std::vector<uint32_t> table;
-    std::vector<float> wscale;
-    const bool fp8 = precision == GW_FP8;
-    lower_layer(L, wf, fp8, img, table, wscale);
-    GW_CHECK_ARG(img.size() <= img_cap && (int)table.size() <= table_cap, "output buffers too small");
-    memcpy(img_out, img.data(), img.size());
-    memcpy(table_out, table.data(), table.size() * 4);
-    const int lout = s.lout(lin);
-    TcIn in{};
-    in.P = in_P;
-    in.L = lin;
-    TcOut out{};
-    out.P = out_P;
-    TcParams q;
-    size_t smem = 0;
-    dim3 grid;
-    plan_conv_tc(q, L, fp8, in, lout, out, nullptr, &smem, &grid, 1);
-    const int meta[20] = {L.n_steps, L.npad, L.gin, L.pin, L.n_chains, L.dspan, L.dmin, q.MT, q.rows, q.a_bytes,
-                          q.sps, q.nst, q.step_bytes, q.ncols, (int)grid.x, q.mout0, q.mout1, (int)q.idesc,
-                          (int)smem, lout};
-    memcpy(meta_out, meta, sizeof(meta));
-    return GW_OK;
-  } catch (const gw::Error& e) {
-    gw::set_last_error(e.what());
-    return e.code;
-  }
-}
-
-namespace gw {
 
 void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,
                        const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st) {
@@ -760,3 +860,45 @@ void launch_gap_linear_blocked(const TcIn& in, int C, int fp8, float in_scale, c
 }
 
 }  // namespace gw
+
+// Host-only inspection of the lowering and launch plan of one layer (no GPU).
+extern "C" int gw_tc_inspect(const int* spec, int precision, const double* wfold, int lin, int in_P, int out_P, int batch,
+                             void* img_out, size_t img_cap, uint32_t* table_out, int table_cap, int* meta_out) {
+  using namespace gw;
+  try {
+    GW_CHECK_ARG(spec && wfold && img_out && table_out && meta_out, "NULL argument");
+    GW_CHECK_ARG(precision == GW_BF16 || precision == GW_FP8, "precision must be BF16 or FP8");
+    LayerDev L;
+    L.s = LayerSpec{spec[0] != 0, spec[1], spec[2], spec[3], spec[4], spec[5], spec[6], spec[7], true, ACT_NONE};
+    const LayerSpec& s = L.s;
+    GW_CHECK_ARG(s.cin >= 1 && s.cout >= 1 && s.k >= 1 && s.stride >= 1 && lin >= 1, "bad layer spec");
+    std::vector<double> wf(wfold, wfold + (size_t)s.cout * s.cin * s.k);
+    std::vector<uint8_t> img;
+    std::vector<uint32_t> table;
+    std::vector<float> wscale;
+    const bool fp8 = precision == GW_FP8;
+    lower_layer(L, wf, fp8, img, table, wscale);
+    GW_CHECK_ARG(img.size() <= img_cap && (int)table.size() <= table_cap, "output buffers too small");
+    memcpy(img_out, img.data(), img.size());
+    memcpy(table_out, table.data(), table.size() * 4);
+    const int lout = s.lout(lin);
+    TcIn in{};
+    in.P = in_P > 0 ? in_P : L.pin;
+    in.L = lin;
+    TcOut out{};
+    out.P = out_P;
+    out.fp32_single = s.cout == 1 ? 1 : 0;
+    TcParams q;
+    size_t smem = 0;
+    dim3 grid;
+    plan_conv_tc(q, L, fp8, in, lout, out, nullptr, &smem, &grid, batch > 0 ? batch : 1, 152);
+    const int meta[20] = {L.n_steps, L.npad,   L.gin,   L.pin,        L.n_chains,   L.dspan, L.dmin,
+                          q.MT,      q.rows,   q.a_bytes, q.resident ? L.n_steps : q.sps, q.nst, q.step_bytes,
+                          q.ncols,   q.tiles_per_item, q.mout, L.coutp, (int)q.idesc, (int)smem, lout};
+    memcpy(meta_out, meta, sizeof(meta));
+    return GW_OK;
+  } catch (const gw::Error& e) {
+    gw::set_last_error(e.what());
+    return e.code;
+  }
+}

@@ -94,7 +94,7 @@ def _declare(lib):
         "gw_launch_count": (I64, []),
         "gw_deepclean_forward_noalloc": (I, [P, P, I64, I64, I, I, P, P]),
         "gw_model_status": (I, [P, P]),
-        "gw_tc_inspect": (I, [C.POINTER(C.c_int), I, C.POINTER(C.c_double), I, I, I, P, SZ,
+        "gw_tc_inspect": (I, [C.POINTER(C.c_int), I, C.POINTER(C.c_double), I, I, I, I, P, SZ,
                               C.POINTER(C.c_uint32), I, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -263,11 +263,11 @@ def gw_launch_count():
     return lib().gw_launch_count()
 
 
-TC_META = ("n_steps", "npad", "groups", "in_P", "chains", "dspan", "dmin", "MT", "rows", "a_bytes", "sps", "nst",
-           "step_bytes", "ncols", "grid_x", "mout0", "mout1", "idesc", "smem", "lout")
+TC_META = ("n_steps", "npad", "groups", "in_P", "Q", "dspan", "dmin", "MT", "rows", "a_bytes", "sps", "nst",
+           "step_bytes", "ncols", "tiles_per_item", "mout", "coutp", "idesc", "smem", "lout")
 
 
-def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P):
+def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P, batch=1):
     """Host-only lowering of one layer: (image bytes, table uint32, meta dict)."""
     spec_a = (C.c_int * 8)(*spec)
     wf = np.ascontiguousarray(wfold, np.float64)
@@ -275,7 +275,7 @@ def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P):
     img = np.zeros(cap, np.uint8)
     table = np.zeros(1 << 14, np.uint32)
     meta = (C.c_int * 20)()
-    _check(lib().gw_tc_inspect(spec_a, precision, wf.ctypes.data_as(C.POINTER(C.c_double)), lin, in_P, out_P,
+    _check(lib().gw_tc_inspect(spec_a, precision, wf.ctypes.data_as(C.POINTER(C.c_double)), lin, in_P, out_P, batch,
                                img.ctypes.data, cap, table.ctypes.data_as(C.POINTER(C.c_uint32)), table.size, meta))
     md = dict(zip(TC_META, list(meta)))
     md["idesc"] &= 0xFFFFFFFF

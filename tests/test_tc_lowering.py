@@ -32,46 +32,46 @@ def f64_to_bf16_bits(x):
 def emulate(spec, x, img, table, md):
     transposed, cin, cout, k, stride, pl, pr, op = spec
     Gn, P, rows, MT, dmin, npad = md["groups"], md["in_P"], md["rows"], md["MT"], md["dmin"], md["npad"]
-    chains, step_bytes, a_bytes = md["chains"], md["step_bytes"], md["a_bytes"]
-    chainP = 2 if transposed else 1
+    Q, coutp, step_bytes, a_bytes = md["Q"], md["coutp"], md["step_bytes"], md["a_bytes"]
     lin = x.shape[1]
-    lout = md["lout"]
+    lout, mout = md["lout"], md["mout"]
     assert rows * 16 * Gn * P <= a_bytes
-    assert md["smem"] <= 227 * 1024 and md["ncols"] <= 512
-    assert chains * MT * npad <= md["ncols"]
+    assert md["smem"] <= 227 * 1024 and md["ncols"] <= 512 and 2 * MT * npad <= md["ncols"]
+    assert Q * coutp <= npad
     xb = np.zeros((Gn * 8, lin))
     xb[:cin] = x
     imgh = img.view(np.uint16)
     out = np.zeros((cout, lout))
-    written = np.zeros(lout, bool)
+    written = np.zeros((cout, lout), int)
     r_idx = np.arange(128)[:, None]
     k_idx = np.arange(16)[None, :]
-    for tile in range(md["grid_x"]):
+    for tile in range(md["tiles_per_item"]):
         m0 = tile * 128 * MT
+        base = m0 + dmin
         A = np.zeros(a_bytes // 2, np.uint16)
         for plane in range(Gn * P):
             g, phi = plane // P, plane % P
             Lp = (lin - phi + P - 1) // P
-            r0 = max(0, -m0 - dmin)
-            r1 = max(r0, min(rows, Lp - m0 - dmin))
+            r0 = max(0, -base)
+            r1 = max(r0, min(rows, Lp - base))
             for r in range(r0, r1):
-                j = m0 + dmin + r
+                j = base + r
                 assert 0 <= j < Lp
-                base = (plane * rows + r) * 8
-                A[base:base + 8] = f64_to_bf16_bits(xb[g * 8:(g + 1) * 8, P * j + phi])
-        D = np.zeros((chains, MT, 128, npad))
+                a0 = (plane * rows + r) * 8
+                A[a0:a0 + 8] = f64_to_bf16_bits(xb[g * 8:(g + 1) * 8, P * j + phi])
+        D = np.zeros((MT, 128, npad))
         for s in range(md["n_steps"]):
             w0, w1 = int(table[2 * s]), int(table[2 * s + 1])
-            chain, first = w1 & 15, (w1 >> 4) & 1
+            assert ((w1 >> 4) & 1) == (1 if s == 0 else 0)
 
             def off(code):
-                g, phi, dd = code & 0xFF, (code >> 8) & 3, (code >> 10) & 63
+                g, phi, dd = code & 63, (code >> 6) & 31, (code >> 11) & 31
                 return ((g * P + phi) * rows + dd) * 16
 
             o0, o1 = off(w0 & 0xFFFF), off(w0 >> 16)
             lbo = o1 - o0
             assert lbo >= 0
-            # B operand: rows n, K-halves at LBO = npad * 16, 8-row groups at SBO = 128
+            # B operand: rows n, K-halves LBO = npad * 16 apart, 8-row groups SBO = 128 apart
             n_idx = np.arange(npad)[:, None]
             baddr = s * step_bytes + (n_idx // 8) * 128 + (n_idx % 8) * 16 + (k_idx // 8) * (npad * 16) + (k_idx % 8) * 2
             assert baddr.max() + 2 <= (s + 1) * step_bytes
@@ -82,17 +82,20 @@ def emulate(spec, x, img, table, md):
                 assert aaddr.min() >= 0 and aaddr.max() + 2 <= a_bytes
                 Am = bf16_bits_to_f64(A[aaddr // 2])
                 acc = Am @ Bm.T
-                D[chain, mt] = acc if first else D[chain, mt] + acc
-        for c in range(chains):
-            mout = md["mout1"] if c else md["mout0"]
-            for mt in range(MT):
-                m = m0 + mt * 128 + np.arange(128)
-                ok = m < mout
-                u = chainP * m[ok] + c
-                assert u.max(initial=-1) < lout
-                out[:, u] = D[c, mt][ok][:, :cout].T
-                written[u] = True
-    assert written.all()
+                D[mt] = acc if s == 0 else D[mt] + acc
+        # epilogue: row m, column n = sigma * coutp + o -> position Q m + sigma
+        for mt in range(MT):
+            for row in range(128):
+                m = m0 + mt * 128 + row
+                if m >= mout:
+                    continue
+                for n in range(npad):
+                    sg, o = n // coutp, n % coutp
+                    u = Q * m + sg
+                    if sg < Q and o < cout and u < lout:
+                        out[o, u] = D[mt, row, n]
+                        written[o, u] += 1
+    assert (written == 1).all()
     return out
 
 
@@ -115,13 +118,17 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("batch", [1, 1 << 20])
 @pytest.mark.parametrize("spec,lin,in_P,out_P", CASES)
-def test_tc_lowering_matches_oracle(spec, lin, in_P, out_P):
+def test_tc_lowering_matches_oracle(spec, lin, in_P, out_P, batch):
+    # batch only steers the launch plan (a huge batch keeps large tiles); the
+    # emulation replays item 0
     transposed, cin, cout, k, stride, pl, pr, op = spec
     w = to_bf16(rng.standard_normal((cout, cin, k)) * 0.2)
     x = to_bf16(rng.standard_normal((cin, lin)))
-    img, table, md = G.gw_tc_inspect(spec, G.GW_BF16, w, lin, in_P, out_P)
-    assert md["in_P"] == in_P
+    # in_P = 0: the input comes in the phase count the layer asks for
+    img, table, md = G.gw_tc_inspect(spec, G.GW_BF16, w, lin, 0, out_P, batch)
+    assert md["in_P"] >= 1
     got = emulate(spec, x, img, table, md)
     if transposed:
         ref = Lyr.conv_transpose1d(x[None], np.transpose(w, (1, 0, 2)), np.zeros(cout), stride, pl, op)[0]
@@ -133,7 +140,17 @@ def test_tc_lowering_matches_oracle(spec, lin, in_P, out_P):
 
 def test_tc_instruction_descriptor_fields():
     # kind::f16: D=F32 (bit 4), A=B=BF16 (bits 7, 10), K-major, N>>3 at 17, M>>4 at 24
-    _, _, md = G.gw_tc_inspect((0, 32, 64, 7, 2, 3, 3, 0), G.GW_BF16, np.zeros((64, 32, 7)), 256, 2, 1)
+    _, _, md = G.gw_tc_inspect((0, 32, 64, 7, 2, 3, 3, 0), G.GW_BF16, np.zeros((64, 32, 7)), 256, 0, 1)
     d = md["idesc"]
     assert (d >> 4) & 3 == 1 and (d >> 7) & 7 == 1 and (d >> 10) & 7 == 1
-    assert (d >> 15) & 3 == 0 and (d >> 17) & 63 == 64 >> 3 and (d >> 24) & 31 == 128 >> 4
+    assert (d >> 15) & 3 == 0 and (d >> 17) & 63 == md["npad"] >> 3 and (d >> 24) & 31 == 128 >> 4
+
+
+def test_tc_layer_plans_fold_positions():
+    # DeepClean layers get N >= 64 columns by folding output positions
+    specs = [(0, 21, 8, 7, 1, 3, 3, 0), (0, 8, 16, 7, 2, 3, 3, 0), (0, 16, 32, 7, 2, 3, 3, 0),
+             (0, 32, 64, 7, 2, 3, 3, 0), (1, 64, 32, 7, 2, 3, 3, 1), (1, 32, 16, 7, 2, 3, 3, 1),
+             (1, 16, 8, 7, 2, 3, 3, 1)]
+    for sp in specs:
+        _, _, md = G.gw_tc_inspect(sp, G.GW_BF16, np.zeros((sp[2], sp[1], sp[3])), 32768, 0, 1)
+        assert md["npad"] >= 64 and md["Q"] * md["coutp"] == md["npad"], (sp, md)
