@@ -580,6 +580,9 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
                      "act_scales must have one entry per conv layer");
         L.act_scale = d->act_scales ? d->act_scales[li] : 1.0f;
       }
+      // a BBHnet shortcut reads the same input as its block's first conv, so it
+      // takes that conv's output folding (and with it the same input phases)
+      if (d->kind == GW_MODEL_BBHNET && li >= 3 && (li - 3) % 3 == 0) L.J = m->layers[li - 2].J;
       tc_pack_layer(L, wf, d->precision, ctx, &m->bytes, m->allocs);
     }
     m->layers.push_back(L);

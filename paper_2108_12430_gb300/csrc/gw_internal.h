@@ -64,6 +64,7 @@ struct LayerDev {
   int coutp = 8;           // output channels per position in the MMA columns
   int dspan = 0;           // extra input rows per plane (tap shift range)
   int dmin = 0;            // smallest tap row shift
+  int J = 0;               // output positions folded per row (0 = chosen by the lowering)
   float act_scale = 1.f;   // FP8: scale of this layer's input activations
   float out_scale = 1.f;   // FP8: scale applied to the outputs for the next layer
 };

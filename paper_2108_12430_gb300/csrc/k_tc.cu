@@ -27,7 +27,7 @@
 // Kernel.  Persistent and warp-specialised: warp 0 stages input tiles by bulk
 // TMA into a 2-deep ring (zero rows for the padding at the edges), warp 1
 // issues the MMAs from one thread into a double-buffered TMEM accumulator,
-// warps 2-5 drain TMEM with tcgen05.ld, add bias (and a residual), apply the
+// warps 2-9 drain TMEM with tcgen05.ld, add bias (and a residual), apply the
 // activation and store the consumer's layout.  Weights stay resident in shared
 // memory when they fit, else stream per tile through a ring of stages.  The
 // BatchNorm is folded into the weights on the host in FP64.  Every wait is
@@ -44,7 +44,11 @@ namespace gw {
 
 namespace {
 
-constexpr int kThreads = 192;  // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+// warp 0 producer, warp 1 MMA, warps 2-9 epilogue: two epilogue warps per
+// TMEM lane quarter (each takes every other 32-column chunk), so that every
+// SM sub-partition has two warps to hide the epilogue's instruction latency
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
 
@@ -85,12 +89,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware until
+// the phase completes (or 0.1 ms pass) instead of spinning on issue slots that
+// the MMA-issuing thread and the epilogue warps need.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(100000u)
       : "memory");
   return ok != 0;
 }
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
       mbar_init(bar(a_full + i), 1);
       mbar_init(bar(a_empty + i), 1);
       mbar_init(bar(acc_full + i), 1);
-      mbar_init(bar(acc_empty + i), 4);  // one arrival per epilogue warp
+      mbar_init(bar(acc_empty + i), kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(bar(drain), 1);
     for (int i = 0; i < p.nst; ++i) {
@@ -377,7 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     __syncwarp();
   } else {
     // ---------------- epilogue: TMEM -> bias/residual/activation -> global ----------------
-    const int quarter = warp & 3;
+    const int quarter = warp & 3;          // TMEM lanes this warp may access
+    const int col_half = (warp - 2) >> 2;  // which 32-column chunks it drains
     const int row = quarter * 32 + lane;
     int i = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
       for (int mt = 0; mt < p.MT; ++mt) {
         const int m = m0 + mt * 128 + row;
         const bool valid = m < p.mout;
-        for (int j = 0; j < p.npad / 32; ++j) {
+        for (int j = col_half; j < p.npad / 32; j += 2) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((s * p.MT + mt) * p.npad + j * 32), v);
           if (!valid) continue;
@@ -555,12 +563,38 @@ int tc_supported() {
 
 // Output positions folded into one M row (J): enough to make N reach 64
 // columns for small channel counts, bounded so the tap halo stays small.
+//
+// Every tcgen05.mma with M = 128, K = 16 occupies the tensor pipe for the same
+// time whatever its N (up to 256), so the number of (row tile, K-step) pairs
+// sets the cost: folding more positions into N cuts the rows, at the price of
+// more K-steps (the tap halo) and a larger input tile and weight image.
+// Measured on GB300: an M=128, K=16 BF16 MMA costs about 100 cycles at N=64,
+// 112 at N=128 and 143 at N=256 (the last at the dense peak), but layers
+// folded to N=128 ran slower end to end than at N=64 (larger input tiles and
+// weight images, fewer tiles per SM to pipeline).  Target N = 64 and halve J
+// until two input stages plus the resident weights fit in shared memory.
 static int choose_j(const LayerSpec& s) {
-  if (s.cout == 1) return 16;
-  const int coutp = (s.cout + 7) / 8 * 8;
+  const int coutp = s.cout == 1 ? 1 : (s.cout + 7) / 8 * 8;
   const int per_j = s.transposed ? 2 * coutp : coutp;
-  int J = std::max(1, 64 / per_j);
-  J = std::min(J, s.transposed ? 4 : (s.stride == 1 ? 8 : 4));
+  int J = s.cout == 1 ? 16 : std::max(1, 64 / per_j);
+  const int G = (s.cin + 7) / 8;
+  for (; J > 1; J /= 2) {
+    const int Q = s.transposed ? 2 * J : J, P = s.transposed ? J : s.stride * J;
+    std::set<int> qs;
+    for (int sg = 0; sg < Q; ++sg)
+      for (int k = 0; k < s.k; ++k) {
+        if (!s.transposed) {
+          qs.insert(s.stride * sg + k - s.pad_l);
+        } else if (pmod_i(sg % 2 + s.pad_l - k, 2) == 0) {
+          qs.insert(sg / 2 + (sg % 2 + s.pad_l - k) / 2);
+        }
+      }
+    const int dspan = floordiv_i(*qs.rbegin(), P) - floordiv_i(*qs.begin(), P);
+    const size_t steps = ((size_t)qs.size() * G + 1) / 2;
+    const size_t npad = std::max(32, (Q * coutp + 31) / 32 * 32);
+    const size_t a_stage = (size_t)G * P * (128 + dspan) * 16;
+    if (P <= 32 && npad <= 256 && 2 * a_stage + steps * 32 * npad <= 200 * 1024) break;
+  }
   return J;
 }
 
@@ -571,14 +605,14 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
   const LayerSpec& s = L.s;
   const int cg = fp8 ? 16 : 8;
   const int G = (s.cin + cg - 1) / cg;
-  const int J = choose_j(s);
+  const int J = L.J > 0 ? L.J : choose_j(s);
   const int Q = s.transposed ? 2 * J : J;
   const int P = s.transposed ? J : s.stride * J;
   const int coutp = s.cout == 1 ? 1 : (s.cout + 7) / 8 * 8;
   // N padded to a multiple of 32 (the epilogue drains 32 columns per load)
   const int npad = std::max(32, (Q * coutp + 31) / 32 * 32);
   GW_CHECK_ARG(npad <= 256, "output columns above 256 are not supported by the tensor-core path");
-  GW_CHECK_ARG(G <= 63 && P <= 31, "layer too wide for the tensor-core path");
+  GW_CHECK_ARG(G <= 63 && P <= 32, "layer too wide for the tensor-core path");  // 6-bit group, 5-bit phase
   if (s.transposed)
     GW_CHECK_ARG(s.stride == 2 && s.pad_l == s.pad_r, "transposed conv must have stride 2 and symmetric padding");
   // contributions (sigma, tap) -> input (phi, d)
@@ -678,6 +712,7 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
   L.n_chains = Q;      // output positions per M row
   L.dspan = dmax - dmin;
   L.dmin = dmin;
+  L.J = J;
   L.coutp = coutp;
 }
 
