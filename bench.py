@@ -350,6 +350,7 @@ def gpu_arm(args):
         bound = "alu"
         peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
     traffic = None
+    configs = extra_configs(G, torch, dev_index, flush)
     cpu = cpu_baseline(budget_s=args.cpu_seconds)
     line = {
         "metric": METRIC,
@@ -380,12 +381,116 @@ def gpu_arm(args):
                      "peak_source": peak_note,
                      "per_unit": f"{dc_flops_per_window()} flop per window x {B} windows per step"},
         "paths": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in paths.items()},
+        "configs": configs,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def bbhnet_flops_per_window(L=2048):
+    """Algorithmic FLOPs of one BBHnet window (stem, 4 blocks, head)."""
+    from paper_2108_12430_gb300 import synth
+    f, lin = 0, L
+    lay = synth.bbhnet_layers()
+    # stem then blocks: conv1 and shortcut read the block input, conv2 conv1's output
+    kind, cin, cout, k, s, pl, pr, op, bn, act = lay[0]
+    lin = (lin + pl + pr - k) // s + 1
+    f += 2 * cout * cin * k * lin
+    for i in range(1, len(lay), 3):
+        c1, c2, sc = lay[i], lay[i + 1], lay[i + 2]
+        l2 = (lin + c1[5] + c1[6] - c1[3]) // c1[4] + 1
+        f += 2 * c1[2] * c1[1] * c1[3] * l2 + 2 * c2[2] * c2[1] * c2[3] * l2 + 2 * sc[2] * sc[1] * sc[3] * l2
+        lin = l2
+    return f + 2 * 256
+
+
+def time_call(torch, fn, steps, warmup, flush=None):
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
+    """Config 1 (one 1 s DeepClean window) latency and config 3 (whitening +
+    BBHnet on 256 x 2 x 4096 raw strain) throughput, BF16 and FP32, each with
+    its error against the FP64 oracle on sampled items."""
+    from oracle import fir as ofir, nets
+    from paper_2108_12430_gb300 import synth
+    out = {}
+    ctx = G.gw_ctx_create(dev_index, 0)
+    try:
+        # config 1
+        x1 = synth.witness_channels(0, C, 4096)
+        ref1 = nets.deepclean_forward(x1[None].astype(np.float32).astype(np.float64), synth.deepclean_params(0),
+                                      synth.DEEPCLEAN_LAYERS)[0]
+        x1d = torch.from_numpy(x1.astype(np.float32)).cuda()
+        y1 = torch.zeros(1, 4096, device="cuda")
+        for name, prec in (("bf16", G.GW_BF16), ("fp32", G.GW_FP32)):
+            m = G.gw_model_create(ctx, G.GW_MODEL_DEEPCLEAN, prec, C, synth.flatten_params(synth.deepclean_params(0)))
+            ms = time_call(torch, lambda: G.gw_deepclean_forward(m, x1d.data_ptr(), 4096, 0, 1, 4096, y1.data_ptr()),
+                           steps, warmup)
+            err = float(np.linalg.norm(y1.cpu().numpy()[0] - ref1) / np.linalg.norm(ref1))
+            out[f"config1_{name}"] = {"workload": "DeepClean forward 1x21x4096", "p50_us": float(np.median(ms) * 1e3),
+                                      "p99_us": float(np.percentile(ms, 99) * 1e3), "rel_l2_vs_fp64_oracle": err}
+            G.gw_model_destroy(m)
+        # config 3: whitening (2049 taps) + BBHnet, batch 256
+        Bc, Lr = 256, 4096
+        fs, nfft = 2048.0, 8192
+        fgrid, psd = synth.psd_grid(fs, nfft)
+        xr, label, snr = synth.injected_strain(31, Bc, Lr)
+        xrd = torch.from_numpy(xr.astype(np.float32)).cuda()
+        wd = torch.zeros(Bc, 2, Lr - 2048, device="cuda")
+        logit = torch.zeros(Bc, device="cuda")
+        h = ofir.whitening_fir(psd, fs, nfft, 2049)
+        idx = [0, 77, 255]
+        xw_ref = ofir.fir_valid(xr[idx].astype(np.float32).astype(np.float64), h)
+        layers, head = synth.bbhnet_params(3)
+        ref3 = nets.bbhnet_forward(xw_ref, layers, head, synth.bbhnet_layers())
+        for name, prec in (("bf16", G.GW_BF16), ("fp32", G.GW_FP32)):
+            fh = G.gw_fir_create_whitening(ctx, psd, fs, 2049, prec)
+            mb = G.gw_model_create(ctx, G.GW_MODEL_BBHNET, prec, 2, synth.flatten_params(layers, head))
+
+            def step():
+                G.gw_whiten(fh, xrd.data_ptr(), Bc, 2, Lr, wd.data_ptr())
+                G.gw_bbhnet_score(mb, wd.data_ptr(), Bc, Lr - 2048, logit.data_ptr())
+
+            ms = time_call(torch, step, steps, warmup, flush)
+            G.gw_profile_enable(True)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            prof = G.gw_profile_read()
+            G.gw_profile_enable(False)
+            got = logit.cpu().numpy()[idx]
+            wgot = wd.cpu().numpy()[idx]
+            werr = float(np.linalg.norm(wgot - xw_ref) / np.linalg.norm(xw_ref))
+            flops = bbhnet_flops_per_window() * Bc + 2 * 2049 * Bc * 2 * 2048
+            out[f"config3_{name}"] = {
+                "workload": "whiten 2049 taps + BBHnet, batch 256 x 2 x 4096",
+                "ms_per_batch": float(np.mean(ms)), "windows_per_s": Bc / (np.mean(ms) / 1e3),
+                "tflops": flops / (np.mean(ms) / 1e3) / 1e12,
+                "whiten_rel_l2": werr, "max_abs_logit_err": float(np.abs(got - ref3).max()),
+                "kernels_ms": {k: v[0] / 3 for k, v in prof.items()}}
+            G.gw_model_destroy(mb)
+            G.gw_fir_destroy(fh)
+    finally:
+        G.gw_ctx_destroy(ctx)
+    return out
 
 
 # ---------------------------------------------------------------------------

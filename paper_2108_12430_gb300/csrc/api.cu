@@ -697,6 +697,30 @@ int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double f
   try {
     f->d_taps = (float*)dev_alloc(ctx, t32.size() * 4, &f->bytes);
     GW_CUDA(cudaMemcpy(f->d_taps, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice));
+    if (precision == GW_BF16) {
+      // y[8 t + r] = sum_{e, c} h[8 c + e - r] x[8 (t + c) + e]: an 8 -> 8
+      // channel conv with K = (ntaps - 1) / 8 + 1 taps over the signal viewed
+      // as 8 "channels" of consecutive samples
+      GW_CHECK_ARG(!tc_supported() ? false : true, "tensor-core path needs an sm_103 device");
+      if ((ntaps - 1) % 8 != 0) throw Error(GW_ENOTIMPL, "BF16 whitening needs ntaps = 8 q + 1");
+      const int K = (ntaps - 1) / 8 + 1;
+      std::vector<double> wf((size_t)64 * K, 0.0);
+      for (int r = 0; r < 8; ++r)
+        for (int e = 0; e < 8; ++e)
+          for (int c = 0; c < K; ++c) {
+            const int k = 8 * c + e - r;
+            if (k >= 0 && k < ntaps) wf[((size_t)r * 8 + e) * K + c] = f->taps[k];
+          }
+      f->tc.s = LayerSpec{false, 8, 8, K, 1, 0, 0, 0, false, ACT_NONE};
+      std::vector<float> zero8(8, 0.f);
+      f->tc.b = (float*)dev_alloc(ctx, 32, &f->bytes);
+      f->allocs.push_back(f->tc.b);
+      GW_CUDA(cudaMemcpy(f->tc.b, zero8.data(), 32, cudaMemcpyHostToDevice));
+      tc_pack_layer(f->tc, wf, GW_BF16, ctx, &f->bytes, f->allocs);
+      f->err = (int*)dev_alloc(ctx, sizeof(int), &f->bytes);
+      f->allocs.push_back(f->err);
+      GW_CUDA(cudaMemset(f->err, 0, sizeof(int)));
+    }
   } catch (...) {
     gw_fir_destroy(f);
     f = nullptr;
@@ -712,10 +736,11 @@ int gw_fir_destroy(gw_fir_t f) {
   GW_CHECK_ARG(f, "fir is NULL");
   cudaDeviceSynchronize();
   if (f->d_taps) cudaFree(f->d_taps);
-  if (f->d_toeplitz) cudaFree(f->d_toeplitz);
+  for (void* p : f->allocs) cudaFree(p);
+  if (f->ws) cudaFree(f->ws);
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
-    f->ctx->in_use -= f->bytes;
+    f->ctx->in_use -= f->bytes + f->ws_bytes;
   }
   delete f;
   GW_API_END
@@ -735,8 +760,36 @@ int gw_whiten(gw_fir_t f, const float* x, int B, int C, int L_in, float* y, void
   GW_CHECK_ARG(f && x && y, "NULL argument");
   GW_CHECK_ARG(B >= 1 && C >= 1 && L_in >= f->ntaps, "need B, C >= 1 and L_in >= ntaps");
   const int lout = L_in - f->ntaps + 1;
-  Prof p("fir_f32", (cudaStream_t)cuda_stream);
-  launch_fir_f32(x, L_in, y, lout, B * C, f->d_taps, f->ntaps, lout, (cudaStream_t)cuda_stream);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (f->precision == GW_FP32) {
+    Prof p("fir_f32", st);
+    launch_fir_f32(x, L_in, y, lout, B * C, f->d_taps, f->ntaps, lout, st);
+  } else {
+    GW_CHECK_ARG(L_in % 8 == 0, "BF16 whitening needs L_in a multiple of 8");
+    const int lin8 = L_in / 8, lout8 = lout / 8;
+    TcOut xin = blocked_out(nullptr, 8, lin8, f->tc.pin);
+    const size_t need = (size_t)B * C * xin.bstride * 2;
+    if (need > f->ws_bytes) {
+      GW_CUDA(cudaDeviceSynchronize());
+      if (f->ws) dev_free(f->ctx, f->ws, f->ws_bytes, nullptr);
+      f->ws = nullptr;
+      f->ws_bytes = 0;
+      f->ws = dev_alloc(f->ctx, need, nullptr);
+      f->ws_bytes = need;
+    }
+    xin.p = f->ws;
+    {
+      Prof p("to_blocked", st);
+      launch_to_blocked(x, L_in, 1, B * C, 8, lin8, nullptr, nullptr, 1.f, xin, 0, st, 8);
+    }
+    TcOut o{};
+    o.p = y;
+    o.bstride = lout;
+    o.P = 1;
+    o.fp32_d2s = 1;
+    Prof p("conv_tc.whiten", st);
+    launch_conv_tc(f->tc, as_input(xin, lin8), lout8, o, B * C, f->err, st);
+  }
   GW_API_END
 }
 

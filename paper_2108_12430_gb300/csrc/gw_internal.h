@@ -100,7 +100,13 @@ struct gw_fir {
   int ntaps = 0, precision = 0;
   std::vector<double> taps;
   float* d_taps = nullptr;
-  void* d_toeplitz = nullptr;  // BF16 tensor-core operand image
+  // BF16: the FIR as an 8 -> 8 channel conv over the space-to-depth view of
+  // the signal (Toeplitz weights W[r][e][c] = h[8 c + e - r])
+  gw::LayerDev tc;
+  std::vector<void*> allocs;
+  int* err = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
   size_t bytes = 0;
 };
 
@@ -179,15 +185,18 @@ struct TcOut {
   int64_t rbstride, rgstride, rpstride;
   int rP;
   int fp8_out;           // write e4m3 (scaled by out_scale) instead of bf16
+  int fp32_d2s;          // 8-channel layer: write FP32 [B][bstride], channel o of position u at 8 u + o
 };
 int tc_supported();
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wfold, int precision, gw_ctx* ctx,
                    size_t* counter, std::vector<void*>& allocs);
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err_flag,
                     cudaStream_t st);
-// FP32 [B][C][x_ld] (item b at x + b*xb) -> blocked bf16 / e4m3, optionally standardised.
+// FP32 element (b, c, t) at x + b*xb + c*xc + t*ts -> blocked bf16 / e4m3,
+// optionally standardised (ts = 8, xc = 1: space-to-depth of one signal).
 void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,
-                       const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st);
+                       const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st,
+                       int64_t ts = 1);
 // Global average pool over a blocked activation + linear head -> FP32 logits.
 void launch_gap_linear_blocked(const TcIn& in, int C, int fp8, float in_scale, const float* w,
                                const float* b, float* out, int B, cudaStream_t st);

@@ -76,6 +76,7 @@ struct TcParams {
   int* err;
   int coutp_log, out_P_log, res_P_log;  // power-of-two shifts for the epilogue addressing
   int min_plen;                          // rows of the shortest input plane
+  int fp32_d2s;                          // write the 8 channels of position u as FP32 samples 8u..8u+7
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -197,10 +198,10 @@ __device__ __forceinline__ float act_fn(float v, int act) {
   return v;
 }
 
-// Byte offset (M sub-tile 0) of the slice coded g | phi << 6 | dd << 11 in a
+// Byte offset (M sub-tile 0) of the slice coded g | phi << 8 | dd << 14 in a
 // tile of P planes per group, `rows` 16-byte rows per plane.
 __device__ __forceinline__ uint32_t slice_off(uint32_t code, int P, int rows) {
-  const uint32_t g = code & 63u, phi = (code >> 6) & 31u, dd = (code >> 11) & 31u;
+  const uint32_t g = code & 255u, phi = (code >> 8) & 63u, dd = code >> 14;
   return ((g * (uint32_t)P + phi) * (uint32_t)rows + dd) * 16u;
 }
 
@@ -245,8 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
   // adds stage offsets), plane offsets and lengths, bias and scales
   const uint32_t stage_b = p.resident ? 0u : (uint32_t)p.sps;
   for (int i = tid; i < p.n_steps; i += kThreads) {
-    const uint32_t w0 = p.table[2 * i];
-    const uint32_t o0 = slice_off(w0 & 0xFFFFu, p.in_P, p.rows), o1 = slice_off(w0 >> 16, p.in_P, p.rows);
+    const uint32_t o0 = slice_off(p.table[2 * i], p.in_P, p.rows), o1 = slice_off(p.table[2 * i + 1], p.in_P, p.rows);
     s_adesc[i] = make_desc(sA + o0, o1 - o0, 128u);
     const uint32_t pos = p.resident ? (uint32_t)i : (uint32_t)i % stage_b;
     s_bdesc[i] = make_desc(sW + pos * (uint32_t)p.step_bytes, (uint32_t)p.npad * 16u, 128u);
@@ -448,7 +448,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
             }
 #pragma unroll
             for (int e = 0; e < 8; ++e) x[e] = act_fn(x[e], p.act);
-            if (p.fp8_out) {
+            if (p.fp32_d2s) {
+              // depth-to-space: channel o of position u is output sample 8 u + o
+              float4* op = reinterpret_cast<float4*>(outb + (int64_t)u * 32);
+              op[0] = make_float4(x[0], x[1], x[2], x[3]);
+              op[1] = make_float4(x[4], x[5], x[6], x[7]);
+            } else if (p.fp8_out) {
               __align__(8) __nv_fp8_e4m3 o8[8];
 #pragma unroll
               for (int e = 0; e < 8; ++e) o8[e] = __nv_fp8_e4m3(x[e] * p.out_scale);
@@ -476,9 +481,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
   if (warp == 1) tmem_dealloc(tmem, (uint32_t)p.ncols);
 }
 
-// FP32 [B][C][*] -> blocked layout (bf16 rows of 8 channels, or e4m3 rows of 16).
-__global__ void to_blocked_kernel(const float* __restrict__ x, int64_t xb, int64_t xc, int B, int C, int L,
-                                  const float* __restrict__ mean, const float* __restrict__ istd, float scale,
+// FP32 element (b, c, t) at x[b xb + c xc + t ts] -> blocked layout (bf16 rows
+// of 8 channels, or e4m3 rows of 16).  ts = 8, xc = 1 turns one signal into 8
+// "channels" of consecutive samples (space-to-depth).
+__global__ void to_blocked_kernel(const float* __restrict__ x, int64_t xb, int64_t xc, int64_t ts, int B, int C,
+                                  int L, const float* __restrict__ mean, const float* __restrict__ istd, float scale,
                                   char* __restrict__ out, int64_t ob, int64_t og, int64_t op, int P, int fp8) {
   const int cg = fp8 ? 16 : 8;
   const int G = (C + cg - 1) / cg;
@@ -493,7 +500,7 @@ __global__ void to_blocked_kernel(const float* __restrict__ x, int64_t xb, int64
       const int c = g * cg + i;
       float a = 0.f;
       if (i < cg && c < C) {
-        a = x[(int64_t)b * xb + (int64_t)c * xc + t];
+        a = x[(int64_t)b * xb + (int64_t)c * xc + (int64_t)t * ts];
         if (mean) a = (a - mean[c]) * istd[c];
       }
       v[i] = a;
@@ -612,7 +619,7 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
   // N padded to a multiple of 32 (the epilogue drains 32 columns per load)
   const int npad = std::max(32, (Q * coutp + 31) / 32 * 32);
   GW_CHECK_ARG(npad <= 256, "output columns above 256 are not supported by the tensor-core path");
-  GW_CHECK_ARG(G <= 63 && P <= 32, "layer too wide for the tensor-core path");  // 6-bit group, 5-bit phase
+  GW_CHECK_ARG(G <= 255 && P <= 63, "layer too wide for the tensor-core path");  // 8-bit group, 6-bit phase
   if (s.transposed)
     GW_CHECK_ARG(s.stride == 2 && s.pad_l == s.pad_r, "transposed conv must have stride 2 and symmetric padding");
   // contributions (sigma, tap) -> input (phi, d)
@@ -637,9 +644,9 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
     dmax = std::max(dmax, c.d);
     pos.insert({c.phi, c.d});
   }
-  GW_CHECK_ARG(dmax - dmin < 32, "tap span too large");
+  GW_CHECK_ARG(dmax - dmin < 2048, "tap span too large");
   struct Slice { int g, phi, dd; bool dummy; };
-  auto key = [](const Slice& a) { return (a.g * 32 + a.phi) * 32 + a.dd; };
+  auto key = [](const Slice& a) { return ((int64_t)a.g * 64 + a.phi) * 4096 + a.dd; };
   std::vector<std::pair<Slice, Slice>> steps;
   std::vector<Slice> left;
   for (auto& ps : pos) {
@@ -676,15 +683,16 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
   }
   // weight of column (sigma, o), slice (g, phi, d), channel c: the tap k
   // that maps (sigma, k) to (phi, d), if any
-  std::vector<int> tap_of((size_t)Q * P * 32, -1);
-  for (auto& c : cons) tap_of[((size_t)c.sigma * P + c.phi) * 32 + (c.d - dmin)] = c.k;
+  const size_t nd = (size_t)(dmax - dmin + 1);
+  std::vector<int> tap_of((size_t)Q * P * nd, -1);
+  for (auto& c : cons) tap_of[((size_t)c.sigma * P + c.phi) * nd + (c.d - dmin)] = c.k;
   for (int si = 0; si < n_steps; ++si) {
     for (int half = 0; half < 2; ++half) {
       const Slice& sl = half ? steps[si].second : steps[si].first;
       for (int n = 0; n < npad; ++n) {
         const int sg = n / coutp, o = n % coutp;
         if (sl.dummy || sg >= Q || o >= s.cout) continue;
-        const int k = tap_of[((size_t)sg * P + sl.phi) * 32 + sl.dd];
+        const int k = tap_of[((size_t)sg * P + sl.phi) * nd + sl.dd];
         if (k < 0) continue;
         uint8_t* dst = img.data() + si * step_bytes + ((size_t)half * npad + n) * 16;
         for (int kk = 0; kk < cg; ++kk) {
@@ -701,9 +709,10 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
         }
       }
     }
-    auto code = [](const Slice& a) { return (uint32_t)a.g | ((uint32_t)a.phi << 6) | ((uint32_t)a.dd << 11); };
-    table[2 * si] = code(steps[si].first) | (code(steps[si].second) << 16);
-    table[2 * si + 1] = si == 0 ? 16u : 0u;
+    // one 32-bit code per slice: group (8 bits) | phase (6 bits) << 8 | row shift << 14
+    auto code = [](const Slice& a) { return (uint32_t)a.g | ((uint32_t)a.phi << 8) | ((uint32_t)a.dd << 14); };
+    table[2 * si] = code(steps[si].first);
+    table[2 * si + 1] = code(steps[si].second);
   }
   L.n_steps = n_steps;
   L.npad = npad;
@@ -821,7 +830,9 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.cout = s.cout;
   q.act = s.act;
   q.out = (char*)out.p;
-  const int oesz = out.fp32_single ? 4 : (out.fp8_out ? 1 : 2);
+  GW_CHECK_ARG(!out.fp32_d2s || s.cout == 8, "depth-to-space output needs 8 channels");
+  q.fp32_d2s = out.fp32_d2s;
+  const int oesz = (out.fp32_single || out.fp32_d2s) ? 4 : (out.fp8_out ? 1 : 2);
   q.out_b = out.bstride * oesz;
   q.out_g = out.gstride * oesz;
   q.out_p = out.pstride * oesz;
@@ -876,12 +887,12 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
 }
 
 void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,
-                       const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st) {
+                       const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st, int64_t ts) {
   const int esz = fp8 ? 1 : 2;
   const int cg = fp8 ? 16 : 8;
   const int64_t total = (int64_t)B * ((C + cg - 1) / cg) * L;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  to_blocked_kernel<<<grid, 256, 0, st>>>(x, xb, xc, B, C, L, mean, istd, scale, (char*)out.p, out.bstride * esz,
+  to_blocked_kernel<<<grid, 256, 0, st>>>(x, xb, xc, ts, B, C, L, mean, istd, scale, (char*)out.p, out.bstride * esz,
                                           out.gstride * esz, out.pstride * esz, out.P, fp8);
   GW_LAUNCH_CHECK();
 }

@@ -120,3 +120,24 @@ def test_bbhnet_batch256_sampled_bf16(ctx):
     idx = [0, 1, 100, 255]
     ref = nets.bbhnet_forward(x[idx], params, head, synth.bbhnet_layers())
     np.testing.assert_allclose(out.cpu().numpy()[idx], ref, atol=0.05)
+
+
+@pytest.mark.parametrize("B,C,L_in", [(256, 2, 4096), (3, 1, 2056), (2, 2, 6144)])
+def test_whiten_bf16(ctx, B, C, L_in):
+    # the FIR runs as an 8 -> 8 channel tensor-core conv on the space-to-depth
+    # view of the signal; compared with the oracle's valid-mode FIR
+    from oracle import fir as ofir
+    fs, nfft = 2048.0, 8192
+    f, psd = synth.psd_grid(fs, nfft)
+    fh = G.gw_fir_create_whitening(ctx.h, psd, fs, 2049, G.GW_BF16)
+    ctx.objs.append((G.gw_fir_destroy, fh))
+    x = synth.colored_noise(B + L_in, L_in, fs, n_ch=B * C).reshape(B, C, L_in)
+    lout = L_in - 2048
+    y = torch.zeros(B, C, lout, device="cuda")
+    G.gw_whiten(fh, dev(x).data_ptr(), B, C, L_in, y.data_ptr())
+    torch.cuda.synchronize()
+    h = ofir.whitening_fir(psd, fs, nfft, 2049)
+    xr = x.reshape(B * C, L_in)
+    yr = y.reshape(B * C, lout).cpu().numpy()
+    for r in sorted({0, B * C // 2, B * C - 1}):
+        assert rel_l2(yr[r], ofir.fir_valid(xr[r], h)) <= TOL16, r

@@ -62,13 +62,12 @@ def emulate(spec, x, img, table, md):
         D = np.zeros((MT, 128, npad))
         for s in range(md["n_steps"]):
             w0, w1 = int(table[2 * s]), int(table[2 * s + 1])
-            assert ((w1 >> 4) & 1) == (1 if s == 0 else 0)
 
             def off(code):
-                g, phi, dd = code & 63, (code >> 6) & 31, (code >> 11) & 31
+                g, phi, dd = code & 255, (code >> 8) & 63, code >> 14
                 return ((g * P + phi) * rows + dd) * 16
 
-            o0, o1 = off(w0 & 0xFFFF), off(w0 >> 16)
+            o0, o1 = off(w0), off(w1)
             lbo = o1 - o0
             assert lbo >= 0
             # B operand: rows n, K-halves LBO = npad * 16 apart, 8-row groups SBO = 128 apart
@@ -115,6 +114,8 @@ CASES = [
     ((0, 64, 64, 7, 1, 3, 3, 0), 150, 1, 2),
     ((0, 128, 256, 1, 2, 0, 0, 0), 300, 2, 1),
     ((0, 256, 256, 7, 1, 3, 3, 0), 140, 1, 1),
+    # the 2049-tap whitening FIR as an 8 -> 8 channel conv on the space-to-depth view
+    ((0, 8, 8, 257, 1, 0, 0, 0), 600, 1, 1),
 ]
 
 
