@@ -215,7 +215,7 @@ static const char* kDcNames[8] = {"conv_f32.enc1", "conv_f32.enc2", "conv_f32.en
 // DeepClean on B windows in FP32.  Input element (b, c, t) at
 // x + b*xb + c*xc + t; the first layer standardises when mean != null.
 void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
-                          float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st) {
+                   float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st, const int64_t* item_off) {
   const auto& Ls = m->layers;
   const float* in = x;
   int64_t ib = xb, ic = xc;
@@ -236,6 +236,7 @@ void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool sta
     a.w = Ls[li].w; a.bias = Ls[li].b;
     a.in_mean = (li == 0 && standardise) ? m->in_mean : nullptr;
     a.in_istd = (li == 0 && standardise) ? m->in_istd : nullptr;
+    a.item_off = li == 0 ? item_off : nullptr;
     a.B = B; a.lin = lin; a.lout = lout; a.s = s;
     {
       Prof p(kDcNames[li], st);
@@ -246,7 +247,7 @@ void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool sta
   }
 }
 
-static void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st) {
+void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st) {
   const auto& Ls = m->layers;
   const size_t per = (size_t)B * 32 * L;
   float* buf[3] = {ws, ws + per, ws + 2 * per};
@@ -288,7 +289,7 @@ static void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits,
 // ---- tensor-core runners -------------------------------------------------------
 // Blocked activation of `cout` channels x `lout` positions in P phase planes
 // (element strides; rows of 8 bf16 channels).
-static TcOut blocked_out(void* buf, int cout, int lout, int P) {
+TcOut blocked_out(void* buf, int cout, int lout, int P) {
   TcOut o{};
   const int G = (cout + 7) / 8;
   const int64_t Lp = (lout + P - 1) / P;
@@ -300,7 +301,7 @@ static TcOut blocked_out(void* buf, int cout, int lout, int P) {
   return o;
 }
 
-static TcIn as_input(const TcOut& o, int lout) {
+TcIn as_input(const TcOut& o, int lout) {
   TcIn i{};
   i.p = o.p;
   i.bstride = o.bstride;
@@ -315,11 +316,11 @@ static const char* kDcTcNames[8] = {"conv_tc.enc1", "conv_tc.enc2", "conv_tc.enc
                                     "conv_tc.dec1", "conv_tc.dec2", "conv_tc.dec3", "conv_tc.out"};
 
 // Per-item elements of the largest inter-layer activation of a DeepClean window.
-static int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 2048; }
+int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 2048; }
 
 // DeepClean on B windows through the tensor-core kernels.  `in` is the
 // blocked BF16 input (ring windows or a converted batch); y gets FP32 [B][y_ld].
-static void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1,
+void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1,
                          int* err, cudaStream_t st) {
   const auto& Ls = m->layers;
   void* bufs[2] = {buf0, buf1};
@@ -347,7 +348,7 @@ static void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y
 }
 
 // BBHnet on B items of [2][L] FP32 through the tensor-core kernels.
-static void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st) {
+void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st) {
   const auto& Ls = m->layers;
   const int64_t per = (int64_t)B * 32 * L;  // elements of the largest activation
   void* in0 = ws;
@@ -394,7 +395,7 @@ static void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, 
   launch_gap_linear_blocked(as_input(h, l), Ls.back().s.cout, 0, 1.f, m->head_w, m->head_b, logits, B, st);
 }
 
-static size_t bbhnet_tc_ws_bytes(int B, int L) { return (size_t)B * 8 * L * 2 + 3 * (size_t)B * 32 * L * 2; }
+size_t bbhnet_tc_ws_bytes(int B, int L) { return (size_t)B * 8 * L * 2 + 3 * (size_t)B * 32 * L * 2; }
 
 }  // namespace gw
 

@@ -133,6 +133,7 @@ struct ConvF32Args {
   const float* res; int64_t rb, rc;   // optional residual added before the activation
   const float* w; const float* bias;  // folded weights [C_out][C_in][K], bias [C_out]
   const float* in_mean; const float* in_istd;  // optional input standardisation
+  const int64_t* item_off;            // optional device table: element offset of item b (replaces b*xb)
   int B, lin, lout;
   LayerSpec s;
 };
@@ -145,7 +146,14 @@ void launch_gap_linear_f32(const float* h, int64_t hb, int64_t hc, int B, int C,
 // DeepClean forward in FP32 over B windows (api.cu): input element (b, c, t)
 // at x + b*xb + c*xc + t, output [B][y_ld]; buf0 / buf1 each hold B*8*L floats.
 void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
-                   float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st);
+                   float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st,
+                   const int64_t* item_off = nullptr);
+
+// ---- model runners (api.cu) ------------------------------------------------------
+struct TcIn;
+struct TcOut;
+void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st);
+size_t bbhnet_tc_ws_bytes(int B, int L);
 
 // ---- stream kernels (k_stream.cu) -------------------------------------------
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring,
@@ -175,6 +183,9 @@ struct TcIn {
   const void* p;
   int64_t off0, bstride, boff, gstride, pstride;
   int P, L;
+  // optional device table: element offset of item b (replaces off0 + b*bstride
+  // + b*boff*cg), so that one launch reads windows of many streams' rings
+  const int64_t* item_off = nullptr;
 };
 struct TcOut {
   void* p;               // blocked activations, or FP32 [B][bstride] when fp32_single
@@ -187,6 +198,18 @@ struct TcOut {
   int fp8_out;           // write e4m3 (scaled by out_scale) instead of bf16
   int fp32_d2s;          // 8-channel layer: write FP32 [B][bstride], channel o of position u at 8 u + o
 };
+// Blocked output of `cout` channels x `lout` positions in P planes, and its view
+// as the next layer's input (api.cu).
+TcOut blocked_out(void* buf, int cout, int lout, int P);
+TcIn as_input(const TcOut& o, int lout);
+int64_t deepclean_tc_act_elems(int L);
+// DeepClean on B windows through the tensor-core kernels: `in` is the first
+// layer's blocked input, y gets FP32 [B][y_ld]; buf0/buf1 hold
+// B * deepclean_tc_act_elems(L) elements each.
+void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1, int* err,
+                  cudaStream_t st);
+// BBHnet on B items of FP32 [2][L]; ws holds bbhnet_tc_ws_bytes(B, L).
+void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st);
 int tc_supported();
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wfold, int precision, gw_ctx* ctx,
                    size_t* counter, std::vector<void*>& allocs);

@@ -319,6 +319,37 @@ def test_streamed_equals_full_pass_for_local_model():
             np.testing.assert_allclose(-cl[k], full[t], atol=1e-12)
 
 
+def test_pipeline_timing_with_delta_filters():
+    # With a model that predicts zero, cleaned = strain; with a decimator that
+    # is a unit impulse at its centre tap and a whitening filter that is a unit
+    # impulse at its centre tap, w[n] = d[n] = c[2n] = strain[2n].  The BBHnet
+    # input of snapshot k is then strain at even times ending at 2 n_end_k, and
+    # its logit must equal BBHnet applied to that window directly.
+    from oracle import pipeline
+    W, S, n, Lb = 256, 64, 12, 128
+    layers = synth.bbhnet_layers()
+    params, head = synth.bbhnet_params(4)
+    strain = [rng.standard_normal(n * S) for _ in range(2)]
+    wit = [np.zeros((3, n * S)) for _ in range(2)]
+    zero = lambda wins: np.zeros((wins.shape[0], wins.shape[-1]))
+    f_dec = np.zeros(127); f_dec[63] = 1.0
+    h = np.zeros(33); h[16] = 1.0
+    delta = 40
+    cl, logits = pipeline.run_pipeline(wit, strain, W, S, n, stream.AVERAGE, delta, [zero, zero], f_dec, h,
+                                       params, head, layers, Lb=Lb)
+    for k in range(n):
+        t = stream.emit_times(k, S, delta)
+        ok = t >= 0
+        np.testing.assert_allclose(cl[0, k][ok], strain[0][t[ok]], atol=1e-12)
+        me = pipeline.m_end(k, S, delta)
+        ne = me - 16
+        win = np.zeros((1, 2, Lb))
+        for i, nn in enumerate(range(ne - Lb, ne)):
+            if nn >= 0:
+                win[0, :, i] = [strain[0][2 * nn], strain[1][2 * nn]]
+        assert abs(logits[k] - nets.bbhnet_forward(win, params, head, layers)[0]) < 1e-9
+
+
 # ----------------------------------------------------------------------------
 # Gradient: central finite differences and PyTorch autograd in float64
 # ----------------------------------------------------------------------------
