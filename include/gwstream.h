@@ -148,6 +148,14 @@ int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double f
                             int precision, gw_fir_t* out);
 int gw_fir_destroy(gw_fir_t f);
 int gw_fir_ntaps(gw_fir_t f);
+/* Anti-alias low-pass for resampling by 2 (the paper resamples its 4096 Hz
+ * cleaned strain before BBHnet in the end-to-end ensemble, Methods,
+ * "Offline Deployment"; the filter itself is unspecified, so this is a
+ * reading): a Hann-windowed sinc with cutoff fc at sample rate fs,
+ * h[j] ~ (2 fc / fs) sinc(2 fc / fs (j - (ntaps-1)/2)) w_Hann[j], normalised to
+ * sum 1 (unit DC gain), designed in FP64.  ntaps odd.  BF16 needs
+ * ntaps = 8 q + 1 (GW_ENOTIMPL otherwise). */
+int gw_fir_create_lowpass(gw_ctx_t ctx, double fc, double fs, int ntaps, int precision, gw_fir_t* out);
 /* Host copy of the FP64 taps (ntaps doubles). */
 int gw_fir_taps(gw_fir_t f, double* taps_out);
 /* Valid-mode filtering y[b][c][n] = sum_k h[k] x[b][c][n + k],
@@ -200,6 +208,101 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
 int64_t gw_stream_head(gw_stream_t s);
 /* Device-side status of the stream: GW_OK or GW_ENONFINITE (sticky until reset). */
 int gw_stream_status(gw_stream_t s, void* cuda_stream);
+
+/* ---- serving loop ------------------------------------------------------------
+ * Many streams, each of n_det detectors, served by one persistent loop that
+ * batches the pending snapshots of different streams into one device tick
+ * (the paper's inference service answers many concurrent clients whose
+ * requests each carry one snapshot of new samples, with the snapshot state
+ * kept on the GPU: Methods, "Streaming IaaS", "Online Deployment", and the
+ * end-to-end ensemble of "Offline Deployment").  A snapshot of stream s runs
+ * the whole path:
+ *   1. ring update of the witness and strain state (stride S new samples);
+ *   2. DeepClean on the window of the last `window` samples (one model per
+ *      detector);
+ *   3. subtraction and aggregation as for gw_stream (agg_mode, agg_delay),
+ *      giving S cleaned samples c[tau], tau in [k S - agg_delay, (k+1) S - agg_delay);
+ *   4. 2x resampling with the decimator FIR f (Kf taps, odd):
+ *      d[m] = sum_j f[j] c[2 m + j - (Kf-1)/2], c[tau < 0] = 0; d[m] is
+ *      computed as soon as every c it reads has been emitted;
+ *   5. whitening with the FIR h (Kh taps, odd), centred:
+ *      w[n] = sum_j h[j] d[n + j - (Kh-1)/2], d[m < 0] = 0, computed as soon
+ *      as its inputs exist;
+ *   6. BBHnet on the newest bbh_len whitened samples of every detector
+ *      (channel = detector, w[n < 0] = 0), giving one logit.
+ * Steps 4-6 are readings: the paper gives neither the resampler nor the exact
+ * sample alignment.  Snapshots of one stream run in submission order, at most
+ * one per tick; snapshots of different streams share ticks.  Each tick is one
+ * CUDA-graph launch (when use_graphs) of the batch rounded up to a bucket.
+ *
+ * Ownership: the server copies weights handles (the models and FIRs must
+ * outlive it); submit copies the inputs before it returns; clean_out and
+ * score_out are written by the server's completion thread and must stay
+ * valid until gw_server_wait for the ticket returns GW_OK (or the server is
+ * destroyed).  All calls are thread-safe. */
+typedef struct gw_server* gw_server_t;
+typedef struct gw_server_desc {
+  int n_det;        /* detectors per stream, 1 or 2 (BBHnet's input channels) */
+  int n_witness;    /* witness channels per detector */
+  int window;       /* DeepClean window W (samples at the input rate) */
+  int max_stride;   /* largest stride a stream may open with (multiple of 8) */
+  int max_streams;  /* slot-table size: streams open at once */
+  int max_batch;    /* most snapshots in one tick (1 .. max_streams) */
+  int max_pending;  /* request slots: submitted, not yet completed (>= max_batch) */
+  int agg_mode;     /* enum gw_agg_mode */
+  int agg_delay;    /* 0 <= agg_delay <= window - max_stride */
+  int bbh_len;      /* BBHnet input length at the resampled rate */
+  int max_wait_us;  /* a tick waits up to this long for max_batch snapshots (0 = launch when the device is free) */
+  int max_inflight; /* ticks queued on the device at once, 1 .. 4 */
+  int use_graphs;   /* 1 = each tick is one CUDA-graph launch; 0 = eager launches */
+} gw_server_desc;
+typedef struct gw_server_stats {
+  int64_t snapshots;      /* completed since the last reset */
+  int64_t ticks;          /* device ticks since the last reset */
+  int64_t kernels;        /* kernels launched by those ticks */
+  double mean_batch;      /* snapshots per tick */
+  double p50_us, p99_us, mean_us, max_us;  /* submit -> result latency */
+  double busy_s;          /* wall time from the first submit to the last completion */
+} gw_server_stats;
+/* deepclean: n_det models (same precision, n_in = n_witness); bbhnet: a
+ * BBHnet with n_in = n_det, or NULL to skip scoring (score_out gets NaN);
+ * decimator / whitening: FIRs with odd tap counts (their FP32 taps are used).
+ * Preallocates the tick workspace for max_batch snapshots (GW_EBUDGET if it
+ * does not fit) and captures the graphs. */
+int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* deepclean, gw_model_t bbhnet,
+                     gw_fir_t decimator, gw_fir_t whitening, gw_server_t* out);
+/* Opens a stream with the given stride (a multiple of 8, and of the first
+ * DeepClean layer's phase count for BF16; <= max_stride; divides window).
+ * Its device state is allocated now against the context's budget:
+ * GW_EBUDGET if it does not fit, GW_ESTATE if every slot is taken. */
+int gw_server_open(gw_server_t s, int stride, int* stream_id);
+/* Waits for the stream's snapshots in flight, then frees its state and slot.
+ * GW_ESTATE if snapshots of it are still pending. */
+int gw_server_close(gw_server_t s, int stream_id);
+/* Bytes of device state one stream of this stride takes. */
+int64_t gw_server_stream_bytes(gw_server_t s, int stride);
+/* Queues one snapshot: witness [n_det][n_witness][stride], strain
+ * [n_det][stride] (host FP32); results: clean_out [n_det][stride] (host),
+ * score_out one float (host, may be NULL).  Blocks while every request slot
+ * is taken (GW_ETIMEOUT after 10 s).  GW_ENONFINITE: a non-finite input
+ * sample (nothing is queued). */
+int gw_server_submit(gw_server_t s, int stream_id, const float* witness, const float* strain, float* clean_out,
+                     float* score_out, uint64_t* ticket);
+/* GW_OK once the ticket's results are written; GW_ETIMEOUT after timeout_us
+ * (< 0 = no limit); GW_EINVAL for a ticket never issued; the server's sticky
+ * device error (GW_ETIMEOUT / GW_ECUDA) if a tick failed. */
+int gw_server_wait(gw_server_t s, uint64_t ticket, int64_t timeout_us);
+int gw_server_stats_read(gw_server_t s, int reset, gw_server_stats* out);
+/* Replays an arrival schedule from a host thread of the library (a load
+ * generator whose pace does not depend on the caller's language): request i
+ * of stream ids[i] is submitted at t0 + t_us[i] (non-decreasing), with the
+ * inputs witness[i], strain[i] and outputs clean[i], score[i]; then all are
+ * waited for.  latency_us[i] (may be NULL) receives submit -> completion
+ * time.  Returns GW_OK or the first error. */
+int gw_server_replay(gw_server_t s, int n, const int* ids, const double* t_us, const float* const* witness,
+                     const float* const* strain, float* const* clean, float* score, double* latency_us);
+/* Stops the loop after the queued work, frees every stream and the workspace. */
+int gw_server_destroy(gw_server_t s);
 
 /* ---- instrumentation ---------------------------------------------------------
  * Process-wide, for benchmarks.  gw_profile_enable(1) clears the record and

@@ -26,7 +26,14 @@ struct ProfRec {
 };
 static std::vector<ProfRec> g_prof;
 
+// While a CUDA graph is being captured on this thread, launches are neither
+// counted nor timed here: the graph's kernels are counted at each replay.
+static thread_local bool g_capturing = false;
+void prof_set_capturing(bool on) { g_capturing = on; }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 Prof::Prof(const char* name, cudaStream_t s) : slot(-1), st(s) {
+  if (g_capturing) return;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_prof_on) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -215,7 +222,7 @@ static const char* kDcNames[8] = {"conv_f32.enc1", "conv_f32.enc2", "conv_f32.en
 // DeepClean on B windows in FP32.  Input element (b, c, t) at
 // x + b*xb + c*xc + t; the first layer standardises when mean != null.
 void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
-                   float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st, const int64_t* item_off) {
+                   float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st, const float* const* item_ptr) {
   const auto& Ls = m->layers;
   const float* in = x;
   int64_t ib = xb, ic = xc;
@@ -236,7 +243,7 @@ void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool sta
     a.w = Ls[li].w; a.bias = Ls[li].b;
     a.in_mean = (li == 0 && standardise) ? m->in_mean : nullptr;
     a.in_istd = (li == 0 && standardise) ? m->in_istd : nullptr;
-    a.item_off = li == 0 ? item_off : nullptr;
+    a.item_ptr = li == 0 ? item_ptr : nullptr;
     a.B = B; a.lin = lin; a.lout = lout; a.s = s;
     {
       Prof p(kDcNames[li], st);
@@ -377,16 +384,24 @@ void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* w
     const int next_P = blk < 3 ? Ls[1 + 3 * (blk + 1)].pin : 1;
     TcOut a = blocked_out(buf[a_i], c1.s.cout, l2, c2.pin);
     TcOut o = blocked_out(buf[o_i], c2.s.cout, l2, next_P);
-    Prof p("conv_tc.bbhnet", st);
-    launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
-    launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
+    {
+      Prof p("conv_tc.bbhnet", st);
+      launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
+    }
+    {
+      Prof p("conv_tc.bbhnet", st);
+      launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
+    }
     TcOut o2 = o;
     o2.res = o.p;
     o2.rbstride = o.bstride;
     o2.rgstride = o.gstride;
     o2.rpstride = o.pstride;
     o2.rP = o.P;
-    launch_conv_tc(c2, as_input(a, l2), l2, o2, B, m->err, st);
+    {
+      Prof p("conv_tc.bbhnet", st);
+      launch_conv_tc(c2, as_input(a, l2), l2, o2, B, m->err, st);
+    }
     h = o;
     hi = o_i;
     l = l2;
@@ -396,6 +411,7 @@ void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* w
 }
 
 size_t bbhnet_tc_ws_bytes(int B, int L) { return (size_t)B * 8 * L * 2 + 3 * (size_t)B * 32 * L * 2; }
+size_t bbhnet_f32_ws_bytes(int B, int L) { return 3 * (size_t)B * 32 * L * 4; }
 
 }  // namespace gw
 
@@ -445,23 +461,6 @@ static T* salloc(gw_stream* s, size_t count) {
 }  // namespace gw
 
 using namespace gw;
-
-#define GW_API_BEGIN try {
-#define GW_API_END                                                  \
-  }                                                                 \
-  catch (const gw::Error& e) {                                      \
-    gw::set_last_error(e.what());                                   \
-    return e.code;                                                  \
-  }                                                                 \
-  catch (const std::bad_alloc&) {                                   \
-    gw::set_last_error("host allocation failed");                   \
-    return GW_ENOMEM;                                               \
-  }                                                                 \
-  catch (const std::exception& e) {                                 \
-    gw::set_last_error(e.what());                                   \
-    return GW_EINVAL;                                               \
-  }                                                                 \
-  return GW_OK;
 
 extern "C" {
 
@@ -677,23 +676,16 @@ int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, v
   GW_API_END
 }
 
-int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps, int precision,
-                            gw_fir_t* out) {
+// Uploads FP64-designed taps (and, for BF16, their Toeplitz conv lowering).
+static gw_fir* fir_from_taps(gw_ctx_t ctx, std::vector<double> taps, int precision) {
+  const int ntaps = (int)taps.size();
   gw_fir* f = nullptr;
-  GW_API_BEGIN
-  GW_CHECK_ARG(ctx && psd && out, "NULL argument");
-  *out = nullptr;
-  GW_CHECK_ARG(n_psd >= 3 && fs > 0, "bad PSD grid");
-  const int N = 2 * (n_psd - 1);
-  GW_CHECK_ARG(ntaps >= 1 && (ntaps & 1) && ntaps <= N, "ntaps must be odd and <= nfft");
-  GW_CHECK_ARG(precision == GW_FP32 || precision == GW_BF16, "FIR precision must be FP32 or BF16");
-  for (int j = 0; j < n_psd; ++j) GW_CHECK_ARG(psd[j] > 0 && std::isfinite(psd[j]), "PSD must be positive and finite");
   GW_CUDA(cudaSetDevice(ctx->device));
   f = new gw_fir();
   f->ctx = ctx;
   f->ntaps = ntaps;
   f->precision = precision;
-  f->taps = design_whitening(psd, n_psd, fs, ntaps);
+  f->taps = std::move(taps);
   std::vector<float> t32(f->taps.begin(), f->taps.end());
   try {
     f->d_taps = (float*)dev_alloc(ctx, t32.size() * 4, &f->bytes);
@@ -724,11 +716,49 @@ int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double f
     }
   } catch (...) {
     gw_fir_destroy(f);
-    f = nullptr;
     throw;
   }
-  *out = f;
-  f = nullptr;
+  return f;
+}
+
+// Hann-windowed sinc low-pass normalised to unit gain at DC, in FP64.
+static std::vector<double> design_lowpass(double fc, double fs, int ntaps) {
+  std::vector<double> h(ntaps);
+  const double c = 0.5 * (ntaps - 1), nu = 2.0 * fc / fs;
+  double sum = 0.0;
+  for (int j = 0; j < ntaps; ++j) {
+    const double x = nu * (j - c);
+    const double sinc = x == 0.0 ? 1.0 : std::sin(M_PI * x) / (M_PI * x);
+    const double win = ntaps > 1 ? 0.5 - 0.5 * std::cos(2.0 * M_PI * j / (ntaps - 1)) : 1.0;
+    h[j] = nu * sinc * win;
+    sum += h[j];
+  }
+  for (double& v : h) v /= sum;
+  return h;
+}
+
+int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps, int precision,
+                            gw_fir_t* out) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && psd && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(n_psd >= 3 && fs > 0, "bad PSD grid");
+  const int N = 2 * (n_psd - 1);
+  GW_CHECK_ARG(ntaps >= 1 && (ntaps & 1) && ntaps <= N, "ntaps must be odd and <= nfft");
+  GW_CHECK_ARG(precision == GW_FP32 || precision == GW_BF16, "FIR precision must be FP32 or BF16");
+  for (int j = 0; j < n_psd; ++j) GW_CHECK_ARG(psd[j] > 0 && std::isfinite(psd[j]), "PSD must be positive and finite");
+  *out = fir_from_taps(ctx, design_whitening(psd, n_psd, fs, ntaps), precision);
+  GW_API_END
+}
+
+int gw_fir_create_lowpass(gw_ctx_t ctx, double fc, double fs, int ntaps, int precision, gw_fir_t* out) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(fs > 0 && fc > 0 && fc < 0.5 * fs, "cutoff must lie in (0, fs / 2)");
+  GW_CHECK_ARG(ntaps >= 1 && (ntaps & 1) && ntaps <= 65537, "ntaps must be odd and <= 65537");
+  GW_CHECK_ARG(precision == GW_FP32 || precision == GW_BF16, "FIR precision must be FP32 or BF16");
+  *out = fir_from_taps(ctx, design_lowpass(fc, fs, ntaps), precision);
   GW_API_END
 }
 
@@ -827,6 +857,8 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
         s->ring_f32[i] = salloc<float>(s, (size_t)C * 2 * s->R);
       else
         s->ring_bf16[i] = salloc<__nv_bfloat16>(s, (size_t)G * 2 * s->R * 8);
+      launch_ring_fill(prec == GW_FP32 ? (void*)s->ring_f32[i] : (void*)s->ring_bf16[i], prec != GW_FP32, (int)C, G,
+                       2 * s->R, deepclean[i]->in_mean, deepclean[i]->in_istd, nullptr);
       s->strain[i] = salloc<float>(s, (size_t)s->R);
       s->acc[i] = salloc<float>(s, (size_t)s->R);
     }
@@ -839,6 +871,7 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
     s->stage_out = salloc<float>(s, (size_t)d->n_det * nb * S);
     s->status = salloc<int>(s, 2);
     s->err = s->status + 1;
+    GW_CUDA(cudaDeviceSynchronize());
   } catch (...) {
     stream_free(s);
     s = nullptr;

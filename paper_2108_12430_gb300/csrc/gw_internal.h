@@ -30,6 +30,24 @@ void set_last_error(const std::string& msg);
   } while (0)
 #define GW_LAUNCH_CHECK() GW_CUDA(cudaGetLastError())
 
+// Body of every extern "C" entry point: no exception crosses the ABI.
+#define GW_API_BEGIN try {
+#define GW_API_END                                \
+  }                                               \
+  catch (const gw::Error& e) {                    \
+    gw::set_last_error(e.what());                 \
+    return e.code;                                \
+  }                                               \
+  catch (const std::bad_alloc&) {                 \
+    gw::set_last_error("host allocation failed"); \
+    return GW_ENOMEM;                             \
+  }                                               \
+  catch (const std::exception& e) {               \
+    gw::set_last_error(e.what());                 \
+    return GW_EINVAL;                             \
+  }                                               \
+  return GW_OK;
+
 // ---- layer description ----------------------------------------------------
 enum Act { ACT_NONE = 0, ACT_TANH = 1, ACT_RELU = 2 };
 
@@ -121,6 +139,8 @@ struct Prof {
   int slot;
   cudaStream_t st;
 };
+void prof_set_capturing(bool on);  // this thread is capturing a CUDA graph
+void add_launches(int64_t n);      // kernels launched by a graph replay
 
 // ---- device memory accounting --------------------------------------------
 void* dev_alloc(gw_ctx* ctx, size_t bytes, size_t* counter);
@@ -133,7 +153,7 @@ struct ConvF32Args {
   const float* res; int64_t rb, rc;   // optional residual added before the activation
   const float* w; const float* bias;  // folded weights [C_out][C_in][K], bias [C_out]
   const float* in_mean; const float* in_istd;  // optional input standardisation
-  const int64_t* item_off;            // optional device table: element offset of item b (replaces b*xb)
+  const float* const* item_ptr;       // optional device table: address of item b's (0, 0) (replaces x + b*xb)
   int B, lin, lout;
   LayerSpec s;
 };
@@ -147,13 +167,14 @@ void launch_gap_linear_f32(const float* h, int64_t hb, int64_t hc, int B, int C,
 // at x + b*xb + c*xc + t, output [B][y_ld]; buf0 / buf1 each hold B*8*L floats.
 void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool standardise, int B, int L,
                    float* y, int64_t y_ld, float* buf0, float* buf1, cudaStream_t st,
-                   const int64_t* item_off = nullptr);
+                   const float* const* item_ptr = nullptr);
 
 // ---- model runners (api.cu) ------------------------------------------------------
 struct TcIn;
 struct TcOut;
 void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st);
 size_t bbhnet_tc_ws_bytes(int B, int L);
+size_t bbhnet_f32_ws_bytes(int B, int L);
 
 // ---- stream kernels (k_stream.cu) -------------------------------------------
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring,
@@ -164,6 +185,10 @@ void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float*
 void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n,
                            __nv_bfloat16* ring, int64_t R, int64_t head, int P, const float* mean,
                            const float* istd, int* status, cudaStream_t st);
+// Sets every position of a witness ring (2R = R2 positions per channel) to
+// the standardised zero sample (-mean_c / std_c), or to 0 when mean is null.
+void launch_ring_fill(void* ring, int bf16, int C, int G, int64_t R2, const float* mean, const float* istd,
+                      cudaStream_t st);
 void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head,
                         int* status, cudaStream_t st);
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R,
@@ -183,9 +208,10 @@ struct TcIn {
   const void* p;
   int64_t off0, bstride, boff, gstride, pstride;
   int P, L;
-  // optional device table: element offset of item b (replaces off0 + b*bstride
-  // + b*boff*cg), so that one launch reads windows of many streams' rings
-  const int64_t* item_off = nullptr;
+  // optional device table: address of element (b, 0, 0) of item b (replaces
+  // base + off0 + b*bstride + b*boff*cg), so that one launch reads windows of
+  // many streams' rings
+  const void* const* item_ptr = nullptr;
 };
 struct TcOut {
   void* p;               // blocked activations, or FP32 [B][bstride] when fp32_single

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) conv_f32_kernel(ConvF32Args a, int C
 #pragma unroll
     for (int j = 0; j < kPPT; ++j) acc[c][j] = 0.f;
 
-  const float* xb = a.x + (a.item_off ? a.item_off[b] : (int64_t)b * a.xb);
+  const float* xb = a.item_ptr ? a.item_ptr[b] : a.x + (int64_t)b * a.xb;
   for (int ci0 = 0; ci0 < s.cin; ci0 += CI) {
     __syncthreads();
     for (int e = tid; e < CI * span; e += kThreads) {

@@ -138,7 +138,46 @@ int grid_for(int64_t n) {
   return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
 }
 
+// Every position of a witness ring set to the standardised value of a zero
+// sample, (0 - mean_c) / std_c (0 in padding channels): the stream's missing
+// past counts as zero input, which the model's standardisation maps here.
+// bf16: rows of 8 channels, G groups x R2 rows (the phase-plane order does
+// not matter, every row of a group holds the same value); fp32: [C][R2].
+__global__ void ring_fill_kernel(void* __restrict__ ring, int bf16, int C, int G, int64_t R2,
+                                 const float* __restrict__ mean, const float* __restrict__ istd) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (bf16) {
+    uint4* rows = reinterpret_cast<uint4*>(ring);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)G * R2; e += stride) {
+      const int grp = (int)(e / R2);
+      __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = grp * 8 + j;
+        v8[j] = __float2bfloat16_rn(c < C ? -mean[c] * istd[c] : 0.f);
+      }
+      rows[e] = *reinterpret_cast<const uint4*>(v8);
+    }
+  } else {
+    float* r = reinterpret_cast<float*>(ring);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)C * R2; e += stride) {
+      const int c = (int)(e / R2);
+      r[e] = -mean[c] * istd[c];
+    }
+  }
+}
+
 }  // namespace
+
+void launch_ring_fill(void* ring, int bf16, int C, int G, int64_t R2, const float* mean, const float* istd,
+                      cudaStream_t st) {
+  if (!mean) {
+    GW_CUDA(cudaMemsetAsync(ring, 0, (size_t)(bf16 ? (int64_t)G * R2 * 16 : (int64_t)C * R2 * 4), st));
+    return;
+  }
+  ring_fill_kernel<<<304, 256, 0, st>>>(ring, bf16, C, G, R2, mean, istd);
+  GW_LAUNCH_CHECK();
+}
 
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring, int64_t R,
                           int64_t head, const float* mean, const float* istd, int* status, cudaStream_t st) {

@@ -77,8 +77,7 @@ struct TcParams {
   int coutp_log, out_P_log, res_P_log;  // power-of-two shifts for the epilogue addressing
   int min_plen;                          // rows of the shortest input plane
   int fp32_d2s;                          // write the 8 channels of position u as FP32 samples 8u..8u+7
-  const int64_t* item_off;               // optional per-item element offsets of the input
-  int in_esz;                            // input element size (bytes)
+  const char* const* item_ptr;           // optional per-item input addresses (window start)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -283,8 +282,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
       const int m0 = (t - b * p.tiles_per_item) * 128 * p.MT;
       const int base = m0 + p.dmin;
       const uint32_t sAs = sA + (uint32_t)s * (uint32_t)p.a_bytes;
-      const char* src0 = p.item_off
-                             ? p.in + p.item_off[b] * p.in_esz + (int64_t)base * 16
+      const char* src0 = p.item_ptr
+                             ? p.item_ptr[b] + (int64_t)base * 16
                              : p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)base + (int64_t)b * p.in_boff) * 16;
       if (base >= 0 && base + p.rows <= p.min_plen) {
         // interior tile: every plane is one full run of rows
@@ -769,8 +768,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.in_off0 = in.off0 * esz;
   q.in_b = in.bstride * esz;
   q.in_boff = in.boff;
-  q.item_off = in.item_off;
-  q.in_esz = esz;
+  q.item_ptr = reinterpret_cast<const char* const*>(in.item_ptr);
   q.in_g = in.gstride * esz;
   q.in_p = in.pstride * esz;
   q.in_P = in.P;

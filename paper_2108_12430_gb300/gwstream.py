@@ -38,7 +38,9 @@ EXPORTS = (
     "gw_fir_create_whitening", "gw_fir_destroy", "gw_fir_ntaps", "gw_fir_taps", "gw_whiten",
     "gw_stream_create", "gw_stream_destroy", "gw_stream_push", "gw_stream_head", "gw_stream_status",
     "gw_profile_enable", "gw_profile_read", "gw_launch_count", "gw_deepclean_forward_noalloc",
-    "gw_model_status", "gw_tc_inspect",
+    "gw_model_status", "gw_tc_inspect", "gw_fir_create_lowpass",
+    "gw_server_create", "gw_server_open", "gw_server_close", "gw_server_stream_bytes", "gw_server_submit",
+    "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
 )
 
 
@@ -58,6 +60,18 @@ class gw_model_desc(C.Structure):
 class gw_stream_desc(C.Structure):
     _fields_ = [("n_det", C.c_int), ("n_witness", C.c_int), ("window", C.c_int), ("stride", C.c_int),
                 ("max_batch", C.c_int), ("agg_mode", C.c_int), ("agg_delay", C.c_int)]
+
+
+class gw_server_desc(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("n_det", "n_witness", "window", "max_stride", "max_streams", "max_batch",
+                                        "max_pending", "agg_mode", "agg_delay", "bbh_len", "max_wait_us",
+                                        "max_inflight", "use_graphs")]
+
+
+class gw_server_stats(C.Structure):
+    _fields_ = [("snapshots", C.c_int64), ("ticks", C.c_int64), ("kernels", C.c_int64), ("mean_batch", C.c_double),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double),
+                ("busy_s", C.c_double)]
 
 
 _lib = None
@@ -96,6 +110,16 @@ def _declare(lib):
         "gw_model_status": (I, [P, P]),
         "gw_tc_inspect": (I, [C.POINTER(C.c_int), I, C.POINTER(C.c_double), I, I, I, I, P, SZ,
                               C.POINTER(C.c_uint32), I, C.POINTER(C.c_int)]),
+        "gw_fir_create_lowpass": (I, [P, C.c_double, C.c_double, I, I, C.POINTER(P)]),
+        "gw_server_create": (I, [P, C.POINTER(gw_server_desc), C.POINTER(P), P, P, P, C.POINTER(P)]),
+        "gw_server_open": (I, [P, I, C.POINTER(I)]),
+        "gw_server_close": (I, [P, I]),
+        "gw_server_stream_bytes": (I64, [P, I]),
+        "gw_server_submit": (I, [P, I, P, P, P, P, C.POINTER(C.c_uint64)]),
+        "gw_server_wait": (I, [P, C.c_uint64, I64]),
+        "gw_server_stats_read": (I, [P, I, C.POINTER(gw_server_stats)]),
+        "gw_server_replay": (I, [P, I, P, P, P, P, P, P, P]),
+        "gw_server_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -196,6 +220,12 @@ def gw_fir_create_whitening(ctx, psd, fs, ntaps, precision=GW_FP32):
     return h
 
 
+def gw_fir_create_lowpass(ctx, fc, fs, ntaps, precision=GW_FP32):
+    h = P()
+    _check(lib().gw_fir_create_lowpass(ctx, fc, fs, ntaps, precision, C.byref(h)))
+    return h
+
+
 def gw_fir_destroy(f):
     _check(lib().gw_fir_destroy(f))
 
@@ -243,6 +273,71 @@ def gw_stream_head(s):
 
 def gw_stream_status(s, stream=0):
     return lib().gw_stream_status(s, stream or None)
+
+
+def gw_server_create(ctx, deepclean, bbhnet, decimator, whitening, *, n_det, n_witness, window, max_stride,
+                     max_streams, max_batch, max_pending=0, agg_mode=GW_AGG_AVERAGE, agg_delay=0, bbh_len=2048,
+                     max_wait_us=0, max_inflight=2, use_graphs=1):
+    d = gw_server_desc(n_det, n_witness, window, max_stride, max_streams, max_batch,
+                       max_pending or 4 * max_batch, agg_mode, agg_delay, bbh_len, max_wait_us, max_inflight,
+                       use_graphs)
+    arr = (P * 2)(*(list(deepclean) + [None] * (2 - len(deepclean))))
+    h = P()
+    _check(lib().gw_server_create(ctx, C.byref(d), arr, bbhnet, decimator, whitening, C.byref(h)))
+    return h
+
+
+def gw_server_open(s, stride):
+    sid = I()
+    _check(lib().gw_server_open(s, stride, C.byref(sid)))
+    return sid.value
+
+
+def gw_server_close(s, sid):
+    _check(lib().gw_server_close(s, sid))
+
+
+def gw_server_stream_bytes(s, stride):
+    return _check(lib().gw_server_stream_bytes(s, stride))
+
+
+def gw_server_submit(s, sid, witness, strain, clean_out, score_out=None):
+    """witness [n_det][C][S], strain [n_det][S], clean_out [n_det][S], score_out [1]: float32 numpy arrays that
+    must stay alive until gw_server_wait returns for the ticket."""
+    for a in (witness, strain, clean_out) + ((score_out,) if score_out is not None else ()):
+        assert a.dtype == np.float32 and a.flags.c_contiguous
+    t = C.c_uint64()
+    _check(lib().gw_server_submit(s, sid, witness.ctypes.data, strain.ctypes.data, clean_out.ctypes.data,
+                                  score_out.ctypes.data if score_out is not None else None, C.byref(t)))
+    return t.value
+
+
+def gw_server_wait(s, ticket, timeout_us=-1):
+    _check(lib().gw_server_wait(s, ticket, timeout_us))
+
+
+def gw_server_stats_read(s, reset=False):
+    st = gw_server_stats()
+    _check(lib().gw_server_stats_read(s, 1 if reset else 0, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in gw_server_stats._fields_}
+
+
+def gw_server_replay(s, ids, t_us, witness, strain, clean, score=None, latency_us=None):
+    """ids int32 [n], t_us float64 [n]; witness / strain / clean: lists of float32 arrays (one per request);
+    score float32 [n] and latency_us float64 [n] optional outputs."""
+    n = len(ids)
+    ids = np.ascontiguousarray(ids, np.int32)
+    t_us = np.ascontiguousarray(t_us, np.float64)
+    wp = np.array([a.ctypes.data for a in witness], np.uint64)
+    sp = np.array([a.ctypes.data for a in strain], np.uint64)
+    cp = np.array([a.ctypes.data for a in clean], np.uint64)
+    _check(lib().gw_server_replay(s, n, ids.ctypes.data, t_us.ctypes.data, wp.ctypes.data, sp.ctypes.data,
+                                  cp.ctypes.data, score.ctypes.data if score is not None else None,
+                                  latency_us.ctypes.data if latency_us is not None else None))
+
+
+def gw_server_destroy(s):
+    _check(lib().gw_server_destroy(s))
 
 
 def gw_profile_enable(on=True):

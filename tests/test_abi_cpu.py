@@ -43,3 +43,19 @@ def test_error_paths_without_gpu():
     assert lib.gw_model_destroy(None) == gwstream.GW_EINVAL
     assert lib.gw_stream_push(None, 1, None, None, None, 0, None) == gwstream.GW_EINVAL
     assert gwstream.gw_version().startswith("gwstream")
+
+
+def test_server_error_paths_without_gpu():
+    lib = gwstream.lib()
+    h = ctypes.c_void_p()
+    sid = ctypes.c_int()
+    assert lib.gw_server_create(None, None, None, None, None, None, ctypes.byref(h)) == gwstream.GW_EINVAL
+    assert lib.gw_server_open(None, 256, ctypes.byref(sid)) == gwstream.GW_EINVAL
+    assert lib.gw_server_close(None, 0) == gwstream.GW_EINVAL
+    assert lib.gw_server_submit(None, 0, None, None, None, None, None) == gwstream.GW_EINVAL
+    assert lib.gw_server_wait(None, 1, 0) == gwstream.GW_EINVAL
+    assert lib.gw_server_stats_read(None, 0, None) == gwstream.GW_EINVAL
+    assert lib.gw_server_destroy(None) == gwstream.GW_EINVAL
+    assert lib.gw_server_stream_bytes(None, 256) == gwstream.GW_EINVAL
+    assert lib.gw_fir_create_lowpass(None, 900.0, 4096.0, 127, 0, ctypes.byref(h)) == gwstream.GW_EINVAL
+    assert b"NULL" in lib.gw_last_error()

@@ -95,6 +95,13 @@ def test_stream_two_detectors_bf16(ctx):
         assert rel_l2(g, ref) <= TOL16
 
 
+def test_stream_standardised_input_bf16(ctx):
+    W, S = 1024, 128
+    for g, ref in run_stream_case(ctx, W, S, [2, 3, 1, 4], G.GW_AGG_AVERAGE, W - S, seed=4, n_det=2,
+                                  precision=G.GW_BF16, standardise=True):
+        assert rel_l2(g, ref) <= TOL16
+
+
 @pytest.mark.parametrize("B,L", [(3, 2048), (2, 512), (1, 16)])
 def test_bbhnet_bf16(ctx, B, L):
     x = np.random.default_rng(B * 1000 + L).standard_normal((B, 2, L))

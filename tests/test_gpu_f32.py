@@ -123,12 +123,20 @@ def test_whiten_fp32(ctx, B, C, L_in):
         assert rel_l2(yr[r], ofir.fir_valid(xr[r], h)) <= TOL32
 
 
-def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G.GW_FP32):
-    """Push the given batch sizes through a stream; compare with the oracle."""
+def stream_standardisation(seed, d):
+    r = np.random.default_rng(1000 + seed + d)
+    return r.normal(0, 0.2, 21).astype(np.float32), r.uniform(0.7, 1.4, 21).astype(np.float32)
+
+
+def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G.GW_FP32, standardise=False):
+    """Push the given batch sizes through a stream; compare with the oracle.
+    With standardise, the models carry input mean / std, and the missing past
+    before time 0 is a zero input sample that the model standardises."""
     n_total = sum(pushes)
     wit = [synth.witness_channels(seed + 10 * d, 21, n_total * S) for d in range(n_det)]
     strn = [synth.coupled_strain(seed + 10 * d, wit[d]) for d in range(n_det)]
-    models = [ctx.deepclean(seed + d, precision) for d in range(n_det)]
+    ms = [stream_standardisation(seed, d) if standardise else (None, None) for d in range(n_det)]
+    models = [ctx.deepclean(seed + d, precision, *ms[d]) for d in range(n_det)]
     s = G.gw_stream_create(ctx.h, models, n_det, 21, W, S, max(pushes), mode, delta)
     ctx.objs.append((G.gw_stream_destroy, s))
     got = [[] for _ in range(n_det)]
@@ -149,7 +157,8 @@ def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G
         w32 = wit[d].astype(np.float32).astype(np.float64)
         s32 = strn[d].astype(np.float32).astype(np.float64)
         params = synth.deepclean_params(seed + d)
-        fwd = lambda wins: nets.deepclean_forward(wins, params, synth.DEEPCLEAN_LAYERS)
+        mean, std = [None if a is None else a.astype(np.float64) for a in ms[d]]
+        fwd = lambda wins: nets.deepclean_forward(wins, params, synth.DEEPCLEAN_LAYERS, mean, std)
         snaps = None
         if mode == ostream.LATEST:
             snaps = list(range(n_total))
@@ -172,6 +181,13 @@ def test_stream_matches_oracle_fp32(ctx, mode, delta):
 def test_stream_two_detectors_fp32(ctx):
     W, S = 512, 64
     for g, ref in run_stream_case(ctx, W, S, [2, 6, 1, 8], G.GW_AGG_AVERAGE, W - S, seed=3, n_det=2):
+        assert rel_l2(g, ref) <= TOL32
+
+
+@pytest.mark.parametrize("mode,delta", [(G.GW_AGG_LATEST, 0), (G.GW_AGG_AVERAGE, 1024 - 128)])
+def test_stream_standardised_input_fp32(ctx, mode, delta):
+    W, S = 1024, 128
+    for g, ref in run_stream_case(ctx, W, S, [2, 3, 1, 4], mode, delta, seed=4, n_det=2, standardise=True):
         assert rel_l2(g, ref) <= TOL32
 
 
