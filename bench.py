@@ -351,6 +351,7 @@ def gpu_arm(args):
         peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
     traffic = None
     configs = extra_configs(G, torch, dev_index, flush)
+    configs.update(serve_configs(G, dev_index))
     cpu = cpu_baseline(budget_s=args.cpu_seconds)
     line = {
         "metric": METRIC,
@@ -493,6 +494,166 @@ def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
     return out
 
 
+SERVE_STREAMS, SERVE_STRIDES, SERVE_BUDGET = 64, (128, 256, 512), 20 * 2 ** 30
+
+
+def serve_configs(G, dev_index, seconds=1.5, precisions=None):
+    """Config 5: end-to-end serving of 64 concurrent two-detector streams with
+    strides 128 / 256 / 512 (DeepClean 21 x 32768 per detector -> subtract ->
+    resample to 2048 Hz -> whiten (2049 taps) -> BBHnet 2 x 2048), per-stream
+    state on the device admitted under a 20 GB budget, one CUDA-graph launch
+    per tick.  Requests are replayed by the library's native load generator
+    through the public submit / wait calls, host buffers in and out, at three
+    loads: saturation (every stream always has snapshots queued), Poisson
+    arrivals at half the saturated rate, and Poisson arrivals at each stream's
+    real-time rate (4096 / stride snapshots/s).  Latency = submit (or
+    scheduled arrival) -> results written to the caller's buffers.  A stream
+    has at most one snapshot in a tick, so one stream alone cannot go faster
+    than the tick rate; the loaded points give every stream the same rate."""
+    from paper_2108_12430_gb300 import synth
+    out = {}
+    fs2, nfft = 2048.0, 8192
+    _, psd = synth.psd_grid(fs2, nfft)
+    rng = np.random.default_rng(55)
+    pool_n, out_n = 16, 1024
+    pools = {}
+    for S in SERVE_STRIDES:
+        wit = synth.witness_channels(77 + S, C, pool_n * S).reshape(C, pool_n, S).transpose(1, 0, 2)
+        wit = np.ascontiguousarray(np.stack([wit, wit[::-1]], 1), np.float32)          # [pool][2][C][S]
+        strn = np.ascontiguousarray(rng.standard_normal((pool_n, 2, S)) * 0.1, np.float32)
+        pools[S] = (wit, strn, np.zeros((out_n, 2, S), np.float32))
+    stride_of = np.array([SERVE_STRIDES[i % 3] for i in range(SERVE_STREAMS)])
+
+    def addresses(ids, seq):
+        wa, sa, ca = (np.zeros(len(ids), np.uint64) for _ in range(3))
+        for S in SERVE_STRIDES:
+            sel = stride_of[ids] == S
+            w, x, c = pools[S]
+            j = seq[sel]
+            wa[sel] = w.ctypes.data + (j % pool_n).astype(np.uint64) * np.uint64(2 * C * S * 4)
+            sa[sel] = x.ctypes.data + (j % pool_n).astype(np.uint64) * np.uint64(2 * S * 4)
+            ca[sel] = c.ctypes.data + (j % out_n).astype(np.uint64) * np.uint64(2 * S * 4)
+        return wa, sa, ca
+
+    for name, prec in (("bf16", G.GW_BF16), ("fp32", G.GW_FP32)):
+        if precisions and name not in precisions:
+            continue
+        ctx = G.gw_ctx_create(dev_index, SERVE_BUDGET)
+        objs = []
+        try:
+            dcs = [G.gw_model_create(ctx, G.GW_MODEL_DEEPCLEAN, prec, C,
+                                     synth.flatten_params(synth.deepclean_params(1234 + d))) for d in range(2)]
+            layers, head = synth.bbhnet_params(3)
+            bbh = G.gw_model_create(ctx, G.GW_MODEL_BBHNET, prec, 2, synth.flatten_params(layers, head))
+            fdec = G.gw_fir_create_lowpass(ctx, 900.0, 4096.0, 127)
+            fw = G.gw_fir_create_whitening(ctx, psd, fs2, 2049)
+            objs = [(G.gw_model_destroy, m) for m in dcs + [bbh]] + [(G.gw_fir_destroy, fdec), (G.gw_fir_destroy, fw)]
+            srv = G.gw_server_create(ctx, dcs, bbh, fdec, fw, n_det=2, n_witness=C, window=W, max_stride=512,
+                                     max_streams=SERVE_STREAMS, max_batch=SERVE_STREAMS, max_pending=4 * SERVE_STREAMS,
+                                     agg_mode=G.GW_AGG_AVERAGE, agg_delay=W - 512, bbh_len=2048, max_inflight=2)
+            objs.append((G.gw_server_destroy, srv))
+            fixed = G.gw_ctx_bytes_in_use(ctx)
+            per_stream = G.gw_server_stream_bytes(srv, 256)
+            sids = np.array([G.gw_server_open(srv, int(stride_of[i])) for i in range(SERVE_STREAMS)], np.int32)
+            seq_next = np.zeros(SERVE_STREAMS, np.int64)
+
+            def replay(ids, t_us):
+                seq = np.zeros(len(ids), np.int64)
+                for i in range(SERVE_STREAMS):
+                    sel = ids == i
+                    seq[sel] = seq_next[i] + np.arange(sel.sum())
+                    seq_next[i] += sel.sum()
+                wa, sa, ca = addresses(ids, seq)
+                score = np.zeros(len(ids), np.float32)
+                lat = np.zeros(len(ids))
+                G.gw_server_stats_read(srv, reset=True)
+                t0 = time.perf_counter()
+                G.gw_server_replay(srv, sids[ids], t_us, wa, sa, ca, score, lat)
+                wall = time.perf_counter() - t0
+                st = G.gw_server_stats_read(srv, reset=True)
+                assert np.isfinite(score).all()
+                return {"snapshots": len(ids), "snapshots_per_s": len(ids) / wall, "wall_s": wall,
+                        "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                        "max_us": float(lat.max()), "mean_batch": st["mean_batch"],
+                        "kernels_per_tick": st["kernels"] / max(st["ticks"], 1), "ticks": st["ticks"]}
+
+            def saturated(n):
+                # every request is due at once: throughput only (its latency
+                # is the request's place in the flood)
+                n = max(SERVE_STREAMS, n // SERVE_STREAMS * SERVE_STREAMS)
+                r = replay(np.tile(np.arange(SERVE_STREAMS), n // SERVE_STREAMS), np.zeros(n))
+                return {k: v for k, v in r.items() if not k.endswith("_us")}
+
+            def poisson(total_rate, n, realtime_mix=False):
+                # each stream a Poisson source: equal rates, or rates in the
+                # ratio of the streams' real-time rates 4096 / stride
+                w = 4096.0 / stride_of if realtime_mix else np.ones(SERVE_STREAMS)
+                ids = rng.choice(SERVE_STREAMS, size=n, p=w / w.sum())
+                return replay(ids, np.cumsum(rng.exponential(1e6 / total_rate, n)))
+
+            saturated(SERVE_STREAMS * 8)  # warm-up
+            cal = saturated(SERVE_STREAMS * 32)
+            sat = saturated(int(cal["snapshots_per_s"] * seconds))
+            half = poisson(0.5 * sat["snapshots_per_s"], int(0.5 * sat["snapshots_per_s"] * seconds))
+            high = poisson(0.9 * sat["snapshots_per_s"], int(0.9 * sat["snapshots_per_s"] * seconds))
+            rt_rate = float((4096.0 / stride_of).sum())
+            rt = poisson(rt_rate, int(rt_rate * seconds), realtime_mix=True)
+            for sid in sids:
+                G.gw_server_close(srv, int(sid))
+            G.gw_server_destroy(srv)
+            objs.pop()
+            ticks = tick_profile(G, ctx, dcs, bbh, fdec, fw, pools)
+            out[f"config5_{name}"] = {
+                "workload": "serving 64 streams x 2 detectors, strides 128/256/512, DeepClean 21x32768 -> subtract "
+                            "-> 2x resample -> whiten 2049 taps -> BBHnet 2x2048, AVERAGE delay W-512",
+                "streams": SERVE_STREAMS, "budget_bytes": SERVE_BUDGET, "stream_state_bytes": per_stream,
+                "fixed_bytes": fixed, "streams_admissible_under_budget": int((SERVE_BUDGET - fixed) // per_stream),
+                "saturated": sat, "poisson_half_load": half, "poisson_90pct_load": high,
+                "poisson_realtime": dict(rt, rate_per_s=rt_rate), "tick_kernels_eager": ticks,
+                "launch": "one CUDA graph per tick (batch bucket), inputs read from pinned mapped host slots"}
+        finally:
+            for fn, o in reversed(objs):
+                fn(o)
+            G.gw_ctx_destroy(ctx)
+    return out
+
+
+def tick_profile(G, ctx, dcs, bbh, fdec, fw, pools, n_ticks=20):
+    """Per-kernel device time of one tick at batch 1 and at batch 64, from a
+    server launching eagerly (no graph) with the library's event profiler."""
+    srv = G.gw_server_create(ctx, dcs, bbh, fdec, fw, n_det=2, n_witness=C, window=W, max_stride=512,
+                             max_streams=SERVE_STREAMS, max_batch=SERVE_STREAMS, max_pending=4 * SERVE_STREAMS,
+                             agg_mode=G.GW_AGG_AVERAGE, agg_delay=W - 512, bbh_len=2048, max_inflight=1,
+                             use_graphs=0, max_wait_us=50_000)  # a tick launches once `batch` snapshots are queued
+    res = {}
+    try:
+        sids = [G.gw_server_open(srv, 256) for _ in range(SERVE_STREAMS)]
+        wit, strn, outs = pools[256]
+        score = np.zeros(1, np.float32)
+        for batch in (1, SERVE_STREAMS):
+            # the batching window closes when max_batch snapshots are queued or
+            # after 50 ms, so a tick holds exactly `batch` snapshots
+            for rep in range(2):  # warm-up, then profiled
+                G.gw_profile_enable(rep == 1)
+                for t in range(n_ticks):
+                    tk = [G.gw_server_submit(srv, sids[i], wit[t % len(wit)], strn[t % len(strn)],
+                                             outs[(t * batch + i) % len(outs)], score) for i in range(batch)]
+                    for x in tk:
+                        G.gw_server_wait(srv, x, 60_000_000)
+            prof = G.gw_profile_read()
+            G.gw_profile_enable(False)
+            tot = sum(v[0] for v in prof.values()) / n_ticks
+            res[f"batch{batch}"] = {"sum_kernel_ms_per_tick": tot,
+                                    "kernels": {k: round(v[0] / n_ticks * 1e3, 2) for k, v in
+                                                sorted(prof.items(), key=lambda kv: -kv[1][0])},
+                                    "unit": "us per tick (both detector branches summed)"}
+        for sid in sids:
+            G.gw_server_close(srv, sid)
+    finally:
+        G.gw_server_destroy(srv)
+    return res
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle: baseline leg and the reference arm
 # ---------------------------------------------------------------------------
@@ -568,12 +729,20 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--only", choices=["bf16", "fp32"], default=None,
                     help="time one path only (profiling)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="only the serving configuration (config 5); prints its JSON")
     ap.add_argument("--lite", action="store_true",
                     help="timed device pushes only: no e2e, accuracy, CPU baseline or JSON contract line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.serve_only:
+        from paper_2108_12430_gb300 import build as Bld
+        Bld.build()
+        from paper_2108_12430_gb300 import gwstream as G
+        import torch
+        print(json.dumps(serve_configs(G, torch.cuda.current_device(), precisions=args.only and [args.only])))
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

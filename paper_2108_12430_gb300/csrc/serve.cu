@@ -549,22 +549,24 @@ int submit_impl(gw_server* s, int sid, const float* witness, const float* strain
   rq.stream = sid;
   s->streams[sid].pending++;  // keeps the stream from closing while its inputs are copied
   lk.unlock();
-  // copy into the pinned slot, checking finiteness on the way
-  bool finite = true;
+  // copy into the pinned slot; a sample is NaN or Inf iff its exponent bits
+  // are all set, checked as an integer OR-reduction (vectorisable)
+  uint32_t bad = 0;
+  auto copy_check = [&bad](uint32_t* dst, const uint32_t* src, size_t n) {
+    uint32_t b = 0;
+    for (size_t i = 0; i < n; ++i) {
+      const uint32_t u = src[i];
+      dst[i] = u;
+      b |= (uint32_t)((u & 0x7f800000u) == 0x7f800000u);
+    }
+    bad |= b;
+  };
   for (int det = 0; det < nd; ++det) {
-    float* dst = rq.in + (size_t)det * (C + 1) * S;
-    const float* w = witness + (size_t)det * C * S;
-    for (size_t i = 0; i < (size_t)C * S; ++i) {
-      const float v = w[i];
-      finite &= std::isfinite(v);
-      dst[i] = v;
-    }
-    const float* x = strain + (size_t)det * S;
-    for (int i = 0; i < S; ++i) {
-      finite &= std::isfinite(x[i]);
-      dst[(size_t)C * S + i] = x[i];
-    }
+    uint32_t* dst = reinterpret_cast<uint32_t*>(rq.in + (size_t)det * (C + 1) * S);
+    copy_check(dst, reinterpret_cast<const uint32_t*>(witness + (size_t)det * C * S), (size_t)C * S);
+    copy_check(dst + (size_t)C * S, reinterpret_cast<const uint32_t*>(strain + (size_t)det * S), (size_t)S);
   }
+  const bool finite = bad == 0;
   lk.lock();
   if (!finite) {
     rq.stream = -1;

@@ -323,14 +323,14 @@ def gw_server_stats_read(s, reset=False):
 
 
 def gw_server_replay(s, ids, t_us, witness, strain, clean, score=None, latency_us=None):
-    """ids int32 [n], t_us float64 [n]; witness / strain / clean: lists of float32 arrays (one per request);
-    score float32 [n] and latency_us float64 [n] optional outputs."""
+    """ids int32 [n], t_us float64 [n]; witness / strain / clean: lists of float32 arrays (one per request) or
+    uint64 arrays of their host addresses; score float32 [n] and latency_us float64 [n] optional outputs."""
     n = len(ids)
     ids = np.ascontiguousarray(ids, np.int32)
     t_us = np.ascontiguousarray(t_us, np.float64)
-    wp = np.array([a.ctypes.data for a in witness], np.uint64)
-    sp = np.array([a.ctypes.data for a in strain], np.uint64)
-    cp = np.array([a.ctypes.data for a in clean], np.uint64)
+    addr = lambda xs: (np.ascontiguousarray(xs, np.uint64) if isinstance(xs, np.ndarray) and xs.dtype == np.uint64
+                       else np.array([a.ctypes.data for a in xs], np.uint64))
+    wp, sp, cp = addr(witness), addr(strain), addr(clean)
     _check(lib().gw_server_replay(s, n, ids.ctypes.data, t_us.ctypes.data, wp.ctypes.data, sp.ctypes.data,
                                   cp.ctypes.data, score.ctypes.data if score is not None else None,
                                   latency_us.ctypes.data if latency_us is not None else None))
