@@ -304,6 +304,61 @@ int gw_server_replay(gw_server_t s, int n, const int* ids, const double* t_us, c
 /* Stops the loop after the queued work, frees every stream and the workspace. */
 int gw_server_destroy(gw_server_t s);
 
+/* ---- training ---------------------------------------------------------------
+ * DeepClean is retrained regularly on recent data (main text, on the model's
+ * validity and retraining; no loss is given).  Loss (a reading): the
+ * band-limited, inverse-PSD-weighted mean square error
+ *   L = (1 / N) sum_{b,n} r[b][n]^2,   r = g (*) (strain - y_hat)  (valid mode,
+ *   N = B (L - Kg + 1)),
+ * where g is designed by gw_fir_create_band_loss.  BatchNorm uses its running
+ * statistics, so it folds into the weights; the trained parameters are every
+ * layer's raw w, b, gamma, beta in the canonical order of gw_model_create
+ * (running mean / var get gradient 0).  All training calls are FP32 (SIMT
+ * FMA) and stream-ordered on device pointers. */
+typedef struct gw_trainer* gw_trainer_t;
+typedef struct gw_trainer_desc {
+  int n_in;        /* witness channels */
+  int max_batch;   /* largest B of a forward */
+  int length;      /* window length L (multiple of 8) */
+  int checkpoint;  /* 1: keep only the four block inputs and recompute inside the backward */
+} gw_trainer_desc;
+/* in_mean / in_std: host [n_in] input standardisation (may be NULL). */
+int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_mean, const float* in_std,
+                      gw_trainer_t* out);
+int gw_trainer_destroy(gw_trainer_t t);
+/* Length of the flat raw parameter vector (= gw_model_param_count). */
+int64_t gw_trainer_param_count(gw_trainer_t t);
+int64_t gw_trainer_bytes(gw_trainer_t t);
+/* Training forward: params device FP32 raw parameters (caller-owned, read
+ * again by the backward), x device [B][n_in][L] raw witness windows, y_hat
+ * device [B][L].  Folds BatchNorm on the device and keeps the tape for the
+ * next gw_trainer_backward (one forward in flight per trainer). */
+int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int B, float* y_hat, void* cuda_stream);
+/* dy_hat device [B][L] = dLoss/dy_hat; dparams device [param_count] receives
+ * dLoss/dparams of the last forward's parameters (overwritten). */
+int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, void* cuda_stream);
+/* Loss-weight FIR: linear phase, |G(f)|^2 = T(f) S(f_ref) / S(f), T = 1 on
+ * [f1 + ramp, f2 - ramp] with raised-cosine ramps to 0 at f1 and f2, S(f_ref)
+ * interpolated linearly; designed like the whitening filter (centred inverse
+ * real DFT, Hann window, FP64). */
+int gw_fir_create_band_loss(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps, double f1, double f2,
+                            double ramp, double f_ref, int precision, gw_fir_t* out);
+/* loss: device scalar; r: device [B][L - ntaps + 1] (kept for the backward);
+ * strain, y_hat: device [B][L]. */
+int gw_band_loss(gw_fir_t g, const float* strain, const float* y_hat, int B, int L, float* loss, float* r,
+                 void* cuda_stream);
+/* dy_hat = dloss * dL/dy_hat = -(2 dloss / N) sum_k g[k] r[m - k]; dloss a
+ * device scalar or NULL (1). */
+int gw_band_loss_backward(gw_fir_t g, const float* r, int B, int L, const float* dloss, float* dy_hat,
+                          void* cuda_stream);
+/* Adjoint of gw_whiten: dx[b][c][m] = sum_k h[k] dy[b][c][m - k], m < L_in,
+ * dy [B][C][L_in - ntaps + 1]; FP32 taps whatever the FIR's precision. */
+int gw_fir_backward(gw_fir_t f, const float* dy, int B, int C, int L_in, float* dx, void* cuda_stream);
+/* Adam with bias correction on FP32 master parameters (device arrays of n);
+ * step counts from 1. */
+int gw_adam_step(float* params, const float* grads, float* m, float* v, int64_t n, int step, float lr, float beta1,
+                 float beta2, float eps, void* cuda_stream);
+
 /* ---- instrumentation ---------------------------------------------------------
  * Process-wide, for benchmarks.  gw_profile_enable(1) clears the record and
  * brackets every kernel launch the library makes with a pair of CUDA events on

@@ -192,10 +192,14 @@ static void* model_workspace(gw_model* m, size_t bytes) {
 // Zero-phase inverse real DFT of the amplitude A_j = sqrt(2 / (fs S_j)),
 // centred on tap (ntaps-1)/2, truncated and Hann-windowed:
 //   h0[n] = (A_0 + A_{N/2} cos(pi n) + 2 sum_{j=1}^{N/2-1} A_j cos(2 pi j n / N)) / N.
-static std::vector<double> design_whitening(const double* psd, int n_psd, double fs, int ntaps) {
-  const int N = 2 * (n_psd - 1);
-  std::vector<double> A(n_psd), ctab(N);
-  for (int j = 0; j < n_psd; ++j) A[j] = std::sqrt(2.0 / (fs * psd[j]));
+// Zero-phase FIR from real amplitudes A_j on the DFT grid j = 0 .. N/2
+// (N = 2 (n_amp - 1)): the centred inverse real DFT
+//   h0[n] = (A_0 + A_{N/2} (-1)^n + 2 sum_{j=1}^{N/2-1} A_j cos(2 pi j n / N)) / N,
+// n = -(ntaps-1)/2 .. (ntaps-1)/2, times a Hann window over the taps (FP64).
+static std::vector<double> design_zero_phase(const std::vector<double>& A, int ntaps) {
+  const int n_amp = (int)A.size();
+  const int N = 2 * (n_amp - 1);
+  std::vector<double> ctab(N);
   for (int m = 0; m < N; ++m) ctab[m] = std::cos(2.0 * M_PI * (double)m / (double)N);
   const int c = (ntaps - 1) / 2;
   std::vector<double> h(ntaps);
@@ -214,6 +218,39 @@ static std::vector<double> design_whitening(const double* psd, int n_psd, double
     h[k2] = h0 * 0.5 * (1.0 - std::cos(2.0 * M_PI * k2 / (ntaps - 1)));
   }
   return h;
+}
+
+// Whitening: A(f) = sqrt(2 / (fs S(f))), unit variance for a one-sided PSD.
+static std::vector<double> design_whitening(const double* psd, int n_psd, double fs, int ntaps) {
+  std::vector<double> A(n_psd);
+  for (int j = 0; j < n_psd; ++j) A[j] = std::sqrt(2.0 / (fs * psd[j]));
+  return design_zero_phase(A, ntaps);
+}
+
+// Band-limited inverse-PSD loss weight: |G(f)|^2 = T(f) S(f_ref) / S(f), with
+// T a Tukey band (1 on [f1 + ramp, f2 - ramp], raised-cosine ramps to 0 at f1
+// and f2) and S(f_ref) interpolated linearly on the grid.
+static std::vector<double> design_band_loss(const double* psd, int n_psd, double fs, int ntaps, double f1, double f2,
+                                            double ramp, double f_ref) {
+  const int N = 2 * (n_psd - 1);
+  const double df = fs / N;
+  double pos = f_ref / df;
+  pos = std::min(std::max(pos, 0.0), (double)(n_psd - 1));
+  const int j0 = std::min((int)pos, n_psd - 2);
+  const double s_ref = psd[j0] + (pos - j0) * (psd[j0 + 1] - psd[j0]);
+  std::vector<double> A(n_psd);
+  for (int j = 0; j < n_psd; ++j) {
+    const double f = j * df;
+    double T = 0.0;
+    if (f >= f1 + ramp && f <= f2 - ramp)
+      T = 1.0;
+    else if (f > f1 && f < f1 + ramp)
+      T = 0.5 * (1.0 - std::cos(M_PI * (f - f1) / ramp));
+    else if (f > f2 - ramp && f < f2)
+      T = 0.5 * (1.0 - std::cos(M_PI * (f2 - f) / ramp));
+    A[j] = std::sqrt(T * s_ref / psd[j]);
+  }
+  return design_zero_phase(A, ntaps);
 }
 
 // ---- forward runners ---------------------------------------------------------
@@ -748,6 +785,22 @@ int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double f
   GW_CHECK_ARG(precision == GW_FP32 || precision == GW_BF16, "FIR precision must be FP32 or BF16");
   for (int j = 0; j < n_psd; ++j) GW_CHECK_ARG(psd[j] > 0 && std::isfinite(psd[j]), "PSD must be positive and finite");
   *out = fir_from_taps(ctx, design_whitening(psd, n_psd, fs, ntaps), precision);
+  GW_API_END
+}
+
+int gw_fir_create_band_loss(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps, double f1, double f2,
+                            double ramp, double f_ref, int precision, gw_fir_t* out) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && psd && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(n_psd >= 3 && fs > 0, "bad PSD grid");
+  const int N = 2 * (n_psd - 1);
+  GW_CHECK_ARG(ntaps >= 1 && (ntaps & 1) && ntaps <= N, "ntaps must be odd and <= nfft");
+  GW_CHECK_ARG(f1 >= 0 && ramp > 0 && f1 + 2 * ramp <= f2 && f2 <= 0.5 * fs, "need 0 <= f1, f1 + 2 ramp <= f2 <= fs/2");
+  GW_CHECK_ARG(f_ref >= 0 && f_ref <= 0.5 * fs, "f_ref outside [0, fs/2]");
+  GW_CHECK_ARG(precision == GW_FP32 || precision == GW_BF16, "FIR precision must be FP32 or BF16");
+  for (int j = 0; j < n_psd; ++j) GW_CHECK_ARG(psd[j] > 0 && std::isfinite(psd[j]), "PSD must be positive and finite");
+  *out = fir_from_taps(ctx, design_band_loss(psd, n_psd, fs, ntaps, f1, f2, ramp, f_ref), precision);
   GW_API_END
 }
 

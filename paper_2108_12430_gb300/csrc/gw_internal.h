@@ -154,12 +154,17 @@ struct ConvF32Args {
   const float* w; const float* bias;  // folded weights [C_out][C_in][K], bias [C_out]
   const float* in_mean; const float* in_istd;  // optional input standardisation
   const float* const* item_ptr;       // optional device table: address of item b's (0, 0) (replaces x + b*xb)
+  const float* gy; int64_t gyb, gyc;  // optional: multiply the output by act'(gy) (gy = that activation's output)
+  int gact;
   int B, lin, lout;
   LayerSpec s;
 };
 void launch_conv_f32(const ConvF32Args& a, cudaStream_t st);
+// y[r][n] = scale * sum_k h'[k] x[r][n + k + x_off] for n < lout, x zero outside
+// [0, x_len) (x_len < 0: lout + ntaps - 1, valid mode), h' = h or h reversed.
 void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int rows,
-                    const float* taps, int ntaps, int lout, cudaStream_t st);
+                    const float* taps, int ntaps, int lout, cudaStream_t st, int x_off = 0, int x_len = -1,
+                    int rev = 0, float scale = 1.f);
 void launch_gap_linear_f32(const float* h, int64_t hb, int64_t hc, int B, int C, int L,
                            const float* w, const float* b, float* out, cudaStream_t st);
 

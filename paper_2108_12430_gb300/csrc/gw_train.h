@@ -1,0 +1,55 @@
+// Internal declarations of the training path (train.cu, k_train.cu).
+#pragma once
+
+#include <algorithm>
+
+#include "gw_internal.h"
+
+namespace gw {
+
+constexpr float kBnEps = 1e-5f;
+
+// One layer's raw parameters inside the flat parameter vector (offsets in
+// floats; the BatchNorm ones only when bn) and its folded device copies.
+struct FoldArgs {
+  const float* p;             // raw parameters (device)
+  int64_t off_w, off_b, off_g, off_be, off_mu, off_var;
+  int cin, cout, K, transposed, bn;
+  float* wf;                  // folded [C_out][C_in][K]
+  float* wT;                  // folded, transposed [C_in][C_out][K]
+  float* bf;                  // folded bias [C_out]
+};
+
+// Weight-gradient GEMM: P[chunk][a][c][k] = sum_t A[b][a][t] Bv(b, c, s t + k - p).
+struct WgradArgs {
+  const float* A; int64_t ab, aa; int NA, LA;
+  const float* Bm; int64_t bb, bc; int NC, LB;
+  int K, s, p;
+  int AB, T, chunks_per_b, nj;
+  float* partial;
+};
+
+void launch_fold(const FoldArgs& f, cudaStream_t st);
+// dw_in_major: dWf is [C_in][C_out][K] (transposed conv) instead of [C_out][C_in][K].
+void launch_unfold(const FoldArgs& f, const float* dWf, int dw_in_major, const float* dbf, float* dp,
+                   cudaStream_t st);
+WgradArgs plan_wgrad(int NA, int NC, int K, int s, int LA);
+size_t wgrad_smem(const WgradArgs& w);
+// w.partial must hold B * w.chunks_per_b * NA * NC * K floats; out gets NA * NC * K.
+void launch_wgrad(const WgradArgs& w, int B, float* out, cudaStream_t st);
+// out[n] = sum_{b, t} G[b][n][t]; part holds B * N floats.
+void launch_bias_grad(const float* G, int64_t gb, int64_t gn, int B, int N, int L, float* part, float* out,
+                      cudaStream_t st);
+void launch_standardise(const float* x, int B, int C, int L, const float* mean, const float* istd, float* y,
+                        cudaStream_t st);
+// loss = (1 / (B Lr)) sum r^2 with r = g (*) (strain - y_hat) valid (Lr = L - K + 1);
+// e holds B * L floats, r B * Lr, part B.
+void launch_band_loss(const float* strain, const float* y_hat, int B, int L, const float* taps, int K, float* e,
+                      float* r, float* part, float* loss, cudaStream_t st);
+// dy_hat = dloss * d loss / d y_hat (dloss: device scalar, or null for 1).
+void launch_band_loss_backward(const float* r, int B, int L, const float* taps, int K, const float* dloss,
+                               float* dy_hat, cudaStream_t st);
+void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr, float b1, float b2,
+                 float eps, cudaStream_t st);
+
+}  // namespace gw

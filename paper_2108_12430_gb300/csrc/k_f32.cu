@@ -110,25 +110,37 @@ __global__ void __launch_bounds__(kThreads) conv_f32_kernel(ConvF32Args a, int C
       if (u >= a.lout) continue;
       float v = acc[c][j] + bias;
       if (a.res) v += a.res[(int64_t)b * a.rb + (int64_t)o * a.rc + u];
+      if (a.gy) {
+        // backward: times the derivative of the activation whose output is gy
+        const float yv = a.gy[(int64_t)b * a.gyb + (int64_t)o * a.gyc + u];
+        v *= a.gact == ACT_TANH ? 1.f - yv * yv : (a.gact == ACT_RELU ? (yv > 0.f ? 1.f : 0.f) : 1.f);
+      }
       a.y[(int64_t)b * a.yb + (int64_t)o * a.yc + u] = apply_act(v, s.act);
     }
   }
 }
 
-// Valid-mode FIR: y[r][n] = sum_k h[k] x[r][n + k]; CTA = 1024 outputs of one row.
+// FIR over one row, CTA = 1024 outputs:
+//   y[r][n] = scale * sum_k h'[k] x[r][n + k + x_off],  x zero outside [0, x_len),
+// h' = h (rev = 0) or h reversed (rev = 1).  Valid mode: x_off = 0,
+// x_len = lout + ntaps - 1.  Its adjoint (dx[m] = sum_k h[k] dy[m - k]) is
+// x_off = -(ntaps - 1), rev = 1.
 constexpr int kFirTile = 1024;
 __global__ void __launch_bounds__(kThreads) fir_f32_kernel(const float* __restrict__ x, int64_t x_row,
                                                            float* __restrict__ y, int64_t y_row,
-                                                           const float* __restrict__ h, int ntaps, int lout) {
+                                                           const float* __restrict__ h, int ntaps, int lout,
+                                                           int x_off, int x_len, int rev, float scale) {
   extern __shared__ float smem[];
   float* hs = smem;
   float* xs = smem + ntaps;
   const int r = blockIdx.y, n0 = blockIdx.x * kFirTile;
   const float* xr = x + (int64_t)r * x_row;
   const int span = kFirTile + ntaps - 1;
-  const int lin = lout + ntaps - 1;
-  for (int e = threadIdx.x; e < ntaps; e += kThreads) hs[e] = h[e];
-  for (int e = threadIdx.x; e < span; e += kThreads) xs[e] = (n0 + e < lin) ? xr[n0 + e] : 0.f;
+  for (int e = threadIdx.x; e < ntaps; e += kThreads) hs[e] = h[rev ? ntaps - 1 - e : e];
+  for (int e = threadIdx.x; e < span; e += kThreads) {
+    const int q = n0 + e + x_off;
+    xs[e] = (q >= 0 && q < x_len) ? xr[q] : 0.f;
+  }
   __syncthreads();
   float acc[kFirTile / kThreads];
 #pragma unroll
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) fir_f32_kernel(const float* __restri
 #pragma unroll
   for (int j = 0; j < kFirTile / kThreads; ++j) {
     const int n = n0 + threadIdx.x + j * kThreads;
-    if (n < lout) y[(int64_t)r * y_row + n] = acc[j];
+    if (n < lout) y[(int64_t)r * y_row + n] = scale * acc[j];
   }
 }
 
@@ -192,7 +204,8 @@ void launch_conv_f32(const ConvF32Args& a, cudaStream_t st) {
 }
 
 void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int rows, const float* taps,
-                    int ntaps, int lout, cudaStream_t st) {
+                    int ntaps, int lout, cudaStream_t st, int x_off, int x_len, int rev, float scale) {
+  if (x_len < 0) x_len = lout + ntaps - 1;
   const size_t smem = (size_t)(ntaps + kFirTile + ntaps - 1) * 4;
   GW_CHECK_ARG(smem <= 200 * 1024, "FIR too long for the FP32 kernel");
   static bool attr_set = false;
@@ -201,7 +214,7 @@ void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int 
     attr_set = true;
   }
   dim3 grid((lout + kFirTile - 1) / kFirTile, rows);
-  fir_f32_kernel<<<grid, kThreads, smem, st>>>(x, x_row, y, y_row, taps, ntaps, lout);
+  fir_f32_kernel<<<grid, kThreads, smem, st>>>(x, x_row, y, y_row, taps, ntaps, lout, x_off, x_len, rev, scale);
   GW_LAUNCH_CHECK();
 }
 

@@ -1,0 +1,391 @@
+// DeepClean training step: forward with a tape, band-limited PSD-weighted
+// loss, hand-written backward to the raw (unfolded) parameters, Adam.
+//
+// The paper retrains DeepClean regularly on recent data (main text, model
+// validity and retraining) without giving the loss; the loss here is the
+// reading of the band-limited inverse-PSD-weighted mean square error
+//   L = (1 / N) sum_{b,n} r[b][n]^2,  r = g (*) (s - y_hat)  (valid mode),
+// with |G(f)|^2 = T(f) S(f_ref) / S(f) on the 55-65 Hz band.  BatchNorm runs
+// with its running statistics (eval mode), so it folds into the weights; the
+// trained parameters are the raw w, b, gamma, beta of every layer, kept by the
+// caller in FP32 ("master weights") and folded on the device at every forward.
+//
+// Backward per layer (from the output down), with v = folded conv output and
+// y = act(v):
+//   dv = dy * act'(y)                         (fused into the data gradient)
+//   dW' = wgrad(input, dv), db' = sum dv      (fixed-order reductions)
+//   raw: dw = dW' sc, db = db' sc, dbeta = db', dgamma = a (sum w dW' + db' (b - mean))
+//   d input = conv-transpose of dv with W'^T (conv) / conv of dv with W'^T (transposed conv)
+// Activation checkpointing: with `checkpoint`, only the inputs of the four
+// blocks (enc1-enc2, enc3-enc4, dec1-dec2, dec3-out) are kept and the first
+// layer's output of each block is recomputed during the backward.
+#include "gw_train.h"
+
+namespace gw {
+namespace {
+
+struct TrainLayer {
+  LayerSpec s;
+  int lin = 0, lout = 0;
+  FoldArgs f{};
+};
+
+}  // namespace
+}  // namespace gw
+
+struct gw_trainer {
+  gw_ctx* ctx = nullptr;
+  int n_in = 0, max_batch = 0, L = 0, checkpoint = 0;
+  size_t n_params = 0;
+  std::vector<gw::TrainLayer> layers;
+  float* in_mean = nullptr;
+  float* in_istd = nullptr;
+  float* x_std = nullptr;
+  std::vector<float*> act;  // output of layer l (l < n_layers - 1), or null when recomputed
+  float* scratch = nullptr; // recomputed activation
+  float* dv[2] = {nullptr, nullptr};
+  float* partial = nullptr;
+  float* dWf = nullptr;
+  float* dbf = nullptr;
+  float* bpart = nullptr;
+  float* zero_bias = nullptr;
+  const float* params = nullptr;  // raw parameters of the last forward
+  int B = 0;
+  std::vector<std::pair<void*, size_t>> allocs;
+  size_t bytes = 0;
+};
+
+namespace gw {
+namespace {
+
+template <typename T>
+T* talloc(gw_trainer* t, size_t count) {
+  const size_t b = std::max<size_t>(count * sizeof(T), 256);
+  T* p = (T*)dev_alloc(t->ctx, b, &t->bytes);
+  t->allocs.push_back({p, b});
+  GW_CUDA(cudaMemset(p, 0, b));
+  return p;
+}
+
+void trainer_free(gw_trainer* t) {
+  if (!t) return;
+  cudaDeviceSynchronize();
+  for (auto& a : t->allocs) dev_free(t->ctx, a.first, a.second, nullptr);
+  delete t;
+}
+
+bool recomputed(const gw_trainer* t, int l) { return t->checkpoint && (l % 2 == 0) && l + 1 < (int)t->layers.size(); }
+
+// Forward of layer l from `in` into `out` (out strides: item cout*lout, channel lout).
+void layer_forward(gw_trainer* t, int l, const float* in, float* out, int64_t yb, int64_t yc, int B, cudaStream_t st) {
+  const TrainLayer& T = t->layers[l];
+  ConvF32Args a{};
+  a.x = in;
+  a.xb = (int64_t)T.s.cin * T.lin;
+  a.xc = T.lin;
+  a.y = out;
+  a.yb = yb;
+  a.yc = yc;
+  a.w = T.f.wf;
+  a.bias = T.f.bf;
+  a.B = B;
+  a.lin = T.lin;
+  a.lout = T.lout;
+  a.s = T.s;
+  Prof p("train.conv_fwd", st);
+  launch_conv_f32(a, st);
+}
+
+const float* layer_input(gw_trainer* t, int l) { return l == 0 ? t->x_std : (t->act[l - 1] ? t->act[l - 1] : t->scratch); }
+
+}  // namespace
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" {
+
+int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_mean, const float* in_std,
+                      gw_trainer_t* out) {
+  gw_trainer* t = nullptr;
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && d && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(d->n_in >= 1 && d->n_in <= 256, "n_in out of range");
+  GW_CHECK_ARG(d->max_batch >= 1 && d->max_batch <= 4096, "max_batch out of range");
+  GW_CHECK_ARG(d->length >= 16 && d->length % 8 == 0, "length must be a multiple of 8, >= 16");
+  GW_CHECK_ARG(d->checkpoint == 0 || d->checkpoint == 1, "checkpoint must be 0 or 1");
+  GW_CUDA(cudaSetDevice(ctx->device));
+  t = new gw_trainer();
+  try {
+    t->ctx = ctx;
+    t->n_in = d->n_in;
+    t->max_batch = d->max_batch;
+    t->L = d->length;
+    t->checkpoint = d->checkpoint;
+    const auto specs = deepclean_specs(d->n_in);
+    int64_t off = 0;
+    int lin = d->length;
+    size_t max_act = 0, max_partial = 0, max_w = 0;
+    int max_c = 0;
+    for (const auto& s : specs) {
+      TrainLayer T;
+      T.s = s;
+      T.lin = lin;
+      T.lout = s.lout(lin);
+      FoldArgs& f = T.f;
+      f.cin = s.cin;
+      f.cout = s.cout;
+      f.K = s.k;
+      f.transposed = s.transposed;
+      f.bn = s.bn;
+      f.off_w = off;
+      off += (int64_t)s.cin * s.cout * s.k;
+      f.off_b = off;
+      off += s.cout;
+      if (s.bn) {
+        f.off_g = off;
+        f.off_be = off + s.cout;
+        f.off_mu = off + 2 * s.cout;
+        f.off_var = off + 3 * s.cout;
+        off += 4 * s.cout;
+      }
+      max_act = std::max(max_act, (size_t)std::max(s.cin * T.lin, s.cout * T.lout));
+      const size_t nw = (size_t)s.cin * s.cout * s.k;
+      max_w = std::max(max_w, nw);
+      max_c = std::max(max_c, std::max(s.cin, s.cout));
+      const WgradArgs w = s.transposed ? plan_wgrad(s.cin, s.cout, s.k, s.stride, T.lin)
+                                       : plan_wgrad(s.cout, s.cin, s.k, s.stride, T.lout);
+      max_partial = std::max(max_partial, (size_t)d->max_batch * w.chunks_per_b * nw);
+      t->layers.push_back(T);
+      lin = T.lout;
+    }
+    GW_CHECK_ARG(lin == d->length, "length does not round-trip through the network");
+    t->n_params = (size_t)off;
+    const int Bm = d->max_batch;
+    for (auto& T : t->layers) {
+      const size_t nw = (size_t)T.s.cin * T.s.cout * T.s.k;
+      T.f.wf = talloc<float>(t, nw);
+      T.f.wT = talloc<float>(t, nw);
+      T.f.bf = talloc<float>(t, T.s.cout);
+    }
+    std::vector<float> mean(d->n_in, 0.f), istd(d->n_in, 1.f);
+    for (int c = 0; c < d->n_in; ++c) {
+      if (in_mean) mean[c] = in_mean[c];
+      if (in_std) {
+        GW_CHECK_ARG(in_std[c] > 0 && std::isfinite(in_std[c]), "in_std must be positive");
+        istd[c] = 1.f / in_std[c];
+      }
+    }
+    t->in_mean = talloc<float>(t, d->n_in);
+    t->in_istd = talloc<float>(t, d->n_in);
+    GW_CUDA(cudaMemcpy(t->in_mean, mean.data(), d->n_in * 4, cudaMemcpyHostToDevice));
+    GW_CUDA(cudaMemcpy(t->in_istd, istd.data(), d->n_in * 4, cudaMemcpyHostToDevice));
+    t->x_std = talloc<float>(t, (size_t)Bm * d->n_in * d->length);
+    const int nl = (int)t->layers.size();
+    t->act.assign(nl - 1, nullptr);
+    for (int l = 0; l + 1 < nl; ++l)
+      if (!recomputed(t, l))
+        t->act[l] = talloc<float>(t, (size_t)Bm * t->layers[l].s.cout * t->layers[l].lout);
+    if (t->checkpoint) t->scratch = talloc<float>(t, (size_t)Bm * max_act);
+    t->dv[0] = talloc<float>(t, (size_t)Bm * max_act);
+    t->dv[1] = talloc<float>(t, (size_t)Bm * max_act);
+    t->partial = talloc<float>(t, max_partial);
+    t->dWf = talloc<float>(t, max_w);
+    t->dbf = talloc<float>(t, max_c);
+    t->bpart = talloc<float>(t, (size_t)Bm * max_c);
+    t->zero_bias = talloc<float>(t, max_c);
+  } catch (...) {
+    trainer_free(t);
+    throw;
+  }
+  *out = t;
+  GW_API_END
+}
+
+int gw_trainer_destroy(gw_trainer_t t) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(t, "trainer is NULL");
+  trainer_free(t);
+  GW_API_END
+}
+
+int64_t gw_trainer_param_count(gw_trainer_t t) { return t ? (int64_t)t->n_params : GW_EINVAL; }
+
+int64_t gw_trainer_bytes(gw_trainer_t t) { return t ? (int64_t)t->bytes : GW_EINVAL; }
+
+int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int B, float* y_hat, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(t && params && x && y_hat, "NULL argument");
+  GW_CHECK_ARG(B >= 1 && B <= t->max_batch, "B out of range [1, max_batch]");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  t->params = params;
+  t->B = B;
+  for (auto& T : t->layers) {
+    T.f.p = params;
+    Prof p("train.fold", st);
+    launch_fold(T.f, st);
+  }
+  {
+    Prof p("train.standardise", st);
+    launch_standardise(x, B, t->n_in, t->L, t->in_mean, t->in_istd, t->x_std, st);
+  }
+  const int nl = (int)t->layers.size();
+  const float* in = t->x_std;
+  for (int l = 0; l < nl; ++l) {
+    const TrainLayer& T = t->layers[l];
+    float* out;
+    int64_t yb = (int64_t)T.s.cout * T.lout, yc = T.lout;
+    if (l + 1 == nl) {
+      out = y_hat;
+      yb = t->L;
+      yc = t->L;
+    } else {
+      out = t->act[l] ? t->act[l] : t->scratch;
+    }
+    layer_forward(t, l, in, out, yb, yc, B, st);
+    in = out;
+  }
+  GW_API_END
+}
+
+int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(t && dy_hat && dparams, "NULL argument");
+  GW_CHECK_ARG(t->params && t->B >= 1, "backward before forward");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int B = t->B, nl = (int)t->layers.size();
+  const float* g = dy_hat;  // gradient w.r.t. the current layer's (pre-activation) output
+  int64_t gb = t->L, gn = t->L;
+  int cur = 0;
+  for (int l = nl - 1; l >= 0; --l) {
+    const TrainLayer& T = t->layers[l];
+    const LayerSpec& s = T.s;
+    if (l > 0 && recomputed(t, l - 1)) {
+      // the checkpointed block input is the output of layer l - 2 (or x)
+      const TrainLayer& P = t->layers[l - 1];
+      layer_forward(t, l - 1, layer_input(t, l - 1), t->scratch, (int64_t)P.s.cout * P.lout, P.lout, B, st);
+    }
+    const float* xin = layer_input(t, l);
+    const int64_t xb = (int64_t)s.cin * T.lin, xc = T.lin;
+    WgradArgs w;
+    if (!s.transposed) {
+      w = plan_wgrad(s.cout, s.cin, s.k, s.stride, T.lout);
+      w.A = g; w.ab = gb; w.aa = gn;
+      w.Bm = xin; w.bb = xb; w.bc = xc; w.LB = T.lin;
+    } else {
+      w = plan_wgrad(s.cin, s.cout, s.k, s.stride, T.lin);
+      w.A = xin; w.ab = xb; w.aa = xc;
+      w.Bm = g; w.bb = gb; w.bc = gn; w.LB = T.lout;
+    }
+    w.p = s.pad_l;
+    w.partial = t->partial;
+    {
+      Prof p("train.wgrad", st);
+      launch_wgrad(w, B, t->dWf, st);
+    }
+    {
+      Prof p("train.bgrad", st);
+      launch_bias_grad(g, gb, gn, B, s.cout, T.lout, t->bpart, t->dbf, st);
+    }
+    {
+      Prof p("train.unfold", st);
+      launch_unfold(T.f, t->dWf, s.transposed ? 1 : 0, t->dbf, dparams, st);
+    }
+    if (l == 0) break;
+    // data gradient, times the derivative of layer l-1's activation (whose
+    // output is this layer's input)
+    ConvF32Args a{};
+    a.x = g;
+    a.xb = gb;
+    a.xc = gn;
+    float* dst = t->dv[cur];
+    a.y = dst;
+    a.yb = xb;
+    a.yc = xc;
+    a.w = T.f.wT;
+    a.bias = t->zero_bias;
+    a.B = B;
+    a.lin = T.lout;
+    a.lout = T.lin;
+    LayerSpec ds{};
+    ds.transposed = !s.transposed;
+    ds.cin = s.cout;
+    ds.cout = s.cin;
+    ds.k = s.k;
+    ds.stride = s.stride;
+    ds.pad_l = s.pad_l;
+    ds.pad_r = s.pad_r;
+    ds.out_pad = 0;
+    ds.bn = false;
+    ds.act = ACT_NONE;
+    a.s = ds;
+    a.gy = xin;
+    a.gyb = xb;
+    a.gyc = xc;
+    a.gact = t->layers[l - 1].s.act;
+    {
+      Prof p("train.dgrad", st);
+      launch_conv_f32(a, st);
+    }
+    g = dst;
+    gb = xb;
+    gn = xc;
+    cur ^= 1;
+  }
+  GW_API_END
+}
+
+int gw_band_loss(gw_fir_t f, const float* strain, const float* y_hat, int B, int L, float* loss, float* r,
+                 void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(f && strain && y_hat && loss && r, "NULL argument");
+  GW_CHECK_ARG(B >= 1 && L >= f->ntaps, "need B >= 1 and L >= ntaps");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t need = ((size_t)B * L + (size_t)B) * sizeof(float);
+  if (need > f->ws_bytes) {
+    GW_CUDA(cudaStreamSynchronize(st));
+    if (f->ws) dev_free(f->ctx, f->ws, f->ws_bytes, nullptr);
+    f->ws = nullptr;
+    f->ws_bytes = 0;
+    f->ws = dev_alloc(f->ctx, need, nullptr);
+    f->ws_bytes = need;
+  }
+  float* e = (float*)f->ws;
+  Prof p("band_loss", st);
+  launch_band_loss(strain, y_hat, B, L, f->d_taps, f->ntaps, e, r, e + (size_t)B * L, loss, st);
+  GW_API_END
+}
+
+int gw_band_loss_backward(gw_fir_t f, const float* r, int B, int L, const float* dloss, float* dy_hat,
+                          void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(f && r && dy_hat, "NULL argument");
+  GW_CHECK_ARG(B >= 1 && L >= f->ntaps, "need B >= 1 and L >= ntaps");
+  Prof p("band_loss_bwd", (cudaStream_t)cuda_stream);
+  launch_band_loss_backward(r, B, L, f->d_taps, f->ntaps, dloss, dy_hat, (cudaStream_t)cuda_stream);
+  GW_API_END
+}
+
+int gw_fir_backward(gw_fir_t f, const float* dy, int B, int C, int L_in, float* dx, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(f && dy && dx, "NULL argument");
+  GW_CHECK_ARG(B >= 1 && C >= 1 && L_in >= f->ntaps, "need B, C >= 1 and L_in >= ntaps");
+  const int K = f->ntaps, lout = L_in - K + 1;
+  Prof p("fir_bwd", (cudaStream_t)cuda_stream);
+  launch_fir_f32(dy, lout, dx, L_in, B * C, f->d_taps, K, L_in, (cudaStream_t)cuda_stream, -(K - 1), lout, 1, 1.f);
+  GW_API_END
+}
+
+int gw_adam_step(float* params, const float* grads, float* m, float* v, int64_t n, int step, float lr, float beta1,
+                 float beta2, float eps, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(params && grads && m && v, "NULL argument");
+  GW_CHECK_ARG(n >= 1 && step >= 1, "need n >= 1 and step >= 1");
+  GW_CHECK_ARG(beta1 >= 0 && beta1 < 1 && beta2 >= 0 && beta2 < 1 && eps > 0 && lr >= 0, "bad Adam hyper-parameters");
+  Prof p("adam", (cudaStream_t)cuda_stream);
+  launch_adam(params, grads, m, v, n, step, lr, beta1, beta2, eps, (cudaStream_t)cuda_stream);
+  GW_API_END
+}
+
+}  // extern "C"

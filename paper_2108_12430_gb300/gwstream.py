@@ -41,6 +41,9 @@ EXPORTS = (
     "gw_model_status", "gw_tc_inspect", "gw_fir_create_lowpass",
     "gw_server_create", "gw_server_open", "gw_server_close", "gw_server_stream_bytes", "gw_server_submit",
     "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
+    "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
+    "gw_trainer_backward", "gw_fir_create_band_loss", "gw_band_loss", "gw_band_loss_backward", "gw_fir_backward",
+    "gw_adam_step",
 )
 
 
@@ -72,6 +75,10 @@ class gw_server_stats(C.Structure):
     _fields_ = [("snapshots", C.c_int64), ("ticks", C.c_int64), ("kernels", C.c_int64), ("mean_batch", C.c_double),
                 ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double),
                 ("busy_s", C.c_double)]
+
+
+class gw_trainer_desc(C.Structure):
+    _fields_ = [("n_in", C.c_int), ("max_batch", C.c_int), ("length", C.c_int), ("checkpoint", C.c_int)]
 
 
 _lib = None
@@ -120,6 +127,18 @@ def _declare(lib):
         "gw_server_stats_read": (I, [P, I, C.POINTER(gw_server_stats)]),
         "gw_server_replay": (I, [P, I, P, P, P, P, P, P, P]),
         "gw_server_destroy": (I, [P]),
+        "gw_trainer_create": (I, [P, C.POINTER(gw_trainer_desc), P, P, C.POINTER(P)]),
+        "gw_trainer_destroy": (I, [P]),
+        "gw_trainer_param_count": (I64, [P]),
+        "gw_trainer_bytes": (I64, [P]),
+        "gw_trainer_forward": (I, [P, P, P, I, P, P]),
+        "gw_trainer_backward": (I, [P, P, P, P]),
+        "gw_fir_create_band_loss": (I, [P, C.POINTER(C.c_double), I, C.c_double, I, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, I, C.POINTER(P)]),
+        "gw_band_loss": (I, [P, P, P, I, I, P, P, P]),
+        "gw_band_loss_backward": (I, [P, P, I, I, P, P, P]),
+        "gw_fir_backward": (I, [P, P, I, I, I, P, P]),
+        "gw_adam_step": (I, [P, P, P, P, I64, I, C.c_float, C.c_float, C.c_float, C.c_float, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -338,6 +357,60 @@ def gw_server_replay(s, ids, t_us, witness, strain, clean, score=None, latency_u
 
 def gw_server_destroy(s):
     _check(lib().gw_server_destroy(s))
+
+
+def gw_trainer_create(ctx, n_in, max_batch, length, checkpoint=0, in_mean=None, in_std=None):
+    d = gw_trainer_desc(n_in, max_batch, length, checkpoint)
+    m = None if in_mean is None else np.ascontiguousarray(in_mean, np.float32)
+    s = None if in_std is None else np.ascontiguousarray(in_std, np.float32)
+    h = P()
+    _check(lib().gw_trainer_create(ctx, C.byref(d), m.ctypes.data if m is not None else None,
+                                   s.ctypes.data if s is not None else None, C.byref(h)))
+    return h
+
+
+def gw_trainer_destroy(t):
+    _check(lib().gw_trainer_destroy(t))
+
+
+def gw_trainer_param_count(t):
+    return _check(lib().gw_trainer_param_count(t))
+
+
+def gw_trainer_bytes(t):
+    return _check(lib().gw_trainer_bytes(t))
+
+
+def gw_trainer_forward(t, params_ptr, x_ptr, B, y_ptr, stream=0):
+    _check(lib().gw_trainer_forward(t, params_ptr, x_ptr, B, y_ptr, stream or None))
+
+
+def gw_trainer_backward(t, dy_ptr, dparams_ptr, stream=0):
+    _check(lib().gw_trainer_backward(t, dy_ptr, dparams_ptr, stream or None))
+
+
+def gw_fir_create_band_loss(ctx, psd, fs, ntaps, f1=55.0, f2=65.0, ramp=2.0, f_ref=60.0, precision=GW_FP32):
+    psd = np.ascontiguousarray(psd, np.float64)
+    h = P()
+    _check(lib().gw_fir_create_band_loss(ctx, psd.ctypes.data_as(C.POINTER(C.c_double)), psd.size, fs, ntaps, f1, f2,
+                                         ramp, f_ref, precision, C.byref(h)))
+    return h
+
+
+def gw_band_loss(g, strain_ptr, y_ptr, B, L, loss_ptr, r_ptr, stream=0):
+    _check(lib().gw_band_loss(g, strain_ptr, y_ptr, B, L, loss_ptr, r_ptr, stream or None))
+
+
+def gw_band_loss_backward(g, r_ptr, B, L, dloss_ptr, dy_ptr, stream=0):
+    _check(lib().gw_band_loss_backward(g, r_ptr, B, L, dloss_ptr or None, dy_ptr, stream or None))
+
+
+def gw_fir_backward(f, dy_ptr, B, Cc, L_in, dx_ptr, stream=0):
+    _check(lib().gw_fir_backward(f, dy_ptr, B, Cc, L_in, dx_ptr, stream or None))
+
+
+def gw_adam_step(p_ptr, g_ptr, m_ptr, v_ptr, n, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    _check(lib().gw_adam_step(p_ptr, g_ptr, m_ptr, v_ptr, n, step, lr, beta1, beta2, eps, stream or None))
 
 
 def gw_profile_enable(on=True):
