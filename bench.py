@@ -351,6 +351,7 @@ def gpu_arm(args):
         peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
     traffic = None
     configs = extra_configs(G, torch, dev_index, flush)
+    configs.update(train_config(G, torch, dev_index, flush))
     configs.update(serve_configs(G, dev_index))
     cpu = cpu_baseline(budget_s=args.cpu_seconds)
     line = {
@@ -489,6 +490,66 @@ def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
                 "kernels_ms": {k: v[0] / 3 for k, v in prof.items()}}
             G.gw_model_destroy(mb)
             G.gw_fir_destroy(fh)
+    finally:
+        G.gw_ctx_destroy(ctx)
+    return out
+
+
+def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
+    """Config 4: one DeepClean training step on 32 windows of 21 x 8192 -
+    forward with tape, band-limited PSD-weighted loss (2049-tap weight FIR,
+    55-65 Hz), its backward, the hand-written network backward and an Adam
+    update of the FP32 master parameters - timed with CUDA events, with and
+    without per-block activation checkpointing."""
+    from paper_2108_12430_gb300 import synth
+    Bt, Lt = 32, 8192
+    out = {}
+    ctx = G.gw_ctx_create(dev_index, 0)
+    try:
+        _, psd = synth.psd_grid(4096.0, 8192)
+        g = G.gw_fir_create_band_loss(ctx, psd, 4096.0, 2049)
+        x = torch.from_numpy(np.stack([synth.witness_channels(900 + b, C, Lt) for b in range(Bt)])
+                             .astype(np.float32)).cuda()
+        s = torch.from_numpy((np.random.default_rng(9).standard_normal((Bt, Lt)) * 0.3).astype(np.float32)).cuda()
+        st = torch.cuda.current_stream().cuda_stream
+        for ck in (0, 1):
+            t = G.gw_trainer_create(ctx, C, Bt, Lt, ck)
+            p = torch.from_numpy(synth.flatten_params(synth.deepclean_params(1234))).cuda()
+            m, v, dp = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+            y, dy = torch.empty(Bt, Lt, device="cuda"), torch.empty(Bt, Lt, device="cuda")
+            r = torch.empty(Bt, Lt - 2048, device="cuda")
+            loss = torch.empty(1, device="cuda")
+            it = [0]
+
+            def step():
+                it[0] += 1
+                G.gw_trainer_forward(t, p.data_ptr(), x.data_ptr(), Bt, y.data_ptr(), st)
+                G.gw_band_loss(g, s.data_ptr(), y.data_ptr(), Bt, Lt, loss.data_ptr(), r.data_ptr(), st)
+                G.gw_band_loss_backward(g, r.data_ptr(), Bt, Lt, 0, dy.data_ptr(), st)
+                G.gw_trainer_backward(t, dy.data_ptr(), dp.data_ptr(), st)
+                G.gw_adam_step(p.data_ptr(), dp.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(), it[0], 1e-4,
+                               stream=st)
+
+            l0 = G.gw_launch_count()
+            ms = time_call(torch, step, steps, warmup, flush)
+            launches = (G.gw_launch_count() - l0) / (steps + warmup)
+            G.gw_profile_enable(True)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            prof = G.gw_profile_read()
+            G.gw_profile_enable(False)
+            fwd = dc_flops_per_window(Lt) * Bt
+            flops = 3 * fwd + (fwd // 2 if ck else 0) + 2 * 2 * 2049 * Bt * (Lt - 2048)
+            out[f"config4_fp32{'_checkpoint' if ck else ''}"] = {
+                "workload": "DeepClean training step, 32 x 21 x 8192, band loss 2049 taps, Adam",
+                "ms_per_step": float(np.mean(ms)), "p50_ms": float(np.median(ms)),
+                "windows_per_s": Bt / (np.mean(ms) / 1e3), "tflops": flops / (np.mean(ms) / 1e3) / 1e12,
+                "flops_per_step": flops, "loss": float(loss.item()), "kernels_per_step": launches,
+                "state_bytes": G.gw_trainer_bytes(t),
+                "kernels_ms": {k: round(vv[0] / 3, 4) for k, vv in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+            G.gw_trainer_destroy(t)
+        G.gw_fir_destroy(g)
     finally:
         G.gw_ctx_destroy(ctx)
     return out
@@ -731,12 +792,21 @@ def main():
                     help="time one path only (profiling)")
     ap.add_argument("--serve-only", action="store_true",
                     help="only the serving configuration (config 5); prints its JSON")
+    ap.add_argument("--train-only", action="store_true",
+                    help="only the training configuration (config 4); prints its JSON")
     ap.add_argument("--lite", action="store_true",
                     help="timed device pushes only: no e2e, accuracy, CPU baseline or JSON contract line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.serve_only:
+    if args.train_only:
+        from paper_2108_12430_gb300 import build as Bld
+        Bld.build()
+        from paper_2108_12430_gb300 import gwstream as G
+        import torch
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(train_config(G, torch, torch.cuda.current_device(), flush)))
+    elif args.serve_only:
         from paper_2108_12430_gb300 import build as Bld
         Bld.build()
         from paper_2108_12430_gb300 import gwstream as G

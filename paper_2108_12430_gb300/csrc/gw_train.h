@@ -36,7 +36,8 @@ void launch_unfold(const FoldArgs& f, const float* dWf, int dw_in_major, const f
 WgradArgs plan_wgrad(int NA, int NC, int K, int s, int LA);
 size_t wgrad_smem(const WgradArgs& w);
 // w.partial must hold B * w.chunks_per_b * NA * NC * K floats; out gets NA * NC * K.
-void launch_wgrad(const WgradArgs& w, int B, float* out, cudaStream_t st);
+void launch_wgrad_partial(const WgradArgs& w, int B, cudaStream_t st);
+void launch_wgrad_reduce(const WgradArgs& w, int B, float* out, cudaStream_t st);
 // out[n] = sum_{b, t} G[b][n][t]; part holds B * N floats.
 void launch_bias_grad(const float* G, int64_t gb, int64_t gn, int B, int N, int L, float* part, float* out,
                       cudaStream_t st);

@@ -90,50 +90,57 @@ __global__ void unfold_kernel(FoldArgs f, const float* __restrict__ dWf, int dw_
 // Weight-gradient partials of one chunk of (item, positions):
 //   P[chunk][a][c][k] = sum_{t in chunk} A[b][a][t] Bv(b, c, s t + k - p),
 // Bv = Bm inside [0, LB), 0 outside.  Conv: A = output gradient, Bm = input;
-// transposed conv: A = input, Bm = output gradient.  CTA: AB values of a,
-// all (c, k), T positions; the A tile and the B span sit in shared memory.
+// transposed conv: A = input, Bm = output gradient.  CTA: AB values of a (a
+// power of two), all (c, k), T positions; the A tile (rows padded by one
+// float against bank conflicts) and the B span sit in shared memory.  Thread:
+// one a (AB groups of 256 / AB threads) and NJ of the (c, k) outputs, so one
+// A value feeds NJ multiply-adds per position.  NJ is a compile-time bound
+// (>= w.nj) so that the inner loop has no idle slots.
+template <int NJ>
 __global__ void __launch_bounds__(kThreads) wgrad_partial_kernel(WgradArgs w) {
   extern __shared__ float sm[];
   const int chunk = blockIdx.x, b = chunk / w.chunks_per_b, t0 = (chunk % w.chunks_per_b) * w.T;
   const int a0 = blockIdx.y * w.AB;
   const int span = w.s * (w.T - 1) + w.K;
-  float* As = sm;                 // [AB][T]
-  float* Bs = sm + w.AB * w.T;    // [NC][span]
+  const int as = w.T + 1;
+  float* As = sm;                 // [AB][T + 1]
+  float* Bs = sm + w.AB * as;     // [NC][span]
   const int q0 = w.s * t0 - w.p;
   for (int e = threadIdx.x; e < w.AB * w.T; e += blockDim.x) {
     const int al = e / w.T, t = e % w.T;
     const int a = a0 + al, tt = t0 + t;
-    As[e] = (a < w.NA && tt < w.LA) ? w.A[(int64_t)b * w.ab + (int64_t)a * w.aa + tt] : 0.f;
+    As[al * as + t] = (a < w.NA && tt < w.LA) ? w.A[(int64_t)b * w.ab + (int64_t)a * w.aa + tt] : 0.f;
   }
   for (int e = threadIdx.x; e < w.NC * span; e += blockDim.x) {
     const int c = e / span, q = q0 + e % span;
     Bs[e] = (q >= 0 && q < w.LB) ? w.Bm[(int64_t)b * w.bb + (int64_t)c * w.bc + q] : 0.f;
   }
   __syncthreads();
-  const int n_out = w.AB * w.NC * w.K;
-  float acc[kMaxJ];
-  int aoff[kMaxJ], boff[kMaxJ];
+  const int tpa = kThreads / w.AB;          // threads per a
+  const int al = threadIdx.x / tpa, ck0 = threadIdx.x % tpa;
+  const int nck = w.NC * w.K;
+  float acc[NJ];
+  int boff[NJ];
 #pragma unroll
-  for (int j = 0; j < kMaxJ; ++j) {
+  for (int j = 0; j < NJ; ++j) {
     acc[j] = 0.f;
-    const int e = threadIdx.x + j * kThreads;
-    const int al = e / (w.NC * w.K), r = e % (w.NC * w.K);
-    aoff[j] = e < n_out ? al * w.T : 0;
-    boff[j] = e < n_out ? (r / w.K) * span + r % w.K : 0;
+    const int ck = ck0 + j * tpa;
+    boff[j] = ck < nck ? (ck / w.K) * span + ck % w.K : 0;
   }
+  const float* arow = As + al * as;
   const int tmax = min(w.T, w.LA - t0);
+  const int s = w.s;
   for (int t = 0; t < tmax; ++t) {
+    const float av = arow[t];
 #pragma unroll
-    for (int j = 0; j < kMaxJ; ++j)
-      if (j < w.nj) acc[j] = fmaf(As[aoff[j] + t], Bs[boff[j] + w.s * t], acc[j]);
+    for (int j = 0; j < NJ; ++j) acc[j] = fmaf(av, Bs[boff[j] + s * t], acc[j]);
   }
-  float* out = w.partial + (int64_t)chunk * w.NA * w.NC * w.K;
+  if (a0 + al < w.NA) {
+    float* out = w.partial + (int64_t)chunk * w.NA * nck + (int64_t)(a0 + al) * nck;
 #pragma unroll
-  for (int j = 0; j < kMaxJ; ++j) {
-    const int e = threadIdx.x + j * kThreads;
-    if (j < w.nj && e < n_out) {
-      const int al = e / (w.NC * w.K), r = e % (w.NC * w.K);
-      if (a0 + al < w.NA) out[(int64_t)(a0 + al) * w.NC * w.K + r] = acc[j];
+    for (int j = 0; j < NJ; ++j) {
+      const int ck = ck0 + j * tpa;
+      if (ck < nck) out[ck] = acc[j];
     }
   }
 }
@@ -235,32 +242,56 @@ WgradArgs plan_wgrad(int NA, int NC, int K, int s, int LA) {
   w.K = K;
   w.s = s;
   w.LA = LA;
-  w.AB = std::max(1, std::min(16, kMaxJ * kThreads / (NC * K)));
-  w.AB = std::min(w.AB, NA);
+  // AB: the largest power of two <= min(16, NA) whose thread groups still
+  // cover the (c, k) outputs with at most kMaxJ per thread
+  w.AB = 1;
+  while (w.AB * 2 <= std::min(16, NA) && (NC * K + kThreads / (w.AB * 2) - 1) / (kThreads / (w.AB * 2)) <= kMaxJ)
+    w.AB *= 2;
   w.T = 256;
   while (w.T > 32 && wgrad_smem(w) > 160 * 1024) w.T /= 2;
   w.chunks_per_b = (LA + w.T - 1) / w.T;
-  w.nj = (w.AB * NC * K + kThreads - 1) / kThreads;
+  const int tpa = kThreads / w.AB;
+  w.nj = (NC * K + tpa - 1) / tpa;
   return w;
 }
 
 size_t wgrad_smem(const WgradArgs& w) {
-  return ((size_t)w.AB * w.T + (size_t)w.NC * (w.s * (w.T - 1) + w.K)) * sizeof(float);
+  return ((size_t)w.AB * (w.T + 1) + (size_t)w.NC * (w.s * (w.T - 1) + w.K)) * sizeof(float);
 }
 
-void launch_wgrad(const WgradArgs& w, int B, float* out, cudaStream_t st) {
+void launch_wgrad_partial(const WgradArgs& w, int B, cudaStream_t st) {
   GW_CHECK_ARG(w.nj <= kMaxJ, "weight gradient tile too large");
   const size_t smem = wgrad_smem(w);
   GW_CHECK_ARG(smem <= 200 * 1024, "weight gradient tile exceeds shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
   const int n_chunks = B * w.chunks_per_b;
   dim3 grid(n_chunks, (w.NA + w.AB - 1) / w.AB);
-  wgrad_partial_kernel<<<grid, kThreads, smem, st>>>(w);
+  if (w.nj <= 1)
+    wgrad_partial_kernel<1><<<grid, kThreads, smem, st>>>(w);
+  else if (w.nj <= 2)
+    wgrad_partial_kernel<2><<<grid, kThreads, smem, st>>>(w);
+  else if (w.nj <= 4)
+    wgrad_partial_kernel<4><<<grid, kThreads, smem, st>>>(w);
+  else if (w.nj <= 8)
+    wgrad_partial_kernel<8><<<grid, kThreads, smem, st>>>(w);
+  else if (w.nj <= 16)
+    wgrad_partial_kernel<16><<<grid, kThreads, smem, st>>>(w);
+  else
+    wgrad_partial_kernel<32><<<grid, kThreads, smem, st>>>(w);
   GW_LAUNCH_CHECK();
+}
+
+void launch_wgrad_reduce(const WgradArgs& w, int B, float* out, cudaStream_t st) {
+  const int n_chunks = B * w.chunks_per_b;
   const int64_t n = (int64_t)w.NA * w.NC * w.K;
   reduce_chunks_kernel<<<grid_for(n), kThreads, 0, st>>>(w.partial, n, n_chunks, out);
   GW_LAUNCH_CHECK();

@@ -74,6 +74,9 @@ void trainer_free(gw_trainer* t) {
   delete t;
 }
 
+const char* kWgradNames[8] = {"train.wgrad.enc1", "train.wgrad.enc2", "train.wgrad.enc3", "train.wgrad.enc4",
+                              "train.wgrad.dec1", "train.wgrad.dec2", "train.wgrad.dec3", "train.wgrad.out"};
+
 bool recomputed(const gw_trainer* t, int l) { return t->checkpoint && (l % 2 == 0) && l + 1 < (int)t->layers.size(); }
 
 // Forward of layer l from `in` into `out` (out strides: item cout*lout, channel lout).
@@ -281,8 +284,12 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
     w.p = s.pad_l;
     w.partial = t->partial;
     {
-      Prof p("train.wgrad", st);
-      launch_wgrad(w, B, t->dWf, st);
+      Prof p(l < 8 ? kWgradNames[l] : "train.wgrad", st);
+      launch_wgrad_partial(w, B, st);
+    }
+    {
+      Prof p("train.wgrad_reduce", st);
+      launch_wgrad_reduce(w, B, t->dWf, st);
     }
     {
       Prof p("train.bgrad", st);
