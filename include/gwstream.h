@@ -83,8 +83,15 @@ size_t gw_ctx_bytes_in_use(gw_ctx_t ctx);
  * weights are cast to the model's precision and copied to the device.
  * `in_mean` / `in_std` (host, n_in floats, may be NULL) standardise the
  * input per channel, (x - mean) / std, inside the first kernel.
- * `act_scales` (FP8 only; host, one per conv layer, may be NULL): static
- * per-tensor scale of each layer's input activations.
+ * FP8 (BBHnet only): weights are e4m3 with a per-output-channel scale (max
+ * |w| -> 448); activations are e4m3 with static per-tensor scales s (stored
+ * value e4m3(x s)), accumulation is FP32.  `act_scales` (host, may be NULL):
+ * n_layers + 1 entries, the scale of each conv layer's input (a block
+ * shortcut's entry is not used: its input is its block's input, quantised
+ * with the block's first conv's scale; its output is stored with the block
+ * output's scale) and, last, the scale of the final block's output that the
+ * pooling head reads.  Without act_scales an FP8 model refuses to run until
+ * gw_model_calibrate sets them.
  */
 typedef struct gw_model_desc {
   int kind;               /* enum gw_model_kind */
@@ -94,7 +101,7 @@ typedef struct gw_model_desc {
   size_t n_params;
   const float* in_mean;   /* host [n_in] or NULL */
   const float* in_std;    /* host [n_in] or NULL */
-  const float* act_scales;/* host [n_layers] or NULL */
+  const float* act_scales;/* host [n_layers + 1] or NULL (FP8) */
   int n_act_scales;
 } gw_model_desc;
 
@@ -136,6 +143,15 @@ int gw_deepclean_forward_noalloc(gw_model_t m, const float* x, int64_t ld, int64
 /* BBHnet logits.  x: device FP32 [B][2][L] whitened strain (L a multiple of
  * 16, L >= 16); logits: device FP32 [B]. */
 int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, void* cuda_stream);
+
+/* Static FP8 activation scales from a calibration batch (FP8 BBHnet models;
+ * GW_EINVAL otherwise): runs the model's folded FP32 weights on x (device
+ * [B][2][L]), records max |.| of every quantised tensor, and sets each scale
+ * to 448 / (headroom * max) (headroom >= 1).  scales_out (host, may be NULL)
+ * receives the n_layers + 1 scales in the act_scales order.  Synchronises
+ * cuda_stream. */
+int gw_model_calibrate(gw_model_t m, const float* x, int B, int L, float headroom, float* scales_out,
+                       void* cuda_stream);
 
 /* ---- whitening FIR --------------------------------------------------------
  * Linear-phase whitening filter designed in FP64 on the host from a

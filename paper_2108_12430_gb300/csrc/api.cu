@@ -291,10 +291,17 @@ void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool sta
   }
 }
 
-void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st) {
+void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st,
+                float* amax) {
   const auto& Ls = m->layers;
   const size_t per = (size_t)B * 32 * L;
   float* buf[3] = {ws, ws + per, ws + 2 * per};
+  auto track = [&](const float* t, int64_t n, int slot) {
+    if (!amax) return;
+    Prof p("absmax", st);
+    launch_absmax(t, n, amax + slot, st);
+  };
+  track(x, (int64_t)B * m->n_in * L, 0);
   auto conv = [&](const LayerDev& Ld, const float* in, int64_t ib, int64_t ic, int lin, float* out,
                   const float* res, int act) {
     LayerSpec s = Ld.s;
@@ -311,6 +318,7 @@ void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float*
     return lout;
   };
   int l = conv(Ls[0], x, 2LL * L, L, L, buf[0], nullptr, ACT_RELU);
+  track(buf[0], (int64_t)B * 32 * l, 1);
   int cin = 32, h = 0;
   for (int blk = 0; blk < 4; ++blk) {
     const LayerDev& c1 = Ls[1 + 3 * blk];
@@ -320,8 +328,13 @@ void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float*
     const int a_i = (h + 1) % 3, o_i = (h + 2) % 3;
     const int64_t hb = (int64_t)cin * l, hc = l;
     const int l2 = conv(c1, buf[h], hb, hc, l, buf[a_i], nullptr, ACT_RELU);
+    track(buf[a_i], (int64_t)B * cout * l2, 2 + 3 * blk);
+    // the shortcut output and the block output share the block's output slot
+    const int out_slot = blk < 3 ? 1 + 3 * (blk + 1) : (int)Ls.size();
     conv(sc, buf[h], hb, hc, l, buf[o_i], nullptr, ACT_NONE);
+    track(buf[o_i], (int64_t)B * cout * l2, out_slot);
     conv(c2, buf[a_i], (int64_t)cout * l2, l2, l2, buf[o_i], buf[o_i], ACT_RELU);
+    track(buf[o_i], (int64_t)B * cout * l2, out_slot);
     h = o_i;
     l = l2;
     cin = cout;
@@ -333,15 +346,17 @@ void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float*
 // ---- tensor-core runners -------------------------------------------------------
 // Blocked activation of `cout` channels x `lout` positions in P phase planes
 // (element strides; rows of 8 bf16 channels).
-TcOut blocked_out(void* buf, int cout, int lout, int P) {
+TcOut blocked_out(void* buf, int cout, int lout, int P, bool fp8) {
   TcOut o{};
-  const int G = (cout + 7) / 8;
+  const int cg = fp8 ? 16 : 8;  // channels per 16-byte row
+  const int G = (cout + cg - 1) / cg;
   const int64_t Lp = (lout + P - 1) / P;
   o.p = buf;
-  o.pstride = Lp * 8;
-  o.gstride = (int64_t)P * Lp * 8;
+  o.pstride = Lp * cg;
+  o.gstride = (int64_t)P * Lp * cg;
   o.bstride = (int64_t)G * o.gstride;
   o.P = P;
+  o.fp8_out = fp8 ? 1 : 0;
   return o;
 }
 
@@ -449,6 +464,98 @@ void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* w
 
 size_t bbhnet_tc_ws_bytes(int B, int L) { return (size_t)B * 8 * L * 2 + 3 * (size_t)B * 32 * L * 2; }
 size_t bbhnet_f32_ws_bytes(int B, int L) { return 3 * (size_t)B * 32 * L * 4; }
+
+// BBHnet on e4m3 operands (FP32 accumulation).  Every activation tensor is
+// stored as e4m3 rows of 16 channels, quantised by its consumer's static
+// scale s (q = e4m3(x s)); a layer dequantises its accumulator by
+// wscale[o] / s_in per output channel in the epilogue.  A block's shortcut
+// output is stored with the block output's scale, which its second conv's
+// epilogue divides out before adding it.
+void bbhnet_fp8(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st) {
+  const auto& Ls = m->layers;
+  if (!m->fp8_scaled)
+    throw Error(GW_ESTATE, "FP8 BBHnet has no activation scales: pass act_scales or call gw_model_calibrate");
+  const int64_t per = (int64_t)B * 32 * L;  // bytes of the largest activation (and then some)
+  void* in0 = ws;
+  void* buf[3] = {ws + (size_t)B * 16 * L, ws + (size_t)B * 16 * L + per, ws + (size_t)B * 16 * L + 2 * per};
+  TcOut xin = blocked_out(in0, m->n_in, L, Ls[0].pin, true);
+  {
+    Prof p("to_blocked", st);
+    launch_to_blocked(x, (int64_t)m->n_in * L, L, B, m->n_in, L, nullptr, nullptr, Ls[0].act_scale, xin, 1, st);
+  }
+  int l = Ls[0].s.lout(L);
+  TcOut h = blocked_out(buf[0], Ls[0].s.cout, l, Ls[1].pin, true);
+  {
+    Prof p("conv_tc.bbhnet_fp8", st);
+    launch_conv_tc(Ls[0], as_input(xin, L), l, h, B, m->err, st);
+  }
+  int hi = 0;
+  for (int blk = 0; blk < 4; ++blk) {
+    const LayerDev& c1 = Ls[1 + 3 * blk];
+    LayerDev c2 = Ls[2 + 3 * blk];
+    const LayerDev& sc = Ls[3 + 3 * blk];
+    c2.s.act = ACT_RELU;  // relu(conv2 + shortcut)
+    GW_CHECK_ARG(c1.pin == sc.pin, "block convs must read the same input layout");
+    const int a_i = (hi + 1) % 3, o_i = (hi + 2) % 3;
+    const int l2 = c1.s.lout(l);
+    const int next_P = blk < 3 ? Ls[1 + 3 * (blk + 1)].pin : 1;
+    TcOut a = blocked_out(buf[a_i], c1.s.cout, l2, c2.pin, true);
+    TcOut o = blocked_out(buf[o_i], c2.s.cout, l2, next_P, true);
+    {
+      Prof p("conv_tc.bbhnet_fp8", st);
+      launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
+    }
+    {
+      Prof p("conv_tc.bbhnet_fp8", st);
+      launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
+    }
+    TcOut o2 = o;
+    o2.res = o.p;
+    o2.rbstride = o.bstride;
+    o2.rgstride = o.gstride;
+    o2.rpstride = o.pstride;
+    o2.rP = o.P;
+    {
+      Prof p("conv_tc.bbhnet_fp8", st);
+      launch_conv_tc(c2, as_input(a, l2), l2, o2, B, m->err, st);
+    }
+    h = o;
+    hi = o_i;
+    l = l2;
+  }
+  Prof p("gap_linear_tc", st);
+  launch_gap_linear_blocked(as_input(h, l), Ls.back().s.cout, 1, 1.f / m->fp8_final_scale, m->head_w, m->head_b,
+                            logits, B, st);
+}
+
+// FP8 activation scales from per-layer input scales s[l] (l < n_layers; a
+// shortcut's own entry is not used, its input is its block's first conv's)
+// and the last block's output scale s[n_layers]: sets every layer's input and
+// output scale and uploads its dequantisation factors wscale / s_in.
+static void set_fp8_scales(gw_model* m, const std::vector<float>& s) {
+  auto& Ls = m->layers;
+  const int n = (int)Ls.size();
+  for (int li = 0; li < n; ++li)
+    GW_CHECK_ARG(s[li] > 0 && std::isfinite(s[li]), "activation scales must be positive and finite");
+  GW_CHECK_ARG(s[n] > 0 && std::isfinite(s[n]), "activation scales must be positive and finite");
+  for (int li = 0; li < n; ++li) {
+    LayerDev& L = Ls[li];
+    const bool shortcut = li >= 3 && (li - 3) % 3 == 0;
+    L.act_scale = shortcut ? s[li - 2] : s[li];
+    if (li == 0) {
+      L.out_scale = s[1];
+    } else {
+      const int blk = (li - 1) / 3, role = (li - 1) % 3;  // 0: conv1, 1: conv2, 2: shortcut
+      const float block_out = blk < 3 ? s[1 + 3 * (blk + 1)] : s[n];
+      L.out_scale = role == 0 ? s[2 + 3 * blk] : block_out;
+    }
+    std::vector<float> deq(L.s.cout);
+    for (int o = 0; o < L.s.cout; ++o) deq[o] = m->fp8_wscale[li][o] / L.act_scale;
+    GW_CUDA(cudaMemcpy(L.wscale, deq.data(), deq.size() * 4, cudaMemcpyHostToDevice));
+  }
+  m->fp8_final_scale = s[n];
+  m->fp8_scaled = true;
+}
 
 }  // namespace gw
 
@@ -612,17 +719,19 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
     L.w = upload(m, w32);
     L.b = upload(m, b32);
     if (d->precision != GW_FP32) {
-      if (d->precision == GW_FP8) {
-        GW_CHECK_ARG(d->act_scales == nullptr || d->n_act_scales == (int)specs.size(),
-                     "act_scales must have one entry per conv layer");
-        L.act_scale = d->act_scales ? d->act_scales[li] : 1.0f;
-      }
       // a BBHnet shortcut reads the same input as its block's first conv, so it
       // takes that conv's output folding (and with it the same input phases)
       if (d->kind == GW_MODEL_BBHNET && li >= 3 && (li - 3) % 3 == 0) L.J = m->layers[li - 2].J;
-      tc_pack_layer(L, wf, d->precision, ctx, &m->bytes, m->allocs);
+      std::vector<float> wscale;
+      tc_pack_layer(L, wf, d->precision, ctx, &m->bytes, m->allocs, &wscale);
+      if (d->precision == GW_FP8) m->fp8_wscale.push_back(wscale);
     }
     m->layers.push_back(L);
+  }
+  if (d->precision == GW_FP8 && d->act_scales) {
+    GW_CHECK_ARG(d->n_act_scales == (int)specs.size() + 1,
+                 "act_scales must have one entry per conv layer plus the final output scale");
+    set_fp8_scales(m, std::vector<float>(d->act_scales, d->act_scales + d->n_act_scales));
   }
   if (d->kind == GW_MODEL_BBHNET) {
     std::vector<float> hw(p, p + 256), hb(p + 256, p + 257);
@@ -708,8 +817,38 @@ int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, v
     char* ws = (char*)model_workspace(m, bbhnet_tc_ws_bytes(B, L));
     bbhnet_tc(m, x, B, L, logits, ws, st);
   } else {
-    throw Error(GW_ENOTIMPL, "BBHnet FP8 path not built yet");
+    char* ws = (char*)model_workspace(m, bbhnet_tc_ws_bytes(B, L));
+    bbhnet_fp8(m, x, B, L, logits, ws, st);
   }
+  GW_API_END
+}
+
+int gw_model_calibrate(gw_model_t m, const float* x, int B, int L, float headroom, float* scales_out,
+                       void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(m && x, "NULL argument");
+  GW_CHECK_ARG(m->kind == GW_MODEL_BBHNET && m->precision == GW_FP8, "calibration is for FP8 BBHnet models");
+  GW_CHECK_ARG(B >= 1 && L >= 16 && L % 16 == 0, "need B >= 1 and L a positive multiple of 16");
+  GW_CHECK_ARG(headroom >= 1.f && std::isfinite(headroom), "headroom must be >= 1");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int n = (int)m->layers.size();
+  const size_t f32_ws = bbhnet_f32_ws_bytes(B, L);
+  char* ws = (char*)model_workspace(m, f32_ws + 64 * sizeof(float) + (size_t)B * sizeof(float));
+  float* amax = (float*)(ws + f32_ws);
+  float* logits = amax + 64;
+  GW_CUDA(cudaMemsetAsync(amax, 0, 64 * sizeof(float), st));
+  // the FP8 model keeps its folded FP32 weights: run them and record ranges
+  bbhnet_f32(m, x, B, L, logits, (float*)ws, st, amax);
+  std::vector<float> h(n + 1);
+  GW_CUDA(cudaMemcpyAsync(h.data(), amax, (n + 1) * sizeof(float), cudaMemcpyDeviceToHost, st));
+  GW_CUDA(cudaStreamSynchronize(st));
+  // scale = 448 / (headroom * max |x|): the largest calibration value lands
+  // at 448 / headroom (e4m3's largest finite is 448)
+  std::vector<float> s(n + 1, 1.f);
+  for (int i = 0; i <= n; ++i) s[i] = h[i] > 0 && std::isfinite(h[i]) ? 448.f / (headroom * h[i]) : 1.f;
+  set_fp8_scales(m, s);
+  if (scales_out)
+    for (int i = 0; i <= n; ++i) scales_out[i] = s[i];
   GW_API_END
 }
 

@@ -111,6 +111,12 @@ struct gw_model {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* err = nullptr;        // device error flag of the tensor-core kernels (bounded waits)
+  // FP8: host copies of each layer's per-output-channel weight scales, the
+  // scale of the last block's output (read by the pooling head), and whether
+  // activation scales have been set (at create or by calibration)
+  std::vector<std::vector<float>> fp8_wscale;
+  float fp8_final_scale = 1.f;
+  bool fp8_scaled = false;
 };
 
 struct gw_fir {
@@ -177,7 +183,11 @@ void deepclean_f32(gw_model* m, const float* x, int64_t xb, int64_t xc, bool sta
 // ---- model runners (api.cu) ------------------------------------------------------
 struct TcIn;
 struct TcOut;
-void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st);
+// amax (optional, device [n_layers + 1], zeroed by the caller): max |.| of
+// every conv layer's input and, in the output slot of each residual block,
+// of the shortcut output and the block output (FP8 calibration).
+void bbhnet_f32(gw_model* m, const float* x, int B, int L, float* logits, float* ws, cudaStream_t st,
+                float* amax = nullptr);
 size_t bbhnet_tc_ws_bytes(int B, int L);
 size_t bbhnet_f32_ws_bytes(int B, int L);
 
@@ -231,7 +241,7 @@ struct TcOut {
 };
 // Blocked output of `cout` channels x `lout` positions in P planes, and its view
 // as the next layer's input (api.cu).
-TcOut blocked_out(void* buf, int cout, int lout, int P);
+TcOut blocked_out(void* buf, int cout, int lout, int P, bool fp8 = false);
 TcIn as_input(const TcOut& o, int lout);
 int64_t deepclean_tc_act_elems(int L);
 // DeepClean on B windows through the tensor-core kernels: `in` is the first
@@ -241,9 +251,15 @@ void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, vo
                   cudaStream_t st);
 // BBHnet on B items of FP32 [2][L]; ws holds bbhnet_tc_ws_bytes(B, L).
 void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st);
+// The same on e4m3 operands with the model's static activation scales.
+void bbhnet_fp8(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st);
 int tc_supported();
+// Packs a layer's folded weights for the tensor-core kernel; FP8 also returns
+// the per-output-channel weight scales (max |w| -> 448) in wscale_out.
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wfold, int precision, gw_ctx* ctx,
-                   size_t* counter, std::vector<void*>& allocs);
+                   size_t* counter, std::vector<void*>& allocs, std::vector<float>* wscale_out = nullptr);
+// max |x| over n floats, combined into *amax (atomic max of non-negative floats).
+void launch_absmax(const float* x, int64_t n, float* amax, cudaStream_t st);
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err_flag,
                     cudaStream_t st);
 // FP32 element (b, c, t) at x + b*xb + c*xc + t*ts -> blocked bf16 / e4m3,

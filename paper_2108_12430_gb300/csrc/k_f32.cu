@@ -182,7 +182,31 @@ __global__ void __launch_bounds__(kThreads) gap_linear_f32_kernel(const float* _
   }
 }
 
+// *amax = max(*amax, max_i |x[i]|): block maximum, then an atomic max on the
+// bit pattern (non-negative floats order like their bits as integers, and a
+// maximum does not depend on the order it is taken in).
+__global__ void __launch_bounds__(kThreads) absmax_kernel(const float* __restrict__ x, int64_t n,
+                                                         float* __restrict__ amax) {
+  __shared__ float red[kThreads / 32];
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    m = fmaxf(m, fabsf(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kThreads / 32; ++i) m = fmaxf(m, red[i]);
+    atomicMax(reinterpret_cast<int*>(amax), __float_as_int(m));
+  }
+}
+
 }  // namespace
+
+void launch_absmax(const float* x, int64_t n, float* amax, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, 1216);
+  absmax_kernel<<<(int)std::max<int64_t>(blocks, 1), kThreads, 0, st>>>(x, n, amax);
+  GW_LAUNCH_CHECK();
+}
 
 void launch_conv_f32(const ConvF32Args& a, cudaStream_t st) {
   const LayerSpec& s = a.s;

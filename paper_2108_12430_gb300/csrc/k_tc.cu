@@ -729,7 +729,7 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
 }
 
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wf, int precision, gw_ctx* ctx, size_t* counter,
-                   std::vector<void*>& allocs) {
+                   std::vector<void*>& allocs, std::vector<float>* wscale_out) {
   const LayerSpec& s = L.s;
   const bool fp8 = precision == GW_FP8;
   std::vector<uint8_t> img;
@@ -750,6 +750,7 @@ void tc_pack_layer(LayerDev& L, const std::vector<double>& wf, int precision, gw
     allocs.push_back(d_sc);
     GW_CUDA(cudaMemcpy(d_sc, deq.data(), deq.size() * 4, cudaMemcpyHostToDevice));
     L.wscale = d_sc;
+    if (wscale_out) *wscale_out = wscale;
   }
   L.wq = d_img;
   L.table = d_tab;

@@ -264,8 +264,10 @@ void record_tick(gw_server* s, int Bb, int slot, cudaStream_t a, cudaStream_t b)
     }
     if (s->bbh->precision == GW_FP32)
       bbhnet_f32(s->bbh, s->bbh_x, Bb, s->Lb, s->logits, (float*)s->bbh_ws, a);
-    else
+    else if (s->bbh->precision == GW_BF16)
       bbhnet_tc(s->bbh, s->bbh_x, Bb, s->Lb, s->logits, s->bbh_ws, a);
+    else
+      bbhnet_fp8(s->bbh, s->bbh_x, Bb, s->Lb, s->logits, s->bbh_ws, a);
   }
   Prof p("serve_scores", a);
   launch_serve_scores(items, Bb, s->bbh ? s->logits : nullptr, s->d_err, s->bbh ? s->bbh->err : nullptr,
@@ -634,7 +636,8 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
                "DeepClean precision must be FP32 or BF16");
   if (bbhnet) {
     GW_CHECK_ARG(bbhnet->kind == GW_MODEL_BBHNET && bbhnet->n_in == d->n_det, "BBHnet must have n_in = n_det");
-    GW_CHECK_ARG(bbhnet->precision == GW_FP32 || bbhnet->precision == GW_BF16, "BBHnet precision must be FP32 or BF16");
+    GW_CHECK_ARG(bbhnet->precision != GW_FP8 || bbhnet->fp8_scaled,
+                 "FP8 BBHnet needs activation scales (act_scales or gw_model_calibrate)");
   }
   GW_CHECK_ARG((decimator->ntaps & 1) && (whitening->ntaps & 1), "FIR tap counts must be odd");
   GW_CUDA(cudaSetDevice(ctx->device));

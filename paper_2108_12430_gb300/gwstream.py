@@ -43,7 +43,7 @@ EXPORTS = (
     "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
     "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
     "gw_trainer_backward", "gw_fir_create_band_loss", "gw_band_loss", "gw_band_loss_backward", "gw_fir_backward",
-    "gw_adam_step",
+    "gw_adam_step", "gw_model_calibrate",
 )
 
 
@@ -139,6 +139,7 @@ def _declare(lib):
         "gw_band_loss_backward": (I, [P, P, I, I, P, P, P]),
         "gw_fir_backward": (I, [P, P, I, I, I, P, P]),
         "gw_adam_step": (I, [P, P, P, P, I64, I, C.c_float, C.c_float, C.c_float, C.c_float, P]),
+        "gw_model_calibrate": (I, [P, P, I, I, C.c_float, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -225,6 +226,14 @@ def gw_deepclean_forward(m, x_ptr, ld, window_stride, B, L, y_ptr, stream=0):
 
 def gw_deepclean_forward_noalloc(m, x_ptr, ld, window_stride, B, L, y_ptr, stream=0):
     _check(lib().gw_deepclean_forward_noalloc(m, x_ptr, ld, window_stride, B, L, y_ptr, stream or None))
+
+
+def gw_model_calibrate(m, x_ptr, B, L, headroom=1.0, stream=0):
+    """Sets an FP8 BBHnet's activation scales from a calibration batch; returns them."""
+    n = 14
+    out = np.zeros(n, np.float32)
+    _check(lib().gw_model_calibrate(m, x_ptr, B, L, headroom, out.ctypes.data, stream or None))
+    return out
 
 
 def gw_bbhnet_score(m, x_ptr, B, L, logits_ptr, stream=0):

@@ -29,26 +29,58 @@ def f64_to_bf16_bits(x):
     return (np.asarray(x, np.float32).view(np.uint32) >> 16).astype(np.uint16)
 
 
-def emulate(spec, x, img, table, md):
+def e4m3_table():
+    """All 256 e4m3 codes decoded from the format's definition (sign, 4-bit
+    exponent with bias 7, 3 mantissa bits; exponent 0 subnormal; S.1111.111 NaN)."""
+    v = np.zeros(256)
+    for b in range(256):
+        s, e, m = b >> 7, (b >> 3) & 15, b & 7
+        if e == 15 and m == 7:
+            v[b] = np.nan
+        elif e == 0:
+            v[b] = m / 8.0 * 2.0 ** -6
+        else:
+            v[b] = (1 + m / 8.0) * 2.0 ** (e - 7)
+        v[b] = -v[b] if s else v[b]
+    return v
+
+
+E4M3 = e4m3_table()
+E4M3_CODE = {float(val): b for b, val in enumerate(E4M3) if np.isfinite(val) and not (val == 0 and b)}
+
+
+def f64_to_e4m3_bits(x):
+    # inputs are e4m3-representable: look the code up
+    return np.array([E4M3_CODE[float(v)] for v in np.ravel(x)], np.uint8).reshape(np.shape(x))
+
+
+def emulate(spec, x, img, table, md, fp8=False):
     transposed, cin, cout, k, stride, pl, pr, op = spec
     Gn, P, rows, MT, dmin, npad = md["groups"], md["in_P"], md["rows"], md["MT"], md["dmin"], md["npad"]
     Q, coutp, step_bytes, a_bytes = md["Q"], md["coutp"], md["step_bytes"], md["a_bytes"]
+    # element size, channels per 16-byte row, K of one MMA
+    esz, cg, kstep = (1, 16, 32) if fp8 else (2, 8, 16)
     lin = x.shape[1]
     lout, mout = md["lout"], md["mout"]
     assert rows * 16 * Gn * P <= a_bytes
     assert md["smem"] <= 227 * 1024 and md["ncols"] <= 512 and 2 * MT * npad <= md["ncols"]
     assert Q * coutp <= npad
-    xb = np.zeros((Gn * 8, lin))
+    xb = np.zeros((Gn * cg, lin))
     xb[:cin] = x
-    imgh = img.view(np.uint16)
+    if fp8:
+        imgh = img.view(np.uint8)
+        decode = lambda codes: E4M3[codes]
+    else:
+        imgh = img.view(np.uint16)
+        decode = bf16_bits_to_f64
     out = np.zeros((cout, lout))
     written = np.zeros((cout, lout), int)
     r_idx = np.arange(128)[:, None]
-    k_idx = np.arange(16)[None, :]
+    k_idx = np.arange(kstep)[None, :]
     for tile in range(md["tiles_per_item"]):
         m0 = tile * 128 * MT
         base = m0 + dmin
-        A = np.zeros(a_bytes // 2, np.uint16)
+        A = np.zeros(a_bytes // esz, np.uint8 if fp8 else np.uint16)
         for plane in range(Gn * P):
             g, phi = plane // P, plane % P
             Lp = (lin - phi + P - 1) // P
@@ -57,8 +89,9 @@ def emulate(spec, x, img, table, md):
             for r in range(r0, r1):
                 j = base + r
                 assert 0 <= j < Lp
-                a0 = (plane * rows + r) * 8
-                A[a0:a0 + 8] = f64_to_bf16_bits(xb[g * 8:(g + 1) * 8, P * j + phi])
+                a0 = (plane * rows + r) * cg
+                vals = xb[g * cg:(g + 1) * cg, P * j + phi]
+                A[a0:a0 + cg] = f64_to_e4m3_bits(vals) if fp8 else f64_to_bf16_bits(vals)
         D = np.zeros((MT, 128, npad))
         for s in range(md["n_steps"]):
             w0, w1 = int(table[2 * s]), int(table[2 * s + 1])
@@ -72,14 +105,15 @@ def emulate(spec, x, img, table, md):
             assert lbo >= 0
             # B operand: rows n, K-halves LBO = npad * 16 apart, 8-row groups SBO = 128 apart
             n_idx = np.arange(npad)[:, None]
-            baddr = s * step_bytes + (n_idx // 8) * 128 + (n_idx % 8) * 16 + (k_idx // 8) * (npad * 16) + (k_idx % 8) * 2
-            assert baddr.max() + 2 <= (s + 1) * step_bytes
-            Bm = bf16_bits_to_f64(imgh[baddr // 2])
+            baddr = (s * step_bytes + (n_idx // 8) * 128 + (n_idx % 8) * 16 + (k_idx // cg) * (npad * 16)
+                     + (k_idx % cg) * esz)
+            assert baddr.max() + esz <= (s + 1) * step_bytes
+            Bm = decode(imgh[baddr // esz])
             for mt in range(MT):
                 start = o0 + mt * 2048
-                aaddr = start + (r_idx // 8) * 128 + (r_idx % 8) * 16 + (k_idx // 8) * lbo + (k_idx % 8) * 2
-                assert aaddr.min() >= 0 and aaddr.max() + 2 <= a_bytes
-                Am = bf16_bits_to_f64(A[aaddr // 2])
+                aaddr = start + (r_idx // 8) * 128 + (r_idx % 8) * 16 + (k_idx // cg) * lbo + (k_idx % cg) * esz
+                assert aaddr.min() >= 0 and aaddr.max() + esz <= a_bytes
+                Am = decode(A[aaddr // esz])
                 acc = Am @ Bm.T
                 D[mt] = acc if s == 0 else D[mt] + acc
         # epilogue: row m, column n = sigma * coutp + o -> position Q m + sigma
@@ -137,6 +171,25 @@ def test_tc_lowering_matches_oracle(spec, lin, in_P, out_P, batch):
         ref = Lyr.conv1d(x[None], w, np.zeros(cout), stride, pl, pr)[0]
     assert got.shape == ref.shape
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+FP8_CASES = [c for c in CASES if c[0][0] == 0 and (c[0][2] >= 32 or c[0][1] == 2)]  # BBHnet-shaped convs
+
+
+@pytest.mark.parametrize("spec,lin,in_P,out_P", FP8_CASES)
+def test_tc_lowering_fp8_matches_oracle(spec, lin, in_P, out_P):
+    # e4m3 operands: 16 channels per 16-byte row, K = 32 per MMA; weights
+    # quantised per output channel with max |w| mapped to 448 (FP32 scale)
+    from oracle.quant import to_e4m3
+    transposed, cin, cout, k, stride, pl, pr, op = spec
+    w = rng.standard_normal((cout, cin, k)) * 0.2
+    x = to_e4m3(rng.standard_normal((cin, lin)) * 4)
+    img, table, md = G.gw_tc_inspect(spec, G.GW_FP8, w, lin, 0, out_P, 1)
+    ws = (np.abs(w).max(axis=(1, 2)) / 448.0).astype(np.float32).astype(np.float64)
+    wq = to_e4m3((w / ws[:, None, None]).astype(np.float32))
+    got = emulate(spec, x, img, table, md, fp8=True)
+    ref = Lyr.conv1d(x[None], wq, np.zeros(cout), stride, pl, pr)[0]
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-9)
 
 
 def test_tc_instruction_descriptor_fields():
