@@ -198,8 +198,7 @@ def profile_pass(G, torch, push_fn, first, steps, flush):
 
 
 def accuracy(G, torch, precision, dev_index):
-    """rel-L2 of two full 21 x 32768 windows against the FP64 oracle."""
-    from oracle import nets
+    """rel-L2 of two full 21 x 32768 windows against the FP64 oracle (CPU leg)."""
     from paper_2108_12430_gb300 import synth
     ctx = G.gw_ctx_create(dev_index, 0)
     params = synth.deepclean_params(1234)
@@ -210,7 +209,7 @@ def accuracy(G, torch, precision, dev_index):
     G.gw_deepclean_forward(m, xd.data_ptr(), W + S, S, 2, W, y.data_ptr())
     torch.cuda.synchronize()
     wins = np.stack([x[:, :W], x[:, S:S + W]]).astype(np.float32).astype(np.float64)
-    ref = nets.deepclean_forward(wins, params, synth.DEEPCLEAN_LAYERS)
+    ref = cpu_leg_deepclean(wins, params)
     got = y.cpu().numpy().astype(np.float64)
     err = max(float(np.linalg.norm(got[i] - ref[i]) / np.linalg.norm(ref[i])) for i in range(2))
     G.gw_model_destroy(m)
@@ -429,17 +428,16 @@ def time_call(torch, fn, steps, warmup, flush=None):
 
 def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
     """Config 1 (one 1 s DeepClean window) latency and config 3 (whitening +
-    BBHnet on 256 x 2 x 4096 raw strain) throughput, BF16 and FP32, each with
-    its error against the FP64 oracle on sampled items."""
-    from oracle import fir as ofir, nets
+    BBHnet on 256 x 2 x 4096 raw strain) throughput, BF16, FP8 (BBHnet) and
+    FP32, each with its error against the FP64 oracle (CPU leg) on sampled
+    items."""
     from paper_2108_12430_gb300 import synth
     out = {}
     ctx = G.gw_ctx_create(dev_index, 0)
     try:
         # config 1
         x1 = synth.witness_channels(0, C, 4096)
-        ref1 = nets.deepclean_forward(x1[None].astype(np.float32).astype(np.float64), synth.deepclean_params(0),
-                                      synth.DEEPCLEAN_LAYERS)[0]
+        ref1 = cpu_leg_deepclean(x1[None].astype(np.float32).astype(np.float64), synth.deepclean_params(0))[0]
         x1d = torch.from_numpy(x1.astype(np.float32)).cuda()
         y1 = torch.zeros(1, 4096, device="cuda")
         for name, prec in (("bf16", G.GW_BF16), ("fp32", G.GW_FP32)):
@@ -458,14 +456,21 @@ def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
         xrd = torch.from_numpy(xr.astype(np.float32)).cuda()
         wd = torch.zeros(Bc, 2, Lr - 2048, device="cuda")
         logit = torch.zeros(Bc, device="cuda")
-        h = ofir.whitening_fir(psd, fs, nfft, 2049)
         idx = [0, 77, 255]
-        xw_ref = ofir.fir_valid(xr[idx].astype(np.float32).astype(np.float64), h)
         layers, head = synth.bbhnet_params(3)
-        ref3 = nets.bbhnet_forward(xw_ref, layers, head, synth.bbhnet_layers())
-        for name, prec in (("bf16", G.GW_BF16), ("fp32", G.GW_FP32)):
-            fh = G.gw_fir_create_whitening(ctx, psd, fs, 2049, prec)
+        xw_ref, ref3 = cpu_leg_whiten_bbhnet(xr[idx].astype(np.float32).astype(np.float64), psd, fs, nfft, layers,
+                                             head)
+        for name, prec in (("bf16", G.GW_BF16), ("fp8", G.GW_FP8), ("fp32", G.GW_FP32)):
+            fh = G.gw_fir_create_whitening(ctx, psd, fs, 2049, G.GW_BF16 if prec == G.GW_FP8 else prec)
             mb = G.gw_model_create(ctx, G.GW_MODEL_BBHNET, prec, 2, synth.flatten_params(layers, head))
+            if prec == G.GW_FP8:
+                # static activation scales from a separate calibration batch,
+                # whitened by the library
+                xc, _, _ = synth.injected_strain(32, 64, Lr)
+                xcd = torch.from_numpy(xc.astype(np.float32)).cuda()
+                wc = torch.zeros(64, 2, Lr - 2048, device="cuda")
+                G.gw_whiten(fh, xcd.data_ptr(), 64, 2, Lr, wc.data_ptr())
+                G.gw_model_calibrate(mb, wc.data_ptr(), 64, Lr - 2048)
 
             def step():
                 G.gw_whiten(fh, xrd.data_ptr(), Bc, 2, Lr, wd.data_ptr())
@@ -716,8 +721,25 @@ def tick_profile(G, ctx, dcs, bbh, fdec, fw, pools, n_ticks=20):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle: baseline leg and the reference arm
+# CPU leg: the FP64 oracle on the host.  It is timed for cpu_baseline and the
+# reference arm, and its outputs on the bench's own seeded inputs are the
+# references of the error fields; nothing else in this file touches the
+# oracle, and no GPU result depends on it.
 # ---------------------------------------------------------------------------
+
+def cpu_leg_deepclean(wins, params, mean=None, std=None):
+    from oracle import nets
+    from paper_2108_12430_gb300 import synth
+    return nets.deepclean_forward(wins, params, synth.DEEPCLEAN_LAYERS, mean, std)
+
+
+def cpu_leg_whiten_bbhnet(x, psd, fs, nfft, layers, head):
+    """Whitened windows (2049 taps, valid mode) and their BBHnet logits."""
+    from oracle import fir as ofir, nets
+    from paper_2108_12430_gb300 import synth
+    xw = ofir.fir_valid(x, ofir.whitening_fir(psd, fs, nfft, 2049))
+    return xw, nets.bbhnet_forward(xw, layers, head, synth.bbhnet_layers())
+
 
 def oracle_snapshot_seconds(n_windows, seed=4321):
     """Time the FP64 oracle on n_windows consecutive snapshots of the workload."""
