@@ -133,6 +133,27 @@ def peaks():
             "fallback"
 
 
+def rank_env():
+    """(world size, rank, local rank) from the launcher's environment; (1, 0, 0) alone."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def slowest(dist, world, value, device):
+    """The largest value over all ranks (the slowest rank's timed interval)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every replica processed over the slowest one's time."""
+    return units_per_rank * world / seconds
+
+
 def make_stream_inputs(n_samples, seed=1234):
     from paper_2108_12430_gb300 import synth
     wit = synth.witness_channels(seed, C, n_samples)
@@ -242,9 +263,7 @@ def gpu_arm(args):
     Bld.build()
     from paper_2108_12430_gb300 import gwstream as G
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -278,11 +297,7 @@ def gpu_arm(args):
                 continue
             raise
         ms = np.array(res["ms"])
-        tot = float(ms.sum())
-        if world > 1:
-            t = torch.tensor([tot], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = slowest(dist, world, float(ms.sum()), "cuda")
         if args.lite:
             # profiling runs: only the device-resident timed pushes above
             G.gw_stream_destroy(s)
@@ -300,7 +315,10 @@ def gpu_arm(args):
         wit_h = {first + i: pin(wit[:, (first + i) * n_step:(first + i + 1) * n_step])
                  for i in range(ne2e)}
         str_h = {first + i: pin(strain[(first + i) * n_step:(first + i + 1) * n_step]) for i in range(ne2e)}
+        if world > 1:
+            dist.barrier()
         lat = e2e_pass(G, torch, s, wit_h, str_h, first, ne2e)
+        e2e_tot = slowest(dist, world, float(sum(lat)), "cuda")
         err = accuracy(G, torch, prec, dev_index) if rank == 0 else None
         G.gw_stream_destroy(s)
         G.gw_model_destroy(m)
@@ -311,12 +329,12 @@ def gpu_arm(args):
         prof_steps = min(K, 8)
         conv_flops = dc_flops_per_window() * B * prof_steps
         paths[name] = {
-            "value": B * K * world / (tot / 1e3),
+            "value": job_rate(B * K, world, tot / 1e3),
             "ms_per_step": tot / K,
             "p50_ms": float(np.percentile(ms, 50)),
             "p99_ms": float(np.percentile(ms, 99)),
             "rel_l2_vs_fp64_oracle": err,
-            "e2e_value": B * ne2e * world / (sum(lat) / 1e3),
+            "e2e_value": job_rate(B * ne2e, world, e2e_tot / 1e3),
             "e2e_p50_ms": float(np.percentile(lat, 50)),
             "e2e_p99_ms": float(np.percentile(lat, 99)),
             "gpu_launches_per_step": res["launches_per_step"],
