@@ -48,6 +48,7 @@ namespace {
 // TMEM lane quarter (each takes every other 32-column chunk), so that every
 // SM sub-partition has two warps to hide the epilogue's instruction latency
 constexpr int kEpiWarps = 8;
+constexpr int kMaxA = 6;  // deepest input ring
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
@@ -60,6 +61,7 @@ struct TcParams {
   const char* wimg;
   const uint32_t* table;
   int n_steps, npad, sps, nst, step_bytes, a_bytes, ncols, resident;
+  int na;  // input stages in the A ring (2..kMaxA)
   uint32_t idesc;
   int fp8;
   const float* bias;
@@ -150,19 +152,21 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
+// No "memory" clobber: the MMA reads shared memory through the async proxy
+// only, ordered by the barrier waits and fences (volatile asm keeps its place
+// among the other volatile asm), and without the clobber the compiler may load
+// the next step's descriptors while this one issues.
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -209,29 +213,33 @@ __device__ __forceinline__ uint32_t slice_off(uint32_t code, int P, int rows) {
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  const uint32_t sA = smem_u32(smem);  // 2 stages of a_bytes
-  const uint32_t sW = sA + 2u * (uint32_t)p.a_bytes;
+  const int na = p.na;                 // input stages (the A ring)
+  const uint32_t sA = smem_u32(smem);  // na stages of a_bytes
+  const uint32_t sW = sA + (uint32_t)na * (uint32_t)p.a_bytes;
   const uint32_t stage_bytes = (uint32_t)(p.sps * p.step_bytes);
   const uint32_t w_bytes = p.resident ? (uint32_t)(p.n_steps * p.step_bytes) : (uint32_t)p.nst * stage_bytes;
   const int planes = p.G * p.in_P;
-  uint64_t* bars = (uint64_t*)(smem + 2 * p.a_bytes + ((w_bytes + 127u) & ~127u));
-  // barrier slots: a_full[2], a_empty[2], acc_full[2], acc_empty[2], drain, w_full[nst], w_empty[nst]
-  uint64_t* s_adesc = bars + 9 + 2 * p.nst;                 // [n_steps] A descriptor (stage 0, sub-tile 0)
-  uint64_t* s_bdesc = s_adesc + p.n_steps;                  // [n_steps] B descriptor (stage 0)
-  int64_t* s_poff = reinterpret_cast<int64_t*>(s_bdesc + p.n_steps);  // [planes] byte offset of each plane
+  uint64_t* bars = (uint64_t*)(smem + (size_t)na * p.a_bytes + ((w_bytes + 127u) & ~127u));
+  // barrier slots: a_full[na], a_empty[na], acc_full[2], acc_empty[2], drain, w_full[nst], w_empty[nst]
+  // then, 16-byte aligned, [n_steps] {A descriptor (stage 0, sub-tile 0), B descriptor (stage 0)}
+  uint64_t* s_desc = bars + ((2 * na + 5 + 2 * p.nst + 1) & ~1);
+  int64_t* s_poff = reinterpret_cast<int64_t*>(s_desc + 2 * p.n_steps);  // [planes] byte offset of each plane
   volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(s_poff + planes);
   uint32_t* tslot = (uint32_t*)(abort_flag + 1);
   float* s_bias = reinterpret_cast<float*>(tslot + 2);     // [npad] bias, then [npad] FP8 scales
   float* s_scale = s_bias + p.npad;
   int* s_plen = reinterpret_cast<int*>(s_scale + p.npad);  // [planes] valid rows of each plane
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
-  const int a_full = 0, a_empty = 2, acc_full = 4, acc_empty = 6, drain = 8, w_full = 9, w_empty = 9 + p.nst;
+  const int a_full = 0, a_empty = na, acc_full = 2 * na, acc_empty = 2 * na + 2, drain = 2 * na + 4,
+            w_full = 2 * na + 5, w_empty = 2 * na + 5 + p.nst;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < na; ++i) {
       mbar_init(bar(a_full + i), 1);
       mbar_init(bar(a_empty + i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(bar(acc_full + i), 1);
       mbar_init(bar(acc_empty + i), kEpiWarps);  // one arrival per epilogue warp
     }
@@ -248,9 +256,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
   const uint32_t stage_b = p.resident ? 0u : (uint32_t)p.sps;
   for (int i = tid; i < p.n_steps; i += kThreads) {
     const uint32_t o0 = slice_off(p.table[2 * i], p.in_P, p.rows), o1 = slice_off(p.table[2 * i + 1], p.in_P, p.rows);
-    s_adesc[i] = make_desc(sA + o0, o1 - o0, 128u);
+    s_desc[2 * i] = make_desc(sA + o0, o1 - o0, 128u);
     const uint32_t pos = p.resident ? (uint32_t)i : (uint32_t)i % stage_b;
-    s_bdesc[i] = make_desc(sW + pos * (uint32_t)p.step_bytes, (uint32_t)p.npad * 16u, 128u);
+    s_desc[2 * i + 1] = make_desc(sW + pos * (uint32_t)p.step_bytes, (uint32_t)p.npad * 16u, 128u);
   }
   for (int i = tid; i < planes; i += kThreads) {
     const int g = i / p.in_P, phi = i % p.in_P;
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     }
     int i = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
-      const int s = i & 1, k = i >> 1;
+      const int s = i % na, k = i / na;
       if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
       const int b = t / p.tiles_per_item;
       const int m0 = (t - b * p.tiles_per_item) * 128 * p.MT;
@@ -338,14 +346,18 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     // ---------------- MMA issue: one thread ----------------
     if (lane == 0) {
       bool ok = !p.resident || mbar_wait(bar(w_full), 0u, abort_flag, p.err, kErrWaitW);
+      const bool fp8 = p.fp8 != 0;
+      const int MT = p.MT, npad = p.npad;
+      const uint32_t idesc = p.idesc;
       int i = 0;
       for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x, ++i) {
-        const int s = i & 1, k = i >> 1;
-        if (!mbar_wait(bar(a_full + s), (uint32_t)k & 1u, abort_flag, p.err, kErrWaitA)) break;
+        const int sa = i % na, ka = i / na;  // input stage
+        const int s = i & 1, k = i >> 1;     // accumulator buffer
+        if (!mbar_wait(bar(a_full + sa), (uint32_t)ka & 1u, abort_flag, p.err, kErrWaitA)) break;
         if (k >= 1 && !mbar_wait(bar(acc_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitAcc)) break;
         tc_fence_after();
         // descriptor start addresses count 16-byte units in their low bits
-        const uint64_t a_stage = (uint64_t)(((uint32_t)s * (uint32_t)p.a_bytes) >> 4);
+        const uint64_t a_stage = (uint64_t)(((uint32_t)sa * (uint32_t)p.a_bytes) >> 4);
         const uint32_t d0 = tmem + (uint32_t)(s * p.MT * p.npad);
         for (int c = 0; c < n_chunks; ++c) {
           uint64_t b_stage = 0;
@@ -361,23 +373,41 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
             b_stage = (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
           }
           const int s0 = p.resident ? 0 : c * p.sps, s1 = p.resident ? p.n_steps : min(p.n_steps, s0 + p.sps);
+          // The issue rate of this one thread bounds the tensor pipe for small
+          // N, so the loop is kept lean: one 16-byte descriptor pair per step,
+          // the next pair loaded while the current MMAs issue.
+          const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(s_desc);
+          ulonglong2 cur = tab[s0];
+          if (fp8) {
+            for (int sidx = s0; sidx < s1; ++sidx) {
+              const ulonglong2 nxt = tab[sidx + 1 < s1 ? sidx + 1 : sidx];
+              const uint32_t acc = sidx == 0 ? 0u : 1u;
+              for (int mt = 0; mt < MT; ++mt)  // M sub-tile mt starts 128 rows (2048 bytes) further
+                mma_f8(d0 + (uint32_t)(mt * npad), cur.x + a_stage + (uint64_t)(mt * 128), cur.y + b_stage, idesc,
+                       acc);
+              cur = nxt;
+            }
+          } else if (MT == 1) {
 #pragma unroll 4
-          for (int sidx = s0; sidx < s1; ++sidx) {
-            const uint64_t bdesc = s_bdesc[sidx] + b_stage;
-            const uint64_t adesc = s_adesc[sidx] + a_stage;
-            const uint32_t acc = sidx == 0 ? 0u : 1u;
-            for (int mt = 0; mt < p.MT; ++mt) {
-              // M sub-tile mt starts 128 rows (2048 bytes) further
-              if (p.fp8)
-                mma_f8(d0 + (uint32_t)(mt * p.npad), adesc + (uint64_t)(mt * 128), bdesc, p.idesc, acc);
-              else
-                mma_f16(d0 + (uint32_t)(mt * p.npad), adesc + (uint64_t)(mt * 128), bdesc, p.idesc, acc);
+            for (int sidx = s0; sidx < s1; ++sidx) {
+              const ulonglong2 nxt = tab[sidx + 1 < s1 ? sidx + 1 : sidx];
+              mma_f16(d0, cur.x + a_stage, cur.y + b_stage, idesc, sidx == 0 ? 0u : 1u);
+              cur = nxt;
+            }
+          } else {
+            for (int sidx = s0; sidx < s1; ++sidx) {
+              const ulonglong2 nxt = tab[sidx + 1 < s1 ? sidx + 1 : sidx];
+              const uint32_t acc = sidx == 0 ? 0u : 1u;
+              for (int mt = 0; mt < MT; ++mt)
+                mma_f16(d0 + (uint32_t)(mt * npad), cur.x + a_stage + (uint64_t)(mt * 128), cur.y + b_stage, idesc,
+                        acc);
+              cur = nxt;
             }
           }
           if (!p.resident) mma_commit(bar(w_empty + st));
         }
         if (!ok) break;
-        mma_commit(bar(a_empty + s));
+        mma_commit(bar(a_empty + sa));
         mma_commit(bar(acc_full + s));
       }
       // all MMAs issued by this thread complete before TMEM is released
@@ -823,6 +853,20 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   while (ncols < 2 * MT * L.npad) ncols *= 2;
   GW_CHECK_ARG(ncols <= 512, "accumulators exceed tensor memory");
   q.ncols = ncols;
+  // input stages: as many as fit (up to kMaxA), keeping two CTAs per SM where
+  // the two-stage plan allowed it; more tiles in flight hide the input latency
+  {
+    const size_t wsm0 = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
+    auto smem_for = [&](int na) {
+      return 128 + (size_t)na * q.a_bytes + (wsm0 + 127) / 128 * 128 + 8 * (size_t)(2 * na + 6 + 2 * q.nst) +
+             16 * (size_t)L.n_steps + 12 * planes + 16 + 8 * (size_t)L.npad + 16;
+    };
+    const bool two_per_sm = smem_for(2) <= 113 * 1024 && ncols <= 256;
+    const size_t cap = two_per_sm ? 113 * 1024 : 227 * 1024;
+    int na = 2;
+    while (na < kMaxA && smem_for(na + 1) <= cap) ++na;
+    q.na = na;
+  }
   q.tiles_per_item = (q.mout + 128 * MT - 1) / (128 * MT);
   q.n_tiles = q.tiles_per_item * B;
   // instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3 (kind::f8f6f4),
@@ -867,7 +911,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.wimg = (const char*)L.wq;
   q.table = L.table;
   const size_t wsm = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
-  const size_t smem = 128 + 2 * (size_t)q.a_bytes + (wsm + 127) / 128 * 128 + 8 * (9 + 2 * q.nst) +
+  const size_t smem = 128 + (size_t)q.na * q.a_bytes + (wsm + 127) / 128 * 128 + 8 * (size_t)(2 * q.na + 6 + 2 * q.nst) +
                       16 * (size_t)L.n_steps + 12 * planes + 16 + 8 * (size_t)L.npad + 16;
   GW_CHECK_ARG(smem <= 227 * 1024, "shared memory plan too large");
   *smem_out = smem;
