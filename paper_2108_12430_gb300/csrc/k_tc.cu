@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
   int64_t* s_poff = reinterpret_cast<int64_t*>(s_desc + 2 * p.n_steps);  // [planes] byte offset of each plane
   volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(s_poff + planes);
   uint32_t* tslot = (uint32_t*)(abort_flag + 1);
-  float* s_bias = reinterpret_cast<float*>(tslot + 2);     // [npad] bias, then [npad] FP8 scales
+  // [npad] bias, then [npad] FP8 scales; 16-byte aligned for vector loads
+  float* s_bias = reinterpret_cast<float*>(((uintptr_t)(tslot + 2) + 15) & ~(uintptr_t)15);
   float* s_scale = s_bias + p.npad;
   int* s_plen = reinterpret_cast<int*>(s_scale + p.npad);  // [planes] valid rows of each plane
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     const int quarter = warp & 3;          // TMEM lanes this warp may access
     const int col_half = (warp - 2) >> 2;  // which 32-column chunks it drains
     const int row = quarter * 32 + lane;
+    const bool plain = !p.fp32_single && !p.fp32_d2s && !p.fp8_out && !p.res && !p.wscale;
     int i = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
       const int s = i & 1, k = i >> 1;
@@ -438,6 +440,33 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((s * p.MT + mt) * p.npad + j * 32), v);
           if (!valid) continue;
+          if (plain) {
+            // bf16 out, no residual, no FP8 scale: 4 groups of 8 channels,
+            // straight-line, bias as float4 pairs, no per-group branches
+            // (the common DeepClean / BBHnet case; invalid groups are those
+            // past Q, C_out or the output length, known per column / row)
+            const int n_base = j * 32;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int n0 = n_base + h * 8;
+              const int sg = n0 >> p.coutp_log, o0 = n0 & (p.coutp - 1);
+              const int u = p.Q * m + sg;
+              const float4 b0 = *reinterpret_cast<const float4*>(s_bias + o0);
+              const float4 b1 = *reinterpret_cast<const float4*>(s_bias + o0 + 4);
+              const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+              __align__(16) __nv_bfloat162 o16[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                o16[e] = __floats2bfloat162_rn(act_fn(v[h * 8 + 2 * e] + bb[2 * e], p.act),
+                                               act_fn(v[h * 8 + 2 * e + 1] + bb[2 * e + 1], p.act));
+              if (sg < p.Q && o0 < p.cout && u < p.lout) {
+                char* op = outb + (int64_t)(o0 >> 3) * p.out_g + (int64_t)(u & out_mask) * p.out_p +
+                           (int64_t)(u >> p.out_P_log) * 16;
+                *reinterpret_cast<uint4*>(op) = *reinterpret_cast<const uint4*>(o16);
+              }
+            }
+            continue;
+          }
           if (p.fp32_single) {
             // column n = sigma: output position Q m + sigma, channel 0
             float* y = reinterpret_cast<float*>(outb);
@@ -859,7 +888,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
     const size_t wsm0 = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
     auto smem_for = [&](int na) {
       return 128 + (size_t)na * q.a_bytes + (wsm0 + 127) / 128 * 128 + 8 * (size_t)(2 * na + 6 + 2 * q.nst) +
-             16 * (size_t)L.n_steps + 12 * planes + 16 + 8 * (size_t)L.npad + 16;
+             16 * (size_t)L.n_steps + 12 * planes + 32 + 8 * (size_t)L.npad + 16;
     };
     const bool two_per_sm = smem_for(2) <= 113 * 1024 && ncols <= 256;
     const size_t cap = two_per_sm ? 113 * 1024 : 227 * 1024;
@@ -912,7 +941,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.table = L.table;
   const size_t wsm = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
   const size_t smem = 128 + (size_t)q.na * q.a_bytes + (wsm + 127) / 128 * 128 + 8 * (size_t)(2 * q.na + 6 + 2 * q.nst) +
-                      16 * (size_t)L.n_steps + 12 * planes + 16 + 8 * (size_t)L.npad + 16;
+                      16 * (size_t)L.n_steps + 12 * planes + 32 + 8 * (size_t)L.npad + 16;
   GW_CHECK_ARG(smem <= 227 * 1024, "shared memory plan too large");
   *smem_out = smem;
   const int per_sm = (smem <= 113 * 1024 && ncols <= 256) ? 2 : 1;
