@@ -120,14 +120,27 @@ __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, 
       continue;
     }
     float sum = (tau < head) ? acc[pmod(tau, R)] : 0.f;
-    for (int j = jlo; j <= jhi; ++j) {
-      const int64_t start = head + (int64_t)(j + 1) * S - W;
-      sum += pred[(int64_t)j * pred_ld + (tau - start)];
-      if (emits && k0 + j == k_emit) {
-        const int64_t first = imax64(0, floordiv64(tau, S));
-        const float cnt = (float)(k_emit - first + 1);
-        out[tau - head + delta] = s_tau - sum / cnt;
+    const int j_emit = emits ? (int)(k_emit - k0) : -1;
+    const int64_t first = imax64(0, floordiv64(tau, S));
+    const float cnt = (float)(k_emit - first + 1);
+    // window j holds tau at offset tau - (head + (j+1) S - W) of its prediction
+    const float* pj = pred + (tau - head - S + W);
+    int j = jlo;
+    // eight windows' values are loaded before they are added (in window order),
+    // so each thread keeps eight loads in flight
+    for (; j + 7 <= jhi; j += 8) {
+      float val[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) val[q] = pj[(int64_t)(j + q) * (pred_ld - S)];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        sum += val[q];
+        if (j + q == j_emit) out[tau - head + delta] = s_tau - sum / cnt;
       }
+    }
+    for (; j <= jhi; ++j) {
+      sum += pj[(int64_t)j * (pred_ld - S)];
+      if (j == j_emit) out[tau - head + delta] = s_tau - sum / cnt;
     }
     acc[pmod(tau, R)] = sum;
   }

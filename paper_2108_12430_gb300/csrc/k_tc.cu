@@ -471,11 +471,21 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
             // column n = sigma: output position Q m + sigma, channel 0
             float* y = reinterpret_cast<float*>(outb);
             const float bias = s_bias[0];
+            const int u0 = p.Q * m + j * 32;
+            if (j * 32 + 32 <= p.Q && u0 + 32 <= p.lout && ((uintptr_t)(y + u0) & 15) == 0) {
+              // 32 consecutive samples of this row: eight 16-byte stores
+              float4* y4 = reinterpret_cast<float4*>(y + u0);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const int sg = j * 32 + e;
-              const int u = p.Q * m + sg;
-              if (sg < p.Q && u < p.lout) y[u] = act_fn(v[e] + bias, p.act);
+              for (int e = 0; e < 8; ++e)
+                y4[e] = make_float4(act_fn(v[4 * e] + bias, p.act), act_fn(v[4 * e + 1] + bias, p.act),
+                                    act_fn(v[4 * e + 2] + bias, p.act), act_fn(v[4 * e + 3] + bias, p.act));
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                const int sg = j * 32 + e;
+                const int u = p.Q * m + sg;
+                if (sg < p.Q && u < p.lout) y[u] = act_fn(v[e] + bias, p.act);
+              }
             }
             continue;
           }
