@@ -36,6 +36,10 @@ W, S, B, C = 32768, 256, 64, 21
 METRIC = "streaming snapshots/s and p50/p99 latency, BF16 vs FP32 path at stated error, 1 GB300"
 WORKLOAD = "DeepClean streaming: 21x32768 windows (8 s @ 4096 Hz), stride 256, batch 64, overlap-add"
 L2_BYTES = 129 * 1024 * 1024
+# ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the 8 conv_tc
+# launches of one 64-window push (set to None whenever conv_tc changes until
+# it is captured again)
+CONV_TRAFFIC_BYTES_PER_PUSH = 238_085_632 + 59_392
 
 
 def dc_flops_per_window(L=W):
@@ -51,6 +55,21 @@ def dc_flops_per_window(L=W):
             f += 2 * cout * cin * k * lin
         lin = lout
     return f
+
+
+def dc_act_bytes_per_push(L=W, batch=B, stride=S, c_in=C):
+    """Algorithmic bytes of the 8 conv layers of one push in BF16: the unique
+    ring input once (the batch's windows overlap), then every layer's output
+    written once and read once by the next layer; the prediction in FP32."""
+    from paper_2108_12430_gb300 import synth
+    cpad = (c_in + 7) // 8 * 8
+    total = cpad * (L + (batch - 1) * stride) * 2
+    lin = L
+    for kind, cin, cout, k, s, pl, pr, op, bn, act in synth.DEEPCLEAN_LAYERS:
+        lout = (lin + pl + pr - k) // s + 1 if kind == "conv" else (lin - 1) * s - pl - pr + k + op
+        total += batch * (cout * lout * 4 if cout == 1 else 2 * (cout + 7) // 8 * 8 * lout * 2)
+        lin = lout
+    return total
 
 
 def dc_layer_flops(L=W):
@@ -366,7 +385,9 @@ def gpu_arm(args):
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         bound = "alu"
         peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
-    traffic = None
+    # DRAM bytes (read + write) of the 8 conv launches of one push from an ncu
+    # capture of the current kernel (cold cache; profiles/conv_tc_deepclean_stream_batch64.md)
+    traffic = CONV_TRAFFIC_BYTES_PER_PUSH if headline == "bf16" else None
     configs = extra_configs(G, torch, dev_index, flush)
     configs.update(train_config(G, torch, dev_index, flush))
     configs.update(serve_configs(G, dev_index))
@@ -398,7 +419,9 @@ def gpu_arm(args):
         "roofline": {"bound": bound, "kernel": "conv layers (8 launches per step)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_note,
-                     "per_unit": f"{dc_flops_per_window()} flop per window x {B} windows per step"},
+                     "per_unit": f"{dc_flops_per_window()} flop per window x {B} windows per step",
+                     "traffic_unit": "DRAM bytes per step (the 8 conv launches), ncu cold-cache capture",
+                     "algorithmic_bytes_per_step": dc_act_bytes_per_push()},
         "paths": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in paths.items()},
         "configs": configs,
         "cpu_baseline": cpu,
