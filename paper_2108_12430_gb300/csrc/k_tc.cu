@@ -62,6 +62,9 @@ struct TcParams {
   const uint32_t* table;
   int n_steps, npad, sps, nst, step_bytes, a_bytes, ncols, resident;
   int na;  // input stages in the A ring (2..kMaxA)
+  // output-channel split: a tile is (M tile, column slice); each slice has
+  // ncol = npad / nsplit columns (used when a layer has fewer tiles than SMs)
+  int nsplit, ncol;
   uint32_t idesc;
   int fp8;
   const float* bias;
@@ -122,6 +125,10 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abor
     }
   }
   return true;
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -276,6 +283,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const int n_chunks = p.resident ? 1 : (p.n_steps + p.sps - 1) / p.sps;
+  // Programmatic dependent launch: the next kernel in the stream may start its
+  // own set-up now; everything above (barriers, tables, TMEM) and the resident
+  // weight load below touch only this launch's constant data and run while
+  // the previous kernel finishes.  griddep_wait() blocks until the previous
+  // kernel has completed and its writes are visible (a no-op for a launch
+  // without the attribute).
+  griddep_launch_dependents();
 
   if (warp == 0) {
     // ---------------- producer: input tiles (and weights) by bulk TMA ----------------
@@ -283,12 +297,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
       mbar_expect_tx(bar(w_full), (uint32_t)(p.n_steps * p.step_bytes));
       bulk_g2s(sW, p.wimg, (uint32_t)(p.n_steps * p.step_bytes), bar(w_full));
     }
+    griddep_wait();
     int i = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
       const int s = i % na, k = i / na;
       if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
-      const int b = t / p.tiles_per_item;
-      const int m0 = (t - b * p.tiles_per_item) * 128 * p.MT;
+      const int tm = t / p.nsplit, sl = t - tm * p.nsplit;
+      const int b = tm / p.tiles_per_item;
+      const int m0 = (tm - b * p.tiles_per_item) * 128 * p.MT;
       const int base = m0 + p.dmin;
       const uint32_t sAs = sA + (uint32_t)s * (uint32_t)p.a_bytes;
       const char* src0 = p.item_ptr
@@ -334,9 +350,23 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
             if (use >= 1 && !mbar_wait(bar(w_empty + st), (uint32_t)(use - 1) & 1u, abort_flag, p.err, kErrWaitEmpty))
               break;
             const int s0 = c * p.sps, s1 = min(p.n_steps, s0 + p.sps);
-            const uint32_t bytes = (uint32_t)((s1 - s0) * p.step_bytes);
-            mbar_expect_tx(bar(w_full + st), bytes);
-            bulk_g2s(sW + (uint32_t)st * stage_bytes, p.wimg + (int64_t)s0 * p.step_bytes, bytes, bar(w_full + st));
+            if (p.nsplit == 1) {
+              const uint32_t bytes = (uint32_t)((s1 - s0) * p.step_bytes);
+              mbar_expect_tx(bar(w_full + st), bytes);
+              bulk_g2s(sW + (uint32_t)st * stage_bytes, p.wimg + (int64_t)s0 * p.step_bytes, bytes, bar(w_full + st));
+            } else {
+              // only this slice's rows of both K-halves of every step, each
+              // at its place in the full step layout
+              const uint32_t rows_bytes = (uint32_t)p.ncol * 16u, half = (uint32_t)p.npad * 16u;
+              const uint32_t off = (uint32_t)sl * rows_bytes;
+              mbar_expect_tx(bar(w_full + st), (uint32_t)(2 * (s1 - s0)) * rows_bytes);
+              for (int sx = s0; sx < s1; ++sx)
+                for (uint32_t hh = 0; hh < 2; ++hh) {
+                  const uint32_t o = (uint32_t)(sx - s0) * (uint32_t)p.step_bytes + hh * half + off;
+                  bulk_g2s(sW + (uint32_t)st * stage_bytes + o,
+                           p.wimg + (int64_t)sx * p.step_bytes + hh * half + off, rows_bytes, bar(w_full + st));
+                }
+            }
           }
         }
       }
@@ -348,20 +378,23 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     if (lane == 0) {
       bool ok = !p.resident || mbar_wait(bar(w_full), 0u, abort_flag, p.err, kErrWaitW);
       const bool fp8 = p.fp8 != 0;
-      const int MT = p.MT, npad = p.npad;
+      const int MT = p.MT, npad = p.ncol;  // accumulator columns of one tile (its slice)
       const uint32_t idesc = p.idesc;
       int i = 0;
       for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x, ++i) {
         const int sa = i % na, ka = i / na;  // input stage
         const int s = i & 1, k = i >> 1;     // accumulator buffer
+        const int sl = t % p.nsplit;         // column slice
         if (!mbar_wait(bar(a_full + sa), (uint32_t)ka & 1u, abort_flag, p.err, kErrWaitA)) break;
         if (k >= 1 && !mbar_wait(bar(acc_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitAcc)) break;
         tc_fence_after();
         // descriptor start addresses count 16-byte units in their low bits
         const uint64_t a_stage = (uint64_t)(((uint32_t)sa * (uint32_t)p.a_bytes) >> 4);
-        const uint32_t d0 = tmem + (uint32_t)(s * p.MT * p.npad);
+        const uint32_t d0 = tmem + (uint32_t)(s * MT * npad);
+        // the slice's B rows start sl * ncol rows into each K-half
+        const uint64_t b_slice = (uint64_t)(sl * p.ncol);
         for (int c = 0; c < n_chunks; ++c) {
-          uint64_t b_stage = 0;
+          uint64_t b_stage = b_slice;
           int st = 0;
           if (!p.resident) {
             const int gc = i * n_chunks + c, use = gc / p.nst;
@@ -371,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
               break;
             }
             tc_fence_after();
-            b_stage = (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
+            b_stage = b_slice + (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
           }
           const int s0 = p.resident ? 0 : c * p.sps, s1 = p.resident ? p.n_steps : min(p.n_steps, s0 + p.sps);
           // The issue rate of this one thread bounds the tensor pipe for small
@@ -422,30 +455,33 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     const int col_half = (warp - 2) >> 2;  // which 32-column chunks it drains
     const int row = quarter * 32 + lane;
     const bool plain = !p.fp32_single && !p.fp32_d2s && !p.fp8_out && !p.res && !p.wscale;
+    griddep_wait();  // outputs and residuals are shared with the previous kernels
     int i = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
       const int s = i & 1, k = i >> 1;
       if (!mbar_wait(bar(acc_full + s), (uint32_t)k & 1u, abort_flag, p.err, kErrWaitAcc)) break;
       __syncwarp();
       tc_fence_after();
-      const int b = t / p.tiles_per_item;
-      const int m0 = (t - b * p.tiles_per_item) * 128 * p.MT;
+      const int tm = t / p.nsplit, sl = t - tm * p.nsplit;
+      const int b = tm / p.tiles_per_item;
+      const int m0 = (tm - b * p.tiles_per_item) * 128 * p.MT;
       char* const outb = p.out + (int64_t)b * p.out_b;
       const char* const resb = p.res ? p.res + (int64_t)b * p.res_b : nullptr;
       const int out_mask = p.out_P - 1, res_mask = p.res_P - 1;
       for (int mt = 0; mt < p.MT; ++mt) {
         const int m = m0 + mt * 128 + row;
         const bool valid = m < p.mout;
-        for (int j = col_half; j < p.npad / 32; j += 2) {
+        for (int j = col_half; j < p.ncol / 32; j += 2) {
           float v[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((s * p.MT + mt) * p.npad + j * 32), v);
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((s * p.MT + mt) * p.ncol + j * 32), v);
           if (!valid) continue;
+          const int jg = sl * (p.ncol / 32) + j;  // chunk index among all npad columns
           if (plain) {
             // bf16 out, no residual, no FP8 scale: 4 groups of 8 channels,
             // straight-line, bias as float4 pairs, no per-group branches
             // (the common DeepClean / BBHnet case; invalid groups are those
             // past Q, C_out or the output length, known per column / row)
-            const int n_base = j * 32;
+            const int n_base = jg * 32;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
               const int n0 = n_base + h * 8;
@@ -471,8 +507,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
             // column n = sigma: output position Q m + sigma, channel 0
             float* y = reinterpret_cast<float*>(outb);
             const float bias = s_bias[0];
-            const int u0 = p.Q * m + j * 32;
-            if (j * 32 + 32 <= p.Q && u0 + 32 <= p.lout && ((uintptr_t)(y + u0) & 15) == 0) {
+            const int u0 = p.Q * m + jg * 32;
+            if (jg * 32 + 32 <= p.Q && u0 + 32 <= p.lout && ((uintptr_t)(y + u0) & 15) == 0) {
               // 32 consecutive samples of this row: eight 16-byte stores
               float4* y4 = reinterpret_cast<float4*>(y + u0);
 #pragma unroll
@@ -482,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
             } else {
 #pragma unroll
               for (int e = 0; e < 32; ++e) {
-                const int sg = j * 32 + e;
+                const int sg = jg * 32 + e;
                 const int u = p.Q * m + sg;
                 if (sg < p.Q && u < p.lout) y[u] = act_fn(v[e] + bias, p.act);
               }
@@ -491,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
           }
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            const int n0 = j * 32 + h * 8;
+            const int n0 = jg * 32 + h * 8;
             const int sg = n0 >> p.coutp_log, o0 = n0 & (p.coutp - 1);
             const int u = p.Q * m + sg;
             if (sg >= p.Q || o0 >= p.cout || u >= p.lout) continue;
@@ -888,8 +924,20 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.MT = MT;
   q.rows = 128 * MT + L.dspan;
   q.a_bytes = (int)a_bytes_for(MT);
+  q.tiles_per_item = (q.mout + 128 * MT - 1) / (128 * MT);
+  // output-channel split while a layer has fewer tiles than SMs (small batches
+  // of the deep BBHnet layers): slices of >= 32 columns, each CTA streaming
+  // only its slice of the weights
+  q.nsplit = 1;
+  {
+    const int64_t tiles_m = (int64_t)q.tiles_per_item * B;
+    while (q.nsplit < 8 && L.npad / (2 * q.nsplit) >= 32 && (L.npad / (2 * q.nsplit)) % 32 == 0 &&
+           tiles_m * 2 * q.nsplit <= sms)
+      q.nsplit *= 2;
+  }
+  q.ncol = L.npad / q.nsplit;
   int ncols = 32;
-  while (ncols < 2 * MT * L.npad) ncols *= 2;
+  while (ncols < 2 * MT * q.ncol) ncols *= 2;
   GW_CHECK_ARG(ncols <= 512, "accumulators exceed tensor memory");
   q.ncols = ncols;
   // input stages: as many as fit (up to kMaxA), keeping two CTAs per SM where
@@ -906,11 +954,10 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
     while (na < kMaxA && smem_for(na + 1) <= cap) ++na;
     q.na = na;
   }
-  q.tiles_per_item = (q.mout + 128 * MT - 1) / (128 * MT);
-  q.n_tiles = q.tiles_per_item * B;
+  q.n_tiles = q.tiles_per_item * B * q.nsplit;
   // instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3 (kind::f8f6f4),
-  // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-  q.idesc = (1u << 4) | (fp8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(L.npad >> 3) << 17) |
+  // both K-major, N >> 3 at bit 17, M >> 4 at bit 24 (N = the slice's columns)
+  q.idesc = (1u << 4) | (fp8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(q.ncol >> 3) << 17) |
             ((uint32_t)(128 >> 4) << 24);
   q.fp8 = fp8;
   q.bias = L.b;
@@ -965,13 +1012,25 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
   static int sms = 0;
   if (!sms) sms = sm_count();
   plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B, sms);
-  static bool attr = false;
-  if (!attr) {
+  static bool smem_attr = false;
+  if (!smem_attr) {
     GW_CUDA(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr = true;
+    smem_attr = true;
   }
-  conv_tc_kernel<<<grid, kThreads, smem, st>>>(q);
-  GW_LAUNCH_CHECK();
+  // programmatic stream serialisation: this launch may begin (set-up, weight
+  // loads) while the previous kernel in the stream runs; the kernel waits on
+  // griddepcontrol before touching the previous kernels' data
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  GW_CUDA(cudaLaunchKernelEx(&cfg, conv_tc_kernel, q));
 }
 
 void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,
@@ -1026,9 +1085,9 @@ extern "C" int gw_tc_inspect(const int* spec, int precision, const double* wfold
     size_t smem = 0;
     dim3 grid;
     plan_conv_tc(q, L, fp8, in, lout, out, nullptr, &smem, &grid, batch > 0 ? batch : 1, 152);
-    const int meta[20] = {L.n_steps, L.npad,   L.gin,   L.pin,        L.n_chains,   L.dspan, L.dmin,
+    const int meta[21] = {L.n_steps, L.npad,   L.gin,   L.pin,        L.n_chains,   L.dspan, L.dmin,
                           q.MT,      q.rows,   q.a_bytes, q.resident ? L.n_steps : q.sps, q.nst, q.step_bytes,
-                          q.ncols,   q.tiles_per_item, q.mout, L.coutp, (int)q.idesc, (int)smem, lout};
+                          q.ncols,   q.tiles_per_item, q.mout, L.coutp, (int)q.idesc, (int)smem, lout, q.nsplit};
     memcpy(meta_out, meta, sizeof(meta));
     return GW_OK;
   } catch (const gw::Error& e) {

@@ -441,7 +441,7 @@ def gw_launch_count():
 
 
 TC_META = ("n_steps", "npad", "groups", "in_P", "Q", "dspan", "dmin", "MT", "rows", "a_bytes", "sps", "nst",
-           "step_bytes", "ncols", "tiles_per_item", "mout", "coutp", "idesc", "smem", "lout")
+           "step_bytes", "ncols", "tiles_per_item", "mout", "coutp", "idesc", "smem", "lout", "nsplit")
 
 
 def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P, batch=1):
@@ -451,7 +451,7 @@ def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P, batch=1):
     cap = 1 << 24
     img = np.zeros(cap, np.uint8)
     table = np.zeros(1 << 14, np.uint32)
-    meta = (C.c_int * 20)()
+    meta = (C.c_int * 21)()
     _check(lib().gw_tc_inspect(spec_a, precision, wf.ctypes.data_as(C.POINTER(C.c_double)), lin, in_P, out_P, batch,
                                img.ctypes.data, cap, table.ctypes.data_as(C.POINTER(C.c_uint32)), table.size, meta))
     md = dict(zip(TC_META, list(meta)))

@@ -63,7 +63,9 @@ def emulate(spec, x, img, table, md, fp8=False):
     lin = x.shape[1]
     lout, mout = md["lout"], md["mout"]
     assert rows * 16 * Gn * P <= a_bytes
-    assert md["smem"] <= 227 * 1024 and md["ncols"] <= 512 and 2 * MT * npad <= md["ncols"]
+    # a tile holds one slice of npad / nsplit columns; two accumulators of MT sub-tiles
+    assert npad % md["nsplit"] == 0 and (npad // md["nsplit"]) % 32 == 0
+    assert md["smem"] <= 227 * 1024 and md["ncols"] <= 512 and 2 * MT * (npad // md["nsplit"]) <= md["ncols"]
     assert Q * coutp <= npad
     xb = np.zeros((Gn * cg, lin))
     xb[:cin] = x
@@ -197,7 +199,7 @@ def test_tc_instruction_descriptor_fields():
     _, _, md = G.gw_tc_inspect((0, 32, 64, 7, 2, 3, 3, 0), G.GW_BF16, np.zeros((64, 32, 7)), 256, 0, 1)
     d = md["idesc"]
     assert (d >> 4) & 3 == 1 and (d >> 7) & 7 == 1 and (d >> 10) & 7 == 1
-    assert (d >> 15) & 3 == 0 and (d >> 17) & 63 == md["npad"] >> 3 and (d >> 24) & 31 == 128 >> 4
+    assert (d >> 15) & 3 == 0 and (d >> 17) & 63 == (md["npad"] // md["nsplit"]) >> 3 and (d >> 24) & 31 == 128 >> 4
 
 
 def test_tc_layer_plans_fold_positions():
