@@ -16,11 +16,18 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ int64_t pmod(int64_t a, int64_t m) {
-  const int64_t r = a % m;
-  return r < 0 ? r + m : r;
-}
 __device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+// Ring residue of an absolute sample index (int64, may be negative): one
+// 64-bit reduction per thread; the element loops then step through the ring
+// in 32 bits with wrap(), which needs 0 <= b < m and 0 <= d < m.
+__device__ __forceinline__ uint32_t ring_mod(int64_t a, int64_t m) {
+  const int64_t r = a % m;
+  return (uint32_t)(r < 0 ? r + m : r);
+}
+__device__ __forceinline__ uint32_t wrap(uint32_t b, uint32_t d, uint32_t m) {
+  const uint32_t q = b + d;
+  return q >= m ? q - m : q;
+}
 
 // Witness ring update (standardised on write) and strain ring update.
 // Blocked BF16 ring: channel group g, ring position q (0 <= q < 2R) is the
@@ -32,37 +39,42 @@ __global__ void serve_push_kernel(const ServeItem* __restrict__ items, ServeGeom
   if (!it.active) return;
   const int S = it.S;
   const float* src = it.in;
-  const int64_t R = g.R;
+  const uint32_t R = (uint32_t)g.R, h0 = ring_mod(it.head, g.R);
   if (g.bf16) {
     __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(it.wring);
-    const int64_t plane_rows = 2 * R / g.P;
+    const uint32_t P = (uint32_t)g.P, plane_rows = 2u * R / P;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.G * S; e += gridDim.x * blockDim.x) {
       const int grp = e / S, t = e - grp * S;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = grp * 8 + j;
+        v[j] = c < g.C ? src[c * S + t] : 0.f;  // all loads in flight before the first use
+      }
       __align__(16) __nv_bfloat16 v8[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int c = grp * 8 + j;
-        const float v = c < g.C ? (src[(int64_t)c * S + t] - mean[c]) * istd[c] : 0.f;
-        v8[j] = __float2bfloat16_rn(v);
+        v8[j] = __float2bfloat16_rn(c < g.C ? (v[j] - mean[c]) * istd[c] : 0.f);
       }
-      const int64_t q = pmod(it.head + t, R), q2 = q + R;
+      const uint32_t q = wrap(h0, (uint32_t)t, R), q2 = q + R;
       uint4* base = reinterpret_cast<uint4*>(ring + (int64_t)grp * 2 * R * 8);
       const uint4 val = *reinterpret_cast<const uint4*>(v8);
-      base[(q % g.P) * plane_rows + q / g.P] = val;
-      base[(q2 % g.P) * plane_rows + q2 / g.P] = val;
+      base[(q % P) * plane_rows + q / P] = val;
+      base[(q2 % P) * plane_rows + q2 / P] = val;
     }
   } else {
     float* ring = reinterpret_cast<float*>(it.wring);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.C * S; e += gridDim.x * blockDim.x) {
       const int c = e / S, t = e - c * S;
-      const float v = (src[(int64_t)c * S + t] - mean[c]) * istd[c];
-      const int64_t q = pmod(it.head + t, R);
+      const float v = (src[c * S + t] - mean[c]) * istd[c];
+      const uint32_t q = wrap(h0, (uint32_t)t, R);
       ring[(int64_t)c * 2 * R + q] = v;
       ring[(int64_t)c * 2 * R + q + R] = v;
     }
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < S; t += gridDim.x * blockDim.x)
-    it.strain[pmod(it.head + t, R)] = src[(int64_t)g.C * S + t];
+    it.strain[wrap(h0, (uint32_t)t, R)] = src[g.C * S + t];
 }
 
 // Subtraction and aggregation of one new window per item (the window ends at
@@ -72,26 +84,32 @@ __global__ void serve_sub_ola_kernel(const ServeItem* __restrict__ items, ServeG
   const ServeItem it = items[blockIdx.y];
   if (!it.active) return;
   const int S = it.S, W = g.W;
-  const int64_t head = it.head, k = head / S, R = g.R;
+  const int64_t head = it.head, k = head / S;
   const float* pr = pred + (int64_t)blockIdx.y * W;
+  // window sample e is time tau = head + S - W + e; it is emitted as cleaned
+  // sample o = e - (W - S - delta) when 0 <= o < S
+  const uint32_t R = (uint32_t)g.R, qb = ring_mod(head + S - W, g.R);
+  const uint32_t cb = ring_mod(head - g.delta, g.Rc);
+  const int o_shift = W - S - g.delta;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < W; e += gridDim.x * blockDim.x) {
     const int64_t tau = head + S - W + e;
-    const bool emits = tau >= head - g.delta && tau < head + S - g.delta;
+    const int o = e - o_shift;
+    const bool emits = o >= 0 && o < S;
+    const uint32_t q = wrap(qb, (uint32_t)e, R);
     float value;
     if (g.mode == GW_AGG_LATEST) {
       if (!emits) continue;
       value = pr[e];
     } else {
-      const int64_t q = pmod(tau, R);
       const float sum = (tau < head ? it.acc[q] : 0.f) + pr[e];
       it.acc[q] = sum;
       if (!emits) continue;
       const int64_t first = tau >= 0 ? floordiv64(tau, S) : 0;
       value = sum / (float)(k - first + 1);
     }
-    const float c = (tau >= 0 ? it.strain[pmod(tau, R)] : 0.f) - value;
-    it.out[tau - head + g.delta] = c;
-    if (tau >= 0) it.clean[pmod(tau, g.Rc)] = c;
+    const float c = (tau >= 0 ? it.strain[q] : 0.f) - value;
+    it.out[o] = c;
+    if (tau >= 0) it.clean[wrap(cb, (uint32_t)o, (uint32_t)g.Rc)] = c;
   }
 }
 
@@ -101,13 +119,18 @@ __global__ void serve_decimate_kernel(const ServeItem* __restrict__ items, Serve
   const ServeItem it = items[blockIdx.y];
   if (!it.active) return;
   const int c = (K - 1) / 2;
+  const uint32_t Rc = (uint32_t)g.Rc;
   for (int64_t m = it.m0 + blockIdx.x * blockDim.x + threadIdx.x; m < it.m1; m += gridDim.x * blockDim.x) {
+    // taps j with 2m + j - c < 0 read the zeros before the stream start
+    const int64_t jz = c - 2 * m;
+    const int j0 = jz <= 0 ? 0 : (jz > K ? K : (int)jz);
+    uint32_t q = ring_mod(2 * m - c + j0, g.Rc);
     float a = 0.f;
-    for (int j = 0; j < K; ++j) {
-      const int64_t tau = 2 * m + j - c;
-      if (tau >= 0) a = fmaf(f[j], it.clean[pmod(tau, g.Rc)], a);
+    for (int j = j0; j < K; ++j) {
+      a = fmaf(f[j], it.clean[q], a);
+      q = q + 1 == Rc ? 0u : q + 1;
     }
-    it.dec[pmod(m, g.Rd)] = a;
+    it.dec[ring_mod(m, g.Rd)] = a;
   }
 }
 
@@ -122,20 +145,20 @@ __global__ void serve_whiten_kernel(const ServeItem* __restrict__ items, ServeGe
   const int c = (K - 1) / 2;
   const int nn = (int)(it.n1 - it.n0);
   float* hs = sh;
-  float* ds = sh + K;  // d[n0 - c + i], i < nn + K - 1
+  float* ds = sh + K;  // d[n0 - c + i], i < nn + K - 1 (< Rd)
   for (int j = threadIdx.x; j < K; j += blockDim.x) hs[j] = h[j];
-  for (int i = threadIdx.x; i < nn + K - 1; i += blockDim.x) {
-    const int64_t m = it.n0 - c + i;
-    ds[i] = m >= 0 ? it.dec[pmod(m, g.Rd)] : 0.f;
-  }
+  const uint32_t Rd = (uint32_t)g.Rd, db = ring_mod(it.n0 - c, g.Rd);
+  for (int i = threadIdx.x; i < nn + K - 1; i += blockDim.x)
+    ds[i] = it.n0 - c + i >= 0 ? it.dec[wrap(db, (uint32_t)i, Rd)] : 0.f;
   __syncthreads();
+  const uint32_t Rw = (uint32_t)g.Rw, wb = ring_mod(it.n0, g.Rw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i < nn; i += blockDim.x >> 5) {
     float a = 0.f;
     for (int j = lane; j < K; j += 32) a = fmaf(hs[j], ds[i + j], a);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) it.white[pmod(it.n0 + i, g.Rw)] = a;
+    if (lane == 0) it.white[wrap(wb, (uint32_t)i, Rw)] = a;
   }
 }
 
@@ -146,13 +169,11 @@ __global__ void serve_gather_kernel(const ServeItem* __restrict__ items, int Bb,
   const int r = blockIdx.y;
   const ServeItem it0 = items[r];
   float* dst = x + (int64_t)r * n_det * Lb;
+  const uint32_t Rw = (uint32_t)g.Rw, wb = ring_mod(it0.n1 - Lb, g.Rw);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_det * Lb; e += gridDim.x * blockDim.x) {
     const int d = e / Lb, t = e - d * Lb;
     float v = 0.f;
-    if (it0.active) {
-      const int64_t n = it0.n1 - Lb + t;
-      if (n >= 0) v = items[d * Bb + r].white[pmod(n, g.Rw)];
-    }
+    if (it0.active && it0.n1 - Lb + t >= 0) v = items[d * Bb + r].white[wrap(wb, (uint32_t)t, Rw)];
     dst[e] = v;
   }
 }

@@ -26,64 +26,67 @@ __device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t b) {
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
 }
 
+// The ring position of new sample i is (h0 + i) mod R with h0 = head mod R
+// reduced on the host; i < n <= R, so one conditional subtraction suffices and
+// all ring arithmetic stays in 32 bits.
+__device__ __forceinline__ uint32_t ring_pos(int h0, int i, int R) {
+  uint32_t q = (uint32_t)h0 + (uint32_t)i;
+  return q >= (uint32_t)R ? q - (uint32_t)R : q;
+}
+
 // src [C][src_ld] (n new samples per channel) -> ring [C][2R], standardised.
-__global__ void ring_push_f32_kernel(const float* __restrict__ src, int64_t src_ld, int C, int n,
-                                     float* __restrict__ ring, int64_t R, int64_t head,
-                                     const float* __restrict__ mean, const float* __restrict__ istd,
-                                     int* status) {
-  const int64_t total = (int64_t)C * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / n), i = (int)(e % n);
-    float v = src[(int64_t)c * src_ld + i];
-    if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
-    if (mean) v = (v - mean[c]) * istd[c];
-    const int64_t q = pmod(head + i, R);
-    float* row = ring + (int64_t)c * 2 * R;
-    row[q] = v;
-    row[q + R] = v;
-  }
+// Grid: (samples, channel).
+__global__ void ring_push_f32_kernel(const float* __restrict__ src, int64_t src_ld, int n,
+                                     float* __restrict__ ring, int R, int h0, const float* __restrict__ mean,
+                                     const float* __restrict__ istd, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
+  if (i >= n) return;
+  float v = __ldg(src + (int64_t)c * src_ld + i);
+  if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
+  if (mean) v = (v - mean[c]) * istd[c];
+  const uint32_t q = ring_pos(h0, i, R);
+  float* row = ring + (int64_t)c * 2 * R;
+  row[q] = v;
+  row[q + (uint32_t)R] = v;
 }
 
 // src [C][src_ld] -> ring [G][P][2R / P][8] bf16 (channel-group blocked,
 // P phase planes), standardised.  One thread writes the 8 channels of one
-// (group, time) as a 16-byte store; R is a multiple of P.
-__global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src_ld, int C, int G, int n,
-                                      __nv_bfloat16* __restrict__ ring, int64_t R, int64_t head, int P,
+// (group, time) as a 16-byte store; R is a multiple of P.  Grid: (samples, group).
+__global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src_ld, int C, int n,
+                                      __nv_bfloat16* __restrict__ ring, int R, int h0, int P,
                                       const float* __restrict__ mean, const float* __restrict__ istd,
                                       int* status) {
-  const int64_t plane_rows = 2 * R / P;
-  const int64_t total = (int64_t)G * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int g = (int)(e / n), i = (int)(e % n);
-    __align__(16) __nv_bfloat16 v8[8];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
+  if (i >= n) return;
+  __align__(16) __nv_bfloat16 v8[8];
+  bool bad = false;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = g * 8 + j;
-      float v = 0.f;
-      if (c < C) {
-        v = src[(int64_t)c * src_ld + i];
-        if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
-        if (mean) v = (v - mean[c]) * istd[c];
-      }
-      v8[j] = __float2bfloat16_rn(v);
+  for (int j = 0; j < 8; ++j) {
+    const int c = g * 8 + j;
+    float v = 0.f;
+    if (c < C) {
+      v = __ldg(src + (int64_t)c * src_ld + i);
+      bad |= !isfinite(v);
+      if (mean) v = (v - mean[c]) * istd[c];
     }
-    const int64_t q = pmod(head + i, R);
-    uint4 val = *reinterpret_cast<const uint4*>(v8);
-    uint4* grp = reinterpret_cast<uint4*>(ring + (int64_t)g * 2 * R * 8);
-    grp[(q % P) * plane_rows + q / P] = val;
-    grp[((q + R) % P) * plane_rows + (q + R) / P] = val;
+    v8[j] = __float2bfloat16_rn(v);
   }
+  if (bad) atomicExch(status, GW_ENONFINITE);
+  const uint32_t q = ring_pos(h0, i, R), q2 = q + (uint32_t)R, up = (uint32_t)P;
+  const uint32_t plane_rows = 2u * (uint32_t)R / up;
+  const uint4 val = *reinterpret_cast<const uint4*>(v8);
+  uint4* grp = reinterpret_cast<uint4*>(ring + (int64_t)g * 2 * R * 8);
+  grp[(q % up) * plane_rows + q / up] = val;
+  grp[(q2 % up) * plane_rows + q2 / up] = val;
 }
-
-__global__ void strain_push_kernel(const float* __restrict__ src, int n, float* __restrict__ ring, int64_t R,
-                                   int64_t head, int* status) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float v = src[i];
-    if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
-    ring[pmod(head + i, R)] = v;
-  }
+__global__ void strain_push_kernel(const float* __restrict__ src, int n, float* __restrict__ ring, int R, int h0,
+                                   int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = __ldg(src + i);
+  if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
+  ring[ring_pos(h0, i, R)] = v;
 }
 
 // Fused subtract + aggregate over one batch of n windows (Methods, "Data
@@ -192,10 +195,20 @@ void launch_ring_fill(void* ring, int bf16, int C, int G, int64_t R2, const floa
   GW_LAUNCH_CHECK();
 }
 
+// head reduced to [0, R) on the host; the kernels index the ring in 32 bits
+static int ring_head(int64_t head, int64_t R, int n) {
+  GW_CHECK_ARG(R >= 1 && 2 * R < (int64_t)1 << 31, "ring capacity out of range");
+  GW_CHECK_ARG(n >= 0 && n <= R, "more new samples than the ring holds");
+  const int64_t h = head % R;
+  return (int)(h < 0 ? h + R : h);
+}
+
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring, int64_t R,
                           int64_t head, const float* mean, const float* istd, int* status, cudaStream_t st) {
-  ring_push_f32_kernel<<<grid_for((int64_t)C * n), kThreads, 0, st>>>(src, src_ld, C, n, ring, R, head, mean,
-                                                                       istd, status);
+  const int h0 = ring_head(head, R, n);
+  if (n == 0 || C == 0) return;
+  ring_push_f32_kernel<<<dim3((n + kThreads - 1) / kThreads, C), kThreads, 0, st>>>(src, src_ld, n, ring, (int)R, h0,
+                                                                                     mean, istd, status);
   GW_LAUNCH_CHECK();
 }
 
@@ -203,14 +216,18 @@ void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n
                            int64_t R, int64_t head, int P, const float* mean, const float* istd, int* status,
                            cudaStream_t st) {
   GW_CHECK_ARG(P >= 1 && R % P == 0, "ring capacity must be a multiple of the phase count");
-  ring_push_bf16_kernel<<<grid_for((int64_t)G * n), kThreads, 0, st>>>(src, src_ld, C, G, n, ring, R, head, P,
-                                                                        mean, istd, status);
+  const int h0 = ring_head(head, R, n);
+  if (n == 0 || G == 0) return;
+  ring_push_bf16_kernel<<<dim3((n + kThreads - 1) / kThreads, G), kThreads, 0, st>>>(src, src_ld, C, n, ring, (int)R,
+                                                                                      h0, P, mean, istd, status);
   GW_LAUNCH_CHECK();
 }
 
 void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head, int* status,
                         cudaStream_t st) {
-  strain_push_kernel<<<grid_for(n), kThreads, 0, st>>>(src, n, ring, R, head, status);
+  const int h0 = ring_head(head, R, n);
+  if (n == 0) return;
+  strain_push_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(src, n, ring, (int)R, h0, status);
   GW_LAUNCH_CHECK();
 }
 

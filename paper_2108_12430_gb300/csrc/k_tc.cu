@@ -52,6 +52,10 @@ constexpr int kMaxA = 6;  // deepest input ring
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
+// Source of the zero padding rows of edge tiles (a stage plane holds at most
+// kZeroRows rows; the planner checks it).
+constexpr int kZeroRows = 2048;
+__device__ __align__(128) uint4 g_zero_rows[kZeroRows];
 
 struct TcParams {
   const char* in;
@@ -126,6 +130,32 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abor
   }
   return true;
 }
+// Named barrier 1 over the epilogue warps with an AND-reduction of `ok`: every
+// participating thread gets the same verdict, so the warps leave the tile loop
+// together (a warp that left alone would strand the others in the barrier).
+__device__ __forceinline__ bool epi_bar_and(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)ok), "n"(32 * kEpiWarps)
+      : "memory");
+  return r != 0;
+}
+// Tile t -> (item b, first output row m0, column slice sl).  Within an item
+// the M tiles are visited rotated by the item index, so that the item's edge
+// tiles (first and last, which zero-fill padding rows on the slow path) fall
+// on every CTA about equally often; with the plain order a persistent CTA
+// whose stride is a multiple of half the tiles per item met an edge tile on
+// every other step.
+__device__ __forceinline__ void tile_coords(const TcParams& p, int t, int& b, int& m0, int& sl) {
+  const int tm = t / p.nsplit;
+  sl = t - tm * p.nsplit;
+  b = tm / p.tiles_per_item;
+  int j = tm - b * p.tiles_per_item + b % p.tiles_per_item;
+  if (j >= p.tiles_per_item) j -= p.tiles_per_item;
+  m0 = j * 128 * p.MT;
+}
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -133,14 +163,10 @@ __device__ __forceinline__ void griddep_launch_dependents() {
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
-}
-__device__ __forceinline__ void st_shared_zero16(uint32_t addr) {
-  asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(addr), "r"(0) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -302,9 +328,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
       const int s = i % na, k = i / na;
       if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
-      const int tm = t / p.nsplit, sl = t - tm * p.nsplit;
-      const int b = tm / p.tiles_per_item;
-      const int m0 = (tm - b * p.tiles_per_item) * 128 * p.MT;
+      int b, m0, sl;
+      tile_coords(p, t, b, m0, sl);
       const int base = m0 + p.dmin;
       const uint32_t sAs = sA + (uint32_t)s * (uint32_t)p.a_bytes;
       const char* src0 = p.item_ptr
@@ -318,29 +343,20 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
           bulk_g2s(sAs + (uint32_t)(plane * p.rows) * 16u, src0 + s_poff[plane], (uint32_t)p.rows * 16u,
                    bar(a_full + s));
       } else {
-        // edge tile: rows outside a plane are the layer's zero padding, written
-        // here and made visible to the tensor core before the barrier fires
-        uint32_t total = 0;
-        for (int plane = 0; plane < planes; ++plane) {
-          const int r0 = max(0, -base), r1 = max(r0, min(p.rows, s_plen[plane] - base));
-          for (int r = lane; r < r0; r += 32) st_shared_zero16(sAs + (uint32_t)(plane * p.rows + r) * 16u);
-          for (int r = r1 + lane; r < p.rows; r += 32) st_shared_zero16(sAs + (uint32_t)(plane * p.rows + r) * 16u);
-          total += (uint32_t)(r1 - r0) * 16u;
-        }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) {
-          if (total)
-            mbar_expect_tx(bar(a_full + s), total);
-          else
-            mbar_arrive(bar(a_full + s));
-        }
+        // edge tile: rows outside a plane are the layer's zero padding; they
+        // are copied from a zero buffer by the same bulk engine, so every row
+        // of the stage arrives through the async proxy (no fence, no serial
+        // zero stores) and the stage expects the same bytes as an interior one
+        if (lane == 0) mbar_expect_tx(bar(a_full + s), (uint32_t)(planes * p.rows) * 16u);
         __syncwarp();
         for (int plane = lane; plane < planes; plane += 32) {
-          const int r0 = max(0, -base), r1 = max(r0, min(p.rows, s_plen[plane] - base));
+          const int r0 = min(p.rows, max(0, -base)), r1 = max(r0, min(p.rows, s_plen[plane] - base));
+          const uint32_t dst = sAs + (uint32_t)(plane * p.rows) * 16u;
+          if (r0 > 0) bulk_g2s(dst, g_zero_rows, (uint32_t)r0 * 16u, bar(a_full + s));
           if (r1 > r0)
-            bulk_g2s(sAs + (uint32_t)(plane * p.rows + r0) * 16u, src0 + s_poff[plane] + (int64_t)r0 * 16,
-                     (uint32_t)(r1 - r0) * 16u, bar(a_full + s));
+            bulk_g2s(dst + (uint32_t)r0 * 16u, src0 + s_poff[plane] + (int64_t)r0 * 16, (uint32_t)(r1 - r0) * 16u,
+                     bar(a_full + s));
+          if (p.rows > r1) bulk_g2s(dst + (uint32_t)r1 * 16u, g_zero_rows, (uint32_t)(p.rows - r1) * 16u, bar(a_full + s));
         }
       }
       if (lane == 0) {
@@ -459,12 +475,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
     int i = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
       const int s = i & 1, k = i >> 1;
-      if (!mbar_wait(bar(acc_full + s), (uint32_t)k & 1u, abort_flag, p.err, kErrWaitAcc)) break;
-      __syncwarp();
+      // One warp polls the accumulator barrier; the other seven sleep in the
+      // named barrier instead of spinning on issue slots that the MMA thread,
+      // the producer and the other CTA on the SM need.
+      bool ok = true;
+      if (warp == 2) ok = mbar_wait(bar(acc_full + s), (uint32_t)k & 1u, abort_flag, p.err, kErrWaitAcc);
+      if (!epi_bar_and(ok)) break;
       tc_fence_after();
-      const int tm = t / p.nsplit, sl = t - tm * p.nsplit;
-      const int b = tm / p.tiles_per_item;
-      const int m0 = (tm - b * p.tiles_per_item) * 128 * p.MT;
+      int b, m0, sl;
+      tile_coords(p, t, b, m0, sl);
       char* const outb = p.out + (int64_t)b * p.out_b;
       const char* const resb = p.res ? p.res + (int64_t)b * p.res_b : nullptr;
       const int out_mask = p.out_P - 1, res_mask = p.res_P - 1;
@@ -923,6 +942,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   }
   q.MT = MT;
   q.rows = 128 * MT + L.dspan;
+  GW_CHECK_ARG(q.rows <= kZeroRows, "input tile taller than the zero-row buffer");
   q.a_bytes = (int)a_bytes_for(MT);
   q.tiles_per_item = (q.mout + 128 * MT - 1) / (128 * MT);
   // output-channel split while a layer has fewer tiles than SMs (small batches
