@@ -73,6 +73,7 @@ struct LayerDev {
   // tensor-core path (BF16 / FP8): packed operand image and per-K-step table
   void* wq = nullptr;      // packed B operand image (bf16 or e4m3)
   uint32_t* table = nullptr;
+  std::vector<uint32_t> table_h;  // the same slice codes on the host (launch planning)
   float* wscale = nullptr; // FP8: per-output-channel dequant scale (weight scale * act scale)
   int n_steps = 0;         // K-steps (MMA instructions per M sub-tile)
   int npad = 0;            // N (output channels) padded for the MMA

@@ -48,6 +48,9 @@ namespace {
 // TMEM lane quarter (each takes every other 32-column chunk), so that every
 // SM sub-partition has two warps to hide the epilogue's instruction latency
 constexpr int kEpiWarps = 8;
+// CTAs per SM the planner may ask for (shared memory, TMEM columns and the
+// register file permitting: 65536 / (kThreads * 96 registers))
+constexpr int kMaxCtasPerSm = 2;
 constexpr int kMaxA = 6;  // deepest input ring
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 2000000000ll;
@@ -87,7 +90,15 @@ struct TcParams {
   int min_plen;                          // rows of the shortest input plane
   int fp32_d2s;                          // write the 8 channels of position u as FP32 samples 8u..8u+7
   const char* const* item_ptr;           // optional per-item input addresses (window start)
+  int per_sm;                            // resident CTAs per SM the plan is sized for
+  // Per K-step A operand, packed (start offset >> 4) | (LBO >> 4) << 16 relative
+  // to the stage base, when n_steps <= kParamSteps (else 0 and the shared-memory
+  // descriptor table is used).  Kernel parameters are uniform across the warp,
+  // so the issue loop builds descriptors without per-MMA shared-memory reads.
+  int param_desc;
+  uint32_t apack[192];
 };
+constexpr int kParamSteps = 192;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -238,12 +249,12 @@ __device__ __forceinline__ float act_fn(float v, int act) {
 
 // Byte offset (M sub-tile 0) of the slice coded g | phi << 8 | dd << 14 in a
 // tile of P planes per group, `rows` 16-byte rows per plane.
-__device__ __forceinline__ uint32_t slice_off(uint32_t code, int P, int rows) {
+__host__ __device__ __forceinline__ uint32_t slice_off(uint32_t code, int P, int rows) {
   const uint32_t g = code & 255u, phi = (code >> 8) & 63u, dd = code >> 14;
   return ((g * (uint32_t)P + phi) * (uint32_t)rows + dd) * 16u;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) {
+__global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   const int na = p.na;                 // input stages (the A ring)
@@ -427,6 +438,32 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
           // N, so the loop is kept lean: one 16-byte descriptor pair per step,
           // the next pair loaded while the current MMAs issue.
           const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(s_desc);
+          if (MT == 1 && p.param_desc) {
+            // descriptors from the parameter table: A start and LBO packed per
+            // step, B at a fixed stride from the stage's first step
+            const uint64_t hi = ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+            const uint32_t a_base = (sA >> 4) + (uint32_t)a_stage;
+            const uint64_t b_hi = hi | ((uint64_t)(((uint32_t)p.npad * 16u) >> 4) << 16);
+            const uint32_t b_base = (sW >> 4) + (uint32_t)b_stage, b_step = (uint32_t)p.step_bytes >> 4;
+            if (fp8) {
+              for (int sidx = s0; sidx < s1; ++sidx) {
+                const uint32_t e = p.apack[sidx];
+                mma_f8(d0, hi | (uint64_t)((a_base + (e & 0xFFFFu)) & 0x3FFFu) | ((uint64_t)(e >> 16) << 16),
+                       b_hi | (uint64_t)((b_base + (uint32_t)(sidx - s0) * b_step) & 0x3FFFu), idesc,
+                       sidx == 0 ? 0u : 1u);
+              }
+            } else {
+#pragma unroll 4
+              for (int sidx = s0; sidx < s1; ++sidx) {
+                const uint32_t e = p.apack[sidx];
+                mma_f16(d0, hi | (uint64_t)((a_base + (e & 0xFFFFu)) & 0x3FFFu) | ((uint64_t)(e >> 16) << 16),
+                        b_hi | (uint64_t)((b_base + (uint32_t)(sidx - s0) * b_step) & 0x3FFFu), idesc,
+                        sidx == 0 ? 0u : 1u);
+              }
+            }
+            if (!p.resident) mma_commit(bar(w_empty + st));
+            continue;
+          }
           ulonglong2 cur = tab[s0];
           if (fp8) {
             for (int sidx = s0; sidx < s1; ++sidx) {
@@ -438,12 +475,26 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
               cur = nxt;
             }
           } else if (MT == 1) {
-#pragma unroll 4
-            for (int sidx = s0; sidx < s1; ++sidx) {
-              const ulonglong2 nxt = tab[sidx + 1 < s1 ? sidx + 1 : sidx];
+            // Under load (bulk copies landing, operand reads, epilogue
+            // traffic) a shared-memory read takes longer than issuing several
+            // MMAs, so the descriptor pairs are read four steps ahead.
+            const int last = s1 - 1;
+            ulonglong2 q1 = tab[min(s0 + 1, last)], q2 = tab[min(s0 + 2, last)], q3 = tab[min(s0 + 3, last)];
+            int sidx = s0;
+            for (; sidx + 4 <= s1; sidx += 4) {
               mma_f16(d0, cur.x + a_stage, cur.y + b_stage, idesc, sidx == 0 ? 0u : 1u);
-              cur = nxt;
+              cur = tab[min(sidx + 4, last)];
+              mma_f16(d0, q1.x + a_stage, q1.y + b_stage, idesc, 1u);
+              q1 = tab[min(sidx + 5, last)];
+              mma_f16(d0, q2.x + a_stage, q2.y + b_stage, idesc, 1u);
+              q2 = tab[min(sidx + 6, last)];
+              mma_f16(d0, q3.x + a_stage, q3.y + b_stage, idesc, 1u);
+              q3 = tab[min(sidx + 7, last)];
             }
+            // fewer than four steps left: they are in cur, q1, q2
+            if (sidx < s1) mma_f16(d0, cur.x + a_stage, cur.y + b_stage, idesc, sidx == 0 ? 0u : 1u);
+            if (sidx + 1 < s1) mma_f16(d0, q1.x + a_stage, q1.y + b_stage, idesc, 1u);
+            if (sidx + 2 < s1) mma_f16(d0, q2.x + a_stage, q2.y + b_stage, idesc, 1u);
           } else {
             for (int sidx = s0; sidx < s1; ++sidx) {
               const ulonglong2 nxt = tab[sidx + 1 < s1 ? sidx + 1 : sidx];
@@ -468,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
   } else {
     // ---------------- epilogue: TMEM -> bias/residual/activation -> global ----------------
     const int quarter = warp & 3;          // TMEM lanes this warp may access
-    const int col_half = (warp - 2) >> 2;  // which 32-column chunks it drains
+    const int col_half = (warp - 2) >> 2;  // first 32-column chunk it drains (then every kEpiWarps / 4-th)
     const int row = quarter * 32 + lane;
     const bool plain = !p.fp32_single && !p.fp32_d2s && !p.fp8_out && !p.res && !p.wscale;
     griddep_wait();  // outputs and residuals are shared with the previous kernels
@@ -490,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const TcParams p) 
       for (int mt = 0; mt < p.MT; ++mt) {
         const int m = m0 + mt * 128 + row;
         const bool valid = m < p.mout;
-        for (int j = col_half; j < p.ncol / 32; j += 2) {
+        for (int j = col_half; j < p.ncol / 32; j += kEpiWarps / 4) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((s * p.MT + mt) * p.ncol + j * 32), v);
           if (!valid) continue;
@@ -878,6 +929,7 @@ void tc_pack_layer(LayerDev& L, const std::vector<double>& wf, int precision, gw
   }
   L.wq = d_img;
   L.table = d_tab;
+  L.table_h = table;
 }
 
 // Host-side launch plan: tile size, weight residency or staging, TMEM columns,
@@ -908,7 +960,10 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.n_steps = L.n_steps;
   q.npad = L.npad;
   const size_t wbytes = (size_t)L.n_steps * q.step_bytes;
-  auto a_bytes_for = [&](int mt) { return ((size_t)L.gin * L.pin * (128 * mt + L.dspan) * 16 + 127) / 128 * 128; };
+  // rows per stage plane rounded up to 8: every plane (and so every 8-row
+  // core matrix of a slice with d = 0) starts on a 128-byte boundary
+  auto rows_for = [&](int mt) { return (128 * mt + L.dspan + 7) / 8 * 8; };
+  auto a_bytes_for = [&](int mt) { return (size_t)L.gin * L.pin * rows_for(mt) * 16; };
   const size_t budget = 220 * 1024;
   const size_t planes = (size_t)L.gin * L.pin;
   const size_t fixed = 128 + 8 * 32 + 16 + 16 * (size_t)L.n_steps + 12 * planes + 8 * (size_t)L.npad + 16;
@@ -941,7 +996,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
     GW_CHECK_ARG(MT > 1, "shared memory plan too large");
   }
   q.MT = MT;
-  q.rows = 128 * MT + L.dspan;
+  q.rows = rows_for(MT);
   GW_CHECK_ARG(q.rows <= kZeroRows, "input tile taller than the zero-row buffer");
   q.a_bytes = (int)a_bytes_for(MT);
   q.tiles_per_item = (q.mout + 128 * MT - 1) / (128 * MT);
@@ -968,11 +1023,14 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
       return 128 + (size_t)na * q.a_bytes + (wsm0 + 127) / 128 * 128 + 8 * (size_t)(2 * na + 6 + 2 * q.nst) +
              16 * (size_t)L.n_steps + 12 * planes + 32 + 8 * (size_t)L.npad + 16;
     };
-    const bool two_per_sm = smem_for(2) <= 113 * 1024 && ncols <= 256;
-    const size_t cap = two_per_sm ? 113 * 1024 : 227 * 1024;
+    // shared memory per SM is 228 KB, of which 1 KB per CTA is reserved
+    int per = kMaxCtasPerSm;
+    while (per > 1 && (smem_for(2) > (size_t)(228 / per - 1) * 1024 || ncols * per > 512)) --per;
+    const size_t cap = (size_t)(228 / per - 1) * 1024;
     int na = 2;
     while (na < kMaxA && smem_for(na + 1) <= cap) ++na;
     q.na = na;
+    q.per_sm = per;
   }
   q.n_tiles = q.tiles_per_item * B * q.nsplit;
   // instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3 (kind::f8f6f4),
@@ -1014,6 +1072,14 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.out_P_log = log2_exact(std::max(1, out.P), "output phase count");
   q.res_P_log = log2_exact(q.res_P, "residual phase count");
   q.min_plen = in.L / in.P;
+  q.param_desc = 0;
+  if (L.n_steps <= kParamSteps && (int)L.table_h.size() >= 2 * L.n_steps) {
+    q.param_desc = 1;
+    for (int i = 0; i < L.n_steps; ++i) {
+      const uint32_t o0 = slice_off(L.table_h[2 * i], q.in_P, q.rows), o1 = slice_off(L.table_h[2 * i + 1], q.in_P, q.rows);
+      q.apack[i] = (o0 >> 4) | (((o1 - o0) >> 4) << 16);
+    }
+  }
   q.wimg = (const char*)L.wq;
   q.table = L.table;
   const size_t wsm = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
@@ -1021,8 +1087,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
                       16 * (size_t)L.n_steps + 12 * planes + 32 + 8 * (size_t)L.npad + 16;
   GW_CHECK_ARG(smem <= 227 * 1024, "shared memory plan too large");
   *smem_out = smem;
-  const int per_sm = (smem <= 113 * 1024 && ncols <= 256) ? 2 : 1;
-  *grid_out = dim3(std::min(q.n_tiles, sms * per_sm));
+  *grid_out = dim3(std::min(q.n_tiles, sms * q.per_sm));
 }
 
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err, cudaStream_t st) {
