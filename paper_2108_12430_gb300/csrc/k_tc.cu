@@ -46,13 +46,17 @@ namespace {
 
 // warp 0 producer, warp 1 MMA, warps 2-9 epilogue: two epilogue warps per
 // TMEM lane quarter (each takes every other 32-column chunk), so that every
-// SM sub-partition has two warps to hide the epilogue's instruction latency
+// SM sub-partition has two warps to hide the epilogue's instruction latency.
+// Warp 10 is a second producer: issuing a bulk copy blocks the issuing warp
+// for about a memory round trip, so two warps taking alternate tiles keep
+// twice the copies in flight.
 constexpr int kEpiWarps = 8;
+constexpr int kProdWarps = 2;
 // CTAs per SM the planner may ask for (shared memory, TMEM columns and the
 // register file permitting: 65536 / (kThreads * 96 registers))
 constexpr int kMaxCtasPerSm = 2;
 constexpr int kMaxA = 6;  // deepest input ring
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kThreads = 32 * (kProdWarps + 1 + kEpiWarps);
 constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
 // Source of the zero padding rows of edge tiles (a stage plane holds at most
@@ -328,16 +332,25 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
   // without the attribute).
   griddep_launch_dependents();
 
-  if (warp == 0) {
-    // ---------------- producer: input tiles (and weights) by bulk TMA ----------------
-    if (p.resident && lane == 0) {
+  if (warp == 0 || warp >= 2 + kEpiWarps) {
+    // ---------------- producers: input tiles (and weights) by bulk TMA ----------------
+    const int pw = warp == 0 ? 0 : warp - 1 - kEpiWarps;  // producer index; tiles i with i % nprod == pw
+    // With streamed weights one producer fills both rings: a weight stage
+    // written by two producers taking alternate tiles could be re-armed two
+    // phases ahead of its consumer, which a parity wait cannot tell apart.
+    // (The input ring is safe with two: each producer issues its tiles in
+    // order, and its previous wait implies every older use of the stage was
+    // consumed, so no producer gets more than one phase ahead.)
+    const int nprod = p.resident ? kProdWarps : 1;
+    if (p.resident && lane == 0 && pw == 0) {
       mbar_expect_tx(bar(w_full), (uint32_t)(p.n_steps * p.step_bytes));
       bulk_g2s(sW, p.wimg, (uint32_t)(p.n_steps * p.step_bytes), bar(w_full));
     }
     griddep_wait();
     int i = 0;
-    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
-      const int s = i % na, k = i / na;
+    int s = 0, k = 0;  // ring stage and its use count, advanced without divisions
+    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i, k += (++s == na), s = s == na ? 0 : s) {
+      if (i % nprod != pw) continue;
       if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
       int b, m0, sl;
       tile_coords(p, t, b, m0, sl);
@@ -408,10 +421,10 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
       const int MT = p.MT, npad = p.ncol;  // accumulator columns of one tile (its slice)
       const uint32_t idesc = p.idesc;
       int i = 0;
-      for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x, ++i) {
-        const int sa = i % na, ka = i / na;  // input stage
+      int sa = 0, ka = 0;  // input stage and its use count, advanced without divisions
+      for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x, ++i, ka += (++sa == na), sa = sa == na ? 0 : sa) {
         const int s = i & 1, k = i >> 1;     // accumulator buffer
-        const int sl = t % p.nsplit;         // column slice
+        const int sl = t & (p.nsplit - 1);   // column slice (nsplit is a power of two)
         if (!mbar_wait(bar(a_full + sa), (uint32_t)ka & 1u, abort_flag, p.err, kErrWaitA)) break;
         if (k >= 1 && !mbar_wait(bar(acc_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitAcc)) break;
         tc_fence_after();
@@ -517,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: TMEM -> bias/residual/activation -> global ----------------
+    // ---------------- epilogue (warps 2 .. 1 + kEpiWarps): TMEM -> bias/residual/activation -> global ----------------
     const int quarter = warp & 3;          // TMEM lanes this warp may access
     const int col_half = (warp - 2) >> 2;  // first 32-column chunk it drains (then every kEpiWarps / 4-th)
     const int row = quarter * 32 + lane;
