@@ -39,7 +39,7 @@ L2_BYTES = 129 * 1024 * 1024
 # ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the 8 conv_tc
 # launches of one 64-window push (set to None whenever conv_tc changes until
 # it is captured again)
-CONV_TRAFFIC_BYTES_PER_PUSH = 238_093_824 + 75_264
+CONV_TRAFFIC_BYTES_PER_PUSH = 238_078_464 + 67_328
 
 
 def dc_flops_per_window(L=W):
