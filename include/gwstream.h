@@ -215,9 +215,10 @@ int gw_stream_destroy(gw_stream_t s);
  * mem = GW_MEM_HOST: host pointers; the call copies in, runs, copies out and
  *   returns when clean_out is written.
  * mem = GW_MEM_DEVICE: device pointers; stream-ordered on cuda_stream.
- * Non-finite input samples are rejected with GW_ENONFINITE before the state
- * changes (host mode; device mode checks on the device and reports through
- * gw_stream_status). */
+ * Non-finite input samples are rejected with GW_ENONFINITE and the stream
+ * state is left unchanged (host mode: the staged input is checked on the
+ * device before any state update, clean_out is then unspecified; device mode
+ * checks on the device and reports through gw_stream_status). */
 int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float* strain,
                    float* clean_out, int mem, void* cuda_stream);
 /* Samples pushed so far per detector. */

@@ -577,6 +577,8 @@ struct gw_stream {
   float* stage_out = nullptr;
   int* status = nullptr;
   int* err = nullptr;
+  int* reject = nullptr;    // device: this host-mode push's input had a non-finite sample
+  int* reject_h = nullptr;  // pinned host copy, read after the push's synchronisation
   size_t bytes = 0;
   std::vector<void*> allocs;
 };
@@ -587,6 +589,7 @@ static void stream_free(gw_stream* s) {
   if (!s) return;
   cudaDeviceSynchronize();
   for (void* p : s->allocs) cudaFree(p);
+  if (s->reject_h) cudaFreeHost(s->reject_h);
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     s->ctx->in_use -= s->bytes;
@@ -1061,8 +1064,10 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
     s->act1 = salloc<char>(s, act_elems * esz);
     s->stage_in = salloc<float>(s, (size_t)d->n_det * (C + 1) * nb * S);
     s->stage_out = salloc<float>(s, (size_t)d->n_det * nb * S);
-    s->status = salloc<int>(s, 2);
+    s->status = salloc<int>(s, 3);
     s->err = s->status + 1;
+    s->reject = s->status + 2;
+    GW_CUDA(cudaHostAlloc((void**)&s->reject_h, sizeof(int), cudaHostAllocDefault));
     GW_CUDA(cudaDeviceSynchronize());
   } catch (...) {
     stream_free(s);
@@ -1106,14 +1111,18 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
   const float* wit = witness;
   const float* str = strain;
   float* out = clean_out;
+  // Host mode rejects a push with a non-finite sample before the state
+  // changes: the staged input is checked on the device, the state-changing
+  // kernels (ring, strain and aggregation updates) skip their writes when the
+  // check failed, and the verdict is read back with the results.
+  const int* skip = nullptr;
   if (mem == GW_MEM_HOST) {
     const size_t nw = (size_t)nd * C * n, ns = (size_t)nd * n;
-    for (size_t i = 0; i < nw; ++i)
-      if (!std::isfinite(witness[i])) throw Error(GW_ENONFINITE, "non-finite witness sample");
-    for (size_t i = 0; i < ns; ++i)
-      if (!std::isfinite(strain[i])) throw Error(GW_ENONFINITE, "non-finite strain sample");
+    GW_CUDA(cudaMemsetAsync(s->reject, 0, sizeof(int), st));
     GW_CUDA(cudaMemcpyAsync(s->stage_in, witness, nw * 4, cudaMemcpyHostToDevice, st));
     GW_CUDA(cudaMemcpyAsync(s->stage_in + nw, strain, ns * 4, cudaMemcpyHostToDevice, st));
+    launch_check_finite(s->stage_in, (int64_t)(nw + ns), s->reject, st);
+    skip = s->reject;
     wit = s->stage_in;
     str = s->stage_in + nw;
     out = s->stage_out;
@@ -1126,14 +1135,14 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
     {
       Prof p("ring_push", st);
       if (m->precision == GW_FP32)
-        launch_ring_push_f32(wd, n, C, (int)n, s->ring_f32[d], R, head, m->in_mean, m->in_istd, s->status, st);
+        launch_ring_push_f32(wd, n, C, (int)n, s->ring_f32[d], R, head, m->in_mean, m->in_istd, s->status, st, skip);
       else
         launch_ring_push_bf16(wd, n, C, G, (int)n, s->ring_bf16[d], R, head, m->layers[0].pin, m->in_mean,
-                              m->in_istd, s->status, st);
+                              m->in_istd, s->status, st, skip);
     }
     {
       Prof p("strain_push", st);
-      launch_strain_push(str + (size_t)d * n, (int)n, s->strain[d], R, head, s->status, st);
+      launch_strain_push(str + (size_t)d * n, (int)n, s->strain[d], R, head, s->status, st, skip);
     }
     // window j of this batch ends at head + (j+1) S; in the double-mapped ring
     // the batch's windows are views at uniform stride S from p0.
@@ -1163,14 +1172,16 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
     {
       Prof p("sub_ola", st);
       launch_sub_ola(s->pred, W, n_snap, S, W, R, head, s->d.agg_mode, s->d.agg_delay, s->acc[d], s->strain[d],
-                     out + (size_t)d * n, st);
+                     out + (size_t)d * n, st, skip);
     }
   }
-  s->head += n;
   if (mem == GW_MEM_HOST) {
     GW_CUDA(cudaMemcpyAsync(clean_out, s->stage_out, (size_t)nd * n * 4, cudaMemcpyDeviceToHost, st));
+    GW_CUDA(cudaMemcpyAsync(s->reject_h, s->reject, sizeof(int), cudaMemcpyDeviceToHost, st));
     GW_CUDA(cudaStreamSynchronize(st));
+    if (*s->reject_h) throw Error(GW_ENONFINITE, "non-finite input sample");
   }
+  s->head += n;
   GW_API_END
 }
 

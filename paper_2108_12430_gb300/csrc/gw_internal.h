@@ -193,23 +193,27 @@ size_t bbhnet_tc_ws_bytes(int B, int L);
 size_t bbhnet_f32_ws_bytes(int B, int L);
 
 // ---- stream kernels (k_stream.cu) -------------------------------------------
+// skip (optional device flag): when set at run time the kernel writes nothing
+// (a push whose input was rejected leaves the state unchanged).
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring,
                           int64_t R, int64_t head, const float* mean, const float* istd,
-                          int* status, cudaStream_t st);
+                          int* status, cudaStream_t st, const int* skip = nullptr);
 // Blocked BF16 ring [G][P][2R / P][8]: ring position q (0 <= q < 2R) of
 // channel group g sits in plane q % P, row q / P.
 void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n,
                            __nv_bfloat16* ring, int64_t R, int64_t head, int P, const float* mean,
-                           const float* istd, int* status, cudaStream_t st);
+                           const float* istd, int* status, cudaStream_t st, const int* skip = nullptr);
 // Sets every position of a witness ring (2R = R2 positions per channel) to
 // the standardised zero sample (-mean_c / std_c), or to 0 when mean is null.
 void launch_ring_fill(void* ring, int bf16, int C, int G, int64_t R2, const float* mean, const float* istd,
                       cudaStream_t st);
 void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head,
-                        int* status, cudaStream_t st);
+                        int* status, cudaStream_t st, const int* skip = nullptr);
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R,
                     int64_t head, int mode, int delta, float* acc, const float* strain_ring,
-                    float* out, cudaStream_t st);
+                    float* out, cudaStream_t st, const int* skip = nullptr);
+// Sets *flag to 1 when any of the n floats at x is not finite (the caller zeroes it).
+void launch_check_finite(const float* x, int64_t n, int* flag, cudaStream_t st);
 
 // ---- tensor-core conv path (k_tc.cu) ---------------------------------------------
 // Activation layout of the tensor-core path ("blocked"): channels in groups of

@@ -6,6 +6,8 @@
 // witness ring is double-mapped -- sample t is stored at t mod R and at
 // t mod R + R -- so every window [t - W, t) is one contiguous run starting at
 // (t - W) mod R, which the first conv layer reads in place.
+#include <algorithm>
+
 #include "gw_internal.h"
 
 namespace gw {
@@ -38,9 +40,9 @@ __device__ __forceinline__ uint32_t ring_pos(int h0, int i, int R) {
 // Grid: (samples, channel).
 __global__ void ring_push_f32_kernel(const float* __restrict__ src, int64_t src_ld, int n,
                                      float* __restrict__ ring, int R, int h0, const float* __restrict__ mean,
-                                     const float* __restrict__ istd, int* status) {
+                                     const float* __restrict__ istd, int* status, const int* skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
-  if (i >= n) return;
+  if (i >= n || (skip && *skip)) return;
   float v = __ldg(src + (int64_t)c * src_ld + i);
   if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
   if (mean) v = (v - mean[c]) * istd[c];
@@ -56,9 +58,9 @@ __global__ void ring_push_f32_kernel(const float* __restrict__ src, int64_t src_
 __global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src_ld, int C, int n,
                                       __nv_bfloat16* __restrict__ ring, int R, int h0, int P,
                                       const float* __restrict__ mean, const float* __restrict__ istd,
-                                      int* status) {
+                                      int* status, const int* skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
-  if (i >= n) return;
+  if (i >= n || (skip && *skip)) return;
   __align__(16) __nv_bfloat16 v8[8];
   bool bad = false;
 #pragma unroll
@@ -81,9 +83,9 @@ __global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src
   grp[(q2 % up) * plane_rows + q2 / up] = val;
 }
 __global__ void strain_push_kernel(const float* __restrict__ src, int n, float* __restrict__ ring, int R, int h0,
-                                   int* status) {
+                                   int* status, const int* skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (skip && *skip)) return;
   const float v = __ldg(src + i);
   if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
   ring[ring_pos(h0, i, R)] = v;
@@ -102,7 +104,8 @@ __global__ void strain_push_kernel(const float* __restrict__ src, int n, float* 
 // cleaned = strain(tau) - value, written to out[tau - head + delta].
 __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, int n, int S, int W,
                                int64_t R, int64_t head, int mode, int delta, float* __restrict__ acc,
-                               const float* __restrict__ strain_ring, float* __restrict__ out) {
+                               const float* __restrict__ strain_ring, float* __restrict__ out, const int* skip) {
+  if (skip && *skip) return;
   const int64_t lo = head + S - W;
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
   const int64_t k0 = head / S;
@@ -183,7 +186,29 @@ __global__ void ring_fill_kernel(void* __restrict__ ring, int bf16, int C, int G
   }
 }
 
+// Any non-finite value among n floats (16-byte aligned, n a multiple of 4
+// handled by vector loads, the tail one by one) sets *flag.
+__global__ void check_finite_kernel(const float* __restrict__ x, int64_t n, int* flag) {
+  bool bad = false;
+  const int64_t n4 = n / 4, stride = (int64_t)gridDim.x * blockDim.x;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += stride) {
+    const float4 v = __ldg(x4 + e);
+    bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+  }
+  for (int64_t e = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += stride) bad |= !isfinite(x[e]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
+}
+
 }  // namespace
+
+void launch_check_finite(const float* x, int64_t n, int* flag, cudaStream_t st) {
+  GW_CHECK_ARG(((uintptr_t)x & 15) == 0, "finiteness check needs a 16-byte aligned buffer");
+  if (n <= 0) return;
+  const int64_t blocks = std::min<int64_t>((n / 4 + kThreads - 1) / kThreads + 1, 4 * 152);
+  check_finite_kernel<<<(int)blocks, kThreads, 0, st>>>(x, n, flag);
+  GW_LAUNCH_CHECK();
+}
 
 void launch_ring_fill(void* ring, int bf16, int C, int G, int64_t R2, const float* mean, const float* istd,
                       cudaStream_t st) {
@@ -204,38 +229,41 @@ static int ring_head(int64_t head, int64_t R, int n) {
 }
 
 void launch_ring_push_f32(const float* src, int64_t src_ld, int C, int n, float* ring, int64_t R,
-                          int64_t head, const float* mean, const float* istd, int* status, cudaStream_t st) {
+                          int64_t head, const float* mean, const float* istd, int* status, cudaStream_t st,
+                          const int* skip) {
   const int h0 = ring_head(head, R, n);
   if (n == 0 || C == 0) return;
   ring_push_f32_kernel<<<dim3((n + kThreads - 1) / kThreads, C), kThreads, 0, st>>>(src, src_ld, n, ring, (int)R, h0,
-                                                                                     mean, istd, status);
+                                                                                     mean, istd, status, skip);
   GW_LAUNCH_CHECK();
 }
 
 void launch_ring_push_bf16(const float* src, int64_t src_ld, int C, int G, int n, __nv_bfloat16* ring,
                            int64_t R, int64_t head, int P, const float* mean, const float* istd, int* status,
-                           cudaStream_t st) {
+                           cudaStream_t st, const int* skip) {
   GW_CHECK_ARG(P >= 1 && R % P == 0, "ring capacity must be a multiple of the phase count");
   const int h0 = ring_head(head, R, n);
   if (n == 0 || G == 0) return;
   ring_push_bf16_kernel<<<dim3((n + kThreads - 1) / kThreads, G), kThreads, 0, st>>>(src, src_ld, C, n, ring, (int)R,
-                                                                                      h0, P, mean, istd, status);
+                                                                                      h0, P, mean, istd, status,
+                                                                                      skip);
   GW_LAUNCH_CHECK();
 }
 
 void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head, int* status,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* skip) {
   const int h0 = ring_head(head, R, n);
   if (n == 0) return;
-  strain_push_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(src, n, ring, (int)R, h0, status);
+  strain_push_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(src, n, ring, (int)R, h0, status, skip);
   GW_LAUNCH_CHECK();
 }
 
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R, int64_t head, int mode,
-                    int delta, float* acc, const float* strain_ring, float* out, cudaStream_t st) {
+                    int delta, float* acc, const float* strain_ring, float* out, cudaStream_t st,
+                    const int* skip) {
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
   sub_ola_kernel<<<grid_for(count), kThreads, 0, st>>>(pred, pred_ld, n, S, W, R, head, mode, delta, acc,
-                                                        strain_ring, out);
+                                                        strain_ring, out, skip);
   GW_LAUNCH_CHECK();
 }
 

@@ -224,6 +224,42 @@ def test_stream_errors(ctx):
     assert G.gw_stream_head(s) == 0
 
 
+@pytest.mark.parametrize("prec", [G.GW_FP32, G.GW_BF16])
+def test_rejected_push_leaves_state_unchanged(ctx, prec):
+    # a push with a non-finite witness or strain sample changes nothing: the
+    # valid pushes that follow give exactly what a fresh stream gives
+    m = ctx.deepclean(0, prec)
+    rng = np.random.default_rng(7)
+    W, S, n = 1024, 128, 3
+    w = rng.standard_normal((1, 21, n * S)).astype(np.float32)
+    x = rng.standard_normal((1, n * S)).astype(np.float32)
+
+    def run(reject_first):
+        s = G.gw_stream_create(ctx.h, [m], 1, 21, W, S, 4, G.GW_AGG_AVERAGE, W - S)
+        ctx.objs.append((G.gw_stream_destroy, s))
+        if reject_first:
+            for bad_w in (True, False):
+                wb, xb = w[:, :, :S].copy(), x[:, :S].copy()
+                if bad_w:
+                    wb[0, 20, S - 1] = np.inf
+                else:
+                    xb[0, 5] = np.nan
+                with pytest.raises(G.GwError) as e:
+                    G.gw_stream_push(s, 1, wb, xb, np.zeros((1, S), np.float32))
+                assert e.value.code == G.GW_ENONFINITE
+                assert G.gw_stream_head(s) == 0
+        out = np.zeros((1, n * S), np.float32)
+        for k in range(n):
+            o = np.zeros((1, S), np.float32)
+            G.gw_stream_push(s, 1, np.ascontiguousarray(w[:, :, k * S:(k + 1) * S]),
+                             np.ascontiguousarray(x[:, k * S:(k + 1) * S]), o)
+            out[:, k * S:(k + 1) * S] = o
+        assert G.gw_stream_head(s) == n * S
+        return out
+
+    assert np.array_equal(run(True), run(False))
+
+
 def test_budget_refusal(gpu_lib):
     c = Ctx(budget=4 << 20)
     try:
