@@ -111,6 +111,16 @@ int gw_model_destroy(gw_model_t m);
 /* Synchronises cuda_stream and reports whether a tensor-core kernel of this
  * model gave up a bounded device-side wait (GW_ETIMEOUT) since creation. */
 int gw_model_status(gw_model_t m, void* cuda_stream);
+/* Test of the failure path of the bounded device-side waits (no GPU fault is
+ * involved).  Runs one DeepClean forward (1 window of 4096 samples, zero input)
+ * of a BF16 model in which one CTA of the first layer never arms one input
+ * stage, so that its MMA thread's wait runs out after about 1 s and the
+ * launch unwinds; *observed receives what the host then reads
+ * (GW_ETIMEOUT expected).  The model's error flag is cleared and a normal
+ * forward is run on the same stream: the call returns GW_OK when it succeeds
+ * (GW_ETIMEOUT if the flag is set again).  Synchronises cuda_stream; not to be
+ * called concurrently with other work of the same model. */
+int gw_model_test_wait_timeout(gw_model_t m, int* observed, void* cuda_stream);
 
 /* DeepClean forward over B windows of L samples (L a multiple of 8).
  * x: device FP32; channel c of window b is the L samples starting at

@@ -807,6 +807,43 @@ int gw_model_status(gw_model_t m, void* cuda_stream) {
   GW_API_END
 }
 
+int gw_model_test_wait_timeout(gw_model_t m, int* observed, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(m && observed, "NULL argument");
+  GW_CHECK_ARG(m->kind == GW_MODEL_DEEPCLEAN && m->precision != GW_FP32, "needs a tensor-core DeepClean model");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int B = 1, L = 4096;
+  float* x = nullptr;
+  float* y = nullptr;
+  GW_CUDA(cudaMalloc(&x, (size_t)m->n_in * L * sizeof(float)));
+  GW_CUDA(cudaMalloc(&y, (size_t)L * sizeof(float)));
+  int rc = GW_OK;
+  try {
+    GW_CUDA(cudaMemsetAsync(x, 0, (size_t)m->n_in * L * sizeof(float), st));
+    int h = -1;
+    auto run = [&](bool stall) {
+      if (stall) conv_tc_arm_stall_test();
+      const int r = gw_deepclean_forward(m, x, L, 0, B, L, y, st);
+      if (r != GW_OK) throw Error(r, "forward failed");
+      GW_CUDA(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      GW_CUDA(cudaStreamSynchronize(st));
+    };
+    run(true);
+    *observed = h ? GW_ETIMEOUT : GW_OK;
+    GW_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), st));
+    run(false);  // the context and the model still work
+    if (h) rc = GW_ETIMEOUT;
+  } catch (...) {
+    cudaFree(x);
+    cudaFree(y);
+    throw;
+  }
+  GW_CUDA(cudaFree(x));
+  GW_CUDA(cudaFree(y));
+  return rc;
+  GW_API_END
+}
+
 int gw_bbhnet_score(gw_model_t m, const float* x, int B, int L, float* logits, void* cuda_stream) {
   GW_API_BEGIN
   GW_CHECK_ARG(m && x && logits, "NULL argument");

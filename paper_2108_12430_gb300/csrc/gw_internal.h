@@ -265,6 +265,9 @@ void tc_pack_layer(LayerDev& L, const std::vector<double>& wfold, int precision,
                    size_t* counter, std::vector<void*>& allocs, std::vector<float>* wscale_out = nullptr);
 // max |x| over n floats, combined into *amax (atomic max of non-negative floats).
 void launch_absmax(const float* x, int64_t n, float* amax, cudaStream_t st);
+// The next launch_conv_tc leaves one input stage of CTA 0 unarmed, so that a
+// bounded wait runs out (testing of the failure path; not thread-safe).
+void conv_tc_arm_stall_test();
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err_flag,
                     cudaStream_t st);
 // FP32 element (b, c, t) at x + b*xb + c*xc + t*ts -> blocked bf16 / e4m3,

@@ -101,6 +101,9 @@ struct TcParams {
   // so the issue loop builds descriptors without per-MMA shared-memory reads.
   int param_desc;
   uint32_t apack[192];
+  // test of the bounded waits: CTA 0 never arms the input stage of its first
+  // tile, so its MMA thread's wait runs out and the launch unwinds with kErrWaitA
+  int stall_test;
 };
 constexpr int kParamSteps = 192;
 
@@ -351,6 +354,7 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
     int s = 0, k = 0;  // ring stage and its use count, advanced without divisions
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i, k += (++s == na), s = s == na ? 0 : s) {
       if (i % nprod != pw) continue;
+      if (p.stall_test && blockIdx.x == 0 && i == 0) continue;  // no arrival and no copy: nothing in flight
       if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
       int b, m0, sl;
       tile_coords(p, t, b, m0, sl);
@@ -1103,6 +1107,9 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   *grid_out = dim3(std::min(q.n_tiles, sms * q.per_sm));
 }
 
+static bool g_stall_next = false;
+void conv_tc_arm_stall_test() { g_stall_next = true; }
+
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err, cudaStream_t st) {
   TcParams q;
   size_t smem = 0;
@@ -1110,6 +1117,8 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
   static int sms = 0;
   if (!sms) sms = sm_count();
   plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B, sms);
+  q.stall_test = g_stall_next ? 1 : 0;
+  g_stall_next = false;
   static bool smem_attr = false;
   if (!smem_attr) {
     GW_CUDA(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));

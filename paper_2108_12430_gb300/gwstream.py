@@ -43,7 +43,7 @@ EXPORTS = (
     "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
     "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
     "gw_trainer_backward", "gw_fir_create_band_loss", "gw_band_loss", "gw_band_loss_backward", "gw_fir_backward",
-    "gw_adam_step", "gw_model_calibrate",
+    "gw_adam_step", "gw_model_calibrate", "gw_model_test_wait_timeout",
 )
 
 
@@ -115,6 +115,7 @@ def _declare(lib):
         "gw_launch_count": (I64, []),
         "gw_deepclean_forward_noalloc": (I, [P, P, I64, I64, I, I, P, P]),
         "gw_model_status": (I, [P, P]),
+        "gw_model_test_wait_timeout": (I, [P, C.POINTER(C.c_int), P]),
         "gw_tc_inspect": (I, [C.POINTER(C.c_int), I, C.POINTER(C.c_double), I, I, I, I, P, SZ,
                               C.POINTER(C.c_uint32), I, C.POINTER(C.c_int)]),
         "gw_fir_create_lowpass": (I, [P, C.c_double, C.c_double, I, I, C.POINTER(P)]),
@@ -218,6 +219,14 @@ def gw_model_destroy(m):
 
 def gw_model_status(m, stream=0):
     _check(lib().gw_model_status(m, stream or None))
+
+
+def gw_model_test_wait_timeout(m, stream=0):
+    """Runs the bounded-wait failure test; returns the status the host observed
+    for the stalled launch (raises if the follow-up normal launch fails)."""
+    obs = C.c_int(0)
+    _check(lib().gw_model_test_wait_timeout(m, C.byref(obs), stream or None))
+    return obs.value
 
 
 def gw_deepclean_forward(m, x_ptr, ld, window_stride, B, L, y_ptr, stream=0):

@@ -148,3 +148,22 @@ def test_whiten_bf16(ctx, B, C, L_in):
     yr = y.reshape(B * C, lout).cpu().numpy()
     for r in sorted({0, B * C // 2, B * C - 1}):
         assert rel_l2(yr[r], ofir.fir_valid(xr[r], h)) <= TOL16, r
+
+
+def test_bounded_wait_runs_out_and_context_survives(ctx):
+    # failure detection without a GPU fault: one CTA of the first layer never
+    # arms an input stage, its MMA thread's bounded wait (about 1 s) runs out,
+    # the launch unwinds, the host reads GW_ETIMEOUT; afterwards the same model
+    # and context run a normal forward that matches one from a fresh model
+    m = ctx.deepclean(0, G.GW_BF16)
+    assert G.gw_model_test_wait_timeout(m) == G.GW_ETIMEOUT
+    G.gw_model_status(m)  # the flag was cleared and stays clear
+    x = torch.randn(21, 4096, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    y = torch.empty(4096, device="cuda")
+    G.gw_deepclean_forward(m, x.data_ptr(), 4096, 0, 1, 4096, y.data_ptr())
+    m2 = ctx.deepclean(0, G.GW_BF16)
+    y2 = torch.empty(4096, device="cuda")
+    G.gw_deepclean_forward(m2, x.data_ptr(), 4096, 0, 1, 4096, y2.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(y, y2)
+    G.gw_model_status(m)
