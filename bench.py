@@ -408,6 +408,7 @@ def gpu_arm(args):
     # capture of the current kernel (cold cache; profiles/conv_tc_deepclean_stream_batch64.md)
     traffic = CONV_TRAFFIC_BYTES_PER_PUSH if headline == "bf16" else None
     configs = extra_configs(G, torch, dev_index, flush)
+    configs.update(bulk_config(G, torch, dev_index, flush))
     configs.update(train_config(G, torch, dev_index, flush))
     configs.update(serve_configs(G, dev_index))
     cpu = cpu_baseline(budget_s=args.cpu_seconds)
@@ -556,6 +557,37 @@ def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
                 "kernels_ms": {k: v[0] / 3 for k, v in prof.items()}}
             G.gw_model_destroy(mb)
             G.gw_fir_destroy(fh)
+    finally:
+        G.gw_ctx_destroy(ctx)
+    return out
+
+
+def bulk_config(G, torch, dev_index, flush, steps=10, warmup=3):
+    """Offline bulk mode (Methods, offline deployment: snapshots at r = 0.25 Hz
+    over a recording): 8 s windows at stride S = f_s / r = 16384, 64 windows
+    per push (256 s of data), every sample averaged over the two windows that
+    cover it; BF16, device-resident input; reported as seconds of data cleaned
+    per second."""
+    from paper_2108_12430_gb300 import synth
+    Sb, Bb = 16384, 64
+    out = {}
+    ctx = G.gw_ctx_create(dev_index, 0)
+    try:
+        m = G.gw_model_create(ctx, G.GW_MODEL_DEEPCLEAN, G.GW_BF16, C, synth.flatten_params(synth.deepclean_params(0)))
+        s = G.gw_stream_create(ctx, [m], 1, C, W, Sb, Bb, G.GW_AGG_AVERAGE, W - Sb)
+        n = Bb * Sb
+        wit = torch.from_numpy(synth.witness_channels(77, C, n).astype(np.float32)).cuda()
+        stn = torch.zeros(n, device="cuda")
+        cln = torch.zeros(n, device="cuda")
+        step = lambda: G.gw_stream_push(s, Bb, wit.data_ptr(), stn.data_ptr(), cln.data_ptr(), G.GW_MEM_DEVICE)
+        ms = time_call(torch, step, steps, warmup, flush)
+        per = float(np.mean(ms))
+        out["bulk_bf16"] = {"workload": f"offline bulk: DeepClean {C}x{W} windows at stride {Sb} (r = 0.25 Hz), "
+                                        f"{Bb} windows per push, overlap-add", "ms_per_push": per,
+                            "data_seconds_per_push": n / 4096.0,
+                            "data_seconds_per_s": n / 4096.0 / (per / 1e3)}
+        G.gw_stream_destroy(s)
+        G.gw_model_destroy(m)
     finally:
         G.gw_ctx_destroy(ctx)
     return out

@@ -88,6 +88,15 @@ def test_stream_matches_oracle_bf16(ctx, mode, delta):
         assert rel_l2(g, ref) <= TOL16
 
 
+def test_bulk_stride_half_window_bf16(ctx):
+    # offline bulk mode: snapshots at 1/4 Hz with 8 s windows, i.e. S = W / 2,
+    # every sample averaged over the two windows that cover it
+    W, S = 2048, 1024
+    for g, ref in run_stream_case(ctx, W, S, [4, 2, 5], G.GW_AGG_AVERAGE, W - S, seed=6, precision=G.GW_BF16):
+        assert g.shape == ref.shape
+        assert rel_l2(g, ref) <= TOL16
+
+
 def test_stream_two_detectors_bf16(ctx):
     W, S = 512, 64
     for g, ref in run_stream_case(ctx, W, S, [2, 6, 1, 8], G.GW_AGG_AVERAGE, W - S, seed=3, n_det=2,

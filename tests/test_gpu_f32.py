@@ -167,6 +167,14 @@ def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G
     return res
 
 
+def test_bulk_stride_half_window_fp32(ctx):
+    # offline bulk mode (S = W / 2, two windows per sample)
+    W, S = 2048, 1024
+    for g, ref in run_stream_case(ctx, W, S, [4, 2, 5], G.GW_AGG_AVERAGE, W - S, seed=6):
+        assert g.shape == ref.shape
+        assert rel_l2(g, ref) <= TOL32
+
+
 @pytest.mark.parametrize("mode,delta", [(G.GW_AGG_LATEST, 0), (G.GW_AGG_LATEST, 300),
                                         (G.GW_AGG_AVERAGE, 0), (G.GW_AGG_AVERAGE, 1024 - 128),
                                         (G.GW_AGG_AVERAGE, 200)])
