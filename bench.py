@@ -603,11 +603,14 @@ def study_config(dev_index):
     offline ratio by more than 10%."""
     from paper_2108_12430_gb300 import study
     import time as _t
-    t0 = _t.time()
-    r = study.aggregation_latency_study(device=dev_index)
-    r.pop("losses", None)
-    r["wall_s"] = _t.time() - t0
-    return {"study_aggregation_latency": r}
+    out = {}
+    for name, taps in (("study_aggregation_latency", 0), ("study_aggregation_latency_post2049", 2049)):
+        t0 = _t.time()
+        r = study.aggregation_latency_study(device=dev_index, post_taps=taps)
+        r.pop("losses", None)
+        r["wall_s"] = _t.time() - t0
+        out[name] = r
+    return out
 
 
 def train_config(G, torch, dev_index, flush, steps=10, warmup=3):

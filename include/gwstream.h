@@ -214,6 +214,13 @@ typedef struct gw_stream_desc {
   int max_batch;   /* largest n_snap of one push */
   int agg_mode;    /* enum gw_agg_mode */
   int agg_delay;   /* aggregation latency in samples */
+  /* optional post-processing FIR of K (odd) taps applied to the aggregated
+   * prediction before subtraction (gw_fir_create_bandpass; FP32; the taps are
+   * copied at create, the handle may be destroyed afterwards; NULL = none):
+   *   cleaned[t] = strain[t] - sum_k h[k] p[t + k - c],  c = (K - 1) / 2,
+   * with p the aggregated prediction (0 before time 0).  The samples returned
+   * by a push are then c samples later: [k S - delta - c, k S + S - delta - c). */
+  gw_fir_t post;
 } gw_stream_desc;
 
 int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* desc, const gw_model_t* deepclean,
@@ -370,6 +377,15 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
  * real DFT, Hann window, FP64). */
 int gw_fir_create_band_loss(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps, double f1, double f2,
                             double ramp, double f_ref, int precision, gw_fir_t* out);
+/* Post-processing band-pass for the DeepClean prediction (Methods, online
+ * deployment: the noise estimate is post-processed, then subtracted from the
+ * strain; the post-processing itself is not specified, here it keeps the band
+ * the network was trained on): zero-phase, |H(f)| = T(f) on the grid
+ * f_j = j fs / nfft with T the raised-cosine band of gw_fir_create_band_loss;
+ * centred inverse real DFT, Hann window, FP64 design, FP32 taps (ntaps odd,
+ * <= nfft).  Used through gw_stream_desc.post. */
+int gw_fir_create_bandpass(gw_ctx_t ctx, double fs, int nfft, int ntaps, double f1, double f2, double ramp,
+                           int precision, gw_fir_t* out);
 /* loss: device scalar; r: device [B][L - ntaps + 1] (kept for the backward);
  * strain, y_hat: device [B][L]. */
 int gw_band_loss(gw_fir_t g, const float* strain, const float* y_hat, int B, int L, float* loss, float* r,

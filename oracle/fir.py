@@ -17,6 +17,10 @@ step it does not specify, at a rate it does not state.  Readings taken:
   sqrt(T(f) S(60 Hz) / S(f)), T a Tukey taper equal to 1 on [57, 63] Hz and
   falling to 0 at 55 and 65 Hz (a time-domain form of the inverse-PSD
   weighted 55-65 Hz mean-square error).
+* Post-processing of the prediction before subtraction (Methods, online
+  deployment: the noise estimate is post-processed, then subtracted): the
+  same zero-phase design with target amplitude T(f), a band-pass that keeps
+  the band the network was trained on.
 """
 from __future__ import annotations
 
@@ -80,6 +84,12 @@ def band_loss_fir(psd, fs, nfft, ntaps=2049, f1=55.0, f2=65.0, f_ref=60.0):
     s_ref = np.interp(f_ref, f, psd)
     amp = np.sqrt(tukey_band(f, f1, f2) * s_ref / psd)
     return zero_phase_fir(amp, nfft, ntaps)
+
+
+def bandpass_fir(fs, nfft, ntaps, f1=55.0, f2=65.0, ramp=2.0):
+    """Zero-phase band-pass with target amplitude T(f) (Tukey band)."""
+    f = np.arange(nfft // 2 + 1) * (fs / nfft)
+    return zero_phase_fir(tukey_band(f, f1, f2, ramp), nfft, ntaps)
 
 
 def fir_valid(x, h):

@@ -81,17 +81,50 @@ def clean(strain_total, agg, S, delta):
     return out
 
 
+def clean_post(strain_total, agg, S, delta, h):
+    """Cleaned strain with the aggregated prediction post-processed by the FIR h
+    (K odd taps, c = (K - 1) / 2) before subtraction (Methods, online
+    deployment: the noise estimate is post-processed, then subtracted):
+
+        cleaned[t] = strain[t] - sum_k h[k] p[t + k - c],
+
+    p the aggregated prediction on its emitted times (zero before time 0).
+    Snapshot k then delivers the times [k S - delta - c, k S + S - delta - c):
+    the FIR needs p up to c samples after the output time.  Returns (n, S)."""
+    strain_total = np.asarray(strain_total, np.float64)
+    h = np.asarray(h, np.float64)
+    n = agg.shape[0]
+    K = h.shape[0]
+    c = (K - 1) // 2
+    # p on the times [-delta, n S - delta); times before 0 count as zero
+    t_first = -delta
+    p = np.asarray(agg, np.float64).reshape(-1).copy()
+    p[np.arange(p.size) + t_first < 0] = 0.0
+    out = np.zeros((n, S))
+    j = np.arange(K)
+    for k in range(n):
+        for i, t in enumerate(emit_times(k, S, delta) - c):
+            u = t + j - c  # prediction times, at most the last one emitted
+            ok = u >= 0
+            q = h[ok] @ p[u[ok] - t_first]
+            out[k, i] = (strain_total[t] if t >= 0 else 0.0) - q
+    return out
+
+
 def run_deepclean_stream(forward, witness_total, strain_total, W, S, n_snap,
-                         mode, delta, snaps=None):
+                         mode, delta, snaps=None, post=None):
     """Push n_snap snapshots; returns (predictions (n, W), cleaned (n, S)).
 
     ``forward`` maps a (B, C, W) batch of windows to (B, W) predictions.
     ``snaps`` restricts the windows evaluated (others are not needed by
-    LATEST); by default every snapshot is evaluated.
+    LATEST); by default every snapshot is evaluated.  ``post``: optional
+    post-processing FIR taps (see ``clean_post``).
     """
     ks = range(n_snap) if snaps is None else snaps
     wins = np.stack([window(witness_total, W, S, k) for k in ks])
     preds = np.zeros((n_snap, W))
     preds[list(ks)] = forward(wins)
     agg = aggregate(preds, W, S, mode, delta)
+    if post is not None:
+        return preds, clean_post(strain_total, agg, S, delta, post)
     return preds, clean(strain_total, agg, S, delta)

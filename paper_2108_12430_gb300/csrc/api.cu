@@ -230,6 +230,14 @@ static std::vector<double> design_whitening(const double* psd, int n_psd, double
 // Band-limited inverse-PSD loss weight: |G(f)|^2 = T(f) S(f_ref) / S(f), with
 // T a Tukey band (1 on [f1 + ramp, f2 - ramp], raised-cosine ramps to 0 at f1
 // and f2) and S(f_ref) interpolated linearly on the grid.
+// 1 on [f1 + ramp, f2 - ramp], raised-cosine ramps to 0 at f1 and f2.
+static double tukey_band(double f, double f1, double f2, double ramp) {
+  if (f >= f1 + ramp && f <= f2 - ramp) return 1.0;
+  if (f > f1 && f < f1 + ramp) return 0.5 * (1.0 - std::cos(M_PI * (f - f1) / ramp));
+  if (f > f2 - ramp && f < f2) return 0.5 * (1.0 - std::cos(M_PI * (f2 - f) / ramp));
+  return 0.0;
+}
+
 static std::vector<double> design_band_loss(const double* psd, int n_psd, double fs, int ntaps, double f1, double f2,
                                             double ramp, double f_ref) {
   const int N = 2 * (n_psd - 1);
@@ -239,17 +247,7 @@ static std::vector<double> design_band_loss(const double* psd, int n_psd, double
   const int j0 = std::min((int)pos, n_psd - 2);
   const double s_ref = psd[j0] + (pos - j0) * (psd[j0 + 1] - psd[j0]);
   std::vector<double> A(n_psd);
-  for (int j = 0; j < n_psd; ++j) {
-    const double f = j * df;
-    double T = 0.0;
-    if (f >= f1 + ramp && f <= f2 - ramp)
-      T = 1.0;
-    else if (f > f1 && f < f1 + ramp)
-      T = 0.5 * (1.0 - std::cos(M_PI * (f - f1) / ramp));
-    else if (f > f2 - ramp && f < f2)
-      T = 0.5 * (1.0 - std::cos(M_PI * (f2 - f) / ramp));
-    A[j] = std::sqrt(T * s_ref / psd[j]);
-  }
+  for (int j = 0; j < n_psd; ++j) A[j] = std::sqrt(tukey_band(j * df, f1, f2, ramp) * s_ref / psd[j]);
   return design_zero_phase(A, ntaps);
 }
 
@@ -579,6 +577,11 @@ struct gw_stream {
   int* err = nullptr;
   int* reject = nullptr;    // device: this host-mode push's input had a non-finite sample
   int* reject_h = nullptr;  // pinned host copy, read after the push's synchronisation
+  // post-processing FIR of the aggregated prediction (optional)
+  float* post_taps = nullptr;
+  int post_K = 0;
+  float* pring[2] = {nullptr, nullptr};  // aggregated prediction per detector, ring of Rp
+  int64_t Rp = 0;
   size_t bytes = 0;
   std::vector<void*> allocs;
 };
@@ -967,6 +970,23 @@ int gw_fir_create_whitening(gw_ctx_t ctx, const double* psd, int n_psd, double f
   GW_API_END
 }
 
+int gw_fir_create_bandpass(gw_ctx_t ctx, double fs, int nfft, int ntaps, double f1, double f2, double ramp,
+                           int precision, gw_fir_t* out) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(ctx && out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(fs > 0 && nfft >= 4 && nfft % 2 == 0, "need fs > 0 and an even nfft");
+  GW_CHECK_ARG(ntaps >= 1 && (ntaps & 1) && ntaps <= nfft, "ntaps must be odd and <= nfft");
+  GW_CHECK_ARG(f1 >= 0 && ramp > 0 && f1 + 2 * ramp <= f2 && f2 <= 0.5 * fs, "need 0 <= f1, f1 + 2 ramp <= f2 <= fs/2");
+  GW_CHECK_ARG(precision == GW_FP32, "the post-processing band-pass is FP32");
+  const int n = nfft / 2 + 1;
+  const double df = fs / nfft;
+  std::vector<double> A(n);
+  for (int j = 0; j < n; ++j) A[j] = tukey_band(j * df, f1, f2, ramp);
+  *out = fir_from_taps(ctx, design_zero_phase(A, ntaps), precision);
+  GW_API_END
+}
+
 int gw_fir_create_band_loss(gw_ctx_t ctx, const double* psd, int n_psd, double fs, int ntaps, double f1, double f2,
                             double ramp, double f_ref, int precision, gw_fir_t* out) {
   GW_API_BEGIN
@@ -1068,6 +1088,8 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
   GW_CHECK_ARG(d->max_batch >= 1 && d->max_batch <= 4096, "max_batch out of range");
   GW_CHECK_ARG(d->agg_mode == GW_AGG_LATEST || d->agg_mode == GW_AGG_AVERAGE, "unknown aggregation mode");
   GW_CHECK_ARG(d->agg_delay >= 0 && d->agg_delay <= d->window - d->stride, "agg_delay out of range");
+  GW_CHECK_ARG(!d->post || (d->post->precision == GW_FP32 && (d->post->ntaps & 1) && d->post->ntaps <= 16385),
+               "post-processing FIR must be FP32 with an odd number of taps (<= 16385)");
   for (int i = 0; i < d->n_det; ++i) {
     GW_CHECK_ARG(deepclean[i] && deepclean[i]->kind == GW_MODEL_DEEPCLEAN, "need one DeepClean model per detector");
     GW_CHECK_ARG(deepclean[i]->n_in == d->n_witness, "model n_in != n_witness");
@@ -1080,7 +1102,9 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
   const int prec = deepclean[0]->precision;
   for (int i = 0; i < d->n_det; ++i) s->dc[i] = deepclean[i];
   const int64_t W = d->window, S = d->stride, nb = d->max_batch, C = d->n_witness;
-  s->R = W + (nb - 1) * S;
+  const int64_t post_c = d->post ? (d->post->ntaps - 1) / 2 : 0;
+  // the strain ring also serves the post-processed outputs, c samples older
+  s->R = W + (nb - 1) * S + post_c;
   s->R = (s->R + 15) / 16 * 16;  // whole rows in every phase plane of the ring
   const int G = (int)((C + 7) / 8);
   try {
@@ -1101,6 +1125,15 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
     s->act1 = salloc<char>(s, act_elems * esz);
     s->stage_in = salloc<float>(s, (size_t)d->n_det * (C + 1) * nb * S);
     s->stage_out = salloc<float>(s, (size_t)d->n_det * nb * S);
+    if (d->post) {
+      s->post_K = d->post->ntaps;
+      s->post_taps = salloc<float>(s, (size_t)s->post_K);
+      GW_CUDA(cudaMemcpy(s->post_taps, d->post->d_taps, (size_t)s->post_K * sizeof(float), cudaMemcpyDeviceToDevice));
+      // the FIR of a push reads predictions from c before its first output to
+      // c after its last one
+      s->Rp = (nb * S + 2 * post_c + 64 + 63) / 64 * 64;
+      for (int i = 0; i < d->n_det; ++i) s->pring[i] = salloc<float>(s, (size_t)s->Rp);
+    }
     s->status = salloc<int>(s, 3);
     s->err = s->status + 1;
     s->reject = s->status + 2;
@@ -1209,7 +1242,12 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
     {
       Prof p("sub_ola", st);
       launch_sub_ola(s->pred, W, n_snap, S, W, R, head, s->d.agg_mode, s->d.agg_delay, s->acc[d], s->strain[d],
-                     out + (size_t)d * n, st, skip);
+                     out + (size_t)d * n, st, skip, s->pring[d], s->Rp);
+    }
+    if (s->post_K) {
+      Prof p("post", st);
+      launch_post_sub(s->pring[d], s->Rp, s->post_taps, s->post_K, s->strain[d], R,
+                      head - s->d.agg_delay - (s->post_K - 1) / 2, (int)n, out + (size_t)d * n, st, skip);
     }
   }
   if (mem == GW_MEM_HOST) {

@@ -209,9 +209,17 @@ void launch_ring_fill(void* ring, int bf16, int C, int G, int64_t R2, const floa
                       cudaStream_t st);
 void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head,
                         int* status, cudaStream_t st, const int* skip = nullptr);
+// pring (optional): instead of subtracting, store the aggregated prediction of
+// every emitted time t >= 0 at pring[t mod Rp] (post-processing follows).
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R,
                     int64_t head, int mode, int delta, float* acc, const float* strain_ring,
-                    float* out, cudaStream_t st, const int* skip = nullptr);
+                    float* out, cudaStream_t st, const int* skip = nullptr, float* pring = nullptr,
+                    int64_t Rp = 0);
+// out[i] = strain[t] - sum_k h[k] p[t + k - c] for t = t0 + i, i < count,
+// c = (K - 1) / 2, p read from the ring pring (0 before time 0), strain from
+// its ring (0 before time 0).
+void launch_post_sub(const float* pring, int64_t Rp, const float* h, int K, const float* strain_ring, int64_t R,
+                     int64_t t0, int count, float* out, cudaStream_t st, const int* skip = nullptr);
 // Sets *flag to 1 when any of the n floats at x is not finite (the caller zeroes it).
 void launch_check_finite(const float* x, int64_t n, int* flag, cudaStream_t st);
 

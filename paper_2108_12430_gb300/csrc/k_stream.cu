@@ -104,7 +104,8 @@ __global__ void strain_push_kernel(const float* __restrict__ src, int n, float* 
 // cleaned = strain(tau) - value, written to out[tau - head + delta].
 __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, int n, int S, int W,
                                int64_t R, int64_t head, int mode, int delta, float* __restrict__ acc,
-                               const float* __restrict__ strain_ring, float* __restrict__ out, const int* skip) {
+                               const float* __restrict__ strain_ring, float* __restrict__ out, const int* skip,
+                               float* __restrict__ pring, int64_t Rp) {
   if (skip && *skip) return;
   const int64_t lo = head + S - W;
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
@@ -118,11 +119,20 @@ __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, 
     const int jlo = (int)imax64(0, floordiv64(r, S));
     const int jhi = (int)imin64(n - 1, floordiv64(r + W, S) - 1);
     const float s_tau = (tau >= 0) ? strain_ring[pmod(tau, R)] : 0.f;
+    // an emitted time gets strain - prediction, or with post-processing its
+    // prediction goes to the ring that the post-processing FIR reads
+    auto emit = [&](float value) {
+      if (pring) {
+        if (tau >= 0) pring[pmod(tau, Rp)] = value;
+      } else {
+        out[tau - head + delta] = s_tau - value;
+      }
+    };
     if (mode == GW_AGG_LATEST) {
       if (!emits) continue;
       const int j = (int)(k_emit - k0);
       const int64_t start = head + (int64_t)(j + 1) * S - W;
-      out[tau - head + delta] = s_tau - pred[(int64_t)j * pred_ld + (tau - start)];
+      emit(pred[(int64_t)j * pred_ld + (tau - start)]);
       continue;
     }
     float sum = (tau < head) ? acc[pmod(tau, R)] : 0.f;
@@ -141,12 +151,12 @@ __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, 
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         sum += val[q];
-        if (j + q == j_emit) out[tau - head + delta] = s_tau - sum / cnt;
+        if (j + q == j_emit) emit(sum / cnt);
       }
     }
     for (; j <= jhi; ++j) {
       sum += pj[(int64_t)j * (pred_ld - S)];
-      if (j == j_emit) out[tau - head + delta] = s_tau - sum / cnt;
+      if (j == j_emit) emit(sum / cnt);
     }
     acc[pmod(tau, R)] = sum;
   }
@@ -184,6 +194,33 @@ __global__ void ring_fill_kernel(void* __restrict__ ring, int bf16, int C, int G
       r[e] = -mean[c] * istd[c];
     }
   }
+}
+
+// Post-processing of the aggregated prediction: one CTA per kPostBlock
+// outputs stages the taps and the prediction segment it needs in shared
+// memory; each thread computes one output.
+constexpr int kPostBlock = 256;
+__global__ void post_sub_kernel(const float* __restrict__ pring, int64_t Rp, const float* __restrict__ h, int K,
+                                const float* __restrict__ strain_ring, int64_t R, int64_t t0, int count,
+                                float* __restrict__ out, const int* skip) {
+  if (skip && *skip) return;
+  extern __shared__ float sh[];
+  float* hs = sh;      // [K]
+  float* ps = sh + K;  // p[t_blk - c + i], i < kPostBlock + K - 1
+  const int c = (K - 1) / 2;
+  const int64_t t_blk = t0 + (int64_t)blockIdx.x * kPostBlock;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = h[k];
+  for (int i = threadIdx.x; i < kPostBlock + K - 1; i += blockDim.x) {
+    const int64_t t = t_blk - c + i;
+    ps[i] = t >= 0 ? pring[pmod(t, Rp)] : 0.f;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kPostBlock + threadIdx.x;
+  if (threadIdx.x >= kPostBlock || i >= count) return;
+  float q = 0.f;
+  for (int k = 0; k < K; ++k) q = fmaf(hs[k], ps[threadIdx.x + k], q);
+  const int64_t t = t_blk + threadIdx.x;
+  out[i] = (t >= 0 ? strain_ring[pmod(t, R)] : 0.f) - q;
 }
 
 // Any non-finite value among n floats (16-byte aligned, n a multiple of 4
@@ -260,10 +297,27 @@ void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t
 
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R, int64_t head, int mode,
                     int delta, float* acc, const float* strain_ring, float* out, cudaStream_t st,
-                    const int* skip) {
+                    const int* skip, float* pring, int64_t Rp) {
+  GW_CHECK_ARG(!pring || Rp >= (int64_t)n * S, "prediction ring too small");
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
   sub_ola_kernel<<<grid_for(count), kThreads, 0, st>>>(pred, pred_ld, n, S, W, R, head, mode, delta, acc,
-                                                        strain_ring, out, skip);
+                                                        strain_ring, out, skip, pring, Rp);
+  GW_LAUNCH_CHECK();
+}
+
+void launch_post_sub(const float* pring, int64_t Rp, const float* h, int K, const float* strain_ring, int64_t R,
+                     int64_t t0, int count, float* out, cudaStream_t st, const int* skip) {
+  GW_CHECK_ARG(K >= 1 && (K & 1), "post-processing FIR needs an odd number of taps");
+  if (count <= 0) return;
+  const size_t smem = (size_t)(2 * K + kPostBlock - 1) * sizeof(float);
+  GW_CHECK_ARG(smem <= 200 * 1024, "post-processing FIR too long");
+  static bool attr_set = false;
+  if (!attr_set) {
+    GW_CUDA(cudaFuncSetAttribute(post_sub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  post_sub_kernel<<<(count + kPostBlock - 1) / kPostBlock, kPostBlock, smem, st>>>(pring, Rp, h, K, strain_ring, R, t0,
+                                                                                 count, out, skip);
   GW_LAUNCH_CHECK();
 }
 

@@ -43,7 +43,7 @@ EXPORTS = (
     "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
     "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
     "gw_trainer_backward", "gw_fir_create_band_loss", "gw_band_loss", "gw_band_loss_backward", "gw_fir_backward",
-    "gw_adam_step", "gw_model_calibrate", "gw_model_test_wait_timeout",
+    "gw_adam_step", "gw_model_calibrate", "gw_model_test_wait_timeout", "gw_fir_create_bandpass",
 )
 
 
@@ -62,7 +62,7 @@ class gw_model_desc(C.Structure):
 
 class gw_stream_desc(C.Structure):
     _fields_ = [("n_det", C.c_int), ("n_witness", C.c_int), ("window", C.c_int), ("stride", C.c_int),
-                ("max_batch", C.c_int), ("agg_mode", C.c_int), ("agg_delay", C.c_int)]
+                ("max_batch", C.c_int), ("agg_mode", C.c_int), ("agg_delay", C.c_int), ("post", C.c_void_p)]
 
 
 class gw_server_desc(C.Structure):
@@ -134,6 +134,7 @@ def _declare(lib):
         "gw_trainer_bytes": (I64, [P]),
         "gw_trainer_forward": (I, [P, P, P, I, P, P]),
         "gw_trainer_backward": (I, [P, P, P, P]),
+        "gw_fir_create_bandpass": (I, [P, C.c_double, I, I, C.c_double, C.c_double, C.c_double, I, C.POINTER(P)]),
         "gw_fir_create_band_loss": (I, [P, C.POINTER(C.c_double), I, C.c_double, I, C.c_double, C.c_double,
                                         C.c_double, C.c_double, I, C.POINTER(P)]),
         "gw_band_loss": (I, [P, P, P, I, I, P, P, P]),
@@ -281,8 +282,8 @@ def gw_whiten(f, x_ptr, B, Cc, L_in, y_ptr, stream=0):
     _check(lib().gw_whiten(f, x_ptr, B, Cc, L_in, y_ptr, stream or None))
 
 
-def gw_stream_create(ctx, models, n_det, n_witness, window, stride, max_batch, agg_mode, agg_delay):
-    d = gw_stream_desc(n_det, n_witness, window, stride, max_batch, agg_mode, agg_delay)
+def gw_stream_create(ctx, models, n_det, n_witness, window, stride, max_batch, agg_mode, agg_delay, post=None):
+    d = gw_stream_desc(n_det, n_witness, window, stride, max_batch, agg_mode, agg_delay, post)
     arr = (P * 2)(*(list(models) + [None] * (2 - len(models))))
     h = P()
     _check(lib().gw_stream_create(ctx, C.byref(d), arr, C.byref(h)))
@@ -405,6 +406,12 @@ def gw_trainer_forward(t, params_ptr, x_ptr, B, y_ptr, stream=0):
 
 def gw_trainer_backward(t, dy_ptr, dparams_ptr, stream=0):
     _check(lib().gw_trainer_backward(t, dy_ptr, dparams_ptr, stream or None))
+
+
+def gw_fir_create_bandpass(ctx, fs, nfft, ntaps, f1=55.0, f2=65.0, ramp=2.0, precision=GW_FP32):
+    h = P()
+    _check(lib().gw_fir_create_bandpass(ctx, fs, nfft, ntaps, f1, f2, ramp, precision, C.byref(h)))
+    return h.value
 
 
 def gw_fir_create_band_loss(ctx, psd, fs, ntaps, f1=55.0, f2=65.0, ramp=2.0, f_ref=60.0, precision=GW_FP32):

@@ -13,6 +13,12 @@ strain.  A held-out segment is then cleaned
     delta samples before the window's end - the aggregation latency delta
     moves the kept samples away from the window edge.
 
+Optionally (post_taps > 0) the prediction is post-processed before it is
+subtracted, as in the paper's online pipeline: a zero-phase 55-65 Hz
+band-pass (gw_fir_create_bandpass), offline through the library's FIR,
+online inside the stream (the outputs arrive (post_taps - 1) / 2 samples
+later).
+
 The quantity compared is the paper's: the ratio of the amplitude spectral
 density (Welch, Hann, 2 s segments, 50% overlap) of the cleaned data to that
 of the uncleaned data, and the fraction of frequency bins in [50, 70] Hz in
@@ -36,7 +42,7 @@ def _asd(x):
 
 def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1000, lr=1e-3, batch=32,
                               train_len=8192, window_s=8, stride=256, deltas_s=(0.0, 0.5, 0.75),
-                              precision=G.GW_FP32):
+                              precision=G.GW_FP32, post_taps=0):
     """Runs the study; returns a dict of the training losses, the offline ASD
     ratio near 60 Hz and outside the band, and per aggregation latency the
     fraction of [50, 70] Hz bins off the offline ratio by more than 10%."""
@@ -51,7 +57,8 @@ def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1
     std = wit[:, :n_tr].std(1).astype(np.float32)
     ctx = G.gw_ctx_create(device, 0)
     out = {"seed": seed, "train_seconds": train_s, "eval_seconds": eval_s, "steps": steps, "lr": lr,
-           "window_seconds": window_s, "stride": stride}
+           "window_seconds": window_s, "stride": stride, "post_taps": post_taps}
+    c = (post_taps - 1) // 2 if post_taps else 0
     try:
         # ---- training (rows a9, a10) ----
         t = G.gw_trainer_create(ctx, C, batch, train_len, 0, mean, std)
@@ -88,6 +95,7 @@ def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1
         out["losses"] = losses
         params = p.cpu().numpy()
         m = G.gw_model_create(ctx, G.GW_MODEL_DEEPCLEAN, precision, C, params, mean, std)
+        post = G.gw_fir_create_bandpass(ctx, float(FS), 8192, post_taps) if post_taps else None
 
         # ---- offline: the evaluation segment as one window ----
         e0 = n_tr + W
@@ -96,10 +104,20 @@ def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1
         G.gw_deepclean_forward(m, xe.data_ptr(), n_ev, 0, 1, n_ev, ye.data_ptr())
         torch.cuda.synchronize()
         raw = strain[e0:e0 + n_ev]
-        offline = raw - ye.cpu().numpy().astype(np.float64)
-        edge = 2 * FS  # the offline segment's own padded ends are excluded
-        f, a_raw = _asd(raw[edge:-edge])
-        _, a_off = _asd(offline[edge:-edge])
+        pred = ye.cpu().numpy().astype(np.float64)
+        if post:
+            # valid-mode FIR: output i sits at time i + c of the segment
+            q = torch.empty(n_ev - post_taps + 1, device="cuda")
+            G.gw_whiten(post, ye.data_ptr(), 1, 1, n_ev, q.data_ptr())
+            torch.cuda.synchronize()
+            pred = np.zeros(n_ev)
+            pred[c:n_ev - c] = q.cpu().numpy()
+        offline = raw - pred
+        # spectra over a common span: the offline segment's own padded ends
+        # and the FIR's edges are excluded
+        lo, hi = 2 * FS + c, n_ev - 2 * FS - c
+        f, a_raw = _asd(raw[lo:hi])
+        _, a_off = _asd(offline[lo:hi])
         rat_off = a_off / a_raw
         band = (f >= 50) & (f <= 70)
         line = (f >= 59) & (f <= 61)
@@ -111,8 +129,8 @@ def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1
         per = {}
         for dsec in deltas_s:
             delta = int(round(dsec * FS))
-            sm = G.gw_stream_create(ctx, [m], 1, C, W, stride, 1, G.GW_AGG_LATEST, delta)
-            total = W + n_ev + delta + stride
+            sm = G.gw_stream_create(ctx, [m], 1, C, W, stride, 1, G.GW_AGG_LATEST, delta, post)
+            total = W + n_ev + delta + c + stride
             cleaned = np.zeros(total, np.float32)
             k = 0
             while (k + 1) * stride <= total:
@@ -121,18 +139,20 @@ def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1
                 s_in = np.ascontiguousarray(strain[None, a:a + stride], np.float32)
                 o = np.zeros((1, stride), np.float32)
                 G.gw_stream_push(sm, 1, w_in, s_in, o)
-                t0 = k * stride - delta  # emitted times [k S - delta, k S + S - delta)
+                t0 = k * stride - delta - c  # emitted times [k S - delta - c, k S + S - delta - c)
                 if t0 >= 0:
                     cleaned[t0:t0 + stride] = o[0]
                 k += 1
             G.gw_stream_destroy(sm)
             on = cleaned[W:W + n_ev].astype(np.float64)
-            _, a_on = _asd(on[edge:-edge])
+            _, a_on = _asd(on[lo:hi])
             rat_on = a_on / a_raw
             per[f"{dsec:g}s"] = {
                 "frac_50_70Hz_off_by_10pct": float(np.mean(np.abs(rat_on[band] / rat_off[band] - 1) > 0.1)),
                 "ratio_59_61Hz": float(rat_on[line].mean())}
         out["online"] = per
+        if post:
+            G.gw_fir_destroy(post)
         G.gw_model_destroy(m)
     finally:
         G.gw_ctx_destroy(ctx)

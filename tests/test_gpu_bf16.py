@@ -88,6 +88,14 @@ def test_stream_matches_oracle_bf16(ctx, mode, delta):
         assert rel_l2(g, ref) <= TOL16
 
 
+def test_stream_post_processing_bf16(ctx):
+    W, S = 1024, 128
+    for g, ref in run_stream_case(ctx, W, S, [2, 5, 1, 4], G.GW_AGG_AVERAGE, W - S, seed=9, precision=G.GW_BF16,
+                                  post_taps=257):
+        assert g.shape == ref.shape
+        assert rel_l2(g, ref) <= TOL16
+
+
 def test_bulk_stride_half_window_bf16(ctx):
     # offline bulk mode: snapshots at 1/4 Hz with 8 s windows, i.e. S = W / 2,
     # every sample averaged over the two windows that cover it

@@ -128,7 +128,8 @@ def stream_standardisation(seed, d):
     return r.normal(0, 0.2, 21).astype(np.float32), r.uniform(0.7, 1.4, 21).astype(np.float32)
 
 
-def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G.GW_FP32, standardise=False):
+def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G.GW_FP32, standardise=False,
+                    post_taps=0):
     """Push the given batch sizes through a stream; compare with the oracle.
     With standardise, the models carry input mean / std, and the missing past
     before time 0 is a zero input sample that the model standardises."""
@@ -137,7 +138,14 @@ def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G
     strn = [synth.coupled_strain(seed + 10 * d, wit[d]) for d in range(n_det)]
     ms = [stream_standardisation(seed, d) if standardise else (None, None) for d in range(n_det)]
     models = [ctx.deepclean(seed + d, precision, *ms[d]) for d in range(n_det)]
-    s = G.gw_stream_create(ctx.h, models, n_det, 21, W, S, max(pushes), mode, delta)
+    post, taps = None, None
+    if post_taps:
+        post = G.gw_fir_create_bandpass(ctx.h, 4096.0, 8192, post_taps)
+        # the stream applies the taps in FP32
+        taps = G.gw_fir_taps(post).astype(np.float32).astype(np.float64)
+    s = G.gw_stream_create(ctx.h, models, n_det, 21, W, S, max(pushes), mode, delta, post)
+    if post:
+        G.gw_fir_destroy(post)  # the stream keeps its own copy of the taps
     ctx.objs.append((G.gw_stream_destroy, s))
     got = [[] for _ in range(n_det)]
     t = 0
@@ -162,9 +170,29 @@ def run_stream_case(ctx, W, S, pushes, mode, delta, seed=0, n_det=1, precision=G
         snaps = None
         if mode == ostream.LATEST:
             snaps = list(range(n_total))
-        _, ref = ostream.run_deepclean_stream(fwd, w32, s32, W, S, n_total, mode, delta, snaps)
+        _, ref = ostream.run_deepclean_stream(fwd, w32, s32, W, S, n_total, mode, delta, snaps, post=taps)
         res.append((g, ref))
     return res
+
+
+@pytest.mark.parametrize("mode,delta", [(G.GW_AGG_LATEST, 0), (G.GW_AGG_AVERAGE, 1024 - 128),
+                                        (G.GW_AGG_AVERAGE, 200)])
+def test_stream_post_processing_fp32(ctx, mode, delta):
+    # the aggregated prediction goes through a 129-tap band-pass before it is
+    # subtracted; outputs arrive 64 samples later; two detectors
+    W, S = 1024, 128
+    for g, ref in run_stream_case(ctx, W, S, [3, 1, 5, 4, 2], mode, delta, seed=8, n_det=2, post_taps=129):
+        assert g.shape == ref.shape
+        assert rel_l2(g, ref) <= TOL32
+        np.testing.assert_allclose(g, ref, rtol=1e-4, atol=1e-4)
+
+
+def test_bandpass_design_matches_oracle(ctx):
+    h = G.gw_fir_create_bandpass(ctx.h, 4096.0, 8192, 2049)
+    try:
+        np.testing.assert_allclose(G.gw_fir_taps(h), ofir.bandpass_fir(4096.0, 8192, 2049), rtol=0, atol=1e-13)
+    finally:
+        G.gw_fir_destroy(h)
 
 
 def test_bulk_stride_half_window_fp32(ctx):

@@ -25,3 +25,14 @@ def test_aggregation_latency_study():
     assert on["0.5s"]["frac_50_70Hz_off_by_10pct"] <= 0.02
     assert on["0.75s"]["frac_50_70Hz_off_by_10pct"] <= 0.02
     assert on["0.75s"]["ratio_59_61Hz"] < 0.15
+
+
+def test_study_with_post_processing():
+    # with the 55-65 Hz band-pass on the prediction (as the paper's online
+    # pipeline post-processes the noise estimate before subtracting it) the
+    # out-of-band spectrum is left alone while the 60 Hz coupling is removed
+    r = study.aggregation_latency_study(train_s=128, eval_s=48, steps=800, post_taps=2049)
+    assert r["offline_ratio_59_61Hz"] < 0.2
+    assert 0.95 < r["offline_ratio_80_200Hz"] < 1.05
+    assert 0.95 < r["offline_ratio_20_45Hz"] < 1.05
+    assert r["online"]["0.75s"]["frac_50_70Hz_off_by_10pct"] <= 0.02

@@ -241,6 +241,52 @@ def test_band_loss_filter_response():
     assert np.all(fir.freq_response(g, np.array([20.0, 40.0, 80.0, 200.0, 1000.0]), fs) < 0.01)
 
 
+def test_bandpass_response():
+    fs = 4096.0
+    # long enough for the 6 Hz flat top: within 1% of 1 on [58, 62] Hz
+    h = fir.bandpass_fir(fs, 16384, 8191)
+    assert np.allclose(h, h[::-1], atol=1e-15)
+    np.testing.assert_allclose(fir.freq_response(h, np.linspace(58.0, 62.0, 9), fs), 1.0, atol=0.01)
+    assert np.all(fir.freq_response(h, np.array([0.0, 20.0, 45.0, 50.0, 70.0, 80.0, 200.0, 1000.0]), fs) < 1e-3)
+    # the 2049-tap version used online (0.25 s delay): unit gain at 60 Hz, the
+    # Hann window widens the ramps to about 8 Hz
+    h = fir.bandpass_fir(fs, 8192, 2049)
+    np.testing.assert_allclose(fir.freq_response(h, [60.0], fs), 1.0, atol=0.01)
+    assert np.all(fir.freq_response(h, np.array([0.0, 20.0, 45.0, 75.0, 80.0, 200.0, 1000.0]), fs) < 0.01)
+
+
+def test_clean_post_one_tap_is_plain_subtraction():
+    # with a single unit tap the post-processed path subtracts the aggregated
+    # prediction itself; before time 0 both strain and prediction count as 0
+    x = rng.standard_normal(3000)
+    agg = rng.standard_normal((6, 128))
+    for delta in (0, 100):
+        got = stream.clean_post(x, agg, 128, delta, np.ones(1)).reshape(-1)
+        want = stream.clean(x, agg, 128, delta).reshape(-1)
+        t = np.arange(-delta, 6 * 128 - delta)
+        np.testing.assert_array_equal(got[t >= 0], want[t >= 0])
+        assert np.all(got[t < 0] == 0.0)
+
+
+def test_clean_post_is_a_delayed_convolution():
+    # brute force: the emitted prediction series (zero before time 0), full
+    # convolution with the symmetric taps, read c samples late
+    S, n, delta, K = 64, 9, 40, 31
+    h = np.hanning(K + 2)[1:-1]
+    x = rng.standard_normal(n * S + 100)
+    agg = rng.standard_normal((n, S))
+    got = stream.clean_post(x, agg, S, delta, h)
+    c = (K - 1) // 2
+    t = np.arange(-delta, n * S - delta)  # emitted times
+    p = np.where(t >= 0, agg.reshape(-1), 0.0)
+    # q(t') = sum_j h[j] p(t' + j - c) on t' = t - c; p(u) = 0 for u < -delta
+    pad = np.concatenate([np.zeros(2 * c), p])  # index i <-> time i - 2 c - delta
+    q = np.convolve(pad, h[::-1], mode="valid")  # q[i] = sum_j h[j] pad[i + j] <-> t' = i - c - delta
+    tq = np.arange(q.size) - c - delta
+    want = np.where(tq >= 0, x[np.clip(tq, 0, None)], 0.0) - q
+    np.testing.assert_allclose(got.reshape(-1), want[:n * S], atol=1e-12)
+
+
 def test_decimate_alignment():
     h = fir.lowpass_fir()
     x = np.cos(2 * np.pi * 50.0 * np.arange(4096) / 4096.0)
