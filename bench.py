@@ -274,6 +274,25 @@ def e2e_pass(G, torch, s, wit_h, str_h, first, steps):
     return lat
 
 
+def e2e_pipelined(G, torch, s, wit_h, str_h, first, steps):
+    """Queued host-buffer pushes through the public API: each step's H2D copy,
+    compute and D2H copy of its cleaned samples (into its own pinned buffer)
+    are queued with gw_stream_push_async; one gw_stream_sync ends the timed
+    region.  Returns the wall time in ms."""
+    outs = [torch.empty(B * S, dtype=torch.float32).pin_memory() for _ in range(steps)]
+    lib = G.lib()
+    h = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        rc = lib.gw_stream_push_async(s, B, wit_h[first + i].data_ptr(), str_h[first + i].data_ptr(),
+                                      outs[i].data_ptr(), h)
+        if rc < 0:
+            raise G.GwError(rc, lib.gw_last_error().decode())
+    G.gw_stream_sync(s)
+    return (time.perf_counter() - t0) * 1e3
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -288,7 +307,8 @@ def gpu_arm(args):
         dist.init_process_group("nccl")
     dev_index = torch.cuda.current_device()
     K, Wm = args.steps, args.warmup
-    n_total = (Wm + K + 8) * B * S
+    npipe = max(K, 8)  # pipelined host-buffer steps
+    n_total = (Wm + K + 8 + npipe) * B * S
     wit, strain = make_stream_inputs(n_total, seed=1234 + rank)
     wit_d = torch.from_numpy(wit).cuda()
     str_d = torch.from_numpy(strain).cuda()
@@ -334,10 +354,16 @@ def gpu_arm(args):
         wit_h = {first + i: pin(wit[:, (first + i) * n_step:(first + i + 1) * n_step])
                  for i in range(ne2e)}
         str_h = {first + i: pin(strain[(first + i) * n_step:(first + i + 1) * n_step]) for i in range(ne2e)}
+        f2 = first + ne2e
+        wit_h.update({f2 + i: pin(wit[:, (f2 + i) * n_step:(f2 + i + 1) * n_step]) for i in range(npipe)})
+        str_h.update({f2 + i: pin(strain[(f2 + i) * n_step:(f2 + i + 1) * n_step]) for i in range(npipe)})
         if world > 1:
             dist.barrier()
         lat = e2e_pass(G, torch, s, wit_h, str_h, first, ne2e)
         e2e_tot = slowest(dist, world, float(sum(lat)), "cuda")
+        if world > 1:
+            dist.barrier()
+        pipe_ms = slowest(dist, world, e2e_pipelined(G, torch, s, wit_h, str_h, f2, npipe), "cuda")
         err = accuracy(G, torch, prec, dev_index) if rank == 0 else None
         G.gw_stream_destroy(s)
         G.gw_model_destroy(m)
@@ -353,7 +379,9 @@ def gpu_arm(args):
             "p50_ms": float(np.percentile(ms, 50)),
             "p99_ms": float(np.percentile(ms, 99)),
             "rel_l2_vs_fp64_oracle": err,
-            "e2e_value": job_rate(B * ne2e, world, e2e_tot / 1e3),
+            "e2e_value": job_rate(B * npipe, world, pipe_ms / 1e3),
+            "e2e_ms_per_step": pipe_ms / npipe,
+            "e2e_sync_value": job_rate(B * ne2e, world, e2e_tot / 1e3),
             "e2e_p50_ms": float(np.percentile(lat, 50)),
             "e2e_p99_ms": float(np.percentile(lat, 99)),
             "gpu_launches_per_step": res["launches_per_step"],
@@ -433,9 +461,13 @@ def gpu_arm(args):
         "p50_ms": hp["p50_ms"],
         "p99_ms": hp["p99_ms"],
         "rel_l2_vs_fp64_oracle": hp["rel_l2_vs_fp64_oracle"],
-        "e2e": {"value": hp["e2e_value"], "unit": "snapshots/s", "p50_ms": hp["e2e_p50_ms"],
-                "p99_ms": hp["e2e_p99_ms"],
-                "h2d_bytes_per_step": (C + 1) * B * S * 4, "d2h_bytes_per_step": B * S * 4},
+        "e2e": {"value": hp["e2e_value"], "unit": "snapshots/s", "ms_per_step": hp["e2e_ms_per_step"],
+                "h2d_bytes_per_step": (C + 1) * B * S * 4, "d2h_bytes_per_step": B * S * 4 + 4,
+                "mode": "pipelined host-buffer pushes: gw_stream_push_async per step (pinned inputs, "
+                        "H2D + check + compute + D2H of the cleaned samples and the reject flag), "
+                        "one gw_stream_sync at the end of the timed region",
+                "sync": {"value": hp["e2e_sync_value"], "p50_ms": hp["e2e_p50_ms"], "p99_ms": hp["e2e_p99_ms"],
+                         "mode": "gw_stream_push in host mode, returning per step"}},
         "gpu_launches": int(round(hp["gpu_launches_per_step"] * K)),
         "roofline": dict({"bound": bound, "kernel": "conv layers (8 launches per step)", "achieved": achieved,
                           "peak": peak, "unit": unit, "frac": achieved / peak, "traffic": traffic,

@@ -238,6 +238,30 @@ int gw_stream_destroy(gw_stream_t s);
  * checks on the device and reports through gw_stream_status). */
 int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float* strain,
                    float* clean_out, int mem, void* cuda_stream);
+/* Queued host-buffer pushes for a pipelined client (the same computation as
+ * gw_stream_push in host mode).  gw_stream_push_async queues push k: the copy
+ * of its inputs to the device, the device-side check, the snapshot update,
+ * DeepClean, the subtraction and the copy of its cleaned samples to
+ * clean_out, all stream-ordered on cuda_stream, and returns without waiting;
+ * the host can queue push k + 1 while the device still works on push k.
+ * witness / strain / clean_out are host buffers in the layouts of
+ * gw_stream_push; they should be page-locked (cudaHostAlloc or a pinned
+ * allocator: pageable buffers make the copies synchronous) and must stay
+ * valid, the inputs unmodified and clean_out unread, until gw_stream_sync
+ * returns.  All pushes queued before a gw_stream_sync use one cuda_stream
+ * (GW_EINVAL otherwise); at most GW_STREAM_MAX_PENDING are pending
+ * (GW_ESTATE beyond).  gw_stream_push returns GW_ESTATE while pushes are
+ * pending.  The head advances at every queued push.
+ * gw_stream_sync waits for every pending push.  If one of them held a
+ * non-finite sample it returns GW_ENONFINITE and stores its index among the
+ * pending pushes (0 = the oldest) in *first_rejected (may be NULL; -1 when
+ * none): that push and every later pending one left the stream state
+ * unchanged and their clean_out is unspecified, the earlier ones completed,
+ * and the head is rewound to that before the rejected push. */
+#define GW_STREAM_MAX_PENDING 1024
+int gw_stream_push_async(gw_stream_t s, int n_snap, const float* witness, const float* strain,
+                         float* clean_out, void* cuda_stream);
+int gw_stream_sync(gw_stream_t s, int* first_rejected);
 /* Samples pushed so far per detector. */
 int64_t gw_stream_head(gw_stream_t s);
 /* Device-side status of the stream: GW_OK or GW_ENONFINITE (sticky until reset). */

@@ -576,7 +576,22 @@ struct gw_stream {
   int* status = nullptr;
   int* err = nullptr;
   int* reject = nullptr;    // device: this host-mode push's input had a non-finite sample
-  int* reject_h = nullptr;  // pinned host copy, read after the push's synchronisation
+  int* reject_h = nullptr;  // pinned host copies: [0] for a synchronous push, [1 + k] for queued push k
+  // pushes queued by gw_stream_push_async and not yet synchronised: the head
+  // before each, and the CUDA stream they were queued on
+  int pending = 0;
+  std::vector<int64_t> head_q;
+  cudaStream_t async_st = nullptr;
+  // Queued pushes alternate between two staging sets; their input copies run
+  // on cs_in and their output copies on cs_out, so that the copies of pushes
+  // k + 1 and k - 1 overlap the compute of push k.  Events: ev_in[b] inputs
+  // of set b staged, ev_done[b] compute on set b finished, ev_out[b] outputs of
+  // set b copied out.  reject_q[k]: the reject flag as push k's compute left it.
+  float* stage_in_q[2] = {nullptr, nullptr};
+  float* stage_out_q[2] = {nullptr, nullptr};
+  int* reject_q = nullptr;
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   // post-processing FIR of the aggregated prediction (optional)
   float* post_taps = nullptr;
   int post_K = 0;
@@ -593,6 +608,13 @@ static void stream_free(gw_stream* s) {
   cudaDeviceSynchronize();
   for (void* p : s->allocs) cudaFree(p);
   if (s->reject_h) cudaFreeHost(s->reject_h);
+  for (int b = 0; b < 2; ++b) {
+    if (s->ev_in[b]) cudaEventDestroy(s->ev_in[b]);
+    if (s->ev_done[b]) cudaEventDestroy(s->ev_done[b]);
+    if (s->ev_out[b]) cudaEventDestroy(s->ev_out[b]);
+  }
+  if (s->cs_in) cudaStreamDestroy(s->cs_in);
+  if (s->cs_out) cudaStreamDestroy(s->cs_out);
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     s->ctx->in_use -= s->bytes;
@@ -1137,7 +1159,20 @@ int gw_stream_create(gw_ctx_t ctx, const gw_stream_desc* d, const gw_model_t* de
     s->status = salloc<int>(s, 3);
     s->err = s->status + 1;
     s->reject = s->status + 2;
-    GW_CUDA(cudaHostAlloc((void**)&s->reject_h, sizeof(int), cudaHostAllocDefault));
+    GW_CUDA(cudaHostAlloc((void**)&s->reject_h, (1 + GW_STREAM_MAX_PENDING) * sizeof(int), cudaHostAllocDefault));
+    s->head_q.resize(GW_STREAM_MAX_PENDING);
+    s->stage_in_q[0] = s->stage_in;
+    s->stage_out_q[0] = s->stage_out;
+    s->stage_in_q[1] = salloc<float>(s, (size_t)d->n_det * (C + 1) * nb * S);
+    s->stage_out_q[1] = salloc<float>(s, (size_t)d->n_det * nb * S);
+    s->reject_q = salloc<int>(s, GW_STREAM_MAX_PENDING);
+    GW_CUDA(cudaStreamCreateWithFlags(&s->cs_in, cudaStreamNonBlocking));
+    GW_CUDA(cudaStreamCreateWithFlags(&s->cs_out, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      GW_CUDA(cudaEventCreateWithFlags(&s->ev_in[b], cudaEventDisableTiming));
+      GW_CUDA(cudaEventCreateWithFlags(&s->ev_done[b], cudaEventDisableTiming));
+      GW_CUDA(cudaEventCreateWithFlags(&s->ev_out[b], cudaEventDisableTiming));
+    }
     GW_CUDA(cudaDeviceSynchronize());
   } catch (...) {
     stream_free(s);
@@ -1169,34 +1204,15 @@ int gw_stream_status(gw_stream_t s, void* cuda_stream) {
   GW_API_END
 }
 
-int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float* strain, float* clean_out, int mem,
-                   void* cuda_stream) {
-  GW_API_BEGIN
-  GW_CHECK_ARG(s && witness && strain && clean_out, "NULL argument");
+// Queues the device work of one push of n_snap snapshots on st: wit / str /
+// out are device buffers in the layouts of gw_stream_push; skip (device, may
+// be null) is the reject flag that the state-changing kernels obey, and
+// skip_copy (device, may be null) receives its value as this push left it.
+static void stream_compute(gw_stream* s, int n_snap, const float* wit, const float* str, float* out,
+                           const int* skip, int* skip_copy, cudaStream_t st) {
   GW_CHECK_ARG(n_snap >= 1 && n_snap <= s->d.max_batch, "n_snap out of range [1, max_batch]");
-  GW_CHECK_ARG(mem == GW_MEM_HOST || mem == GW_MEM_DEVICE, "mem must be GW_MEM_HOST or GW_MEM_DEVICE");
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   const int C = s->d.n_witness, S = s->d.stride, W = s->d.window, nd = s->d.n_det;
   const int64_t n = (int64_t)n_snap * S;
-  const float* wit = witness;
-  const float* str = strain;
-  float* out = clean_out;
-  // Host mode rejects a push with a non-finite sample before the state
-  // changes: the staged input is checked on the device, the state-changing
-  // kernels (ring, strain and aggregation updates) skip their writes when the
-  // check failed, and the verdict is read back with the results.
-  const int* skip = nullptr;
-  if (mem == GW_MEM_HOST) {
-    const size_t nw = (size_t)nd * C * n, ns = (size_t)nd * n;
-    GW_CUDA(cudaMemsetAsync(s->reject, 0, sizeof(int), st));
-    GW_CUDA(cudaMemcpyAsync(s->stage_in, witness, nw * 4, cudaMemcpyHostToDevice, st));
-    GW_CUDA(cudaMemcpyAsync(s->stage_in + nw, strain, ns * 4, cudaMemcpyHostToDevice, st));
-    launch_check_finite(s->stage_in, (int64_t)(nw + ns), s->reject, st);
-    skip = s->reject;
-    wit = s->stage_in;
-    str = s->stage_in + nw;
-    out = s->stage_out;
-  }
   const int64_t R = s->R, head = s->head;
   const int G = (C + 7) / 8;
   for (int d = 0; d < nd; ++d) {
@@ -1242,7 +1258,7 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
     {
       Prof p("sub_ola", st);
       launch_sub_ola(s->pred, W, n_snap, S, W, R, head, s->d.agg_mode, s->d.agg_delay, s->acc[d], s->strain[d],
-                     out + (size_t)d * n, st, skip, s->pring[d], s->Rp);
+                     out + (size_t)d * n, st, skip, s->pring[d], s->Rp, d == 0 ? skip_copy : nullptr);
     }
     if (s->post_K) {
       Prof p("post", st);
@@ -1250,13 +1266,103 @@ int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float*
                       head - s->d.agg_delay - (s->post_K - 1) / 2, (int)n, out + (size_t)d * n, st, skip);
     }
   }
-  if (mem == GW_MEM_HOST) {
-    GW_CUDA(cudaMemcpyAsync(clean_out, s->stage_out, (size_t)nd * n * 4, cudaMemcpyDeviceToHost, st));
+}
+
+
+int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float* strain, float* clean_out, int mem,
+                   void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(s && witness && strain && clean_out, "NULL argument");
+  GW_CHECK_ARG(mem == GW_MEM_HOST || mem == GW_MEM_DEVICE, "mem must be GW_MEM_HOST or GW_MEM_DEVICE");
+  if (s->pending) throw Error(GW_ESTATE, "asynchronous pushes are pending: call gw_stream_sync first");
+  GW_CHECK_ARG(n_snap >= 1 && n_snap <= s->d.max_batch, "n_snap out of range [1, max_batch]");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (mem == GW_MEM_DEVICE) {
+    stream_compute(s, n_snap, witness, strain, clean_out, nullptr, nullptr, st);
+  } else {
+    // Host mode rejects a push with a non-finite sample before the state
+    // changes: the staged input is checked on the device, the state-changing
+    // kernels (ring, strain and aggregation updates) skip their writes when
+    // the check failed, and the verdict is read back with the results.
+    const size_t n = (size_t)n_snap * s->d.stride, nd = s->d.n_det;
+    const size_t nw = nd * s->d.n_witness * n, ns = nd * n;
+    GW_CUDA(cudaMemsetAsync(s->reject, 0, sizeof(int), st));
+    GW_CUDA(cudaMemcpyAsync(s->stage_in, witness, nw * 4, cudaMemcpyHostToDevice, st));
+    GW_CUDA(cudaMemcpyAsync(s->stage_in + nw, strain, ns * 4, cudaMemcpyHostToDevice, st));
+    launch_check_finite(s->stage_in, (int64_t)(nw + ns), s->reject, st);
+    stream_compute(s, n_snap, s->stage_in, s->stage_in + nw, s->stage_out, s->reject, nullptr, st);
+    GW_CUDA(cudaMemcpyAsync(clean_out, s->stage_out, ns * 4, cudaMemcpyDeviceToHost, st));
     GW_CUDA(cudaMemcpyAsync(s->reject_h, s->reject, sizeof(int), cudaMemcpyDeviceToHost, st));
     GW_CUDA(cudaStreamSynchronize(st));
     if (*s->reject_h) throw Error(GW_ENONFINITE, "non-finite input sample");
   }
-  s->head += n;
+  s->head += (int64_t)n_snap * s->d.stride;
+  GW_API_END
+}
+
+int gw_stream_push_async(gw_stream_t s, int n_snap, const float* witness, const float* strain, float* clean_out,
+                         void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(s && witness && strain && clean_out, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (s->pending) {
+    GW_CHECK_ARG(st == s->async_st, "pending asynchronous pushes were queued on another CUDA stream");
+    if (s->pending >= GW_STREAM_MAX_PENDING)
+      throw Error(GW_ESTATE, "GW_STREAM_MAX_PENDING pushes pending: call gw_stream_sync first");
+  }
+  GW_CHECK_ARG(n_snap >= 1 && n_snap <= s->d.max_batch, "n_snap out of range [1, max_batch]");
+  const int k = s->pending, b = k & 1;
+  const size_t n = (size_t)n_snap * s->d.stride, nd = s->d.n_det;
+  const size_t nw = nd * s->d.n_witness * n, ns = nd * n;
+  float* in = s->stage_in_q[b];
+  float* out = s->stage_out_q[b];
+  // inputs: once the compute of the push before last (same set) is done
+  GW_CUDA(cudaStreamWaitEvent(s->cs_in, s->ev_done[b], 0));
+  GW_CUDA(cudaMemcpyAsync(in, witness, nw * 4, cudaMemcpyHostToDevice, s->cs_in));
+  GW_CUDA(cudaMemcpyAsync(in + nw, strain, ns * 4, cudaMemcpyHostToDevice, s->cs_in));
+  GW_CUDA(cudaEventRecord(s->ev_in[b], s->cs_in));
+  // compute: once the inputs are staged and the outputs of the push before
+  // last (same set) are copied out.  The device flag is cleared once per
+  // sequence of queued pushes: a rejected push leaves it set, so every later
+  // push of the sequence skips its state updates as well and the state stays
+  // that before the rejected push.
+  GW_CUDA(cudaStreamWaitEvent(st, s->ev_in[b], 0));
+  GW_CUDA(cudaStreamWaitEvent(st, s->ev_out[b], 0));
+  if (k == 0) GW_CUDA(cudaMemsetAsync(s->reject, 0, sizeof(int), st));
+  launch_check_finite(in, (int64_t)(nw + ns), s->reject, st);
+  stream_compute(s, n_snap, in, in + nw, out, s->reject, s->reject_q + k, st);
+  GW_CUDA(cudaEventRecord(s->ev_done[b], st));
+  // outputs and this push's verdict
+  GW_CUDA(cudaStreamWaitEvent(s->cs_out, s->ev_done[b], 0));
+  GW_CUDA(cudaMemcpyAsync(clean_out, out, ns * 4, cudaMemcpyDeviceToHost, s->cs_out));
+  GW_CUDA(cudaMemcpyAsync(s->reject_h + 1 + k, s->reject_q + k, sizeof(int), cudaMemcpyDeviceToHost, s->cs_out));
+  GW_CUDA(cudaEventRecord(s->ev_out[b], s->cs_out));
+  s->async_st = st;
+  s->head_q[s->pending++] = s->head;
+  s->head += (int64_t)n_snap * s->d.stride;
+  GW_API_END
+}
+
+int gw_stream_sync(gw_stream_t s, int* first_rejected) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(s, "stream is NULL");
+  if (first_rejected) *first_rejected = -1;
+  if (!s->pending) return GW_OK;
+  const int n = s->pending;
+  s->pending = 0;
+  GW_CUDA(cudaStreamSynchronize(s->cs_out));
+  GW_CUDA(cudaStreamSynchronize(s->async_st));
+  for (int k = 0; k < n; ++k) {
+    if (s->reject_h[1 + k]) {
+      // push k and every later one skipped their state updates: rewind
+      s->head = s->head_q[k];
+      if (first_rejected) *first_rejected = k;
+      GW_CUDA(cudaMemsetAsync(s->reject, 0, sizeof(int), s->async_st));
+      GW_CUDA(cudaStreamSynchronize(s->async_st));
+      throw Error(GW_ENONFINITE, "non-finite input sample in queued push " + std::to_string(k) +
+                                     "; it and the later queued pushes were not applied");
+    }
+  }
   GW_API_END
 }
 

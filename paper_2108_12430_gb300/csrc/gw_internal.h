@@ -211,10 +211,11 @@ void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t
                         int* status, cudaStream_t st, const int* skip = nullptr);
 // pring (optional): instead of subtracting, store the aggregated prediction of
 // every emitted time t >= 0 at pring[t mod Rp] (post-processing follows).
+// skip_copy (optional): receives *skip (0 without skip) before anything else.
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R,
                     int64_t head, int mode, int delta, float* acc, const float* strain_ring,
                     float* out, cudaStream_t st, const int* skip = nullptr, float* pring = nullptr,
-                    int64_t Rp = 0);
+                    int64_t Rp = 0, int* skip_copy = nullptr);
 // out[i] = strain[t] - sum_k h[k] p[t + k - c] for t = t0 + i, i < count,
 // c = (K - 1) / 2, p read from the ring pring (0 before time 0), strain from
 // its ring (0 before time 0).

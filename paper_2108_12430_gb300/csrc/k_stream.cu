@@ -105,7 +105,8 @@ __global__ void strain_push_kernel(const float* __restrict__ src, int n, float* 
 __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, int n, int S, int W,
                                int64_t R, int64_t head, int mode, int delta, float* __restrict__ acc,
                                const float* __restrict__ strain_ring, float* __restrict__ out, const int* skip,
-                               float* __restrict__ pring, int64_t Rp) {
+                               float* __restrict__ pring, int64_t Rp, int* skip_copy) {
+  if (skip_copy && blockIdx.x == 0 && threadIdx.x == 0) *skip_copy = skip ? *skip : 0;
   if (skip && *skip) return;
   const int64_t lo = head + S - W;
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
@@ -297,11 +298,11 @@ void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t
 
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R, int64_t head, int mode,
                     int delta, float* acc, const float* strain_ring, float* out, cudaStream_t st,
-                    const int* skip, float* pring, int64_t Rp) {
+                    const int* skip, float* pring, int64_t Rp, int* skip_copy) {
   GW_CHECK_ARG(!pring || Rp >= (int64_t)n * S, "prediction ring too small");
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
   sub_ola_kernel<<<grid_for(count), kThreads, 0, st>>>(pred, pred_ld, n, S, W, R, head, mode, delta, acc,
-                                                        strain_ring, out, skip, pring, Rp);
+                                                        strain_ring, out, skip, pring, Rp, skip_copy);
   GW_LAUNCH_CHECK();
 }
 

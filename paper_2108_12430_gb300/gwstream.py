@@ -36,7 +36,8 @@ EXPORTS = (
     "gw_last_error", "gw_version", "gw_ctx_create", "gw_ctx_destroy", "gw_ctx_bytes_in_use",
     "gw_model_param_count", "gw_model_create", "gw_model_destroy", "gw_deepclean_forward", "gw_bbhnet_score",
     "gw_fir_create_whitening", "gw_fir_destroy", "gw_fir_ntaps", "gw_fir_taps", "gw_whiten",
-    "gw_stream_create", "gw_stream_destroy", "gw_stream_push", "gw_stream_head", "gw_stream_status",
+    "gw_stream_create", "gw_stream_destroy", "gw_stream_push", "gw_stream_push_async", "gw_stream_sync",
+    "gw_stream_head", "gw_stream_status",
     "gw_profile_enable", "gw_profile_read", "gw_launch_count", "gw_deepclean_forward_noalloc",
     "gw_model_status", "gw_tc_inspect", "gw_fir_create_lowpass",
     "gw_server_create", "gw_server_open", "gw_server_close", "gw_server_stream_bytes", "gw_server_submit",
@@ -108,6 +109,8 @@ def _declare(lib):
         "gw_stream_create": (I, [P, C.POINTER(gw_stream_desc), C.POINTER(P), C.POINTER(P)]),
         "gw_stream_destroy": (I, [P]),
         "gw_stream_push": (I, [P, I, P, P, P, I, P]),
+        "gw_stream_push_async": (I, [P, I, P, P, P, P]),
+        "gw_stream_sync": (I, [P, C.POINTER(I)]),
         "gw_stream_head": (I64, [P]),
         "gw_stream_status": (I, [P, P]),
         "gw_profile_enable": (I, [I]),
@@ -303,6 +306,33 @@ def gw_stream_push(s, n_snap, witness, strain, clean_out, mem=GW_MEM_HOST, strea
     else:
         args = (witness, strain, clean_out)
     _check(lib().gw_stream_push(s, n_snap, args[0], args[1], args[2], mem, stream or None))
+
+
+GW_STREAM_MAX_PENDING = 1024
+
+
+def gw_stream_push_async(s, n_snap, witness, strain, clean_out, stream=0):
+    """Queues a host-buffer push; the buffers are host addresses (ints) of
+    page-locked memory, or C-contiguous float32 numpy arrays (kept alive and
+    unmodified by the caller until gw_stream_sync)."""
+    ptrs = []
+    for a in (witness, strain, clean_out):
+        if isinstance(a, np.ndarray):
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+            a = a.ctypes.data
+        ptrs.append(a)
+    _check(lib().gw_stream_push_async(s, n_snap, ptrs[0], ptrs[1], ptrs[2], stream or None))
+
+
+def gw_stream_sync(s):
+    """Waits for the queued pushes.  A push with a non-finite sample raises
+    GwError(GW_ENONFINITE) whose first_rejected is its index among them."""
+    k = I(-1)
+    rc = lib().gw_stream_sync(s, C.byref(k))
+    if rc < 0:
+        e = GwError(rc, lib().gw_last_error().decode())
+        e.first_rejected = k.value
+        raise e
 
 
 def gw_stream_head(s):
