@@ -532,7 +532,10 @@ def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
     try:
         # config 1
         x1 = synth.witness_channels(0, C, 4096)
+        t0 = time.perf_counter()
         ref1 = cpu_leg_deepclean(x1[None].astype(np.float32).astype(np.float64), synth.deepclean_params(0))[0]
+        out["config1_oracle"] = {"kind": "oracle", "us_per_forward": (time.perf_counter() - t0) * 1e6,
+                                 "cores": cpu_threads(), "sample": "the one window whose output the error fields use"}
         x1d = torch.from_numpy(x1.astype(np.float32)).cuda()
         y1 = torch.zeros(1, 4096, device="cuda")
         for name, prec in (("bf16", G.GW_BF16), ("fp32", G.GW_FP32)):
@@ -553,8 +556,13 @@ def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
         logit = torch.zeros(Bc, device="cuda")
         idx = [0, 77, 255]
         layers, head = synth.bbhnet_params(3)
+        t0 = time.perf_counter()
         xw_ref, ref3 = cpu_leg_whiten_bbhnet(xr[idx].astype(np.float32).astype(np.float64), psd, fs, nfft, layers,
                                              head)
+        out["config3_oracle"] = {"kind": "oracle", "windows_per_s": len(idx) / (time.perf_counter() - t0),
+                                 "cores": cpu_threads(),
+                                 "sample": f"{len(idx)} windows (whitening design + FIR + BBHnet) whose outputs the "
+                                           "error fields use"}
         for name, prec in (("bf16", G.GW_BF16), ("fp8", G.GW_FP8), ("fp32", G.GW_FP32)):
             fh = G.gw_fir_create_whitening(ctx, psd, fs, 2049, G.GW_BF16 if prec == G.GW_FP8 else prec)
             mb = G.gw_model_create(ctx, G.GW_MODEL_BBHNET, prec, 2, synth.flatten_params(layers, head))

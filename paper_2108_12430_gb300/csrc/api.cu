@@ -404,6 +404,18 @@ void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, vo
   }
 }
 
+// Profile scope names of BBHnet's 13 conv launches in launch order: the stem,
+// then per block its first conv, its shortcut and its second conv.
+static const char* kBbhNames[2][13] = {
+    {"conv_tc.bbhnet.stem", "conv_tc.bbhnet.b1c1", "conv_tc.bbhnet.b1sc", "conv_tc.bbhnet.b1c2",
+     "conv_tc.bbhnet.b2c1", "conv_tc.bbhnet.b2sc", "conv_tc.bbhnet.b2c2", "conv_tc.bbhnet.b3c1",
+     "conv_tc.bbhnet.b3sc", "conv_tc.bbhnet.b3c2", "conv_tc.bbhnet.b4c1", "conv_tc.bbhnet.b4sc",
+     "conv_tc.bbhnet.b4c2"},
+    {"conv_tc.bbhnet_fp8.stem", "conv_tc.bbhnet_fp8.b1c1", "conv_tc.bbhnet_fp8.b1sc", "conv_tc.bbhnet_fp8.b1c2",
+     "conv_tc.bbhnet_fp8.b2c1", "conv_tc.bbhnet_fp8.b2sc", "conv_tc.bbhnet_fp8.b2c2", "conv_tc.bbhnet_fp8.b3c1",
+     "conv_tc.bbhnet_fp8.b3sc", "conv_tc.bbhnet_fp8.b3c2", "conv_tc.bbhnet_fp8.b4c1", "conv_tc.bbhnet_fp8.b4sc",
+     "conv_tc.bbhnet_fp8.b4c2"}};
+
 // BBHnet on B items of [2][L] FP32 through the tensor-core kernels.
 void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st) {
   const auto& Ls = m->layers;
@@ -419,7 +431,7 @@ void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* w
   int l = Ls[0].s.lout(L);
   TcOut h = blocked_out(buf[0], Ls[0].s.cout, l, Ls[1].pin);
   {
-    Prof p("conv_tc.bbhnet", st);
+    Prof p(kBbhNames[0][0], st);
     launch_conv_tc(Ls[0], as_input(xin, L), l, h, B, m->err, st);
   }
   int hi = 0;
@@ -435,11 +447,11 @@ void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* w
     TcOut a = blocked_out(buf[a_i], c1.s.cout, l2, c2.pin);
     TcOut o = blocked_out(buf[o_i], c2.s.cout, l2, next_P);
     {
-      Prof p("conv_tc.bbhnet", st);
+      Prof p(kBbhNames[0][1 + 3 * blk], st);
       launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
     }
     {
-      Prof p("conv_tc.bbhnet", st);
+      Prof p(kBbhNames[0][2 + 3 * blk], st);
       launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
     }
     TcOut o2 = o;
@@ -449,7 +461,7 @@ void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* w
     o2.rpstride = o.pstride;
     o2.rP = o.P;
     {
-      Prof p("conv_tc.bbhnet", st);
+      Prof p(kBbhNames[0][3 + 3 * blk], st);
       launch_conv_tc(c2, as_input(a, l2), l2, o2, B, m->err, st);
     }
     h = o;
@@ -484,7 +496,7 @@ void bbhnet_fp8(gw_model* m, const float* x, int B, int L, float* logits, char* 
   int l = Ls[0].s.lout(L);
   TcOut h = blocked_out(buf[0], Ls[0].s.cout, l, Ls[1].pin, true);
   {
-    Prof p("conv_tc.bbhnet_fp8", st);
+    Prof p(kBbhNames[1][0], st);
     launch_conv_tc(Ls[0], as_input(xin, L), l, h, B, m->err, st);
   }
   int hi = 0;
@@ -500,11 +512,11 @@ void bbhnet_fp8(gw_model* m, const float* x, int B, int L, float* logits, char* 
     TcOut a = blocked_out(buf[a_i], c1.s.cout, l2, c2.pin, true);
     TcOut o = blocked_out(buf[o_i], c2.s.cout, l2, next_P, true);
     {
-      Prof p("conv_tc.bbhnet_fp8", st);
+      Prof p(kBbhNames[1][1 + 3 * blk], st);
       launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
     }
     {
-      Prof p("conv_tc.bbhnet_fp8", st);
+      Prof p(kBbhNames[1][2 + 3 * blk], st);
       launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
     }
     TcOut o2 = o;
@@ -514,7 +526,7 @@ void bbhnet_fp8(gw_model* m, const float* x, int B, int L, float* logits, char* 
     o2.rpstride = o.pstride;
     o2.rP = o.P;
     {
-      Prof p("conv_tc.bbhnet_fp8", st);
+      Prof p(kBbhNames[1][3 + 3 * blk], st);
       launch_conv_tc(c2, as_input(a, l2), l2, o2, B, m->err, st);
     }
     h = o;
