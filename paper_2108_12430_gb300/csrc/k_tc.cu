@@ -56,6 +56,7 @@ constexpr int kProdWarps = 2;
 // register file permitting: 65536 / (kThreads * 96 registers))
 constexpr int kMaxCtasPerSm = 2;
 constexpr int kMaxA = 6;  // deepest input ring
+constexpr int kMaxW = 8;  // deepest ring of streamed weight stages
 constexpr int kThreads = 32 * (kProdWarps + 1 + kEpiWarps);
 constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
@@ -1035,17 +1036,24 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   // input stages: as many as fit (up to kMaxA), keeping two CTAs per SM where
   // the two-stage plan allowed it; more tiles in flight hide the input latency
   {
-    const size_t wsm0 = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
-    auto smem_for = [&](int na) {
-      return 128 + (size_t)na * q.a_bytes + (wsm0 + 127) / 128 * 128 + 8 * (size_t)(2 * na + 6 + 2 * q.nst) +
+    auto smem_for = [&](int na, int nst) {
+      const size_t wsm0 = q.resident ? wbytes : (size_t)nst * q.sps * q.step_bytes;
+      return 128 + (size_t)na * q.a_bytes + (wsm0 + 127) / 128 * 128 + 8 * (size_t)(2 * na + 6 + 2 * nst) +
              16 * (size_t)L.n_steps + 12 * planes + 32 + 8 * (size_t)L.npad + 16;
     };
     // shared memory per SM is 228 KB, of which 1 KB per CTA is reserved
     int per = kMaxCtasPerSm;
-    while (per > 1 && (smem_for(2) > (size_t)(228 / per - 1) * 1024 || ncols * per > 512)) --per;
+    while (per > 1 && (smem_for(2, q.nst) > (size_t)(228 / per - 1) * 1024 || ncols * per > 512)) --per;
     const size_t cap = (size_t)(228 / per - 1) * 1024;
+    // streamed weights first get a deeper ring (every tile streams the whole
+    // weight image, several times the bytes of its input tile), then the
+    // input ring takes what is left
+    if (!q.resident) {
+      const int chunks = (L.n_steps + q.sps - 1) / q.sps;
+      while (q.nst < kMaxW && q.nst < chunks && smem_for(2, q.nst + 1) <= cap) ++q.nst;
+    }
     int na = 2;
-    while (na < kMaxA && smem_for(na + 1) <= cap) ++na;
+    while (na < kMaxA && smem_for(na + 1, q.nst) <= cap) ++na;
     q.na = na;
     q.per_sm = per;
   }
