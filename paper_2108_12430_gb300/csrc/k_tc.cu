@@ -77,6 +77,9 @@ struct TcParams {
   // output-channel split: a tile is (M tile, column slice); each slice has
   // ncol = npad / nsplit columns (used when a layer has fewer tiles than SMs)
   int nsplit, ncol;
+  // streamed weight stages: bytes per K-step in a stage (step_bytes, or with
+  // wcompact = 1 only the slice's rows, packed [K-half][ncol rows] per step)
+  int wstep, wcompact;
   uint32_t idesc;
   int fp8;
   const float* bias;
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
   const int na = p.na;                 // input stages (the A ring)
   const uint32_t sA = smem_u32(smem);  // na stages of a_bytes
   const uint32_t sW = sA + (uint32_t)na * (uint32_t)p.a_bytes;
-  const uint32_t stage_bytes = (uint32_t)(p.sps * p.step_bytes);
+  const uint32_t stage_bytes = (uint32_t)(p.sps * p.wstep);
   const uint32_t w_bytes = p.resident ? (uint32_t)(p.n_steps * p.step_bytes) : (uint32_t)p.nst * stage_bytes;
   const int planes = p.G * p.in_P;
   uint64_t* bars = (uint64_t*)(smem + (size_t)na * p.a_bytes + ((w_bytes + 127u) & ~127u));
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
     const uint32_t o0 = slice_off(p.table[2 * i], p.in_P, p.rows), o1 = slice_off(p.table[2 * i + 1], p.in_P, p.rows);
     s_desc[2 * i] = make_desc(sA + o0, o1 - o0, 128u);
     const uint32_t pos = p.resident ? (uint32_t)i : (uint32_t)i % stage_b;
-    s_desc[2 * i + 1] = make_desc(sW + pos * (uint32_t)p.step_bytes, (uint32_t)p.npad * 16u, 128u);
+    s_desc[2 * i + 1] = make_desc(sW + pos * (uint32_t)p.wstep, (uint32_t)p.npad * 16u, 128u);
   }
   for (int i = tid; i < planes; i += kThreads) {
     const int g = i / p.in_P, phi = i % p.in_P;
@@ -401,13 +404,14 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
               bulk_g2s(sW + (uint32_t)st * stage_bytes, p.wimg + (int64_t)s0 * p.step_bytes, bytes, bar(w_full + st));
             } else {
               // only this slice's rows of both K-halves of every step, each
-              // at its place in the full step layout
+              // at its place in the full step layout, or packed (wcompact)
               const uint32_t rows_bytes = (uint32_t)p.ncol * 16u, half = (uint32_t)p.npad * 16u;
               const uint32_t off = (uint32_t)sl * rows_bytes;
+              const uint32_t dhalf = p.wcompact ? rows_bytes : half, doff = p.wcompact ? 0u : off;
               mbar_expect_tx(bar(w_full + st), (uint32_t)(2 * (s1 - s0)) * rows_bytes);
               for (int sx = s0; sx < s1; ++sx)
                 for (uint32_t hh = 0; hh < 2; ++hh) {
-                  const uint32_t o = (uint32_t)(sx - s0) * (uint32_t)p.step_bytes + hh * half + off;
+                  const uint32_t o = (uint32_t)(sx - s0) * (uint32_t)p.wstep + hh * dhalf + doff;
                   bulk_g2s(sW + (uint32_t)st * stage_bytes + o,
                            p.wimg + (int64_t)sx * p.step_bytes + hh * half + off, rows_bytes, bar(w_full + st));
                 }
@@ -436,8 +440,9 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
         // descriptor start addresses count 16-byte units in their low bits
         const uint64_t a_stage = (uint64_t)(((uint32_t)sa * (uint32_t)p.a_bytes) >> 4);
         const uint32_t d0 = tmem + (uint32_t)(s * MT * npad);
-        // the slice's B rows start sl * ncol rows into each K-half
-        const uint64_t b_slice = (uint64_t)(sl * p.ncol);
+        // the slice's B rows start sl * ncol rows into each K-half (at the
+        // stage's start when the slice is packed)
+        const uint64_t b_slice = p.wcompact ? 0ull : (uint64_t)(sl * p.ncol);
         for (int c = 0; c < n_chunks; ++c) {
           uint64_t b_stage = b_slice;
           int st = 0;
@@ -461,8 +466,9 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
             // step, B at a fixed stride from the stage's first step
             const uint64_t hi = ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
             const uint32_t a_base = (sA >> 4) + (uint32_t)a_stage;
-            const uint64_t b_hi = hi | ((uint64_t)(((uint32_t)p.npad * 16u) >> 4) << 16);
-            const uint32_t b_base = (sW >> 4) + (uint32_t)b_stage, b_step = (uint32_t)p.step_bytes >> 4;
+            const uint32_t b_rows = p.wcompact ? (uint32_t)p.ncol : (uint32_t)p.npad;  // K-half distance
+            const uint64_t b_hi = hi | ((uint64_t)((b_rows * 16u) >> 4) << 16);
+            const uint32_t b_base = (sW >> 4) + (uint32_t)b_stage, b_step = (uint32_t)p.wstep >> 4;
             if (fp8) {
               for (int sidx = s0; sidx < s1; ++sidx) {
                 const uint32_t e = p.apack[sidx];
@@ -1029,6 +1035,17 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
       q.nsplit *= 2;
   }
   q.ncol = L.npad / q.nsplit;
+  // streamed weights of a split layer: stages hold only the slice's rows,
+  // packed, so that a 16 KB stage carries nsplit times as many K-steps (the
+  // packed layout is addressed by the parameter-table MMA path only)
+  q.wstep = q.step_bytes;
+  q.wcompact = 0;
+  if (q.nsplit > 1 && !q.resident && MT == 1 && L.n_steps <= kParamSteps && (int)L.table_h.size() >= 2 * L.n_steps) {
+    q.wcompact = 1;
+    q.wstep = q.step_bytes / q.nsplit;
+    q.sps = std::min(L.n_steps, std::max(1, 16384 / q.wstep));
+    q.nst = 1;
+  }
   int ncols = 32;
   while (ncols < 2 * MT * q.ncol) ncols *= 2;
   GW_CHECK_ARG(ncols <= 512, "accumulators exceed tensor memory");
@@ -1037,7 +1054,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   // the two-stage plan allowed it; more tiles in flight hide the input latency
   {
     auto smem_for = [&](int na, int nst) {
-      const size_t wsm0 = q.resident ? wbytes : (size_t)nst * q.sps * q.step_bytes;
+      const size_t wsm0 = q.resident ? wbytes : (size_t)nst * q.sps * q.wstep;
       return 128 + (size_t)na * q.a_bytes + (wsm0 + 127) / 128 * 128 + 8 * (size_t)(2 * na + 6 + 2 * nst) +
              16 * (size_t)L.n_steps + 12 * planes + 32 + 8 * (size_t)L.npad + 16;
     };
@@ -1105,9 +1122,10 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
       q.apack[i] = (o0 >> 4) | (((o1 - o0) >> 4) << 16);
     }
   }
+  GW_CHECK_ARG(!q.wcompact || (q.param_desc && q.MT == 1), "packed weight stages need the parameter-table MMA path");
   q.wimg = (const char*)L.wq;
   q.table = L.table;
-  const size_t wsm = q.resident ? wbytes : (size_t)q.nst * q.sps * q.step_bytes;
+  const size_t wsm = q.resident ? wbytes : (size_t)q.nst * q.sps * q.wstep;
   const size_t smem = 128 + (size_t)q.na * q.a_bytes + (wsm + 127) / 128 * 128 + 8 * (size_t)(2 * q.na + 6 + 2 * q.nst) +
                       16 * (size_t)L.n_steps + 12 * planes + 32 + 8 * (size_t)L.npad + 16;
   GW_CHECK_ARG(smem <= 227 * 1024, "shared memory plan too large");
@@ -1186,6 +1204,7 @@ extern "C" int gw_tc_inspect(const int* spec, int precision, const double* wfold
     std::vector<float> wscale;
     const bool fp8 = precision == GW_FP8;
     lower_layer(L, wf, fp8, img, table, wscale);
+    L.table_h = table;  // as on the device path: the plan may use the parameter-table MMA path
     GW_CHECK_ARG(img.size() <= img_cap && (int)table.size() <= table_cap, "output buffers too small");
     memcpy(img_out, img.data(), img.size());
     memcpy(table_out, table.data(), table.size() * 4);
