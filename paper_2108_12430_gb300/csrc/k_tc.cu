@@ -57,6 +57,11 @@ constexpr int kProdWarps = 2;
 constexpr int kMaxCtasPerSm = 2;
 constexpr int kMaxA = 6;  // deepest input ring
 constexpr int kMaxW = 8;  // deepest ring of streamed weight stages
+constexpr int kWProd = 2;  // producer warps filling a streamed weight ring
+// Bytes of a streamed weight stage: every stage costs the MMA thread a commit
+// and the producer a wait, so large layers get few large stages; the packed
+// stages of split layers (small batches) stay small, their tiles are few.
+constexpr int kWStage = 65536, kWStagePacked = 16384;
 constexpr int kThreads = 32 * (kProdWarps + 1 + kEpiWarps);
 constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
@@ -78,8 +83,9 @@ struct TcParams {
   // ncol = npad / nsplit columns (used when a layer has fewer tiles than SMs)
   int nsplit, ncol;
   // streamed weight stages: bytes per K-step in a stage (step_bytes, or with
-  // wcompact = 1 only the slice's rows, packed [K-half][ncol rows] per step)
-  int wstep, wcompact;
+  // wcompact = 1 only the slice's rows, packed [K-half][ncol rows] per step),
+  // and the producer warps that fill them (1, or 2 with an even nst)
+  int wstep, wcompact, wprod;
   uint32_t idesc;
   int fp8;
   const float* bias;
@@ -341,13 +347,17 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
 
   if (warp == 0 || warp >= 2 + kEpiWarps) {
     // ---------------- producers: input tiles (and weights) by bulk TMA ----------------
-    const int pw = warp == 0 ? 0 : warp - 1 - kEpiWarps;  // producer index; tiles i with i % nprod == pw
-    // With streamed weights one producer fills both rings: a weight stage
-    // written by two producers taking alternate tiles could be re-armed two
-    // phases ahead of its consumer, which a parity wait cannot tell apart.
-    // (The input ring is safe with two: each producer issues its tiles in
-    // order, and its previous wait implies every older use of the stage was
-    // consumed, so no producer gets more than one phase ahead.)
+    const int pw = warp == 0 ? 0 : warp - 1 - kEpiWarps;  // producer index
+    // Resident weights: the producers take alternate tiles' inputs.  The input
+    // ring is safe with two: each producer issues its tiles in order, and its
+    // previous wait implies every older use of the stage was consumed, so no
+    // producer gets more than one phase ahead.  Streamed weights: producer 0
+    // loads every input tile, and the weight chunks alternate between the
+    // p.wprod producers by chunk parity.  With an even number of stages every
+    // weight stage then belongs to one producer, which re-arms it only after
+    // its own wait for the previous use; taking alternate tiles instead, two
+    // producers could re-arm a stage two phases ahead of its consumer, which a
+    // parity wait cannot tell apart.
     const int nprod = p.resident ? kProdWarps : 1;
     if (p.resident && lane == 0 && pw == 0) {
       mbar_expect_tx(bar(w_full), (uint32_t)(p.n_steps * p.step_bytes));
@@ -357,44 +367,48 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
     int i = 0;
     int s = 0, k = 0;  // ring stage and its use count, advanced without divisions
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i, k += (++s == na), s = s == na ? 0 : s) {
-      if (i % nprod != pw) continue;
+      const bool do_a = i % nprod == pw, do_w = !p.resident && pw < p.wprod;
+      if (!do_a && !do_w) continue;
       if (p.stall_test && blockIdx.x == 0 && i == 0) continue;  // no arrival and no copy: nothing in flight
-      if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
       int b, m0, sl;
       tile_coords(p, t, b, m0, sl);
-      const int base = m0 + p.dmin;
-      const uint32_t sAs = sA + (uint32_t)s * (uint32_t)p.a_bytes;
-      const char* src0 = p.item_ptr
-                             ? p.item_ptr[b] + (int64_t)base * 16
-                             : p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)base + (int64_t)b * p.in_boff) * 16;
-      if (base >= 0 && base + p.rows <= p.min_plen) {
-        // interior tile: every plane is one full run of rows
-        if (lane == 0) mbar_expect_tx(bar(a_full + s), (uint32_t)(planes * p.rows) * 16u);
-        __syncwarp();
-        for (int plane = lane; plane < planes; plane += 32)
-          bulk_g2s(sAs + (uint32_t)(plane * p.rows) * 16u, src0 + s_poff[plane], (uint32_t)p.rows * 16u,
-                   bar(a_full + s));
-      } else {
-        // edge tile: rows outside a plane are the layer's zero padding; they
-        // are copied from a zero buffer by the same bulk engine, so every row
-        // of the stage arrives through the async proxy (no fence, no serial
-        // zero stores) and the stage expects the same bytes as an interior one
-        if (lane == 0) mbar_expect_tx(bar(a_full + s), (uint32_t)(planes * p.rows) * 16u);
-        __syncwarp();
-        for (int plane = lane; plane < planes; plane += 32) {
-          const int r0 = min(p.rows, max(0, -base)), r1 = max(r0, min(p.rows, s_plen[plane] - base));
-          const uint32_t dst = sAs + (uint32_t)(plane * p.rows) * 16u;
-          if (r0 > 0) bulk_g2s(dst, g_zero_rows, (uint32_t)r0 * 16u, bar(a_full + s));
-          if (r1 > r0)
-            bulk_g2s(dst + (uint32_t)r0 * 16u, src0 + s_poff[plane] + (int64_t)r0 * 16, (uint32_t)(r1 - r0) * 16u,
+      if (do_a) {
+        if (k >= 1 && !mbar_wait(bar(a_empty + s), (uint32_t)(k - 1) & 1u, abort_flag, p.err, kErrWaitEmpty)) break;
+        const int base = m0 + p.dmin;
+        const uint32_t sAs = sA + (uint32_t)s * (uint32_t)p.a_bytes;
+        const char* src0 = p.item_ptr
+                               ? p.item_ptr[b] + (int64_t)base * 16
+                               : p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)base + (int64_t)b * p.in_boff) * 16;
+        if (base >= 0 && base + p.rows <= p.min_plen) {
+          // interior tile: every plane is one full run of rows
+          if (lane == 0) mbar_expect_tx(bar(a_full + s), (uint32_t)(planes * p.rows) * 16u);
+          __syncwarp();
+          for (int plane = lane; plane < planes; plane += 32)
+            bulk_g2s(sAs + (uint32_t)(plane * p.rows) * 16u, src0 + s_poff[plane], (uint32_t)p.rows * 16u,
                      bar(a_full + s));
-          if (p.rows > r1) bulk_g2s(dst + (uint32_t)r1 * 16u, g_zero_rows, (uint32_t)(p.rows - r1) * 16u, bar(a_full + s));
+        } else {
+          // edge tile: rows outside a plane are the layer's zero padding; they
+          // are copied from a zero buffer by the same bulk engine, so every row
+          // of the stage arrives through the async proxy (no fence, no serial
+          // zero stores) and the stage expects the same bytes as an interior one
+          if (lane == 0) mbar_expect_tx(bar(a_full + s), (uint32_t)(planes * p.rows) * 16u);
+          __syncwarp();
+          for (int plane = lane; plane < planes; plane += 32) {
+            const int r0 = min(p.rows, max(0, -base)), r1 = max(r0, min(p.rows, s_plen[plane] - base));
+            const uint32_t dst = sAs + (uint32_t)(plane * p.rows) * 16u;
+            if (r0 > 0) bulk_g2s(dst, g_zero_rows, (uint32_t)r0 * 16u, bar(a_full + s));
+            if (r1 > r0)
+              bulk_g2s(dst + (uint32_t)r0 * 16u, src0 + s_poff[plane] + (int64_t)r0 * 16, (uint32_t)(r1 - r0) * 16u,
+                       bar(a_full + s));
+            if (p.rows > r1) bulk_g2s(dst + (uint32_t)r1 * 16u, g_zero_rows, (uint32_t)(p.rows - r1) * 16u, bar(a_full + s));
+          }
         }
       }
       if (lane == 0) {
-        if (!p.resident) {
+        if (do_w) {
           for (int c = 0; c < n_chunks; ++c) {
             const int gc = i * n_chunks + c, st = gc % p.nst, use = gc / p.nst;
+            if (gc % p.wprod != pw) continue;
             if (use >= 1 && !mbar_wait(bar(w_empty + st), (uint32_t)(use - 1) & 1u, abort_flag, p.err, kErrWaitEmpty))
               break;
             const int s0 = c * p.sps, s1 = min(p.n_steps, s0 + p.sps);
@@ -1009,7 +1023,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
       q.nst = 1;
       break;
     }
-    const int sps = std::max(1, (int)(16384 / q.step_bytes));
+    const int sps = std::max(1, (int)(kWStage / q.step_bytes));
     int nst = std::min(3, (L.n_steps + sps - 1) / sps);
     while (nst > 1 && a2 + (size_t)nst * sps * q.step_bytes + fixed > budget) --nst;
     if (a2 + (size_t)nst * sps * q.step_bytes + fixed <= budget) {
@@ -1043,7 +1057,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   if (q.nsplit > 1 && !q.resident && MT == 1 && L.n_steps <= kParamSteps && (int)L.table_h.size() >= 2 * L.n_steps) {
     q.wcompact = 1;
     q.wstep = q.step_bytes / q.nsplit;
-    q.sps = std::min(L.n_steps, std::max(1, 16384 / q.wstep));
+    q.sps = std::min(L.n_steps, std::max(1, kWStagePacked / q.wstep));
     q.nst = 1;
   }
   int ncols = 32;
@@ -1065,11 +1079,25 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
     // streamed weights first get a deeper ring (every tile streams the whole
     // weight image, several times the bytes of its input tile), then the
     // input ring takes what is left
+    q.wprod = 1;
+    int na_min = 2;
     if (!q.resident) {
       const int chunks = (L.n_steps + q.sps - 1) / q.sps;
       while (q.nst < kMaxW && q.nst < chunks && smem_for(2, q.nst + 1) <= cap) ++q.nst;
+      // a second weight stage before a second input stage: the weights are
+      // the larger stream, and the loads of one stage then overlap the MMAs
+      // of the other
+      if (q.nst < 2 && chunks >= 2 && smem_for(1, 2) <= cap) {
+        q.nst = 2;
+        na_min = 1;
+      }
+      // two weight producers need an even ring (each owns every other stage)
+      if (kWProd == 2 && q.nst >= 2) {
+        q.nst &= ~1;
+        q.wprod = 2;
+      }
     }
-    int na = 2;
+    int na = na_min;
     while (na < kMaxA && smem_for(na + 1, q.nst) <= cap) ++na;
     q.na = na;
     q.per_sm = per;
