@@ -57,6 +57,7 @@ constexpr int kProdWarps = 2;
 constexpr int kMaxCtasPerSm = 2;
 constexpr int kMaxA = 6;  // deepest input ring
 constexpr int kMaxW = 8;  // deepest ring of streamed weight stages
+constexpr int kTilesPerSm = 8;  // larger M tiles only while a layer keeps this many tiles per SM
 constexpr int kWProd = 2;  // producer warps filling a streamed weight ring
 // Bytes of a streamed weight stage: every stage costs the MMA thread a commit
 // and the producer a wait, so large layers get few large stages; the packed
@@ -1010,7 +1011,7 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   // prefer small tiles while there are fewer than 8 tiles per SM: the
   // persistent pipeline overlaps tiles, and more tiles balance the SMs
   while (MT > 1 && (2 * MT * L.npad > 512 || MT > tiles_needed ||
-                    (int64_t)((q.mout + 128 * MT - 1) / (128 * MT)) * B < 8LL * sms))
+                    (int64_t)((q.mout + 128 * MT - 1) / (128 * MT)) * B < (int64_t)kTilesPerSm * sms))
     MT /= 2;
   q.resident = 0;
   q.sps = 1;
