@@ -442,12 +442,14 @@ int gw_adam_step(float* params, const float* grads, float* m, float* v, int64_t 
  * `lin` = input length; in_P / out_P = phase planes of input (0 = the
  * layer's own) and output; `batch` = items the launch plan is made for.
  * Writes the packed B-operand image (per K-step: 2 K-halves x npad rows x 16
- * bytes), the 2-word-per-step table and 21 ints of meta: n_steps, npad,
+ * bytes), the 2-word-per-step table and 26 ints of meta: n_steps, npad,
  * groups, input phases, output positions per row (Q), tap span, min tap
  * shift, M sub-tiles per tile, rows per plane, A stage bytes, steps per
  * weight stage, weight stages, step bytes, TMEM columns, tiles per item,
  * valid rows, channels per position, instruction descriptor, dynamic shared
- * memory bytes, output length, output-column slices per tile. */
+ * memory bytes, output length, output-column slices per tile, bytes per
+ * K-step in a weight stage, packed slice stages (0/1), weight-stage producer
+ * warps, input stages, CTAs per SM. */
 int gw_tc_inspect(const int* spec, int precision, const double* wfold, int lin, int in_P, int out_P, int batch,
                   void* img_out, size_t img_cap, uint32_t* table_out, int table_cap, int* meta_out);
 int gw_profile_enable(int on);

@@ -1248,9 +1248,10 @@ extern "C" int gw_tc_inspect(const int* spec, int precision, const double* wfold
     size_t smem = 0;
     dim3 grid;
     plan_conv_tc(q, L, fp8, in, lout, out, nullptr, &smem, &grid, batch > 0 ? batch : 1, 152);
-    const int meta[21] = {L.n_steps, L.npad,   L.gin,   L.pin,        L.n_chains,   L.dspan, L.dmin,
+    const int meta[26] = {L.n_steps, L.npad,   L.gin,   L.pin,        L.n_chains,   L.dspan, L.dmin,
                           q.MT,      q.rows,   q.a_bytes, q.resident ? L.n_steps : q.sps, q.nst, q.step_bytes,
-                          q.ncols,   q.tiles_per_item, q.mout, L.coutp, (int)q.idesc, (int)smem, lout, q.nsplit};
+                          q.ncols,   q.tiles_per_item, q.mout, L.coutp, (int)q.idesc, (int)smem, lout, q.nsplit,
+                          q.wstep,   q.wcompact, q.wprod, q.na, q.per_sm};
     memcpy(meta_out, meta, sizeof(meta));
     return GW_OK;
   } catch (const gw::Error& e) {

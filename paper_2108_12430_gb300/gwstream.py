@@ -487,7 +487,8 @@ def gw_launch_count():
 
 
 TC_META = ("n_steps", "npad", "groups", "in_P", "Q", "dspan", "dmin", "MT", "rows", "a_bytes", "sps", "nst",
-           "step_bytes", "ncols", "tiles_per_item", "mout", "coutp", "idesc", "smem", "lout", "nsplit")
+           "step_bytes", "ncols", "tiles_per_item", "mout", "coutp", "idesc", "smem", "lout", "nsplit",
+           "wstep", "wcompact", "wprod", "na", "per_sm")
 
 
 def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P, batch=1):
@@ -497,7 +498,7 @@ def gw_tc_inspect(spec, precision, wfold, lin, in_P, out_P, batch=1):
     cap = 1 << 24
     img = np.zeros(cap, np.uint8)
     table = np.zeros(1 << 14, np.uint32)
-    meta = (C.c_int * 21)()
+    meta = (C.c_int * len(TC_META))()
     _check(lib().gw_tc_inspect(spec_a, precision, wf.ctypes.data_as(C.POINTER(C.c_double)), lin, in_P, out_P, batch,
                                img.ctypes.data, cap, table.ctypes.data_as(C.POINTER(C.c_uint32)), table.size, meta))
     md = dict(zip(TC_META, list(meta)))

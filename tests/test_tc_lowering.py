@@ -210,3 +210,58 @@ def test_tc_layer_plans_fold_positions():
     for sp in specs:
         _, _, md = G.gw_tc_inspect(sp, G.GW_BF16, np.zeros((sp[2], sp[1], sp[3])), 32768, 0, 1)
         assert md["npad"] >= 64 and md["Q"] * md["coutp"] == md["npad"], (sp, md)
+
+
+def _bbhnet_plans(precision, batch):
+    """Launch plans of BBHnet's 13 conv layers at `batch` items of 2048 samples."""
+    from paper_2108_12430_gb300 import synth
+    names = ["stem", "b1c1", "b1c2", "b1sc", "b2c1", "b2c2", "b2sc", "b3c1", "b3c2", "b3sc", "b4c1", "b4c2", "b4sc"]
+    lin, out = 2048, {}
+    for nm, l in zip(names, synth.bbhnet_layers()):
+        _, cin, cout, k, s, pl, pr, op, _, _ = l
+        li = lin_out if nm.endswith("c2") else (lin_blk if nm.endswith("sc") else lin)
+        _, _, md = G.gw_tc_inspect((0, cin, cout, k, s, pl, pr, op), precision, np.zeros((cout, cin, k)), li, 0, 1,
+                                   batch)
+        if nm.endswith("c1"):
+            lin_blk, lin_out = li, md["lout"]
+        if nm == "stem" or nm.endswith("sc"):
+            lin = md["lout"]
+        out[nm] = md
+    return out
+
+
+@pytest.mark.parametrize("precision", [G.GW_BF16, G.GW_FP8])
+@pytest.mark.parametrize("batch", [1, 2, 3, 16, 64, 100, 256, 1024])
+def test_tc_plans_fit_and_weight_rings_are_well_formed(precision, batch):
+    # every plan fits the SM (shared memory per CTA and per SM, TMEM columns);
+    # a streamed weight ring filled by two producers has an even number of
+    # stages (each producer owns every other stage), packed slice stages
+    # belong to split layers only, and a stage holds whole K-steps
+    for nm, md in _bbhnet_plans(precision, batch).items():
+        assert md["smem"] <= 227 * 1024 and md["per_sm"] * (md["smem"] + 1024) <= 228 * 1024, (nm, md)
+        assert md["ncols"] <= 512 and md["per_sm"] * md["ncols"] <= 512, (nm, md)
+        assert 1 <= md["na"] <= 6, (nm, md)
+        resident = md["sps"] == md["n_steps"] and md["nst"] == 1 and md["wprod"] == 1
+        if md["wprod"] == 2:
+            assert md["nst"] >= 2 and md["nst"] % 2 == 0, (nm, md)
+        if md["wcompact"]:
+            assert md["nsplit"] > 1 and md["MT"] == 1 and md["wstep"] * md["nsplit"] == md["step_bytes"], (nm, md)
+        else:
+            assert md["wstep"] == md["step_bytes"], (nm, md)
+        if not resident:
+            assert md["sps"] * md["wstep"] <= 64 * 1024, (nm, md)
+            assert md["na"] >= 2 or md["nst"] >= 2, (nm, md)  # loads overlap MMAs in one ring or the other
+
+
+def test_tc_plans_stream_the_deep_layers_in_large_stages():
+    # at batch 256 the 256-channel layers stream their weights in 64 KB stages
+    # (two, filled by two producers); at batch 1 they are split over 8 CTAs
+    # and each streams only its packed slice
+    big = _bbhnet_plans(G.GW_BF16, 256)
+    for nm in ("b4c1", "b4c2"):
+        md = big[nm]
+        assert md["nsplit"] == 1 and md["sps"] * md["wstep"] == 64 * 1024 and md["nst"] == 2 and md["wprod"] == 2
+    small = _bbhnet_plans(G.GW_BF16, 1)
+    for nm in ("b4c1", "b4c2"):
+        md = small[nm]
+        assert md["nsplit"] == 8 and md["wcompact"] == 1 and md["wstep"] == md["step_bytes"] // 8
