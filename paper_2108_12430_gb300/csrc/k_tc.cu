@@ -24,12 +24,14 @@
 // two slices of a step are LBO apart: the im2col matrix is never formed.
 // B holds the folded weights arranged per (sigma, o) column and slice.
 //
-// Kernel.  Persistent and warp-specialised: warp 0 stages input tiles by bulk
-// TMA into a 2-deep ring (zero rows for the padding at the edges), warp 1
-// issues the MMAs from one thread into a double-buffered TMEM accumulator,
-// warps 2-9 drain TMEM with tcgen05.ld, add bias (and a residual), apply the
-// activation and store the consumer's layout.  Weights stay resident in shared
-// memory when they fit, else stream per tile through a ring of stages.  The
+// Kernel.  Persistent and warp-specialised: warps 0 and 10 stage input tiles
+// by bulk TMA into a ring of up to 6 stages (alternate tiles; zero rows for the
+// padding at the edges), warp 1 issues the MMAs from one thread into a
+// double-buffered TMEM accumulator, warps 2-9 drain TMEM with tcgen05.ld, add
+// bias (and a residual), apply the activation and store the consumer's layout.
+// Weights stay resident in shared memory when they fit, else stream per tile
+// through a ring of stages (warp 0 then stages every input tile, and both
+// producers fill the weight ring, each owning alternate stages).  The
 // BatchNorm is folded into the weights on the host in FP64.  Every wait is
 // bounded (1 s): on timeout the kernel records an error flag and unwinds.
 #include <cuda_fp8.h>
@@ -59,9 +61,10 @@ constexpr int kMaxA = 6;  // deepest input ring
 constexpr int kMaxW = 8;  // deepest ring of streamed weight stages
 constexpr int kTilesPerSm = 8;  // larger M tiles only while a layer keeps this many tiles per SM
 constexpr int kWProd = 2;  // producer warps filling a streamed weight ring
-// Bytes of a streamed weight stage: every stage costs the MMA thread a commit
-// and the producer a wait, so large layers get few large stages; the packed
-// stages of split layers (small batches) stay small, their tiles are few.
+// Bytes of a streamed weight stage: each stage costs its producer one issue
+// round (wait, expect, copy) of about the same time whatever its size, so
+// large layers get few large stages; the packed stages of split layers
+// (small batches, few tiles) stay small.
 constexpr int kWStage = 65536, kWStagePacked = 16384;
 constexpr int kThreads = 32 * (kProdWarps + 1 + kEpiWarps);
 constexpr long long kWaitCycles = 2000000000ll;
