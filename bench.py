@@ -441,6 +441,7 @@ def gpu_arm(args):
     configs.update(train_config(G, torch, dev_index, flush))
     configs.update(serve_configs(G, dev_index))
     cpu = cpu_baseline(budget_s=args.cpu_seconds)
+    cpu["one_core"] = cpu_baseline_one_core()
     line = {
         "metric": METRIC,
         "value": hp["value"],
@@ -930,6 +931,20 @@ def cpu_baseline(budget_s=15.0):
     return {"value": n / t, "unit": "snapshots/s", "cores": cpu_threads(), "kind": "oracle",
             "sample": f"{n} consecutive 21x32768 windows (stride 256, batches of 32) through the FP64 numpy "
                       f"oracle DeepClean + aggregation, {t:.1f} s"}
+
+
+def cpu_baseline_one_core(n_windows=8):
+    """The same oracle in a child process (fork + exec) whose numerical
+    libraries are held to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = f"import bench; bench.oracle_snapshot_seconds(1); print(bench.oracle_snapshot_seconds({n_windows}, seed=4322))"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"unavailable": (r.stderr.strip().splitlines() or ["child failed"])[-1][:200]}
+    t = float(r.stdout.strip().splitlines()[-1])
+    return {"value": n_windows / t, "unit": "snapshots/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_windows} consecutive 21x32768 windows (stride 256) through the FP64 numpy oracle "
+                      f"DeepClean + aggregation in one thread, {t:.1f} s"}
 
 
 def reference_arm(args):
