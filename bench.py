@@ -938,10 +938,14 @@ def cpu_baseline_one_core(n_windows=8):
     libraries are held to one thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = f"import bench; bench.oracle_snapshot_seconds(1); print(bench.oracle_snapshot_seconds({n_windows}, seed=4322))"
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    if r.returncode != 0:
-        return {"unavailable": (r.stderr.strip().splitlines() or ["child failed"])[-1][:200]}
-    t = float(r.stdout.strip().splitlines()[-1])
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=300)
+        if r.returncode != 0:
+            return {"unavailable": (r.stderr.strip().splitlines() or ["child failed"])[-1][:200]}
+        t = float(r.stdout.strip().splitlines()[-1])
+    except (subprocess.TimeoutExpired, ValueError, IndexError) as e:
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
     return {"value": n_windows / t, "unit": "snapshots/s", "cores": 1, "kind": "oracle",
             "sample": f"{n_windows} consecutive 21x32768 windows (stride 256) through the FP64 numpy oracle "
                       f"DeepClean + aggregation in one thread, {t:.1f} s"}
