@@ -238,8 +238,9 @@ int gw_stream_destroy(gw_stream_t s);
  * checks on the device and reports through gw_stream_status). */
 int gw_stream_push(gw_stream_t s, int n_snap, const float* witness, const float* strain,
                    float* clean_out, int mem, void* cuda_stream);
-/* Queued host-buffer pushes for a pipelined client (the same computation as
- * gw_stream_push in host mode).  gw_stream_push_async queues push k: the copy
+/* Queued host-buffer pushes for a pipelined client: the same computation as
+ * gw_stream_push in host mode (Methods, "Streaming IaaS", "Data aggregation"
+ * and "Aggregation latency"), with the client's requests overlapping.  gw_stream_push_async queues push k: the copy
  * of its inputs to the device, the device-side check, the snapshot update,
  * DeepClean, the subtraction and the copy of its cleaned samples to
  * clean_out, all stream-ordered on cuda_stream, and returns without waiting;
