@@ -143,7 +143,8 @@ int gw_deepclean_forward(gw_model_t m, const float* x, int64_t ld, int64_t windo
  * Limits: FP32 models only (GW_ENOTIMPL otherwise) and B * L <= 32768 samples
  * (GW_EINVAL beyond).  The first call on each device looks up the array's
  * device address on the current device; make that first call before any
- * CUDA stream capture.  All calls share the one array, so calls that overlap
+ * CUDA stream capture.  The current CUDA device must be the model's
+ * (GW_EINVAL otherwise).  All calls share the one array, so calls that overlap
  * on the GPU (different streams, or different host threads) race and must be
  * serialised by the caller; the array needs no clearing, because each layer
  * overwrites what the next layer reads.  Arguments as gw_deepclean_forward. */
@@ -436,7 +437,8 @@ int gw_adam_step(float* params, const float* grads, float* m, float* v, int64_t 
  * `names_len` bytes of '\n'-separated names in the order of the other two
  * arrays (at most `max_entries` each).  Returns the number of names, or a
  * negative code.  gw_launch_count returns the number of kernels launched by
- * the library since load (always counted). */
+ * the library since load (always counted); gw_alloc_count the number of
+ * device allocations (cudaMalloc calls) the library has made since load. */
 /* Host-only inspection of how the tensor-core path lowers one conv layer
  * (no GPU is touched): `spec` = {transposed, c_in, c_out, k, stride, pad_left,
  * pad_right, out_pad}; `wfold` = folded weights [c_out][c_in][k] (FP64);
@@ -456,6 +458,7 @@ int gw_tc_inspect(const int* spec, int precision, const double* wfold, int lin, 
 int gw_profile_enable(int on);
 int gw_profile_read(char* names, size_t names_len, double* total_ms, int64_t* launches, int max_entries);
 int64_t gw_launch_count(void);
+int64_t gw_alloc_count(void);
 
 #ifdef __cplusplus
 }

@@ -61,9 +61,11 @@ static void prof_clear() {
 
 // ---- device memory with a per-context budget ------------------------------
 static std::mutex g_alloc_mu;
+static std::atomic<int64_t> g_dev_allocs{0};
 
 void* dev_alloc(gw_ctx* ctx, size_t bytes, size_t* counter) {
   if (bytes == 0) return nullptr;
+  g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     if (ctx->budget && ctx->in_use + bytes > ctx->budget)
@@ -691,6 +693,7 @@ int gw_profile_read(char* names, size_t names_len, double* total_ms, int64_t* la
 }
 
 int64_t gw_launch_count(void) { return g_launches.load(); }
+int64_t gw_alloc_count(void) { return g_dev_allocs.load(); }
 
 int gw_ctx_create(int device, size_t hbm_budget_bytes, gw_ctx_t* out) {
   GW_API_BEGIN

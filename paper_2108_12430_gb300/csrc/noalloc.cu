@@ -60,6 +60,9 @@ extern "C" int gw_deepclean_forward_noalloc(gw_model_t m, const float* x, int64_
     int device = 0;
     GW_CUDA(cudaGetDevice(&device));
     GW_CHECK_ARG(device >= 0 && device < kMaxDevices, "device index out of range");
+    // the weights, the input statistics and the caller's buffers live on the
+    // model's device; the scratch address and the launches must be that device's
+    GW_CHECK_ARG(device == m->ctx->device, "the current CUDA device is not the model's device");
     float* buf = scratch_address(device);
     const int64_t per = (int64_t)B * 8 * L;
     gw::deepclean_f32(m, x, window_stride, ld, true, B, L, y, L, buf, buf + per, (cudaStream_t)cuda_stream);

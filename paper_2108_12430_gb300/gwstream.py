@@ -38,7 +38,7 @@ EXPORTS = (
     "gw_fir_create_whitening", "gw_fir_destroy", "gw_fir_ntaps", "gw_fir_taps", "gw_whiten",
     "gw_stream_create", "gw_stream_destroy", "gw_stream_push", "gw_stream_push_async", "gw_stream_sync",
     "gw_stream_head", "gw_stream_status",
-    "gw_profile_enable", "gw_profile_read", "gw_launch_count", "gw_deepclean_forward_noalloc",
+    "gw_profile_enable", "gw_profile_read", "gw_launch_count", "gw_alloc_count", "gw_deepclean_forward_noalloc",
     "gw_model_status", "gw_tc_inspect", "gw_fir_create_lowpass",
     "gw_server_create", "gw_server_open", "gw_server_close", "gw_server_stream_bytes", "gw_server_submit",
     "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
@@ -116,6 +116,7 @@ def _declare(lib):
         "gw_profile_enable": (I, [I]),
         "gw_profile_read": (I, [C.c_char_p, SZ, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
         "gw_launch_count": (I64, []),
+        "gw_alloc_count": (I64, []),
         "gw_deepclean_forward_noalloc": (I, [P, P, I64, I64, I, I, P, P]),
         "gw_model_status": (I, [P, P]),
         "gw_model_test_wait_timeout": (I, [P, C.POINTER(C.c_int), P]),
@@ -484,6 +485,10 @@ def gw_profile_read(max_entries=64):
 
 def gw_launch_count():
     return lib().gw_launch_count()
+
+
+def gw_alloc_count():
+    return lib().gw_alloc_count()
 
 
 TC_META = ("n_steps", "npad", "groups", "in_P", "Q", "dspan", "dmin", "MT", "rows", "a_bytes", "sps", "nst",
