@@ -128,3 +128,37 @@ def run_deepclean_stream(forward, witness_total, strain_total, W, S, n_snap,
     if post is not None:
         return preds, clean_post(strain_total, agg, S, delta, post)
     return preds, clean(strain_total, agg, S, delta)
+
+
+def aggregate_by_window(preds, W, S, mode, delta, ks=None):
+    """The aggregation of ``aggregate`` written per window instead of per
+    sample, for long streams: for each emitted snapshot k (all of them, or
+    those in ``ks``) the S emitted times are handled together, and the loop
+    runs over the windows j = 0 .. k in order, adding window j's prediction
+    wherever its span [(j+1) S - W, (j+1) S) holds an emitted time.  The mean
+    is that sum over the number of covering windows.  preds (n, W) holds
+    every window's prediction; returns (len(ks), S)."""
+    preds = np.asarray(preds, np.float64)
+    n = preds.shape[0]
+    assert 0 <= delta <= W - S
+    ks = list(range(n)) if ks is None else list(ks)
+    out = np.zeros((len(ks), S))
+    for r, k in enumerate(ks):
+        if mode == LATEST:
+            out[r] = preds[k, W - S - delta:W - delta]
+            continue
+        tau = emit_times(k, S, delta)
+        total = np.zeros(S)
+        count = np.zeros(S)
+        # windows ending (at (j+1) S) before the first emitted time k S - delta
+        # cover none of it; starting the loop a little earlier than that
+        # changes nothing
+        for j in range(max(0, k - (W + delta) // S - 1), k + 1):
+            start = (j + 1) * S - W
+            cover = (tau >= start) & (tau < start + W)
+            if not cover.any():
+                continue
+            total[cover] += preds[j, tau[cover] - start]
+            count[cover] += 1
+        out[r] = total / count
+    return out

@@ -9,7 +9,7 @@ import pytest
 import torch
 import torch.nn.functional as F
 
-from oracle import fir, grad, layers as Lyr, nets, stream
+from oracle import fir, grad, layers as Lyr, nets, spectral, stream
 from paper_2108_12430_gb300 import synth
 
 rng = np.random.default_rng(12345)
@@ -345,6 +345,85 @@ def test_average_is_mean_of_covering_windows():
         assert abs(agg[k, i] - sum(vals) / len(vals)) < 1e-12
     np.testing.assert_allclose(stream.aggregate(preds, W, S, stream.AVERAGE, 0),
                                stream.aggregate(preds, W, S, stream.LATEST, 0))
+
+
+@pytest.mark.parametrize("W,S", [(256, 32), (128, 64), (64, 64), (96, 8)])
+def test_aggregate_by_window_equals_per_sample_definition(W, S):
+    # the per-window form used for long streams against the per-sample
+    # statement (brute force on short streams), every mode and latency
+    n = 3 * W // S + 2
+    preds = rng.standard_normal((n, W))
+    for mode in (stream.LATEST, stream.AVERAGE):
+        for delta in sorted({0, 3, S // 2, W // 2, W - S} & set(range(0, W - S + 1))):
+            ref = stream.aggregate(preds, W, S, mode, delta)
+            np.testing.assert_allclose(stream.aggregate_by_window(preds, W, S, mode, delta), ref, atol=1e-12)
+            ks = [0, n // 2, n - 1]
+            np.testing.assert_allclose(stream.aggregate_by_window(preds, W, S, mode, delta, ks), ref[ks], atol=1e-12)
+
+
+def test_aggregate_by_window_full_overlap_count():
+    # with delta = W - S a sample emitted once the stream holds W samples is
+    # the mean of exactly W / S windows: a prediction equal to the window
+    # index j gives the mean of k - W/S + 1 .. k
+    W, S, n = 512, 64, 30
+    preds = np.repeat(np.arange(n, dtype=np.float64)[:, None], W, 1)
+    agg = stream.aggregate_by_window(preds, W, S, stream.AVERAGE, W - S)
+    for k in range(W // S, n):
+        np.testing.assert_allclose(agg[k], np.full(S, k - (W // S - 1) / 2.0), atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Welch ASD (cleaning-quality measure of Methods, "Aggregation latency")
+# ----------------------------------------------------------------------------
+
+def test_welch_matches_scipy():
+    from scipy.signal import welch
+    x = rng.standard_normal(4096 * 12)
+    f, p = spectral.welch_psd(x, 4096.0)
+    f2, p2 = welch(x, fs=4096.0, window="hann", nperseg=8192, noverlap=4096)
+    np.testing.assert_allclose(f, f2)
+    np.testing.assert_allclose(p, p2, rtol=1e-10)
+
+
+def test_welch_pure_tone_peak_closed_form():
+    # A sin(2 pi f0 t) with f0 on a bin: the windowed DFT at f0 is A/2 sum w,
+    # so the one-sided density there is A^2 (sum w)^2 / (2 fs sum w^2); for
+    # the periodic Hann window sum w = N/2 and sum w^2 = 3N/8, giving A^2 N / (3 fs)
+    fs, N, A = 4096.0, 8192, 0.7
+    f0 = 60.0  # 120 bins at df = 0.5 Hz
+    t = np.arange(10 * N) / fs
+    f, p = spectral.welch_psd(A * np.sin(2 * np.pi * f0 * t + 0.3), fs)
+    j = int(round(f0 / (fs / N)))
+    assert abs(p[j] / (A * A * N / (3 * fs)) - 1) < 1e-6
+    # the two neighbouring bins hold a quarter of the amplitude each, and the
+    # density integrates to the tone's power A^2 / 2
+    np.testing.assert_allclose(p[j - 1:j + 2:2], p[j] / 4, rtol=1e-6)
+    assert abs(p.sum() * (fs / N) - A * A / 2) < 1e-6
+
+
+def test_welch_white_noise_flat_and_scaling():
+    # white noise of variance s2 has the flat one-sided density 2 s2 / fs;
+    # the ASD of a scaled series is the scaled ASD, so ratios of scaled series
+    # are exact
+    fs, s = 4096.0, 1.7
+    x = rng.standard_normal(4096 * 64) * s
+    f, a = spectral.welch_asd(x, fs)
+    inner = (f > 10) & (f < 2000)
+    assert abs(np.mean(a[inner] ** 2) / (2 * s * s / fs) - 1) < 0.01
+    _, r = spectral.asd_ratio(0.25 * x, x, fs)
+    np.testing.assert_allclose(r, 0.25, rtol=1e-12)
+
+
+def test_frac_bins_off():
+    f = np.arange(0, 100, 0.5)
+    off = np.ones_like(f)
+    on = np.ones_like(f)
+    band = (f >= 50) & (f <= 70)
+    idx = np.flatnonzero(band)
+    on[idx[:8]] = 1.2   # 8 bins 20% off
+    on[idx[8:12]] = 1.05  # within 10%
+    on[f < 50] = 3.0    # outside the band: ignored
+    assert spectral.frac_bins_off(on, off, f) == pytest.approx(8 / band.sum())
 
 
 def test_streamed_equals_full_pass_for_local_model():
