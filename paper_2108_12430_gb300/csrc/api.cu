@@ -176,6 +176,7 @@ static void model_free(gw_model* m) {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     m->ctx->in_use -= m->bytes + m->ws_bytes;
   }
+  fused_plan_destroy(m->fused);
   delete m;
 }
 
@@ -381,6 +382,12 @@ int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 2048; }
 // blocked BF16 input (ring windows or a converted batch); y gets FP32 [B][y_ld].
 void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1,
                          int* err, cudaStream_t st) {
+  if (in.item_ptr == nullptr && fused_supported(m, L)) {
+    // the whole network in one launch, activations in shared memory
+    Prof p("deepclean_fused", st);
+    launch_deepclean_fused(m, in, B, L, y, y_ld, err, st);
+    return;
+  }
   const auto& Ls = m->layers;
   void* bufs[2] = {buf0, buf1};
   int lin = L;
@@ -751,6 +758,8 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
   m->n_in = d->n_in;
   const auto specs = specs_for(d->kind, d->n_in);
   const float* p = d->params;
+  std::vector<std::vector<double>> wfold;
+  std::vector<std::vector<float>> bfold;
   for (size_t li = 0; li < specs.size(); ++li) {
     const LayerSpec& s = specs[li];
     std::vector<double> wf, bf;
@@ -759,6 +768,8 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
     LayerDev L;
     L.s = s;
     std::vector<float> w32(wf.begin(), wf.end()), b32(bf.begin(), bf.end());
+    wfold.push_back(wf);
+    bfold.push_back(b32);
     L.w = upload(m, w32);
     L.b = upload(m, b32);
     if (d->precision != GW_FP32) {
@@ -771,6 +782,7 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
     }
     m->layers.push_back(L);
   }
+  if (d->kind == GW_MODEL_DEEPCLEAN && d->precision == GW_BF16) m->fused = fused_plan_create(m, wfold, bfold);
   if (d->precision == GW_FP8 && d->act_scales) {
     GW_CHECK_ARG(d->n_act_scales == (int)specs.size() + 1,
                  "act_scales must have one entry per conv layer plus the final output scale");

@@ -88,6 +88,8 @@ struct LayerDev {
   float out_scale = 1.f;   // FP8: scale applied to the outputs for the next layer
 };
 
+struct FusedPlan;
+
 }  // namespace gw
 
 // ---- public object structs --------------------------------------------------
@@ -118,6 +120,8 @@ struct gw_model {
   std::vector<std::vector<float>> fp8_wscale;
   float fp8_final_scale = 1.f;
   bool fp8_scaled = false;
+  // BF16 DeepClean: the whole-network tensor-core kernel's plan (or null)
+  gw::FusedPlan* fused = nullptr;
 };
 
 struct gw_fir {
@@ -272,11 +276,38 @@ int tc_supported();
 // the per-output-channel weight scales (max |w| -> 448) in wscale_out.
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wfold, int precision, gw_ctx* ctx,
                    size_t* counter, std::vector<void*>& allocs, std::vector<float>* wscale_out = nullptr);
+// BF16 lowering of one folded layer (L.J > 0 fixes the positions folded per
+// MMA row): packed B-operand image [steps][2 K-halves][npad rows][16 bytes]
+// and the per-step slice codes; fills the lowering fields of L.
+void tc_lower_layer(LayerDev& L, const std::vector<double>& wf, std::vector<uint8_t>& img,
+                    std::vector<uint32_t>& table);
+// Byte offset of slice `code` in a buffer of P planes per channel group and
+// `rows` 16-byte rows per plane.
+uint32_t tc_slice_offset(uint32_t code, int P, int rows);
+
+// ---- fused DeepClean (k_fused.cu) ------------------------------------------------
+struct FusedPlan;
+// Lowers the folded layers (wfold[l] = FP64 folded weights, b32[l] = FP32
+// bias) for the fused kernel and uploads its weight images; nullptr when the
+// layer table does not fit the kernel.
+FusedPlan* fused_plan_create(gw_model* m, const std::vector<std::vector<double>>& wfold,
+                             const std::vector<std::vector<float>>& bias);
+void fused_plan_destroy(FusedPlan* f);
+// True when windows of L samples can run through the fused kernel.
+bool fused_supported(gw_model* m, int L);
+// DeepClean on B windows of L samples: `in` is the first layer's blocked
+// input (ring windows or a converted batch, no per-item table), y gets FP32
+// [B][y_ld].
+void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y, int64_t y_ld, int* err,
+                            cudaStream_t st);
+
 // max |x| over n floats, combined into *amax (atomic max of non-negative floats).
 void launch_absmax(const float* x, int64_t n, float* amax, cudaStream_t st);
-// The next launch_conv_tc leaves one input stage of CTA 0 unarmed, so that a
-// bounded wait runs out (testing of the failure path; not thread-safe).
+// The calling thread's next tensor-core launch (launch_conv_tc or
+// launch_deepclean_fused) leaves one input stage of CTA 0 unarmed, so that a
+// bounded wait runs out (testing of the failure path).
 void conv_tc_arm_stall_test();
+bool tc_take_stall_test();
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err_flag,
                     cudaStream_t st);
 // FP32 element (b, c, t) at x + b*xb + c*xc + t*ts -> blocked bf16 / e4m3,

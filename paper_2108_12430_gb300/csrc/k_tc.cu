@@ -41,10 +41,13 @@
 #include <set>
 
 #include "gw_internal.h"
+#include "tc_ptx.h"
 
 namespace gw {
 
 namespace {
+
+using namespace ptx;
 
 // warp 0 producer, warp 1 MMA, warps 2-9 epilogue: two epilogue warps per
 // TMEM lane quarter (each takes every other 32-column chunk), so that every
@@ -67,7 +70,6 @@ constexpr int kWProd = 2;  // producer warps filling a streamed weight ring
 // (small batches, few tiles) stay small.
 constexpr int kWStage = 65536, kWStagePacked = 16384;
 constexpr int kThreads = 32 * (kProdWarps + 1 + kEpiWarps);
-constexpr long long kWaitCycles = 2000000000ll;
 constexpr int kErrWaitA = 1, kErrWaitW = 2, kErrWaitAcc = 4, kErrWaitEmpty = 8, kErrDrain = 16;
 // Source of the zero padding rows of edge tiles (a stage plane holds at most
 // kZeroRows rows; the planner checks it).
@@ -121,47 +123,6 @@ struct TcParams {
 };
 constexpr int kParamSteps = 192;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-// try_wait with a suspend-time hint: a waiting thread sleeps in hardware until
-// the phase completes (or 0.1 ms pass) instead of spinning on issue slots that
-// the MMA-issuing thread and the epilogue warps need.
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(100000u)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for a barrier phase.  Gives up when another role has aborted,
-// or after kWaitCycles SM clocks (about 1 s at the GB300's clocks; then it
-// records `code` and raises the abort flag itself).  The limit uses the
-// SM-local cycle counter: it is cheap to read, so a waiting thread reacts to
-// the phase flip at once.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag, int* err, int code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      *abort_flag = 1u;
-      atomicOr(err, code);
-      return false;
-    }
-  }
-  return true;
-}
 // Named barrier 1 over the epilogue warps with an AND-reduction of `ok`: every
 // participating thread gets the same verdict, so the warps leave the tile loop
 // together (a warp that left alone would strand the others in the barrier).
@@ -188,80 +149,6 @@ __device__ __forceinline__ void tile_coords(const TcParams& p, int t, int& b, in
   if (j >= p.tiles_per_item) j -= p.tiles_per_item;
   m0 = j * 128 * p.MT;
 }
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-// Shared-memory matrix descriptor, no swizzle, K-major: start address, LBO =
-// byte distance between the two K-adjacent core matrices, SBO = byte distance
-// between core matrices adjacent in M/N; bits 46-48 hold the fixed 0b001.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-// No "memory" clobber: the MMA reads shared memory through the async proxy
-// only, ordered by the barrier waits and fences (volatile asm keeps its place
-// among the other volatile asm), and without the clobber the compiler may load
-// the next step's descriptors while this one issues.
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-// 32 consecutive accumulator columns of this thread's TMEM lane, one wait.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// The tensor-core path stores activations in bf16 (relative step 2^-8), so
-// the hardware tanh approximation (relative error about 2^-11) is used; the
-// FP32 path keeps tanhf.
-__device__ __forceinline__ float tanh_fast(float v) {
-  float r;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-
 __device__ __forceinline__ float act_fn(float v, int act) {
   if (act == ACT_TANH) return tanh_fast(v);
   if (act == ACT_RELU) return fmaxf(v, 0.f);
@@ -945,6 +832,15 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
   L.coutp = coutp;
 }
 
+void tc_lower_layer(LayerDev& L, const std::vector<double>& wf, std::vector<uint8_t>& img,
+                    std::vector<uint32_t>& table) {
+  std::vector<float> wscale;
+  lower_layer(L, wf, false, img, table, wscale);
+  L.table_h = table;
+}
+
+uint32_t tc_slice_offset(uint32_t code, int P, int rows) { return slice_off(code, P, rows); }
+
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wf, int precision, gw_ctx* ctx, size_t* counter,
                    std::vector<void*>& allocs, std::vector<float>* wscale_out) {
   const LayerSpec& s = L.s;
@@ -1165,8 +1061,15 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   *grid_out = dim3(std::min(q.n_tiles, sms * q.per_sm));
 }
 
-static bool g_stall_next = false;
+// Armed by the failure-path test on its own thread and taken by that
+// thread's next tensor-core launch (the per-layer or the fused kernel).
+static thread_local bool g_stall_next = false;
 void conv_tc_arm_stall_test() { g_stall_next = true; }
+bool tc_take_stall_test() {
+  const bool s = g_stall_next;
+  g_stall_next = false;
+  return s;
+}
 
 void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& out, int B, int* err, cudaStream_t st) {
   TcParams q;
@@ -1175,8 +1078,7 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
   static int sms = 0;
   if (!sms) sms = sm_count();
   plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B, sms);
-  q.stall_test = g_stall_next ? 1 : 0;
-  g_stall_next = false;
+  q.stall_test = tc_take_stall_test() ? 1 : 0;
   static bool smem_attr = false;
   if (!smem_attr) {
     GW_CUDA(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
