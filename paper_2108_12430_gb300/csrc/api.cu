@@ -1245,17 +1245,17 @@ static void stream_compute(gw_stream* s, int n_snap, const float* wit, const flo
   for (int d = 0; d < nd; ++d) {
     gw_model* m = s->dc[d];
     const float* wd = wit + (size_t)d * C * n;
-    {
-      Prof p("ring_push", st);
-      if (m->precision == GW_FP32)
+    if (m->precision == GW_FP32) {
+      {
+        Prof p("ring_push", st);
         launch_ring_push_f32(wd, n, C, (int)n, s->ring_f32[d], R, head, m->in_mean, m->in_istd, s->status, st, skip);
-      else
-        launch_ring_push_bf16(wd, n, C, G, (int)n, s->ring_bf16[d], R, head, m->layers[0].pin, m->in_mean,
-                              m->in_istd, s->status, st, skip);
-    }
-    {
+      }
       Prof p("strain_push", st);
       launch_strain_push(str + (size_t)d * n, (int)n, s->strain[d], R, head, s->status, st, skip);
+    } else {
+      Prof p("stream_push", st);
+      launch_stream_push_bf16(wd, n, C, G, (int)n, s->ring_bf16[d], R, head, m->layers[0].pin, m->in_mean,
+                              m->in_istd, str + (size_t)d * n, s->strain[d], s->status, st, skip);
     }
     // window j of this batch ends at head + (j+1) S; in the double-mapped ring
     // the batch's windows are views at uniform stride S from p0.

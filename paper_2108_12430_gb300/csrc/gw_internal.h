@@ -213,6 +213,11 @@ void launch_ring_fill(void* ring, int bf16, int C, int G, int64_t R2, const floa
                       cudaStream_t st);
 void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t head,
                         int* status, cudaStream_t st, const int* skip = nullptr);
+// launch_ring_push_bf16 and launch_strain_push in one launch (programmatic
+// dependent of the previous kernel in the stream).
+void launch_stream_push_bf16(const float* src, int64_t src_ld, int C, int G, int n, __nv_bfloat16* ring, int64_t R,
+                             int64_t head, int P, const float* mean, const float* istd, const float* strain_src,
+                             float* strain_ring, int* status, cudaStream_t st, const int* skip = nullptr);
 // pring (optional): instead of subtracting, store the aggregated prediction of
 // every emitted time t >= 0 at pring[t mod Rp] (post-processing follows).
 // skip_copy (optional): receives *skip (0 without skip) before anything else.

@@ -82,6 +82,48 @@ __global__ void ring_push_bf16_kernel(const float* __restrict__ src, int64_t src
   grp[(q % up) * plane_rows + q / up] = val;
   grp[(q2 % up) * plane_rows + q2 / up] = val;
 }
+// One snapshot update of a BF16 stream in one launch: blockIdx.y < G writes
+// the witness ring's channel group blockIdx.y (as ring_push_bf16_kernel),
+// blockIdx.y == G the strain ring.  Launched as a programmatic dependent of
+// the previous push's aggregation kernel, whose strain reads share ring slots
+// with these writes: it waits for that kernel before touching memory.
+__global__ void stream_push_bf16_kernel(const float* __restrict__ src, int64_t src_ld, int C, int G, int n,
+                                        __nv_bfloat16* __restrict__ ring, int R, int h0, int P,
+                                        const float* __restrict__ mean, const float* __restrict__ istd,
+                                        const float* __restrict__ strain_src, float* __restrict__ strain_ring,
+                                        int* status, const int* skip) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
+  if (i >= n || (skip && *skip)) return;
+  if (g == G) {
+    const float v = __ldg(strain_src + i);
+    if (!isfinite(v)) atomicExch(status, GW_ENONFINITE);
+    strain_ring[ring_pos(h0, i, R)] = v;
+    return;
+  }
+  __align__(16) __nv_bfloat16 v8[8];
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = g * 8 + j;
+    float v = 0.f;
+    if (c < C) {
+      v = __ldg(src + (int64_t)c * src_ld + i);
+      bad |= !isfinite(v);
+      if (mean) v = (v - mean[c]) * istd[c];
+    }
+    v8[j] = __float2bfloat16_rn(v);
+  }
+  if (bad) atomicExch(status, GW_ENONFINITE);
+  const uint32_t q = ring_pos(h0, i, R), q2 = q + (uint32_t)R, up = (uint32_t)P;
+  const uint32_t plane_rows = 2u * (uint32_t)R / up;
+  const uint4 val = *reinterpret_cast<const uint4*>(v8);
+  uint4* grp = reinterpret_cast<uint4*>(ring + (int64_t)g * 2 * R * 8);
+  grp[(q % up) * plane_rows + q / up] = val;
+  grp[(q2 % up) * plane_rows + q2 / up] = val;
+}
+
 __global__ void strain_push_kernel(const float* __restrict__ src, int n, float* __restrict__ ring, int R, int h0,
                                    int* status, const int* skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,6 +148,10 @@ __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, 
                                int64_t R, int64_t head, int mode, int delta, float* __restrict__ acc,
                                const float* __restrict__ strain_ring, float* __restrict__ out, const int* skip,
                                float* __restrict__ pring, int64_t Rp, int* skip_copy) {
+  // a programmatic dependent of the DeepClean kernel that writes pred (a no-op
+  // when launched without the attribute)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (skip_copy && blockIdx.x == 0 && threadIdx.x == 0) *skip_copy = skip ? *skip : 0;
   if (skip && *skip) return;
   const int64_t lo = head + S - W;
@@ -296,14 +342,40 @@ void launch_strain_push(const float* src, int n, float* ring, int64_t R, int64_t
   GW_LAUNCH_CHECK();
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel of the stream finishes; it waits (griddepcontrol)
+// for that kernel before touching memory, so only the launch latency overlaps.
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  GW_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+}
+
 void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int64_t R, int64_t head, int mode,
                     int delta, float* acc, const float* strain_ring, float* out, cudaStream_t st,
                     const int* skip, float* pring, int64_t Rp, int* skip_copy) {
   GW_CHECK_ARG(!pring || Rp >= (int64_t)n * S, "prediction ring too small");
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
-  sub_ola_kernel<<<grid_for(count), kThreads, 0, st>>>(pred, pred_ld, n, S, W, R, head, mode, delta, acc,
-                                                        strain_ring, out, skip, pring, Rp, skip_copy);
-  GW_LAUNCH_CHECK();
+  launch_pdl(sub_ola_kernel, dim3(grid_for(count)), dim3(kThreads), st, pred, pred_ld, n, S, W, R, head, mode, delta,
+             acc, strain_ring, out, skip, pring, Rp, skip_copy);
+}
+
+void launch_stream_push_bf16(const float* src, int64_t src_ld, int C, int G, int n, __nv_bfloat16* ring, int64_t R,
+                             int64_t head, int P, const float* mean, const float* istd, const float* strain_src,
+                             float* strain_ring, int* status, cudaStream_t st, const int* skip) {
+  GW_CHECK_ARG(P >= 1 && R % P == 0, "ring capacity must be a multiple of the phase count");
+  const int h0 = ring_head(head, R, n);
+  if (n == 0) return;
+  launch_pdl(stream_push_bf16_kernel, dim3((n + kThreads - 1) / kThreads, G + 1), dim3(kThreads), st, src, src_ld, C,
+             G, n, ring, (int)R, h0, P, mean, istd, strain_src, strain_ring, status, skip);
 }
 
 void launch_post_sub(const float* pring, int64_t Rp, const float* h, int K, const float* strain_ring, int64_t R,
