@@ -134,7 +134,7 @@ __global__ void strain_push_kernel(const float* __restrict__ src, int n, float* 
 }
 
 // Fused subtract + aggregate over one batch of n windows (Methods, "Data
-// aggregation", "Aggregation latency").  Window j of the batch covers times
+// aggregation", "Aggregation latency"); LATEST mode (AVERAGE: below).  Window j of the batch covers times
 // [head + (j+1) S - W, head + (j+1) S).  One thread per time tau of the
 // union of the batch's windows:
 //   AVERAGE: sum = acc[tau] (windows of earlier batches, zero for new times)
@@ -207,6 +207,77 @@ __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, 
     }
     acc[pmod(tau, R)] = sum;
   }
+}
+
+// AVERAGE aggregation with the windows of a batch split over the 8 warps of
+// a block: the block handles 32 consecutive times (one per lane); warp q sums,
+// in window order, its contiguous block of windows [q b, q b + b), b =
+// ceil(n / 8), and keeps its running sum at the emitting window.  Warp 0 then
+// adds, per time, the accumulator (earlier batches) and the eight block sums
+// in block order: the emitted value is the sum up to the emitting window, the
+// accumulator keeps the full sum.  Every load of a warp reads 32 consecutive
+// floats of one window's prediction.
+constexpr int kOlaWarps = 8;
+__global__ void __launch_bounds__(32 * kOlaWarps) sub_ola_avg_kernel(
+    const float* __restrict__ pred, int64_t pred_ld, int n, int S, int W, int64_t R, int64_t head, int delta,
+    float* __restrict__ acc, const float* __restrict__ strain_ring, float* __restrict__ out, const int* skip,
+    float* __restrict__ pring, int64_t Rp, int* skip_copy) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (skip_copy && blockIdx.x == 0 && threadIdx.x == 0) *skip_copy = skip ? *skip : 0;
+  if (skip && *skip) return;
+  __shared__ float part[kOlaWarps][33], upto[kOlaWarps][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const bool valid = e < count;
+  const int64_t tau = head + S - W + e, r = tau - head;
+  const int64_t k_emit = floordiv64(tau + delta, S);
+  const bool emits = valid && (tau >= head - delta) && (tau < head + (int64_t)n * S - delta);
+  const int j_emit = emits ? (int)(k_emit - head / S) : -1;
+  const int jlo = (int)imax64(0, floordiv64(r, S));
+  const int jhi = (int)imin64(n - 1, floordiv64(r + W, S) - 1);
+  const int blk = (n + kOlaWarps - 1) / kOlaWarps;
+  const int ja = max(jlo, warp * blk), jb = valid ? min(jhi, warp * blk + blk - 1) : -1;
+  // window j holds tau at offset tau - (head + (j+1) S - W) of its prediction
+  const float* pj = pred + (tau - head - S + W);
+  float sum = 0.f, at_emit = 0.f;
+  int j = ja;
+  for (; j + 7 <= jb; j += 8) {
+    float val[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) val[q] = pj[(int64_t)(j + q) * (pred_ld - S)];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sum += val[q];
+      if (j + q == j_emit) at_emit = sum;
+    }
+  }
+  for (; j <= jb; ++j) {
+    sum += pj[(int64_t)j * (pred_ld - S)];
+    if (j == j_emit) at_emit = sum;
+  }
+  part[warp][lane] = sum;
+  upto[warp][lane] = at_emit;
+  __syncthreads();
+  if (warp != 0 || !valid) return;
+  float total = (tau < head) ? acc[pmod(tau, R)] : 0.f, value = 0.f;
+  const int q_emit = j_emit >= 0 ? j_emit / blk : -1;
+#pragma unroll
+  for (int q = 0; q < kOlaWarps; ++q) {
+    if (q == q_emit) value = total + upto[q][lane];
+    total += part[q][lane];
+  }
+  if (emits) {
+    const int64_t first = imax64(0, floordiv64(tau, S));
+    value /= (float)(k_emit - first + 1);
+    if (pring) {
+      if (tau >= 0) pring[pmod(tau, Rp)] = value;
+    } else {
+      out[tau - head + delta] = ((tau >= 0) ? strain_ring[pmod(tau, R)] : 0.f) - value;
+    }
+  }
+  acc[pmod(tau, R)] = total;
 }
 
 int grid_for(int64_t n) {
@@ -364,6 +435,11 @@ void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int
                     const int* skip, float* pring, int64_t Rp, int* skip_copy) {
   GW_CHECK_ARG(!pring || Rp >= (int64_t)n * S, "prediction ring too small");
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
+  if (mode == GW_AGG_AVERAGE) {
+    launch_pdl(sub_ola_avg_kernel, dim3((unsigned)((count + 31) / 32)), dim3(32 * kOlaWarps), st, pred, pred_ld, n,
+               S, W, R, head, delta, acc, strain_ring, out, skip, pring, Rp, skip_copy);
+    return;
+  }
   launch_pdl(sub_ola_kernel, dim3(grid_for(count)), dim3(kThreads), st, pred, pred_ld, n, S, W, R, head, mode, delta,
              acc, strain_ring, out, skip, pring, Rp, skip_copy);
 }
