@@ -36,10 +36,11 @@ W, S, B, C = 32768, 256, 64, 21
 METRIC = "streaming snapshots/s and p50/p99 latency, BF16 vs FP32 path at stated error, 1 GB300"
 WORKLOAD = "DeepClean streaming: 21x32768 windows (8 s @ 4096 Hz), stride 256, batch 64, overlap-add"
 L2_BYTES = 129 * 1024 * 1024
-# ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the 8 conv_tc
-# launches of one 64-window push (set to None whenever conv_tc changes until
-# it is captured again)
-CONV_TRAFFIC_BYTES_PER_PUSH = 238_078_464 + 67_328
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the whole-network DeepClean kernel on this workload, from the ncu capture
+# summarised in profiles/deepclean_fused_stream_batch64.md (None when the
+# kernel has changed since that capture)
+FUSED_TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def dc_flops_per_window(L=W):
@@ -57,19 +58,15 @@ def dc_flops_per_window(L=W):
     return f
 
 
-def dc_act_bytes_per_push(L=W, batch=B, stride=S, c_in=C):
-    """Algorithmic bytes of the 8 conv layers of one push in BF16: the unique
-    ring input once (the batch's windows overlap), then every layer's output
-    written once and read once by the next layer; the prediction in FP32."""
-    from paper_2108_12430_gb300 import synth
+def dc_algorithmic_bytes_per_push(L=W, batch=B, stride=S, c_in=C):
+    """Algorithmic bytes of one push's DeepClean: the unique witness input
+    once (BF16, channels padded to groups of 8; the batch's windows overlap),
+    the FP32 predictions written once, and the aggregation's read-modify-write
+    of the overlap-add accumulator and the strain read over the batch's span
+    (the parameters, 0.08 MB, are not counted)."""
     cpad = (c_in + 7) // 8 * 8
-    total = cpad * (L + (batch - 1) * stride) * 2
-    lin = L
-    for kind, cin, cout, k, s, pl, pr, op, bn, act in synth.DEEPCLEAN_LAYERS:
-        lout = (lin + pl + pr - k) // s + 1 if kind == "conv" else (lin - 1) * s - pl - pr + k + op
-        total += batch * (cout * lout * 4 if cout == 1 else 2 * (cout + 7) // 8 * 8 * lout * 2)
-        lin = lout
-    return total
+    span = L + (batch - 1) * stride
+    return cpad * span * 2 + batch * L * 4 + span * 4 * 3
 
 
 def dc_layer_flops(L=W):
@@ -368,11 +365,11 @@ def gpu_arm(args):
         G.gw_stream_destroy(s)
         G.gw_model_destroy(m)
         G.gw_ctx_destroy(ctx)
-        conv_keys = [k for k in prof if k.startswith("conv")]
-        conv_ms = sum(prof[k][0] for k in conv_keys)
-        conv_n = sum(prof[k][1] for k in conv_keys)
+        # DeepClean's kernels: the whole-network kernel (BF16) or the eight
+        # per-layer convolutions (FP32)
+        dc_ms = sum(v[0] for k, v in prof.items() if k.startswith("conv") or k == "deepclean_fused")
         prof_steps = min(K, 8)
-        conv_flops = dc_flops_per_window() * B * prof_steps
+        dc_flops = dc_flops_per_window() * B * prof_steps
         paths[name] = {
             "value": job_rate(B * K, world, tot / 1e3),
             "ms_per_step": tot / K,
@@ -385,7 +382,7 @@ def gpu_arm(args):
             "e2e_p50_ms": float(np.percentile(lat, 50)),
             "e2e_p99_ms": float(np.percentile(lat, 99)),
             "gpu_launches_per_step": res["launches_per_step"],
-            "conv_tflops": conv_flops / (conv_ms / 1e3) / 1e12 if conv_ms else None,
+            "deepclean_tflops": dc_flops / (dc_ms / 1e3) / 1e12 if dc_ms else None,
             "kernels": {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps}
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "clocks": cs.summary(),
@@ -402,39 +399,35 @@ def gpu_arm(args):
         return
     hp = paths[headline]
     kernels = hp["kernels"]
-    # dominant kernel family: the conv layers (same kernel, different shapes)
-    conv_ms_step = sum(v["ms_per_step"] for k, v in kernels.items() if k.startswith("conv"))
-    conv_s = conv_ms_step / 1e3
     flops_step = dc_flops_per_window() * B
-    achieved = flops_step / conv_s / 1e12
-    unit = "TFLOP/s"
-    extra = {}
     if headline == "bf16":
-        # DeepClean's 8-64-channel layers move 602 MB of activations per push
-        # for 31.5 GFLOP: an arithmetic intensity below the BF16 ridge point, so
-        # the binding roofline is HBM bandwidth; the tensor fraction is reported
-        # beside it
-        ai = flops_step / dc_act_bytes_per_push()
+        # one launch of the whole-network kernel per push: a dense
+        # contraction far above the ridge point (31.5 GFLOP on ~11 MB of
+        # algorithmic traffic), so the binding roofline is the tensor core
+        kname = "deepclean_fused"
+        k_ms = kernels[kname]["ms_per_step"] / kernels[kname]["launches_per_step"]
+        achieved = flops_step / (k_ms / 1e3) / 1e12
+        peak = pk["bf16_tflops"]
+        ai = flops_step / dc_algorithmic_bytes_per_push()
         ridge = pk["bf16_tflops"] * 1e12 / (pk["hbm_gbs"] * 1e9)
-        extra = {"arithmetic_intensity_flop_per_byte": ai, "ridge_flop_per_byte": ridge,
-                 "tensor_tflops": achieved, "tensor_peak_tflops": pk["bf16_tflops"],
-                 "tensor_frac": achieved / pk["bf16_tflops"]}
-        if ai < ridge:
-            bound, unit = "hbm", "GB/s"
-            achieved = dc_act_bytes_per_push() / conv_s / 1e9
-            peak = pk["hbm_gbs"]
-            peak_note = f"HBM copy bandwidth, {pk_src}"
-        else:
-            bound = "tensor"
-            peak = pk["bf16_tflops"]
-            peak_note = f"dense bf16 burst, {pk_src}"
+        roofline = {"bound": "tensor", "kernel": kname + " (1 launch per step)", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": FUSED_TRAFFIC_BYTES_PER_LAUNCH,
+                    "peak_source": f"dense bf16 burst, {pk_src} (the kernel is timed alone: one launch per push)",
+                    "launch_ms": k_ms, "flop_per_launch": flops_step,
+                    "per_unit": f"{dc_flops_per_window()} flop per 21x32768 window x {B} windows per launch",
+                    "algorithmic_bytes_per_launch": dc_algorithmic_bytes_per_push(),
+                    "arithmetic_intensity_flop_per_byte": ai, "ridge_flop_per_byte": ridge,
+                    "traffic_unit": "DRAM bytes per launch (ncu capture, cold cache)"}
+        if FUSED_TRAFFIC_BYTES_PER_LAUNCH:
+            roofline["traffic_over_algorithmic"] = FUSED_TRAFFIC_BYTES_PER_LAUNCH / dc_algorithmic_bytes_per_push()
     else:
+        conv_ms_step = sum(v["ms_per_step"] for k, v in kernels.items() if k.startswith("conv"))
+        achieved = flops_step / (conv_ms_step / 1e3) / 1e12
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound = "alu"
-        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
-    # DRAM bytes (read + write) of the 8 conv launches of one push from an ncu
-    # capture of the current kernel (cold cache; profiles/conv_tc_deepclean_stream_batch64.md)
-    traffic = CONV_TRAFFIC_BYTES_PER_PUSH if headline == "bf16" else None
+        roofline = {"bound": "alu", "kernel": "conv_f32 (8 launches per step)", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
     configs = extra_configs(G, torch, dev_index, flush)
     configs.update(bulk_config(G, torch, dev_index, flush))
     configs.update(study_config(dev_index))
@@ -470,18 +463,23 @@ def gpu_arm(args):
                 "sync": {"value": hp["e2e_sync_value"], "p50_ms": hp["e2e_p50_ms"], "p99_ms": hp["e2e_p99_ms"],
                          "mode": "gw_stream_push in host mode, returning per step"}},
         "gpu_launches": int(round(hp["gpu_launches_per_step"] * K)),
-        "roofline": dict({"bound": bound, "kernel": "conv layers (8 launches per step)", "achieved": achieved,
-                          "peak": peak, "unit": unit, "frac": achieved / peak, "traffic": traffic,
-                          "peak_source": peak_note,
-                          "per_unit": f"{dc_flops_per_window()} flop and (bf16) the activation bytes of "
-                                      f"dc_act_bytes_per_push per window x {B} windows per step",
-                          "traffic_unit": "DRAM bytes per step (the 8 conv launches), ncu cold-cache capture",
-                          "algorithmic_bytes_per_step": dc_act_bytes_per_push()}, **extra),
+        "roofline": roofline,
         "paths": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in paths.items()},
         "configs": configs,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
+    # per-kernel breakdowns go to stderr, so that the one JSON line stays short
+    detail = {"paths_kernels": {k: v.get("kernels") for k, v in paths.items()},
+              "configs_kernels": {k: {kk: vv for kk, vv in v.items() if "kernel" in kk}
+                                  for k, v in configs.items() if isinstance(v, dict)}}
+    print(json.dumps(detail), file=sys.stderr)
+    for v in line["paths"].values():
+        v.pop("kernels", None)
+    for v in line["configs"].values():
+        if isinstance(v, dict):
+            for kk in [kk for kk in v if "kernel" in kk and kk != "kernels_per_tick"]:
+                v.pop(kk)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -921,16 +919,32 @@ def cpu_threads():
     return os.cpu_count() or 1
 
 
-def cpu_baseline(budget_s=15.0):
-    oracle_snapshot_seconds(1)
-    n, t, seed = 0, 0.0, 4321
-    while t < budget_s and n < 1024:
-        t += oracle_snapshot_seconds(32, seed=seed)
-        n += 32
-        seed += 1
-    return {"value": n / t, "unit": "snapshots/s", "cores": cpu_threads(), "kind": "oracle",
-            "sample": f"{n} consecutive 21x32768 windows (stride 256, batches of 32) through the FP64 numpy "
-                      f"oracle DeepClean + aggregation, {t:.1f} s"}
+def cpu_baseline(budget_s=12.0, n_max=1024, seed=4321):
+    """The FP64 oracle on the host's cores: consecutive 21 x 32768 snapshot
+    windows of one stream (stride 256) spread over one worker process per
+    core (each held to one BLAS thread), then the overlap-add aggregation
+    (latency W - S) and the subtraction, timed end to end after a warm-up
+    round; the sample size is set so that it takes about budget_s."""
+    from oracle import pool, stream as ostream
+    from paper_2108_12430_gb300 import synth
+    workers = pool.host_cores()
+    params = synth.deepclean_params(1234)
+    wit = synth.witness_channels(seed, C, W + (n_max - 1) * S)
+    strain = synth.coupled_strain(seed, wit)
+    with pool.DeepCleanPool(wit, W, S, params, synth.DEEPCLEAN_LAYERS, workers=workers, chunk=1) as P:
+        t0 = time.perf_counter()
+        P.forward(range(workers))  # one window per worker: the rate of one round
+        per_round = time.perf_counter() - t0
+        n = int(min(n_max, max(workers, int(budget_s / max(per_round, 1e-3)) * workers)))
+        t0 = time.perf_counter()
+        preds = P.forward(range(n))
+        agg = ostream.aggregate_by_window(preds, W, S, ostream.AVERAGE, W - S)
+        ostream.clean(strain, agg, S, W - S)
+        t = time.perf_counter() - t0
+    return {"value": n / t, "unit": "snapshots/s", "cores": workers, "kind": "oracle",
+            "sample": f"{n} consecutive 21x32768 windows (stride 256) through the FP64 numpy oracle DeepClean "
+                      f"({workers} worker processes, one BLAS thread each) + overlap-add aggregation "
+                      f"(delay W-S) + subtraction, {t:.1f} s"}
 
 
 def cpu_baseline_one_core(n_windows=8):
@@ -952,25 +966,44 @@ def cpu_baseline_one_core(n_windows=8):
 
 
 def reference_arm(args):
+    """The method's reference implementation here is the FP64 oracle (the
+    paper's method has no runnable code): each step is one round of
+    snapshot windows, one per host core, through the oracle's DeepClean,
+    then their overlap-add aggregation and subtraction."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    oracle_snapshot_seconds(1)
-    for _ in range(args.warmup):
-        oracle_snapshot_seconds(1)
-    ts = [oracle_snapshot_seconds(1) for _ in range(args.steps)]
+    from oracle import pool, stream as ostream
+    from paper_2108_12430_gb300 import synth
+    workers = pool.host_cores()
+    n_steps = args.warmup + args.steps
+    n_win = workers * n_steps
+    wit = synth.witness_channels(4321, C, W + (n_win - 1) * S)
+    strain = synth.coupled_strain(4321, wit)
+    params = synth.deepclean_params(1234)
+    ts = []
+    with pool.DeepCleanPool(wit, W, S, params, synth.DEEPCLEAN_LAYERS, workers=workers, chunk=1) as P:
+        for i in range(n_steps):
+            ks = range(i * workers, (i + 1) * workers)
+            t0 = time.perf_counter()
+            preds = P.forward(ks)
+            agg = ostream.aggregate_by_window(preds, W, S, ostream.AVERAGE, 0)
+            ostream.clean(strain, agg, S, 0)
+            if i >= args.warmup:
+                ts.append(time.perf_counter() - t0)
     tot = sum(ts)
-    v = args.steps / tot
+    v = args.steps * workers / tot
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "snapshots/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "window": W, "stride": S, "batch": B,
-                                        "reference_sample": "1 snapshot (one window) per step"},
+                                        "reference_sample": f"{workers} windows (one per host core) per step"},
         "p50_ms": float(np.percentile(ts, 50) * 1e3), "p99_ms": float(np.percentile(ts, 99) * 1e3),
-        "cpu_baseline": {"value": v, "unit": "snapshots/s", "cores": cpu_threads(), "kind": "oracle",
-                         "sample": "1 window of 21x32768 per step through the FP64 numpy oracle"},
+        "cpu_baseline": {"value": v, "unit": "snapshots/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{workers} windows of 21x32768 per step through the FP64 numpy oracle, "
+                                   "one worker process per core"},
         "e2e": {"value": v, "unit": "snapshots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -981,7 +1014,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gw", "reference"], default="gw")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--only", choices=["bf16", "fp32"], default=None,
                     help="time one path only (profiling)")
     ap.add_argument("--serve-only", action="store_true",
