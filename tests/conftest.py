@@ -22,3 +22,11 @@ def gpu_lib():
     from paper_2108_12430_gb300 import gwstream
 
     return gwstream.lib()
+
+
+@pytest.fixture(scope="session")
+def gpu_free_lib():
+    """The C-ABI library for its host-only entry points (no GPU needed)."""
+    from paper_2108_12430_gb300 import gwstream
+
+    return gwstream.lib()
