@@ -364,6 +364,64 @@ int gw_server_replay(gw_server_t s, int n, const int* ids, const double* t_us, c
 /* Stops the loop after the queued work, frees every stream and the workspace. */
 int gw_server_destroy(gw_server_t s);
 
+/* ---- one scored stream ---------------------------------------------------
+ * The problem statement's call shape for one stream: create a stream with its
+ * window and stride, push a snapshot of new samples, get back the cleaned
+ * strain and the detection score (Methods, "Streaming IaaS": each request
+ * carries floor(f_s / r) = stride new samples and the state stays on the
+ * device; "Data aggregation": the response is the newest cleaned samples;
+ * the end-to-end ensemble of "Offline Deployment": the two detectors'
+ * cleaned strain is resampled, whitened and scored by BBHnet).  It is the
+ * serving loop above with one stream in one slot, so a push computes exactly
+ * what gw_server_submit computes (steps 1-6 there):
+ *   gw_scored_stream_create = gw_server_create (max_streams = max_batch = 1)
+ *                             + gw_server_open(stride);
+ *   gw_scored_stream_push   = gw_server_submit: witness [n_det][n_witness]
+ *                             [stride], strain [n_det][stride] (host FP32,
+ *                             copied before it returns); clean_out
+ *                             [n_det][stride] and score_out (one float) are
+ *                             host buffers written when the ticket
+ *                             completes (they must stay valid until then);
+ *   gw_scored_stream_wait   = gw_server_wait (GW_ETIMEOUT after timeout_us,
+ *                             < 0 = no limit);
+ *   gw_scored_stream_destroy closes the stream and frees the server.
+ * Pushes run in order; up to max_pending may be queued (a push blocks while
+ * all are taken, GW_ETIMEOUT after 10 s).  Arguments and errors otherwise as
+ * gw_server_create / _open / _submit / _wait. */
+typedef struct gw_scored_stream* gw_scored_stream_t;
+int gw_scored_stream_create(gw_ctx_t ctx, const gw_model_t* deepclean, gw_model_t bbhnet, gw_fir_t decimator,
+                            gw_fir_t whitening, int n_det, int n_witness, int window, int stride, int agg_mode,
+                            int agg_delay, int bbh_len, int max_pending, gw_scored_stream_t* out);
+int gw_scored_stream_push(gw_scored_stream_t s, const float* witness, const float* strain, float* clean_out,
+                          float* score_out, uint64_t* ticket);
+int gw_scored_stream_wait(gw_scored_stream_t s, uint64_t ticket, int64_t timeout_us);
+int gw_scored_stream_destroy(gw_scored_stream_t s);
+
+/* ---- stream placement over devices ------------------------------------------
+ * Streams are independent and only each stream's own state update is
+ * sequential (Methods, "Streaming IaaS"), so serving shards by stream with no
+ * collective: each stream lives on one device (one context and server per
+ * device).  gw_partition_streams places n streams on n_dev devices (host only,
+ * no GPU call):
+ *   stride[i]   stride of stream i (its real-time load is proportional to
+ *               1 / stride: snapshots per second at a fixed sample rate);
+ *   bytes[i]    its device state (gw_server_stream_bytes);
+ *   budget[d]   free bytes on device d, or < 0 when the device is not
+ *               available (for example a rank that left);
+ *   current     (may be NULL) the present placement: a stream keeps its
+ *               device while that device is available and has room, so a
+ *               rebalance after a device leaves moves only that device's
+ *               streams;
+ *   device_out  receives the device of every stream (-1: placed nowhere);
+ *   load_out    (n_dev, may be NULL) receives each device's summed 1/stride.
+ * The streams to place go, in decreasing load (ties by index), to the
+ * available device with the least load so far that has room (ties by
+ * index): the placement is a deterministic function of the arguments, so
+ * every rank of a job computes the same one.  GW_EBUDGET when some stream
+ * fits on no device (the others are still placed). */
+int gw_partition_streams(int n, const int* stride, const int64_t* bytes, int n_dev, const int64_t* budget,
+                         const int* current, int* device_out, double* load_out);
+
 /* ---- training ---------------------------------------------------------------
  * DeepClean is retrained regularly on recent data (main text, on the model's
  * validity and retraining; no loss is given).  Loss (a reading): the

@@ -7,7 +7,9 @@
 #include <cmath>
 #include <atomic>
 #include <map>
+#include <map>
 #include <mutex>
+#include <set>
 
 #include "gw_internal.h"
 
@@ -57,6 +59,33 @@ static void prof_clear() {
     cudaEventDestroy(r.b);
   }
   g_prof.clear();
+}
+
+// ---- per-device launch state ----------------------------------------------
+static std::mutex g_dev_mu;
+static std::set<std::pair<int, const void*>> g_smem_limit_set;
+static std::map<int, int> g_sm_count;
+
+void set_smem_limit_once(const void* func, int bytes) {
+  int dev = 0;
+  GW_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  const auto key = std::make_pair(dev, func);
+  if (g_smem_limit_set.count(key)) return;
+  GW_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  g_smem_limit_set.insert(key);
+}
+
+int current_sm_count() {
+  int dev = 0;
+  GW_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_sm_count.find(dev);
+  if (it != g_sm_count.end()) return it->second;
+  int n = 0;
+  GW_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  g_sm_count[dev] = n > 0 ? n : 152;
+  return g_sm_count[dev];
 }
 
 // ---- device memory with a per-context budget ------------------------------
@@ -382,7 +411,7 @@ int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 2048; }
 // blocked BF16 input (ring windows or a converted batch); y gets FP32 [B][y_ld].
 void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1,
                          int* err, cudaStream_t st) {
-  if (in.item_ptr == nullptr && fused_supported(m, L)) {
+  if (fused_supported(m, L)) {
     // the whole network in one launch, activations in shared memory
     Prof p("deepclean_fused", st);
     launch_deepclean_fused(m, in, B, L, y, y_ld, err, st);

@@ -153,6 +153,18 @@ struct Prof {
 void prof_set_capturing(bool on);  // this thread is capturing a CUDA graph
 void add_launches(int64_t n);      // kernels launched by a graph replay
 
+// ---- per-device launch state ----------------------------------------------
+// A kernel's dynamic shared-memory limit is a per-device attribute: it is set
+// once per (device, kernel), on the calling thread's current device, the first
+// time that device launches the kernel.  Thread-safe.
+void set_smem_limit_once(const void* func, int bytes);
+template <typename... A>
+void set_smem_limit_once(void (*func)(A...), int bytes) {
+  set_smem_limit_once(reinterpret_cast<const void*>(func), bytes);
+}
+// Multiprocessor count of the calling thread's current device (cached per device).
+int current_sm_count();
+
 // ---- device memory accounting --------------------------------------------
 void* dev_alloc(gw_ctx* ctx, size_t bytes, size_t* counter);
 void dev_free(gw_ctx* ctx, void* p, size_t bytes, size_t* counter);
@@ -301,8 +313,8 @@ void fused_plan_destroy(FusedPlan* f);
 // True when windows of L samples can run through the fused kernel.
 bool fused_supported(gw_model* m, int L);
 // DeepClean on B windows of L samples: `in` is the first layer's blocked
-// input (ring windows or a converted batch, no per-item table), y gets FP32
-// [B][y_ld].
+// input (ring windows, a converted batch, or per-window addresses in
+// in.item_ptr), y gets FP32 [B][y_ld].
 void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y, int64_t y_ld, int* err,
                             cudaStream_t st);
 

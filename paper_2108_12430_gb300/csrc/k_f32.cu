@@ -217,11 +217,7 @@ void launch_conv_f32(const ConvF32Args& a, cudaStream_t st) {
   while (CI > 1 && (size_t)(CI * span_max + CB * CI * s.k) * 4 > 96 * 1024) CI /= 2;
   if (CI > s.cin) CI = s.cin;
   const size_t smem = (size_t)(CI * span_max + CB * CI * s.k) * 4;
-  static bool attr_set = false;
-  if (!attr_set) {
-    GW_CUDA(cudaFuncSetAttribute(conv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    attr_set = true;
-  }
+  set_smem_limit_once(conv_f32_kernel, 96 * 1024);
   dim3 grid((a.lout + TL - 1) / TL, (s.cout + CB - 1) / CB, a.B);
   conv_f32_kernel<<<grid, kThreads, smem, st>>>(a, CB, CI);
   GW_LAUNCH_CHECK();
@@ -232,11 +228,7 @@ void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int 
   if (x_len < 0) x_len = lout + ntaps - 1;
   const size_t smem = (size_t)(ntaps + kFirTile + ntaps - 1) * 4;
   GW_CHECK_ARG(smem <= 200 * 1024, "FIR too long for the FP32 kernel");
-  static bool attr_set = false;
-  if (!attr_set) {
-    GW_CUDA(cudaFuncSetAttribute(fir_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  set_smem_limit_once(fir_f32_kernel, 200 * 1024);
   dim3 grid((lout + kFirTile - 1) / kFirTile, rows);
   fir_f32_kernel<<<grid, kThreads, smem, st>>>(x, x_row, y, y_row, taps, ntaps, lout, x_off, x_len, rev, scale);
   GW_LAUNCH_CHECK();

@@ -107,6 +107,9 @@ struct FParams {
   // + (x % P0) in_p + (x / P0 + b in_boff) 16 bytes
   const char* in;
   int64_t in_off0, in_b, in_boff, in_g, in_p;
+  // optional per-window addresses of element (b, 0, 0), replacing in + in_off0
+  // + b in_b + b in_boff 16 (the serving loop's windows in many streams' rings)
+  const char* const* item_ptr;
   float* y;
   int64_t y_ld;
   int Lw, T, tiles, n_items;
@@ -398,7 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
         int rm0[kLayers];
         fused_tile_rows(p.T, p.Lw, t, rm0, nullptr, nullptr);
         const int rin0 = rm0[0] + L0::dmin;  // first input row of every plane
-        const char* src0 = p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)rin0 + (int64_t)b * p.in_boff) * 16;
+        const char* src0 = p.item_ptr ? p.item_ptr[b] + (int64_t)rin0 * 16
+                                      : p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)rin0 + (int64_t)b * p.in_boff) * 16;
         const uint32_t dst0 = sm.in0 + (uint32_t)s * p.in_bytes;
         if (lane == 0) mbar_expect_tx(sm.bar(kInFull + s), (uint32_t)(planes * L0::rows) * 16u);
         ++armed[s];
@@ -676,7 +680,7 @@ void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y,
                             cudaStream_t st) {
   FusedPlan* f = m->fused;
   GW_CHECK_ARG(f && fused_supported(m, L), "fused DeepClean does not support this window length");
-  GW_CHECK_ARG(in.P == fz::L0::P && in.item_ptr == nullptr, "fused DeepClean: unexpected input layout");
+  GW_CHECK_ARG(in.P == fz::L0::P, "fused DeepClean: unexpected input layout");
   FParams q = f->q;
   layer_louts(m, L, q.lout);
   q.in = (const char*)in.p;
@@ -685,6 +689,7 @@ void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y,
   q.in_boff = in.boff;
   q.in_g = in.gstride * 2;
   q.in_p = in.pstride * 2;
+  q.item_ptr = reinterpret_cast<const char* const*>(in.item_ptr);
   q.y = y;
   q.y_ld = y_ld;
   q.Lw = L;
@@ -693,12 +698,8 @@ void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y,
   q.n_items = q.tiles * B;
   q.err = err;
   q.stall_test = tc_take_stall_test() ? 1 : 0;
-  int dev = 0, sms = 0;
-  GW_CUDA(cudaGetDevice(&dev));
-  GW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // the attribute is per device: set it on every launch (cheap) rather than
-  // once per process
-  GW_CUDA(cudaFuncSetAttribute(deepclean_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem));
+  const int sms = current_sm_count();
+  set_smem_limit_once(deepclean_fused_kernel, 227 * 1024);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::min(sms, q.n_items));
   cfg.blockDim = dim3(kThreads);

@@ -220,11 +220,7 @@ void launch_serve_whiten(const ServeItem* items, int n, const ServeGeom& g, cons
                          cudaStream_t st) {
   const size_t smem = serve_whiten_smem(K, max_new);
   GW_CHECK_ARG(smem <= 200 * 1024, "whitening FIR too long for the streaming kernel");
-  static bool attr_set = false;
-  if (!attr_set) {
-    GW_CUDA(cudaFuncSetAttribute(serve_whiten_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  set_smem_limit_once(serve_whiten_kernel, 200 * 1024);
   serve_whiten_kernel<<<dim3(1, n), kThreads, smem, st>>>(items, g, taps, K);
   GW_LAUNCH_CHECK();
 }

@@ -460,11 +460,7 @@ void launch_post_sub(const float* pring, int64_t Rp, const float* h, int K, cons
   if (count <= 0) return;
   const size_t smem = (size_t)(2 * K + kPostBlock - 1) * sizeof(float);
   GW_CHECK_ARG(smem <= 200 * 1024, "post-processing FIR too long");
-  static bool attr_set = false;
-  if (!attr_set) {
-    GW_CUDA(cudaFuncSetAttribute(post_sub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  set_smem_limit_once(post_sub_kernel, 200 * 1024);
   post_sub_kernel<<<(count + kPostBlock - 1) / kPostBlock, kPostBlock, smem, st>>>(pring, Rp, h, K, strain_ring, R, t0,
                                                                                  count, out, skip);
   GW_LAUNCH_CHECK();

@@ -658,12 +658,6 @@ __global__ void gap_linear_blocked_kernel(const char* __restrict__ in, int64_t i
 inline int pmod_i(int a, int m) { return ((a % m) + m) % m; }
 inline int floordiv_i(int a, int b) { return (a - pmod_i(a, b)) / b; }
 
-int sm_count() {
-  int dev = 0, n = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return 152;
-  return n > 0 ? n : 152;
-}
 
 }  // namespace
 
@@ -1075,15 +1069,9 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
   TcParams q;
   size_t smem = 0;
   dim3 grid;
-  static int sms = 0;
-  if (!sms) sms = sm_count();
-  plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B, sms);
+  plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B, current_sm_count());
   q.stall_test = tc_take_stall_test() ? 1 : 0;
-  static bool smem_attr = false;
-  if (!smem_attr) {
-    GW_CUDA(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    smem_attr = true;
-  }
+  set_smem_limit_once(conv_tc_kernel, 227 * 1024);
   // programmatic stream serialisation: this launch may begin (set-up, weight
   // loads) while the previous kernel in the stream runs; the kernel waits on
   // griddepcontrol before touching the previous kernels' data

@@ -263,16 +263,12 @@ void launch_wgrad_partial(const WgradArgs& w, int B, cudaStream_t st) {
   GW_CHECK_ARG(w.nj <= kMaxJ, "weight gradient tile too large");
   const size_t smem = wgrad_smem(w);
   GW_CHECK_ARG(smem <= 200 * 1024, "weight gradient tile exceeds shared memory");
-  static bool attr_set = false;
-  if (!attr_set) {
-    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    GW_CUDA(cudaFuncSetAttribute(wgrad_partial_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  set_smem_limit_once(wgrad_partial_kernel<1>, 200 * 1024);
+  set_smem_limit_once(wgrad_partial_kernel<2>, 200 * 1024);
+  set_smem_limit_once(wgrad_partial_kernel<4>, 200 * 1024);
+  set_smem_limit_once(wgrad_partial_kernel<8>, 200 * 1024);
+  set_smem_limit_once(wgrad_partial_kernel<16>, 200 * 1024);
+  set_smem_limit_once(wgrad_partial_kernel<32>, 200 * 1024);
   const int n_chunks = B * w.chunks_per_b;
   dim3 grid(n_chunks, (w.NA + w.AB - 1) / w.AB);
   if (w.nj <= 1)

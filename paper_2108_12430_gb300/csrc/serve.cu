@@ -914,4 +914,79 @@ int gw_server_destroy(gw_server_t s) {
   GW_API_END
 }
 
+// ---- one scored stream (the problem statement's call shape) ---------------------
+// A one-slot server holding one open stream: push = submit, wait = wait.
+struct gw_scored_stream {
+  gw_server_t srv = nullptr;
+  int id = -1;
+};
+
+int gw_scored_stream_create(gw_ctx_t ctx, const gw_model_t* deepclean, gw_model_t bbhnet, gw_fir_t decimator,
+                            gw_fir_t whitening, int n_det, int n_witness, int window, int stride, int agg_mode,
+                            int agg_delay, int bbh_len, int max_pending, gw_scored_stream_t* out) {
+  gw_scored_stream* ss = nullptr;
+  GW_API_BEGIN
+  GW_CHECK_ARG(out, "NULL argument");
+  *out = nullptr;
+  GW_CHECK_ARG(max_pending >= 1 && max_pending <= 4096, "max_pending out of range [1, 4096]");
+  gw_server_desc d{};
+  d.n_det = n_det;
+  d.n_witness = n_witness;
+  d.window = window;
+  d.max_stride = stride;
+  d.max_streams = 1;
+  d.max_batch = 1;
+  d.max_pending = max_pending;
+  d.agg_mode = agg_mode;
+  d.agg_delay = agg_delay;
+  d.bbh_len = bbh_len;
+  d.max_wait_us = 0;
+  d.max_inflight = 2;
+  d.use_graphs = 1;
+  ss = new gw_scored_stream();
+  int rc = gw_server_create(ctx, &d, deepclean, bbhnet, decimator, whitening, &ss->srv);
+  if (rc == GW_OK) {
+    rc = gw_server_open(ss->srv, stride, &ss->id);
+    if (rc != GW_OK) {
+      const std::string msg = gw_last_error();
+      gw_server_destroy(ss->srv);
+      gw::set_last_error(msg);
+    }
+  }
+  if (rc != GW_OK) {
+    delete ss;
+    return rc;  // the message was set by the failing call
+  }
+  *out = ss;
+  GW_API_END
+}
+
+int gw_scored_stream_push(gw_scored_stream_t s, const float* witness, const float* strain, float* clean_out,
+                          float* score_out, uint64_t* ticket) {
+  if (!s) {
+    gw::set_last_error("scored stream is NULL");
+    return GW_EINVAL;
+  }
+  return gw_server_submit(s->srv, s->id, witness, strain, clean_out, score_out, ticket);
+}
+
+int gw_scored_stream_wait(gw_scored_stream_t s, uint64_t ticket, int64_t timeout_us) {
+  if (!s) {
+    gw::set_last_error("scored stream is NULL");
+    return GW_EINVAL;
+  }
+  return gw_server_wait(s->srv, ticket, timeout_us);
+}
+
+int gw_scored_stream_destroy(gw_scored_stream_t s) {
+  if (!s) {
+    gw::set_last_error("scored stream is NULL");
+    return GW_EINVAL;
+  }
+  gw_server_close(s->srv, s->id);
+  const int rc = gw_server_destroy(s->srv);
+  delete s;
+  return rc;
+}
+
 }  // extern "C"

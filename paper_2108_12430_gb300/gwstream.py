@@ -45,6 +45,8 @@ EXPORTS = (
     "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
     "gw_trainer_backward", "gw_fir_create_band_loss", "gw_band_loss", "gw_band_loss_backward", "gw_fir_backward",
     "gw_adam_step", "gw_model_calibrate", "gw_model_test_wait_timeout", "gw_fir_create_bandpass",
+    "gw_scored_stream_create", "gw_scored_stream_push", "gw_scored_stream_wait", "gw_scored_stream_destroy",
+    "gw_partition_streams",
 )
 
 
@@ -146,6 +148,12 @@ def _declare(lib):
         "gw_fir_backward": (I, [P, P, I, I, I, P, P]),
         "gw_adam_step": (I, [P, P, P, P, I64, I, C.c_float, C.c_float, C.c_float, C.c_float, P]),
         "gw_model_calibrate": (I, [P, P, I, I, C.c_float, P, P]),
+        "gw_scored_stream_create": (I, [P, C.POINTER(P), P, P, P, I, I, I, I, I, I, I, I, C.POINTER(P)]),
+        "gw_scored_stream_push": (I, [P, P, P, P, P, C.POINTER(C.c_uint64)]),
+        "gw_scored_stream_wait": (I, [P, C.c_uint64, I64]),
+        "gw_scored_stream_destroy": (I, [P]),
+        "gw_partition_streams": (I, [I, C.POINTER(C.c_int), C.POINTER(C.c_int64), I, C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -379,6 +387,52 @@ def gw_server_submit(s, sid, witness, strain, clean_out, score_out=None):
     _check(lib().gw_server_submit(s, sid, witness.ctypes.data, strain.ctypes.data, clean_out.ctypes.data,
                                   score_out.ctypes.data if score_out is not None else None, C.byref(t)))
     return t.value
+
+
+def gw_scored_stream_create(ctx, deepclean, bbhnet, decimator, whitening, n_witness, window, stride, agg_mode,
+                            agg_delay, bbh_len, max_pending=64):
+    dcs = (P * len(deepclean))(*deepclean)
+    out = P()
+    _check(lib().gw_scored_stream_create(ctx, dcs, bbhnet, decimator, whitening, len(deepclean), n_witness, window,
+                                         stride, agg_mode, agg_delay, bbh_len, max_pending, C.byref(out)))
+    return out
+
+
+def gw_scored_stream_push(s, witness, strain, clean_out, score_out):
+    """witness [n_det][C][S], strain [n_det][S], clean_out [n_det][S], score_out [1]: float32 numpy arrays that
+    must stay alive until gw_scored_stream_wait returns for the ticket."""
+    for a in (witness, strain, clean_out, score_out):
+        assert a.dtype == np.float32 and a.flags.c_contiguous
+    t = C.c_uint64()
+    _check(lib().gw_scored_stream_push(s, witness.ctypes.data, strain.ctypes.data, clean_out.ctypes.data,
+                                       score_out.ctypes.data, C.byref(t)))
+    return t.value
+
+
+def gw_scored_stream_wait(s, ticket, timeout_us=-1):
+    _check(lib().gw_scored_stream_wait(s, ticket, timeout_us))
+
+
+def gw_scored_stream_destroy(s):
+    _check(lib().gw_scored_stream_destroy(s))
+
+
+def gw_partition_streams(strides, bytes_, budgets, current=None, check=True):
+    """Placement of streams on devices (host only): returns (status, device per stream, load per device)."""
+    strides = np.ascontiguousarray(strides, np.int32)
+    bytes_ = np.ascontiguousarray(bytes_, np.int64)
+    budgets = np.ascontiguousarray(budgets, np.int64)
+    n, nd = strides.size, budgets.size
+    out = np.zeros(n, np.int32)
+    load = np.zeros(nd, np.float64)
+    cur = None if current is None else np.ascontiguousarray(current, np.int32)
+    ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+    rc = lib().gw_partition_streams(n, ip(strides), bytes_.ctypes.data_as(C.POINTER(C.c_int64)), nd,
+                                    budgets.ctypes.data_as(C.POINTER(C.c_int64)), ip(cur) if cur is not None else None,
+                                    ip(out), load.ctypes.data_as(C.POINTER(C.c_double)))
+    if check and rc not in (GW_OK, GW_EBUDGET):
+        _check(rc)
+    return rc, out, load
 
 
 def gw_server_wait(s, ticket, timeout_us=-1):

@@ -42,10 +42,12 @@ def _asd(x):
 
 def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1000, lr=1e-3, batch=32,
                               train_len=8192, window_s=8, stride=256, deltas_s=(0.0, 0.5, 0.75),
-                              precision=G.GW_FP32, post_taps=0):
+                              precision=G.GW_FP32, post_taps=0, return_series=False):
     """Runs the study; returns a dict of the training losses, the offline ASD
     ratio near 60 Hz and outside the band, and per aggregation latency the
-    fraction of [50, 70] Hz bins off the offline ratio by more than 10%."""
+    fraction of [50, 70] Hz bins off the offline ratio by more than 10%.
+    return_series: also the raw, offline-cleaned and online-cleaned series
+    over the span the spectra are taken on (key "series")."""
     import torch
     C = 21
     W = window_s * FS
@@ -116,6 +118,7 @@ def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1
         # spectra over a common span: the offline segment's own padded ends
         # and the FIR's edges are excluded
         lo, hi = 2 * FS + c, n_ev - 2 * FS - c
+        series = {"raw": raw[lo:hi], "offline": offline[lo:hi], "online": {}}
         f, a_raw = _asd(raw[lo:hi])
         _, a_off = _asd(offline[lo:hi])
         rat_off = a_off / a_raw
@@ -145,12 +148,15 @@ def aggregation_latency_study(device=0, seed=11, train_s=192, eval_s=64, steps=1
                 k += 1
             G.gw_stream_destroy(sm)
             on = cleaned[W:W + n_ev].astype(np.float64)
+            series["online"][f"{dsec:g}s"] = on[lo:hi]
             _, a_on = _asd(on[lo:hi])
             rat_on = a_on / a_raw
             per[f"{dsec:g}s"] = {
                 "frac_50_70Hz_off_by_10pct": float(np.mean(np.abs(rat_on[band] / rat_off[band] - 1) > 0.1)),
                 "ratio_59_61Hz": float(rat_on[line].mean())}
         out["online"] = per
+        if return_series:
+            out["series"] = series
         if post:
             G.gw_fir_destroy(post)
         G.gw_model_destroy(m)

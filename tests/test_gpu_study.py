@@ -3,15 +3,32 @@ latency"): DeepClean trained with the library's training step on synthetic
 60 Hz coupling removes the coupled noise, and in the causal online scheme an
 aggregation latency away from the window edge reproduces the offline
 subtraction while zero latency does not."""
+import numpy as np
 import pytest
 
+from oracle import spectral
 from paper_2108_12430_gb300 import study
 
 pytestmark = pytest.mark.gpu
 
 
+def check_metrics_against_oracle(r):
+    # the study's spectral arithmetic restated by the oracle (Welch ASD ratio
+    # and the fraction of [50, 70] Hz bins off by more than 10%) on the very
+    # series the study measured
+    ser = r.pop("series")
+    f, rat_off = spectral.asd_ratio(ser["offline"], ser["raw"], 4096.0)
+    line = (f >= 59) & (f <= 61)
+    assert abs(rat_off[line].mean() - r["offline_ratio_59_61Hz"]) <= 1e-9 * abs(r["offline_ratio_59_61Hz"])
+    for key, on in ser["online"].items():
+        _, rat_on = spectral.asd_ratio(on, ser["raw"], 4096.0)
+        assert spectral.frac_bins_off(rat_on, rat_off, f) == r["online"][key]["frac_50_70Hz_off_by_10pct"]
+        assert abs(rat_on[line].mean() - r["online"][key]["ratio_59_61Hz"]) <= 1e-9
+
+
 def test_aggregation_latency_study():
-    r = study.aggregation_latency_study(train_s=128, eval_s=48, steps=800)
+    r = study.aggregation_latency_study(train_s=128, eval_s=48, steps=800, return_series=True)
+    check_metrics_against_oracle(r)
     # training: the band-limited loss falls by two orders of magnitude
     assert r["loss_last"] < r["loss_first"] / 100
     # offline cleaning: the 60 Hz coupling (band SNR 20) is removed, the band
@@ -31,7 +48,8 @@ def test_study_with_post_processing():
     # with the 55-65 Hz band-pass on the prediction (as the paper's online
     # pipeline post-processes the noise estimate before subtracting it) the
     # out-of-band spectrum is left alone while the 60 Hz coupling is removed
-    r = study.aggregation_latency_study(train_s=128, eval_s=48, steps=800, post_taps=2049)
+    r = study.aggregation_latency_study(train_s=128, eval_s=48, steps=800, post_taps=2049, return_series=True)
+    check_metrics_against_oracle(r)
     assert r["offline_ratio_59_61Hz"] < 0.2
     assert 0.95 < r["offline_ratio_80_200Hz"] < 1.05
     assert 0.95 < r["offline_ratio_20_45Hz"] < 1.05
