@@ -23,19 +23,24 @@
 // input is copied by bulk copies from the blocked BF16 input (a stream's
 // ring: every window is a view), the last layer writes the FP32 prediction.
 //
-// Scheduling.  One persistent CTA per SM takes its items two at a time and
-// runs the pair in step, layer by layer: while the epilogue warps drain item
-// A's accumulator of layer l the MMA thread issues item B's layer l, and
-// while B is drained A's layer l + 1 is issued, so the tensor pipe works
-// during the epilogues.  Both items use the same weights: a layer's B-operand
-// image is streamed from global memory in chunks of whole K-steps through a
-// 4-stage ring, each chunk read by both items before it is released.
+// Scheduling.  One persistent CTA per SM keeps kSlots items in flight, one
+// per slot, each with its own TMEM accumulator, MMA-issuing thread and
+// epilogue warps: while one slot's epilogue drains its accumulator of layer
+// l, the other slots' MMAs keep the tensor pipe busy.  An item's activations
+// live in one buffer per slot, rewritten in place layer after layer (a
+// layer's epilogue runs only once all of the layer's MMAs, the buffer's
+// readers, have completed); the first layer's inputs, three times larger,
+// have two buffers that the CTA's items use in turn.  The CTA takes its items
+// in rounds of kSlots, all with the same weights: a layer's B-operand image
+// is streamed from global memory in chunks of whole K-steps through a 4-stage
+// ring, each chunk released once every slot has read it.
 //
-// Warps: 0 stages the input of the next items (bulk copies, zero rows at the
-// window edges), 10 streams the weight chunks, 1 issues the MMAs from one
-// thread into two TMEM accumulators (one per item), 2-9 drain TMEM (bias,
-// tanh, BF16 rounding) into the next layer's buffer.  Every wait is bounded
-// (about 1 s); on timeout the kernel records an error bit and unwinds.
+// Warps: 0 stages the first-layer input of the next items (bulk copies, zero
+// rows at the window edges), 1 streams the weight chunks, one warp per slot
+// issues its MMAs from one thread, and kEpiW warps per slot (one per TMEM lane
+// quarter) drain the accumulator (bias, tanh, BF16 rounding) into the slot's
+// buffer.  Every wait is bounded (about 1 s); on timeout the kernel records an
+// error bit and unwinds.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -55,13 +60,26 @@ constexpr int kTileT = 864;        // output samples per item
 constexpr int kRowsM = 128;        // MMA rows per layer and item
 constexpr int kWStages = 4;        // weight ring
 constexpr int kWChunk = 12288;     // bytes per weight chunk (whole K-steps of one layer)
-constexpr int kEpi = 8;            // epilogue warps per item slot
-// warps: 0 input producer, 1 and 3 + 2 kEpi MMA issue (item slots 0 and 1),
-// 2 .. 1 + 2 kEpi epilogue (kEpi per slot), 2 + 2 kEpi weight producer
-constexpr int kThreads = 32 * (4 + 2 * kEpi);
-constexpr int kWarpWeights = 2 + 2 * kEpi, kWarpMma1 = 3 + 2 * kEpi;
+#ifndef GW_FUSED_SLOTS
+#define GW_FUSED_SLOTS 4
+#endif
+constexpr int kSlots = GW_FUSED_SLOTS;  // items in flight per CTA
+constexpr int kInBufs = 2;         // first-layer input buffers, used by the CTA's items in turn
+constexpr int kEpiW = 4;           // epilogue warps per slot, one per TMEM lane quarter
+// warps: 0 input producer, 1 weight producer, 2-3 MMA issue of slots 0-1,
+// 4 .. 3 + kSlots kEpiW epilogue (kEpiW per slot, in slot order), then MMA
+// issue of slots 2 .. kSlots - 1
+constexpr int kWarpIn = 0, kWarpWeights = 1, kWarpEpi0 = 4, kWarpMmaHi = kWarpEpi0 + kSlots * kEpiW;
+constexpr int kThreads = 32 * (kWarpMmaHi + kSlots - 2);
 constexpr int kAccCols = 64;       // TMEM columns per item accumulator
+constexpr int kTmemCols = kSlots * kAccCols <= 128 ? 128 : 256;
+static_assert(kSlots >= 2 && kSlots * kAccCols <= 256, "slots");
+static_assert(kWarpEpi0 % 4 == 0 && kEpiW == 4, "an epilogue warp's TMEM lane quarter is its warp index mod 4");
 constexpr int kZeroRowsF = 256;
+// Copies of the weight image in global memory: every CTA streams the same
+// chunks at about the same time, and with one copy all of them would queue on
+// the same L2 lines; CTA i reads copy i mod kWReps.
+constexpr int kWReps = 16;
 constexpr int kErrIn = 1, kErrW = 2, kErrAcc = 4, kErrAct = 8, kErrEmpty = 16, kErrDrain = 32;
 
 // the layer tables (fused_tables.h) by index
@@ -100,7 +118,8 @@ __device__ __align__(128) uint4 g_zero_rows_f[kZeroRowsF];
 struct FParams {
   uint32_t chunk_off[fz::kChunks];   // byte offset of each weight chunk in wimg
   uint32_t chunk_bytes[fz::kChunks];
-  const char* wimg;
+  const char* wimg;                  // kWReps copies, wimg_stride bytes apart
+  uint32_t wimg_stride;
   const float* bias;                 // kBiasCount floats
   int lout[kLayers];                 // output length of every layer for this window length
   // input: element (b, c, x) of window b at in + in_off0 + b in_b + (c / 8) in_g
@@ -177,14 +196,20 @@ struct Smem {
   volatile uint32_t* abort_flag;
   int* err;
   __device__ uint32_t bar(int i) const { return smem_u32(&bars[i]); }
-  // activation buffer of item slot s: X (read by odd layers) or Y (even layers >= 2)
-  __device__ uint32_t act(int s, int xy) const { return act0 + (uint32_t)(2 * s + xy) * act_bytes; }
-  __device__ uint32_t input(int s, int l) const {
-    return l == 0 ? in0 + (uint32_t)s * in_bytes : act(s, (l & 1) ? 0 : 1);
-  }
+  // the activation buffer of slot s (the input of layers 1-7, in their layouts)
+  __device__ uint32_t act(int s) const { return act0 + (uint32_t)s * act_bytes; }
+  // first-layer input buffer i
+  __device__ uint32_t input(int i) const { return in0 + (uint32_t)i * in_bytes; }
 };
-enum { kInFull = 0, kInEmpty = 2, kWFull = 4, kWEmpty = 4 + kWStages, kAccFull = 4 + 2 * kWStages,
-       kActReady = kAccFull + 2, kDrain = kActReady + 2, kNBars = kDrain + 2 };
+// The input barriers: full per slot (a slot waits for its items' inputs in
+// order, whichever buffer they are in; a barrier per buffer would let a slot
+// wait for the buffer's next phase while its current one, another slot's
+// item, is still pending, which a parity wait cannot tell apart), empty per
+// buffer (only the producer waits on those, in order).
+enum { kInFull = 0, kInEmpty = kInFull + kSlots, kWFull = kInEmpty + kInBufs, kWEmpty = kWFull + kWStages,
+       kAccFull = kWEmpty + kWStages, kActReady = kAccFull + kSlots, kDrain = kActReady + kSlots,
+       kNBars = kDrain + kSlots };
+
 
 // Descriptor words: low = start address >> 4 (14 bits) | LBO >> 4 << 16, high
 // = SBO >> 4 (128 bytes) | the fixed 0b001 at bit 46.  Start addresses stay
@@ -192,19 +217,20 @@ enum { kInFull = 0, kInEmpty = 2, kWFull = 4, kWEmpty = 4 + kWStages, kAccFull =
 // into the LBO field.
 constexpr uint32_t kDescHi = (128u >> 4) | (1u << 14);
 
-// MMAs of layer l for item slot s of pair k, issued by the slot's own thread
-// from the compile-time step table: the A operand of a step is a slice of the
-// slot's input buffer, the B operand the step's rows of the weight chunk in
-// the ring.  Every chunk is released by both slots' threads (its empty barrier
-// counts two arrivals), each committing after its last MMA on the chunk.
+// MMAs of layer l for the item of round k in one slot, issued by the slot's
+// own thread from the compile-time step table: the A operand of a step is a
+// slice of the input buffer at a_addr, the B operand the step's rows of the
+// weight chunk in the ring.  Every chunk is released by all slots' threads
+// (its empty barrier counts kSlots arrivals), each committing after its last
+// MMA on the chunk.
 template <int l>
-__device__ __forceinline__ bool issue_layer(const Smem& sm, uint32_t d, int k, int s) {
+__device__ __forceinline__ bool issue_layer(const Smem& sm, uint32_t d, int k, uint32_t a_addr) {
   using F = typename Lay<l>::T;
   constexpr uint32_t b_lbo = (((uint32_t)F::npad * 16u) >> 4) << 16;
   constexpr uint32_t idesc = idesc_for(F::npad);
   constexpr uint32_t b_step = (uint32_t)F::step_bytes >> 4;
   const uint64_t hi = (uint64_t)kDescHi << 32;
-  const uint32_t a_base = sm.input(s, l) >> 4;
+  const uint32_t a_base = a_addr >> 4;
 #pragma unroll
   for (int c = 0; c < F::n_chunks; ++c) {
     const int g = k * fz::kChunks + F::chunk0 + c, st = g % kWStages, use = g / kWStages;
@@ -220,40 +246,48 @@ __device__ __forceinline__ bool issue_layer(const Smem& sm, uint32_t d, int k, i
   return true;
 }
 
+// Layer l of the CTA's item j (round k) in slot s.
 template <int l>
-__device__ __forceinline__ bool mma_layer(const Smem& sm, uint32_t tmem, int k, int s, int& act_ph) {
+__device__ __forceinline__ bool mma_layer(const Smem& sm, uint32_t tmem, int k, int j, int s, int& act_ph) {
   // the layer's input is in place, and the slot's accumulator has been
-  // drained by the epilogue (of the previous layer, or of the previous pair's
-  // last layer)
+  // drained by the epilogue (of the previous layer, or of the slot's previous
+  // item's last layer; that epilogue has also finished with the slot's
+  // activation buffer, which the first layer's epilogue rewrites)
+  const int ib = j % kInBufs;
   if (l == 0 && !mbar_spin(sm.bar(kInFull + s), (uint32_t)k & 1u, sm.abort_flag, sm.err, kErrIn)) return false;
   if (l > 0 || k > 0) {
     if (!mbar_spin(sm.bar(kActReady + s), (uint32_t)act_ph & 1u, sm.abort_flag, sm.err, kErrAct)) return false;
     ++act_ph;
   }
   tc_fence_after();
-  if (!issue_layer<l>(sm, tmem + (uint32_t)(s * kAccCols), k, s)) return false;
+  if (!issue_layer<l>(sm, tmem + (uint32_t)(s * kAccCols), k, l == 0 ? sm.input(ib) : sm.act(s))) return false;
   mma_commit(sm.bar(kAccFull + s));
-  if (l == 0) mma_commit(sm.bar(kInEmpty + s));
+  if (l == 0) mma_commit(sm.bar(kInEmpty + ib));
   return true;
 }
 
 // Epilogue of one 32-column chunk of layer l (l < 7) for MMA row R (absolute):
-// bias, tanh, bf16, written into the next layer's input buffer at its phase
-// plane and row; positions outside the layer's output are the next layer's
-// zero padding.
+// bias, tanh, bf16, written into the slot's buffer, in the next layer's
+// layout, at its phase plane and row; positions outside the layer's output
+// are the next layer's zero padding.
 template <int l>
 __device__ __forceinline__ void epi_hidden(const float (&v)[32], int half, int R, int rin0_next, uint32_t out_buf,
                                            int lout, const float* s_bias) {
   using F = typename Lay<l>::T;
   using N = typename Lay<l + 1>::T;
+  // An MMA row of layer l holds Q consecutive outputs, and the next layer has
+  // Q phase planes: the row's outputs land in one row of every plane.
+  static_assert(F::Q == N::P, "output folding and next-layer phases differ");
+  const int rn = R - rin0_next;  // that row of the next layer's buffer
+  if ((unsigned)rn >= (unsigned)N::rows) return;
+  const int u0 = R * F::Q;  // the row's first output position
+  const bool all_in = u0 >= 0 && u0 + F::Q <= lout;
+  const uint32_t row_addr = out_buf + ((uint32_t)rn << 4);
 #pragma unroll
   for (int h = 0; h < 4; ++h) {
     const int n0 = half * 32 + h * 8;
     const int sg = n0 >> F::lgcoutp, o0 = n0 & (F::coutp - 1);
-    const int u = (R << F::lgQ) + sg;
-    const int rn = (u >> N::lgP) - rin0_next;
-    if ((unsigned)rn >= (unsigned)N::rows) continue;
-    const bool in_range = u >= 0 && u < lout;
+    const bool in_range = all_in || (u0 + sg >= 0 && u0 + sg < lout);
     const float4 b0 = *reinterpret_cast<const float4*>(s_bias + BiasOff<l>::v + o0);
     const float4 b1 = *reinterpret_cast<const float4*>(s_bias + BiasOff<l>::v + o0 + 4);
     uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
@@ -263,8 +297,7 @@ __device__ __forceinline__ void epi_hidden(const float (&v)[32], int half, int R
       w2 = pack_bf16x2(tanh_fast(v[h * 8 + 4] + b1.x), tanh_fast(v[h * 8 + 5] + b1.y));
       w3 = pack_bf16x2(tanh_fast(v[h * 8 + 6] + b1.z), tanh_fast(v[h * 8 + 7] + b1.w));
     }
-    const uint32_t addr =
-        out_buf + ((uint32_t)((((o0 >> 3) * N::P + (u & (N::P - 1))) * N::rows + rn)) << 4);
+    const uint32_t addr = row_addr + ((uint32_t)(((o0 >> 3) * N::P + sg) * N::rows) << 4);
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w0), "r"(w1), "r"(w2), "r"(w3)
                  : "memory");
   }
@@ -283,15 +316,14 @@ __device__ __forceinline__ bool epi_bar_and(int s, bool ok) {
   asm volatile(
       "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}"
       : "=r"(r)
-      : "r"((uint32_t)ok), "r"(1 + s), "n"(32 * kEpi)
+      : "r"((uint32_t)ok), "r"(1 + s), "n"(32 * kEpiW)
       : "memory");
   return r != 0;
 }
 
 template <int l>
-__device__ __forceinline__ bool epi_layer(const FParams& p, const Smem& sm, uint32_t tmem, int quarter, int half,
-                                          int lane, int s, bool poller, const EpiItem& e, int& acc_ph,
-                                          const float* s_bias) {
+__device__ __forceinline__ bool epi_layer(const FParams& p, const Smem& sm, uint32_t tmem, int quarter, int lane,
+                                          int s, bool poller, const EpiItem& e, int& acc_ph, const float* s_bias) {
   using F = typename Lay<l>::T;
   const int row = quarter * 32 + lane;  // MMA row = TMEM lane
   bool ok = true;
@@ -299,15 +331,15 @@ __device__ __forceinline__ bool epi_layer(const FParams& p, const Smem& sm, uint
   if (!epi_bar_and(s, ok)) return false;
   ++acc_ph;
   tc_fence_after();
-  if (half * 32 < F::npad) {
+  const int R = e.rm0[l] + row;
+#pragma unroll
+  for (int half = 0; half * 32 < F::npad; ++half) {
     float v[32];
     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * kAccCols + half * 32), v);
-    const int R = e.rm0[l] + row;
     if constexpr (l + 1 < kLayers) {
       using N = typename Lay<l + 1>::T;
       const int rin0 = e.rm0[l + 1] + N::dmin;
-      const uint32_t out_buf = sm.act(s, (l & 1) ? 1 : 0);  // layer l + 1 reads X when it is odd
-      epi_hidden<l>(v, half, R, rin0, out_buf, p.lout[l], s_bias);
+      epi_hidden<l>(v, half, R, rin0, sm.act(s), p.lout[l], s_bias);
     } else {
       // output layer: one channel, Q positions per row -> FP32 prediction
       const int lo = e.t * p.T, hi2 = min(lo + p.T, p.Lw);
@@ -332,13 +364,13 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t base = smem_u32(smem);
-  // [IN 0][IN 1][X 0][Y 0][X 1][Y 1][W ring][barriers, flags, bias]
+  // [IN 0][IN 1][ACT 0 .. ACT kSlots-1][W ring][barriers, flags, bias]
   Smem sm;
   sm.in0 = base;
   sm.in_bytes = p.in_bytes;
   sm.act_bytes = p.act_bytes;
-  sm.act0 = base + 2 * p.in_bytes;
-  sm.w = sm.act0 + 4 * p.act_bytes;
+  sm.act0 = base + kInBufs * p.in_bytes;
+  sm.w = sm.act0 + kSlots * p.act_bytes;
   sm.bars = reinterpret_cast<uint64_t*>(smem + (sm.w - base) + kWStages * kWChunk);
   sm.abort_flag = reinterpret_cast<volatile uint32_t*>(sm.bars + kNBars);
   sm.err = p.err;
@@ -347,18 +379,17 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kInBufs; ++i) mbar_init(sm.bar(kInEmpty + i), 1);
+    for (int i = 0; i < kSlots; ++i) {
       mbar_init(sm.bar(kInFull + i), 1);
-      mbar_init(sm.bar(kInEmpty + i), 1);
       mbar_init(sm.bar(kAccFull + i), 1);
-      mbar_init(sm.bar(kActReady + i), kEpi);
+      mbar_init(sm.bar(kActReady + i), kEpiW);
+      mbar_init(sm.bar(kDrain + i), 1);
     }
     for (int i = 0; i < kWStages; ++i) {
       mbar_init(sm.bar(kWFull + i), 1);
-      mbar_init(sm.bar(kWEmpty + i), 2);  // released by both item slots
+      mbar_init(sm.bar(kWEmpty + i), kSlots);  // released by every slot
     }
-    mbar_init(sm.bar(kDrain), 1);
-    mbar_init(sm.bar(kDrain + 1), 1);
     *sm.abort_flag = 0u;
     fence_barrier_init();
   }
@@ -367,13 +398,13 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
   // non-finite value there would still poison them through the zero weights.
   {
     uint4* a = reinterpret_cast<uint4*>(smem + (sm.act0 - base));
-    const int n16 = (int)(4 * p.act_bytes / 16);
+    const int n16 = (int)(kSlots * p.act_bytes / 16);
     for (int i = tid; i < n16; i += kThreads) a[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   for (int i = tid; i < kBiasCount; i += kThreads) s_bias[i] = p.bias[i];
 
   fence_proxy_async_smem();
-  if (warp == 1) tmem_alloc(smem_u32(tslot), 2 * kAccCols);
+  if (warp == 2) tmem_alloc(smem_u32(tslot), kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -382,63 +413,64 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
 
   const int G = gridDim.x;
   const int my_items = p.n_items > (int)blockIdx.x ? (p.n_items - (int)blockIdx.x + G - 1) / G : 0;
-  const int n_pairs = (my_items + 1) / 2;
+  const int n_rounds = (my_items + kSlots - 1) / kSlots;  // item j of the CTA: round j / kSlots, slot j % kSlots
+  const int mma_slot = warp == 2 ? 0 : warp == 3 ? 1 : warp >= kWarpMmaHi ? 2 + (warp - kWarpMmaHi) : -1;
 
-  if (warp == 0) {
+  if (warp == kWarpIn) {
     // ---------------- input producer: the first layer's buffer of each item ----------------
     using L0 = fz::L0;
     constexpr int planes = L0::G * L0::P;
     griddep_wait();  // the input is written by the previous kernel (ring update)
-    int armed[2] = {0, 0};  // phases of the input barriers armed per slot
-    for (int k = 0; k < n_pairs; ++k) {
-      for (int s = 0; s < 2; ++s) {
-        const int j = 2 * k + s;
-        if (j >= my_items) break;
-        if (k >= 1 && !mbar_wait(sm.bar(kInEmpty + s), (uint32_t)(k - 1) & 1u, sm.abort_flag, p.err, kErrEmpty)) break;
-        if (p.stall_test && blockIdx.x == 0 && j == 0) continue;  // no arrival and no copy: nothing in flight
-        const int item = (int)blockIdx.x + j * G;
-        const int b = item / p.tiles, t = item - b * p.tiles;
-        int rm0[kLayers];
-        fused_tile_rows(p.T, p.Lw, t, rm0, nullptr, nullptr);
-        const int rin0 = rm0[0] + L0::dmin;  // first input row of every plane
-        const char* src0 = p.item_ptr ? p.item_ptr[b] + (int64_t)rin0 * 16
-                                      : p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)rin0 + (int64_t)b * p.in_boff) * 16;
-        const uint32_t dst0 = sm.in0 + (uint32_t)s * p.in_bytes;
-        if (lane == 0) mbar_expect_tx(sm.bar(kInFull + s), (uint32_t)(planes * L0::rows) * 16u);
-        ++armed[s];
-        __syncwarp();
-        for (int plane = lane; plane < planes; plane += 32) {
-          const int g = plane / L0::P, phi = plane - g * L0::P;
-          const int plen = (p.Lw - phi + L0::P - 1) / L0::P;  // rows of this plane inside the window
-          const int r0 = min(L0::rows, max(0, -rin0)), r1 = max(r0, min(L0::rows, plen - rin0));
-          const uint32_t dst = dst0 + (uint32_t)(plane * L0::rows) * 16u;
-          const char* src = src0 + (int64_t)g * p.in_g + (int64_t)phi * p.in_p;
-          if (r0 > 0) bulk_g2s(dst, g_zero_rows_f, (uint32_t)r0 * 16u, sm.bar(kInFull + s));
-          if (r1 > r0)
-            bulk_g2s(dst + (uint32_t)r0 * 16u, src + (int64_t)r0 * 16, (uint32_t)(r1 - r0) * 16u, sm.bar(kInFull + s));
-          if (L0::rows > r1)
-            bulk_g2s(dst + (uint32_t)r1 * 16u, g_zero_rows_f, (uint32_t)(L0::rows - r1) * 16u, sm.bar(kInFull + s));
-        }
-        __syncwarp();
+    // per slot: whether an input phase was armed, and the parity of the last one
+    uint32_t armed_any = 0u, armed_par = 0u;
+    for (int j = 0; j < my_items; ++j) {
+      const int ib = j % kInBufs, use = j / kInBufs;
+      if (use >= 1 && !mbar_wait(sm.bar(kInEmpty + ib), (uint32_t)(use - 1) & 1u, sm.abort_flag, p.err, kErrEmpty))
+        break;
+      if (p.stall_test && blockIdx.x == 0 && j == 0) continue;  // no arrival and no copy: nothing in flight
+      const int item = (int)blockIdx.x + j * G;
+      const int b = item / p.tiles, t = item - b * p.tiles;
+      int rm0[kLayers];
+      fused_tile_rows(p.T, p.Lw, t, rm0, nullptr, nullptr);
+      const int rin0 = rm0[0] + L0::dmin;  // first input row of every plane
+      const char* src0 = p.item_ptr ? p.item_ptr[b] + (int64_t)rin0 * 16
+                                    : p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)rin0 + (int64_t)b * p.in_boff) * 16;
+      const int slot = j % kSlots;
+      const uint32_t full = sm.bar(kInFull + slot), dst0 = sm.input(ib);
+      if (lane == 0) mbar_expect_tx(full, (uint32_t)(planes * L0::rows) * 16u);
+      armed_any |= 1u << slot;
+      armed_par = (armed_par & ~(1u << slot)) | ((uint32_t)(j / kSlots) & 1u) << slot;
+      __syncwarp();
+      for (int plane = lane; plane < planes; plane += 32) {
+        const int g = plane / L0::P, phi = plane - g * L0::P;
+        const int plen = (p.Lw - phi + L0::P - 1) / L0::P;  // rows of this plane inside the window
+        const int r0 = min(L0::rows, max(0, -rin0)), r1 = max(r0, min(L0::rows, plen - rin0));
+        const uint32_t dst = dst0 + (uint32_t)(plane * L0::rows) * 16u;
+        const char* src = src0 + (int64_t)g * p.in_g + (int64_t)phi * p.in_p;
+        if (r0 > 0) bulk_g2s(dst, g_zero_rows_f, (uint32_t)r0 * 16u, full);
+        if (r1 > r0) bulk_g2s(dst + (uint32_t)r0 * 16u, src + (int64_t)r0 * 16, (uint32_t)(r1 - r0) * 16u, full);
+        if (L0::rows > r1) bulk_g2s(dst + (uint32_t)r1 * 16u, g_zero_rows_f, (uint32_t)(L0::rows - r1) * 16u, full);
       }
+      __syncwarp();
       if (*sm.abort_flag) break;
     }
-    // the copies of the last armed phase of each slot have landed
+    // the copies of the last armed phase of each slot's barrier have landed
     if (lane == 0)
-      for (int s = 0; s < 2; ++s)
-        if (armed[s]) mbar_wait_landed(sm.bar(kInFull + s), (uint32_t)(armed[s] - 1) & 1u, p.err, kErrDrain);
+      for (int i = 0; i < kSlots; ++i)
+        if (armed_any >> i & 1u) mbar_wait_landed(sm.bar(kInFull + i), armed_par >> i & 1u, p.err, kErrDrain);
     __syncwarp();
   } else if (warp == kWarpWeights) {
-    // ---------------- weight producer: the layers' chunks, once per pair ----------------
+    // ---------------- weight producer: the layers' chunks, once per round ----------------
     if (lane == 0) {
+      const char* wsrc = p.wimg + (size_t)(blockIdx.x % kWReps) * p.wimg_stride;
       int issued = 0;  // chunks whose copies were started
-      for (int k = 0; k < n_pairs && !*sm.abort_flag; ++k) {
+      for (int k = 0; k < n_rounds && !*sm.abort_flag; ++k) {
         for (int c = 0; c < fz::kChunks; ++c) {
           const int g = k * fz::kChunks + c, st = g % kWStages, use = g / kWStages;
           if (use >= 1 && !mbar_wait(sm.bar(kWEmpty + st), (uint32_t)(use - 1) & 1u, sm.abort_flag, p.err, kErrEmpty))
             break;
           mbar_expect_tx(sm.bar(kWFull + st), p.chunk_bytes[c]);
-          bulk_g2s(sm.w + (uint32_t)st * kWChunk, p.wimg + p.chunk_off[c], p.chunk_bytes[c], sm.bar(kWFull + st));
+          bulk_g2s(sm.w + (uint32_t)st * kWChunk, wsrc + p.chunk_off[c], p.chunk_bytes[c], sm.bar(kWFull + st));
           issued = g + 1;
         }
       }
@@ -447,32 +479,30 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
         if (g >= 0) mbar_wait_landed(sm.bar(kWFull + g % kWStages), (uint32_t)(g / kWStages) & 1u, p.err, kErrDrain);
     }
     __syncwarp();
-  } else if (warp == 1 || warp == kWarpMma1) {
-    // ---------------- MMA issue: one thread per item slot ----------------
-    const int s = warp == 1 ? 0 : 1;
+  } else if (mma_slot >= 0) {
+    // ---------------- MMA issue: one thread per slot ----------------
+    const int s = mma_slot;
     if (lane == 0) {
       int act_ph = 0;  // act_ready phases consumed
-      for (int k = 0; k < n_pairs; ++k) {
-        if (2 * k + s >= my_items) {
-          // no item in this slot (the last pair of an odd count): release the
-          // pair's weight chunks in order, each once it has been loaded (so
-          // that the arrival counts toward that chunk's phase)
+      for (int k = 0; k < n_rounds; ++k) {
+        const int j = k * kSlots + s;
+        if (j >= my_items) {
+          // no item in this slot (the last round): release the round's weight
+          // chunks in order, each once it has been loaded (so that the
+          // arrival counts toward that chunk's phase)
           bool ok = true;
-          for (int c = 0; c < fz::kChunks; ++c) {
+          for (int c = 0; c < fz::kChunks && ok; ++c) {
             const int g = k * fz::kChunks + c, st = g % kWStages, use = g / kWStages;
-            if (!mbar_wait(sm.bar(kWFull + st), (uint32_t)use & 1u, sm.abort_flag, p.err, kErrW)) {
-              ok = false;
-              break;
-            }
-            mbar_arrive(sm.bar(kWEmpty + st));
+            ok = mbar_wait(sm.bar(kWFull + st), (uint32_t)use & 1u, sm.abort_flag, p.err, kErrW);
+            if (ok) mbar_arrive(sm.bar(kWEmpty + st));
           }
           if (!ok) break;
           continue;
         }
-        if (!mma_layer<0>(sm, tmem, k, s, act_ph) || !mma_layer<1>(sm, tmem, k, s, act_ph) ||
-            !mma_layer<2>(sm, tmem, k, s, act_ph) || !mma_layer<3>(sm, tmem, k, s, act_ph) ||
-            !mma_layer<4>(sm, tmem, k, s, act_ph) || !mma_layer<5>(sm, tmem, k, s, act_ph) ||
-            !mma_layer<6>(sm, tmem, k, s, act_ph) || !mma_layer<7>(sm, tmem, k, s, act_ph))
+        if (!mma_layer<0>(sm, tmem, k, j, s, act_ph) || !mma_layer<1>(sm, tmem, k, j, s, act_ph) ||
+            !mma_layer<2>(sm, tmem, k, j, s, act_ph) || !mma_layer<3>(sm, tmem, k, j, s, act_ph) ||
+            !mma_layer<4>(sm, tmem, k, j, s, act_ph) || !mma_layer<5>(sm, tmem, k, j, s, act_ph) ||
+            !mma_layer<6>(sm, tmem, k, j, s, act_ph) || !mma_layer<7>(sm, tmem, k, j, s, act_ph))
           break;
       }
       // every MMA issued by this thread completes before TMEM is released
@@ -480,35 +510,35 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
       mbar_wait(sm.bar(kDrain + s), 0u, sm.abort_flag, p.err, kErrDrain);
     }
     __syncwarp();
-  } else {
-    // ---------------- epilogue (warps 2 .. 1 + 2 kEpi: kEpi per item slot) ----------------
-    const int s = (warp - 2) / kEpi;          // item slot this warp drains
-    const int quarter = warp & 3;             // TMEM lanes this warp may access
-    const int half = ((warp - 2) >> 2) & 1;   // 32-column chunk it drains
-    const bool poller = (warp - 2) % kEpi == 0;  // the slot's first epilogue warp polls the accumulator
+  } else if (warp >= kWarpEpi0 && warp < kWarpMmaHi) {
+    // ---------------- epilogue: kEpiW warps per slot ----------------
+    const int s = (warp - kWarpEpi0) / kEpiW;      // slot this warp drains
+    const int quarter = warp & 3;                  // TMEM lanes this warp may access
+    const bool poller = quarter == 0;              // the slot's first epilogue warp polls the accumulator
     int acc_ph = 0;
     griddep_wait();  // the prediction buffer may be read by the kernels before this one
-    for (int k = 0; k < n_pairs; ++k) {
-      if (2 * k + s >= my_items) break;
+    for (int k = 0; k < n_rounds; ++k) {
+      const int j = k * kSlots + s;
+      if (j >= my_items) break;
       EpiItem e;
-      const int item = (int)blockIdx.x + (2 * k + s) * G;
+      const int item = (int)blockIdx.x + j * G;
       e.b = item / p.tiles;
       e.t = item - e.b * p.tiles;
       fused_tile_rows(p.T, p.Lw, e.t, e.rm0, nullptr, nullptr);
-      if (!epi_layer<0>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<1>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<2>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<3>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<4>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<5>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<6>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<7>(p, sm, tmem, quarter, half, lane, s, poller, e, acc_ph, s_bias))
+      if (!epi_layer<0>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
+          !epi_layer<1>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
+          !epi_layer<2>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
+          !epi_layer<3>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
+          !epi_layer<4>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
+          !epi_layer<5>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
+          !epi_layer<6>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
+          !epi_layer<7>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias))
         break;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, 2 * kAccCols);
+  if (warp == 2) tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace
@@ -608,12 +638,17 @@ FusedPlan* fused_plan_create(gw_model* m, const std::vector<std::vector<double>>
     f->q = q;
     f->q.in_bytes = in_bytes;
     f->q.act_bytes = act_bytes;
-    f->smem = 1024 + 2 * (size_t)in_bytes + 4 * (size_t)act_bytes + (size_t)kWStages * kWChunk + 8 * (size_t)kNBars +
-              32 + 4 * (size_t)kBiasCount;
+    f->smem = 1024 + kInBufs * (size_t)in_bytes + kSlots * (size_t)act_bytes + (size_t)kWStages * kWChunk +
+              8 * (size_t)kNBars + 32 + 4 * (size_t)kBiasCount;
     GW_CHECK_ARG(f->smem <= 227 * 1024, "fused plan: shared memory");
-    void* wimg = dev_alloc(m->ctx, all.size(), &m->bytes);
+    const size_t stride = (all.size() + 127) / 128 * 128;
+    all.resize(stride, 0);
+    std::vector<uint8_t> reps(stride * kWReps);
+    for (int r = 0; r < kWReps; ++r) std::copy(all.begin(), all.end(), reps.begin() + (size_t)r * stride);
+    void* wimg = dev_alloc(m->ctx, reps.size(), &m->bytes);
     m->allocs.push_back(wimg);
-    GW_CUDA(cudaMemcpy(wimg, all.data(), all.size(), cudaMemcpyHostToDevice));
+    GW_CUDA(cudaMemcpy(wimg, reps.data(), reps.size(), cudaMemcpyHostToDevice));
+    f->q.wimg_stride = (uint32_t)stride;
     float* bd = (float*)dev_alloc(m->ctx, biases.size() * sizeof(float), &m->bytes);
     m->allocs.push_back(bd);
     GW_CUDA(cudaMemcpy(bd, biases.data(), biases.size() * sizeof(float), cudaMemcpyHostToDevice));

@@ -192,6 +192,15 @@ def test_server_matches_oracle_bf16(ctx):
     check(rig, STREAMS, got, TOL16, logits_ok)
 
 
+def test_server_bf16_unscaled_network(ctx):
+    # BF16 with DeepClean exactly as created (no output scaling): the
+    # predicted noise is held to the BF16 bound; the logits, of whitened data
+    # that a random network's prediction dominates, only have to be finite
+    rig = Rig(ctx, G.GW_BF16)
+    got = rig.run(STREAMS, interleaved(STREAMS, 4))
+    check(rig, STREAMS, got, TOL16, lambda g, r: None)
+
+
 @pytest.mark.parametrize("prec", [G.GW_FP32, G.GW_BF16])
 def test_same_result_alone_and_in_the_mix(ctx, prec):
     # A stream's results do not depend on which other streams share its ticks,
