@@ -15,6 +15,11 @@ Readings of the unspecified timing, sample for sample:
   known for n < n_end_k = m_end_k - 1024.
 * the BBHnet input at snapshot k is w[n_end_k - Lb, n_end_k) of each detector
   (w at negative n = 0), Lb = 2048 (1 s at 2048 Hz); the score is its logit.
+* with post-processing (the online pipeline's band-pass of the noise estimate
+  before subtraction, ``oracle.stream.clean_post``), the FIR of K taps needs
+  the aggregated prediction c = (K - 1) / 2 samples past an output time, so the
+  cleaned series after snapshot k is known up to (k+1) S - delta - c, and every
+  later stage follows it: c_end_k, m_end_k and n_end_k are those of delta + c.
 """
 from __future__ import annotations
 
@@ -33,24 +38,28 @@ def m_end(k, S, delta):
 
 
 def run_pipeline(witness, strain, W, S, n_snap, mode, delta, dc_fwd, f_dec, h_wht, bbh_params, bbh_head,
-                 bbh_layers, Lb=2048):
+                 bbh_layers, Lb=2048, post=None):
     """One stream of n_det detectors.
 
     witness: list (per detector) of (C, n_snap*S); strain: list of (n_snap*S,).
     dc_fwd: per-detector callables mapping (B, C, W) windows to (B, W).
-    Returns (cleaned (n_det, n_snap, S), logits (n_snap,)).
+    post: optional post-processing FIR taps (odd length) of the aggregated
+    prediction.
+    Returns (cleaned (n_det, n_snap, S), logits (n_snap,)); with post, row k of
+    cleaned holds the times emitted by snapshot k shifted by c.
     """
     n_det = len(witness)
+    c_post = (len(post) - 1) // 2 if post is not None else 0
     cleaned = []
     cstreams = []
     for d in range(n_det):
-        _, cl = stream.run_deepclean_stream(dc_fwd[d], witness[d], strain[d], W, S, n_snap, mode, delta)
+        _, cl = stream.run_deepclean_stream(dc_fwd[d], witness[d], strain[d], W, S, n_snap, mode, delta, post=post)
         cleaned.append(cl)
         # continuous cleaned series c[tau], tau >= 0 (emitted times kS - delta + i)
         total = n_snap * S
         c = np.zeros(total)
         for k in range(n_snap):
-            t = stream.emit_times(k, S, delta)
+            t = stream.emit_times(k, S, delta) - c_post
             ok = (t >= 0) & (t < total)
             c[t[ok]] = cl[k][ok]
         cstreams.append(c)
@@ -58,7 +67,7 @@ def run_pipeline(witness, strain, W, S, n_snap, mode, delta, dc_fwd, f_dec, h_wh
     Kw = len(h_wht)
     logits = np.zeros(n_snap)
     for k in range(n_snap):
-        me = m_end(k, S, delta)
+        me = m_end(k, S, delta + c_post)
         ne = me - (Kw - 1) // 2
         wins = np.zeros((1, n_det, Lb))
         for d in range(n_det):

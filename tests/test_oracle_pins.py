@@ -475,6 +475,43 @@ def test_pipeline_timing_with_delta_filters():
         assert abs(logits[k] - nets.bbhnet_forward(win, params, head, layers)[0]) < 1e-9
 
 
+def test_pipeline_post_processing_timing():
+    # A post-processing FIR that is a unit impulse at its centre tap leaves the
+    # cleaned series unchanged but delays it by c samples; with c = S every
+    # output of snapshot k (cleaned samples and the BBHnet input window, hence
+    # the logit) is the plain pipeline's output of snapshot k - 1.  A one-tap
+    # FIR [1] changes nothing.
+    from oracle import pipeline
+    W, S, n, Lb, delta = 256, 64, 10, 128, 40
+    layers = synth.bbhnet_layers()
+    params, head = synth.bbhnet_params(5)
+    r = np.random.default_rng(12)
+    wit = [r.standard_normal((21, n * S)) for _ in range(2)]
+    strain = [r.standard_normal(n * S) for _ in range(2)]
+    dc = synth.deepclean_params(13)
+    fwd = lambda wins: nets.deepclean_forward(wins, dc, synth.DEEPCLEAN_LAYERS) * 0.05
+    f_dec = r.standard_normal(127) * 0.1
+    h = r.standard_normal(33) * 0.2
+    args = (wit, strain, W, S, n, stream.AVERAGE, delta, [fwd, fwd], f_dec, h, params, head, layers)
+    cl0, lg0 = pipeline.run_pipeline(*args, Lb=Lb)
+    # emitted times before the stream start: the plain pipeline gives minus the
+    # prediction there, the post-processed one reads the prediction at
+    # negative times as zero (there is no data), so both give their own values
+    t = np.stack([stream.emit_times(k, S, delta) for k in range(n)])
+    cl1, lg1 = pipeline.run_pipeline(*args, Lb=Lb, post=np.array([1.0]))
+    ok = np.broadcast_to(t >= 0, cl0.shape)
+    np.testing.assert_array_equal(cl1[ok], cl0[ok])
+    assert np.abs(cl1[~ok]).max() == 0.0
+    np.testing.assert_array_equal(lg1, lg0)
+    imp = np.zeros(2 * S + 1)
+    imp[S] = 1.0
+    cl2, lg2 = pipeline.run_pipeline(*args, Lb=Lb, post=imp)
+    ok1 = np.broadcast_to(t[:-1] >= 0, cl0[:, :-1].shape)
+    np.testing.assert_allclose(cl2[:, 1:][ok1], cl0[:, :-1][ok1], atol=1e-12)
+    assert np.abs(cl2[:, 1:][~ok1]).max() == 0.0 and np.abs(cl2[:, 0]).max() == 0.0
+    np.testing.assert_allclose(lg2[1:], lg0[:-1], atol=1e-9)
+
+
 # ----------------------------------------------------------------------------
 # Gradient: central finite differences and PyTorch autograd in float64
 # ----------------------------------------------------------------------------
