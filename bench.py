@@ -465,24 +465,51 @@ def gpu_arm(args):
         "gpu_launches": int(round(hp["gpu_launches_per_step"] * K)),
         "roofline": roofline,
         "paths": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in paths.items()},
-        "configs": configs,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
-    # per-kernel breakdowns go to stderr, so that the one JSON line stays short
-    detail = {"paths_kernels": {k: v.get("kernels") for k, v in paths.items()},
-              "configs_kernels": {k: {kk: vv for kk, vv in v.items() if "kernel" in kk}
-                                  for k, v in configs.items() if isinstance(v, dict)}}
+    # the full records (per-kernel breakdowns, descriptions) go to stderr, so
+    # that the one JSON line stays short; the line carries the numbers, with
+    # the serving configuration last
+    detail = {"paths_kernels": {k: v.get("kernels") for k, v in paths.items()}, "configs": configs}
     print(json.dumps(detail), file=sys.stderr)
     for v in line["paths"].values():
         v.pop("kernels", None)
-    for v in line["configs"].values():
-        if isinstance(v, dict):
-            for kk in [kk for kk in v if "kernel" in kk and kk != "kernels_per_tick"]:
-                v.pop(kk)
+    line["configs"] = compact_configs(configs)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def compact_configs(configs):
+    """The configs' numbers for the JSON line: scalars (floats to 4 significant
+    digits) and one level of nested dicts of scalars; descriptions, series and
+    per-kernel tables are left to the stderr record.  config5_bf16 comes last."""
+    def keep(v):
+        return isinstance(v, (int, float, bool)) or v is None or (isinstance(v, str) and len(v) <= 40)
+
+    def rnd(v):
+        return float(f"{v:.4g}") if isinstance(v, float) else v
+
+    out = {}
+    order = [k for k in configs if k != "config5_bf16"] + [k for k in configs if k == "config5_bf16"]
+    for k in order:
+        v = configs[k]
+        if not isinstance(v, dict):
+            out[k] = rnd(v) if keep(v) else None
+            continue
+        c = {}
+        for kk, vv in v.items():
+            if "kernel" in kk and kk != "kernels_per_tick":
+                continue
+            if isinstance(vv, dict):
+                sub = {a: rnd(b) for a, b in vv.items() if keep(b) and "kernel" not in a}
+                if sub:
+                    c[kk] = sub
+            elif keep(vv):
+                c[kk] = rnd(vv)
+        out[k] = c
+    return out
 
 
 def bbhnet_flops_per_window(L=2048):
@@ -713,6 +740,9 @@ def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
 
 
 SERVE_STREAMS, SERVE_STRIDES, SERVE_BUDGET = 64, (128, 256, 512), 20 * 2 ** 30
+# while a tick runs, the next one is formed only once the running tick is
+# expected to end within this lead (snapshots arriving meanwhile join it)
+SERVE_FORM_LEAD_US = 60
 
 
 def serve_configs(G, dev_index, seconds=1.5, precisions=None):
@@ -768,7 +798,8 @@ def serve_configs(G, dev_index, seconds=1.5, precisions=None):
             objs = [(G.gw_model_destroy, m) for m in dcs + [bbh]] + [(G.gw_fir_destroy, fdec), (G.gw_fir_destroy, fw)]
             srv = G.gw_server_create(ctx, dcs, bbh, fdec, fw, n_det=2, n_witness=C, window=W, max_stride=512,
                                      max_streams=SERVE_STREAMS, max_batch=SERVE_STREAMS, max_pending=4 * SERVE_STREAMS,
-                                     agg_mode=G.GW_AGG_AVERAGE, agg_delay=W - 512, bbh_len=2048, max_inflight=2)
+                                     agg_mode=G.GW_AGG_AVERAGE, agg_delay=W - 512, bbh_len=2048, max_inflight=2,
+                                     form_lead_us=SERVE_FORM_LEAD_US)
             objs.append((G.gw_server_destroy, srv))
             fixed = G.gw_ctx_bytes_in_use(ctx)
             per_stream = G.gw_server_stream_bytes(srv, 256)
@@ -828,7 +859,8 @@ def serve_configs(G, dev_index, seconds=1.5, precisions=None):
                 "fixed_bytes": fixed, "streams_admissible_under_budget": int((SERVE_BUDGET - fixed) // per_stream),
                 "saturated": sat, "poisson_half_load": half, "poisson_90pct_load": high,
                 "poisson_realtime": dict(rt, rate_per_s=rt_rate), "tick_kernels_eager": ticks,
-                "launch": "one CUDA graph per tick (batch bucket), inputs read from pinned mapped host slots"}
+                "launch": "one CUDA graph per tick (batch bucket), inputs read from pinned mapped host slots",
+                "form_lead_us": SERVE_FORM_LEAD_US}
         finally:
             for fn, o in reversed(objs):
                 fn(o)

@@ -282,6 +282,9 @@ int gw_stream_status(gw_stream_t s, void* cuda_stream);
  *      detector);
  *   3. subtraction and aggregation as for gw_stream (agg_mode, agg_delay),
  *      giving S cleaned samples c[tau], tau in [k S - agg_delay, (k+1) S - agg_delay);
+ *      with desc.post (K taps, c = (K-1)/2) the aggregated estimate is
+ *      band-passed before it is subtracted and the S samples are those of
+ *      tau in [k S - agg_delay - c, (k+1) S - agg_delay - c), as for gw_stream;
  *   4. 2x resampling with the decimator FIR f (Kf taps, odd):
  *      d[m] = sum_j f[j] c[2 m + j - (Kf-1)/2], c[tau < 0] = 0; d[m] is
  *      computed as soon as every c it reads has been emitted;
@@ -315,6 +318,14 @@ typedef struct gw_server_desc {
   int max_wait_us;  /* a tick waits up to this long for max_batch snapshots (0 = launch when the device is free) */
   int max_inflight; /* ticks queued on the device at once, 1 .. 4 */
   int use_graphs;   /* 1 = each tick is one CUDA-graph launch; 0 = eager launches */
+  int form_lead_us; /* 0 = the next tick is formed as soon as a device slot is free; > 0 = while a tick runs, the
+                       next one is formed only when the running tick is expected to end within this many
+                       microseconds (its duration estimated from completed ticks of the same batch bucket), or
+                       once max_batch snapshots are queued: snapshots that arrive meanwhile join it */
+  gw_fir_t post;    /* optional (NULL = none): FP32 FIR of odd length K with which the aggregated noise estimate
+                       is post-processed before it is subtracted (Methods, online deployment), as in
+                       gw_stream_desc.post; a snapshot then returns the cleaned samples of its emitted times less
+                       c = (K - 1) / 2, and resampling, whitening and BBHnet follow that delayed series */
 } gw_server_desc;
 typedef struct gw_server_stats {
   int64_t snapshots;      /* completed since the last reset */

@@ -206,6 +206,9 @@ static void model_free(gw_model* m) {
     m->ctx->in_use -= m->bytes + m->ws_bytes;
   }
   fused_plan_destroy(m->fused);
+  if (m->fork_ev) cudaEventDestroy(m->fork_ev);
+  if (m->join_ev) cudaEventDestroy(m->join_ev);
+  if (m->side) cudaStreamDestroy(m->side);
   delete m;
 }
 
@@ -484,14 +487,20 @@ void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* w
     const int next_P = blk < 3 ? Ls[1 + 3 * (blk + 1)].pin : 1;
     TcOut a = blocked_out(buf[a_i], c1.s.cout, l2, c2.pin);
     TcOut o = blocked_out(buf[o_i], c2.s.cout, l2, next_P);
+    // the shortcut on the side stream, beside the first conv; the second
+    // conv (which adds the shortcut) waits for both
+    GW_CUDA(cudaEventRecord(m->fork_ev, st));
+    GW_CUDA(cudaStreamWaitEvent(m->side, m->fork_ev, 0));
+    {
+      Prof p(kBbhNames[0][2 + 3 * blk], m->side);
+      launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, m->side);
+    }
+    GW_CUDA(cudaEventRecord(m->join_ev, m->side));
     {
       Prof p(kBbhNames[0][1 + 3 * blk], st);
       launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
     }
-    {
-      Prof p(kBbhNames[0][2 + 3 * blk], st);
-      launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
-    }
+    GW_CUDA(cudaStreamWaitEvent(st, m->join_ev, 0));
     TcOut o2 = o;
     o2.res = o.p;
     o2.rbstride = o.bstride;
@@ -549,14 +558,20 @@ void bbhnet_fp8(gw_model* m, const float* x, int B, int L, float* logits, char* 
     const int next_P = blk < 3 ? Ls[1 + 3 * (blk + 1)].pin : 1;
     TcOut a = blocked_out(buf[a_i], c1.s.cout, l2, c2.pin, true);
     TcOut o = blocked_out(buf[o_i], c2.s.cout, l2, next_P, true);
+    // the shortcut on the side stream, beside the first conv; the second
+    // conv (which adds the shortcut) waits for both
+    GW_CUDA(cudaEventRecord(m->fork_ev, st));
+    GW_CUDA(cudaStreamWaitEvent(m->side, m->fork_ev, 0));
+    {
+      Prof p(kBbhNames[1][2 + 3 * blk], m->side);
+      launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, m->side);
+    }
+    GW_CUDA(cudaEventRecord(m->join_ev, m->side));
     {
       Prof p(kBbhNames[1][1 + 3 * blk], st);
       launch_conv_tc(c1, as_input(h, l), l2, a, B, m->err, st);
     }
-    {
-      Prof p(kBbhNames[1][2 + 3 * blk], st);
-      launch_conv_tc(sc, as_input(h, l), l2, o, B, m->err, st);
-    }
+    GW_CUDA(cudaStreamWaitEvent(st, m->join_ev, 0));
     TcOut o2 = o;
     o2.res = o.p;
     o2.rbstride = o.bstride;
@@ -812,6 +827,11 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
     m->layers.push_back(L);
   }
   if (d->kind == GW_MODEL_DEEPCLEAN && d->precision == GW_BF16) m->fused = fused_plan_create(m, wfold, bfold);
+  if (d->kind == GW_MODEL_BBHNET && d->precision != GW_FP32) {
+    GW_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    GW_CUDA(cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming));
+    GW_CUDA(cudaEventCreateWithFlags(&m->join_ev, cudaEventDisableTiming));
+  }
   if (d->precision == GW_FP8 && d->act_scales) {
     GW_CHECK_ARG(d->n_act_scales == (int)specs.size() + 1,
                  "act_scales must have one entry per conv layer plus the final output scale");

@@ -122,6 +122,11 @@ struct gw_model {
   bool fp8_scaled = false;
   // BF16 DeepClean: the whole-network tensor-core kernel's plan (or null)
   gw::FusedPlan* fused = nullptr;
+  // tensor-core BBHnet: a second stream on which each residual block's
+  // shortcut conv runs beside the block's first conv (both read the block
+  // input), forked from and joined back to the caller's stream by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 struct gw_fir {

@@ -22,6 +22,7 @@ struct ServeItem {
   float* clean;       // cleaned ring [Rc] (input rate)
   float* dec;         // decimated ring [Rd]
   float* white;       // whitened ring [Rw]
+  float* pring;       // with post-processing: aggregated prediction ring [Rp]
   const float* in;    // [C + 1][S]: witness rows, then the strain row
   float* out;         // [S] cleaned samples
   float* score;       // detector 0 only: the request's logit
@@ -32,11 +33,17 @@ struct ServeGeom {
   int64_t R, Rc, Rd, Rw;
   int bf16;
   int mode, delta;
+  int post, post_c;   // post-processing FIR present; its half length c = (K - 1) / 2
+  int64_t Rp;
 };
 
 void launch_serve_push(const ServeItem* items, int n, const ServeGeom& g, int S_max, const float* mean,
                        const float* istd, cudaStream_t st);
 void launch_serve_sub_ola(const ServeItem* items, int n, const ServeGeom& g, const float* pred, cudaStream_t st);
+// With post-processing: cleaned samples of the times [head - delta - c,
+// head - delta - c + S) from the prediction ring, h the FIR's K taps.
+void launch_serve_post(const ServeItem* items, int n, const ServeGeom& g, const float* h, int K, int S_max,
+                       cudaStream_t st);
 void launch_serve_decimate(const ServeItem* items, int n, const ServeGeom& g, const float* taps, int K,
                            int max_new, cudaStream_t st);
 size_t serve_whiten_smem(int K, int max_new);

@@ -107,10 +107,47 @@ __global__ void serve_sub_ola_kernel(const ServeItem* __restrict__ items, ServeG
       const int64_t first = tau >= 0 ? floordiv64(tau, S) : 0;
       value = sum / (float)(k - first + 1);
     }
+    if (g.post) {
+      // the post-processing FIR reads the aggregated prediction from its ring
+      if (tau >= 0) it.pring[ring_mod(tau, g.Rp)] = value;
+      continue;
+    }
     const float c = (tau >= 0 ? it.strain[q] : 0.f) - value;
     it.out[o] = c;
     if (tau >= 0) it.clean[wrap(cb, (uint32_t)o, (uint32_t)g.Rc)] = c;
   }
+}
+
+// Post-processing: cleaned[t] = strain[t] - sum_k h[k] p[t + k - c] for the
+// times t = head - delta - c + o, o < S (the prediction at negative times is
+// zero: there is no data before the stream start).  One CTA per kServePost
+// outputs of an item stages the taps and the prediction segment it reads.
+constexpr int kServePost = 256;
+__global__ void serve_post_kernel(const ServeItem* __restrict__ items, ServeGeom g, const float* __restrict__ h,
+                                  int K) {
+  const ServeItem it = items[blockIdx.y];
+  if (!it.active) return;
+  const int o0 = blockIdx.x * kServePost;
+  if (o0 >= it.S) return;
+  extern __shared__ float sh[];
+  float* hs = sh;      // [K]
+  float* ps = sh + K;  // p[t(o0) - c + i], i < kServePost + K - 1
+  const int c = g.post_c;
+  const int64_t t0 = it.head - g.delta - c + o0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = h[k];
+  for (int i = threadIdx.x; i < kServePost + K - 1; i += blockDim.x) {
+    const int64_t u = t0 - c + i;
+    ps[i] = u >= 0 ? it.pring[ring_mod(u, g.Rp)] : 0.f;
+  }
+  __syncthreads();
+  const int o = o0 + threadIdx.x;
+  if (threadIdx.x >= kServePost || o >= it.S) return;
+  float q = 0.f;
+  for (int k = 0; k < K; ++k) q = fmaf(hs[k], ps[threadIdx.x + k], q);
+  const int64_t t = t0 + threadIdx.x;
+  const float v = (t >= 0 ? it.strain[ring_mod(t, g.R)] : 0.f) - q;
+  it.out[o] = v;
+  if (t >= 0) it.clean[ring_mod(t, g.Rc)] = v;
 }
 
 // New decimated samples d[m], m in [m0, m1).
@@ -205,6 +242,15 @@ void launch_serve_push(const ServeItem* items, int n, const ServeGeom& g, int S_
 
 void launch_serve_sub_ola(const ServeItem* items, int n, const ServeGeom& g, const float* pred, cudaStream_t st) {
   serve_sub_ola_kernel<<<dim3(grid_x(g.W), n), kThreads, 0, st>>>(items, g, pred);
+  GW_LAUNCH_CHECK();
+}
+
+void launch_serve_post(const ServeItem* items, int n, const ServeGeom& g, const float* h, int K, int S_max,
+                       cudaStream_t st) {
+  const size_t smem = (size_t)(2 * K + kServePost) * sizeof(float);
+  GW_CHECK_ARG(smem <= 200 * 1024, "post-processing FIR too long for the serving kernel");
+  set_smem_limit_once(serve_post_kernel, 200 * 1024);
+  serve_post_kernel<<<dim3((S_max + kServePost - 1) / kServePost, n), kServePost, smem, st>>>(items, g, h, K);
   GW_LAUNCH_CHECK();
 }
 

@@ -627,31 +627,57 @@ __global__ void to_blocked_kernel(const float* __restrict__ x, int64_t xb, int64
   }
 }
 
-// Global average pool of a blocked activation + linear head; one CTA per item.
+// Global average pool of a blocked activation + linear head; one CTA per
+// item.  A warp takes one phase plane of one channel group at a time (its
+// lanes consecutive 16-byte rows, so that the loads coalesce), sums each
+// channel over its rows in registers, reduces across the warp and adds the
+// plane's sums to per-channel totals in shared memory; then every channel's
+// mean is weighted and the products reduced.
+constexpr int kGapMaxC = 1024;
 __global__ void gap_linear_blocked_kernel(const char* __restrict__ in, int64_t ib, int64_t ig, int64_t ip, int P,
                                           int L, int C, int fp8, float in_scale, const float* __restrict__ w,
                                           const float* __restrict__ bias, float* __restrict__ out) {
-  __shared__ float red[8];
-  const int b = blockIdx.x;
+  __shared__ float acc[kGapMaxC];
+  __shared__ float red[32];
+  const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int cg = fp8 ? 16 : 8;
-  float part = 0.f;
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    const int g = c / cg, i = c % cg;
-    float s = 0.f;
-    for (int t = 0; t < L; ++t) {
-      const char* row = in + (int64_t)b * ib + (int64_t)g * ig + (int64_t)(t % P) * ip + (int64_t)(t / P) * 16;
-      s += fp8 ? float(reinterpret_cast<const __nv_fp8_e4m3*>(row)[i]) * in_scale
-               : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(row)[i]);
+  const int G = (C + cg - 1) / cg, R = (L + P - 1) / P;
+  for (int c = threadIdx.x; c < G * cg; c += blockDim.x) acc[c] = 0.f;
+  __syncthreads();
+  for (int plane = warp; plane < G * P; plane += nwarps) {
+    const int g = plane / P, phase = plane - g * P;
+    const char* base = in + (int64_t)b * ib + (int64_t)g * ig + (int64_t)phase * ip;
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+    for (int r = lane; r < R && r * P + phase < L; r += 32) {
+      const uint4 q = *reinterpret_cast<const uint4*>(base + (int64_t)r * 16);
+      if (fp8) {
+        const __nv_fp8_e4m3* e = reinterpret_cast<const __nv_fp8_e4m3*>(&q);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += float(e[i]);
+      } else {
+        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] += __bfloat162float(e[i]);
+      }
     }
-    part = fmaf(s / (float)L, w[c], part);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    if (lane == 0)
+      for (int i = 0; i < cg; ++i) atomicAdd(&acc[g * cg + i], v[i]);
   }
+  __syncthreads();
+  float part = 0.f;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) part = fmaf(acc[c] * in_scale / (float)L, w[c], part);
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  if (lane == 0) red[warp] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float v = 0.f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i];
-    out[b] = v + bias[0];
+    float t = 0.f;
+    for (int i = 0; i < nwarps; ++i) t += red[i];
+    out[b] = t + bias[0];
   }
 }
 
@@ -1102,6 +1128,7 @@ void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int
 void launch_gap_linear_blocked(const TcIn& in, int C, int fp8, float in_scale, const float* w, const float* b,
                                float* out, int B, cudaStream_t st) {
   const int esz = fp8 ? 1 : 2;
+  GW_CHECK_ARG((C + 15) / 16 * 16 <= kGapMaxC, "too many channels for the pooling head");
   gap_linear_blocked_kernel<<<B, 256, 0, st>>>((const char*)in.p + in.off0 * esz, in.bstride * esz, in.gstride * esz,
                                                in.pstride * esz, in.P, in.L, C, fp8, in_scale, w, b, out);
   GW_LAUNCH_CHECK();

@@ -71,11 +71,14 @@ struct Stream {
   float* clean[2] = {};
   float* dec[2] = {};
   float* white[2] = {};
+  float* pring[2] = {};
 };
 
 struct Tick {
-  int slot = 0, n = 0, bucket = 0;
+  int slot = 0, n = 0, bucket = 0, bi = 0;
   int64_t kernels = 0;
+  double t_launch = 0;  // host time of the launch
+  double t_expect = 0;  // expected completion (launch or the previous tick's expected end, + estimated duration)
   std::vector<int> reqs;
 };
 
@@ -89,6 +92,7 @@ struct gw_server {
   gw_model* bbh = nullptr;
   gw_fir* fdec = nullptr;
   gw_fir* fwht = nullptr;
+  gw_fir* fpost = nullptr;
   gw::ServeGeom geom{};
   int prec = 0, Kf = 0, Kh = 0, Lb = 0, max_new = 0, n_slots = 0;
   std::vector<int> buckets;
@@ -132,6 +136,8 @@ struct gw_server {
   uint64_t next_ticket = 1;
   std::deque<gw::Tick> inflight;
   int64_t tick_seq = 0;
+  std::vector<double> dur_us;  // per bucket: running estimate of a tick's device time (0 = none yet)
+  double t_prev_done = 0;      // completion time of the last completed tick
   bool stop = false, loop_done = false;
   int sticky = 0;
   std::string sticky_msg;
@@ -177,7 +183,7 @@ T* dptr(T* host) {
 
 // Bytes of one detector's state, each part 256-byte aligned.
 struct StateLayout {
-  size_t wring, strain, acc, clean, dec, white, det;
+  size_t wring, strain, acc, clean, dec, white, pring, det;
 };
 StateLayout state_layout(const gw_server* s) {
   const ServeGeom& g = s->geom;
@@ -188,7 +194,8 @@ StateLayout state_layout(const gw_server* s) {
   L.clean = round_up(g.Rc * 4, 256);
   L.dec = round_up(g.Rd * 4, 256);
   L.white = round_up(g.Rw * 4, 256);
-  L.det = L.wring + L.strain + L.acc + L.clean + L.dec + L.white;
+  L.pring = g.post ? round_up(g.Rp * 4, 256) : 0;
+  L.det = L.wring + L.strain + L.acc + L.clean + L.dec + L.white + L.pring;
   return L;
 }
 
@@ -243,6 +250,10 @@ void record_tick(gw_server* s, int Bb, int slot, cudaStream_t a, cudaStream_t b)
     {
       Prof p("serve_sub_ola", sd);
       launch_serve_sub_ola(it, Bb, g, pred, sd);
+    }
+    if (g.post) {
+      Prof p("serve_post", sd);
+      launch_serve_post(it, Bb, g, s->fpost->d_taps, s->fpost->ntaps, s->d.max_stride, sd);
     }
     {
       Prof p("serve_decimate", sd);
@@ -369,6 +380,17 @@ void loop_main(gw_server* s) {
              (!s->queue.empty() && (int)s->inflight.size() < s->n_slots);
     });
     if (s->queue.empty()) break;  // stopping and drained
+    // just-in-time formation: while a tick runs, wait until it is expected to
+    // end within form_lead_us (or a full batch is queued), so that snapshots
+    // arriving meanwhile join the next tick instead of the one after it
+    if (s->d.form_lead_us > 0) {
+      while (!s->stop && !s->inflight.empty() && (int)s->queue.size() < s->d.max_batch) {
+        const double ready = s->inflight.back().t_expect - s->d.form_lead_us, now = now_us();
+        if (now >= ready) break;
+        s->cv_loop.wait_for(lk, std::chrono::microseconds((int64_t)std::max(1.0, ready - now)));
+      }
+      if (s->queue.empty()) continue;
+    }
     if (s->d.max_wait_us > 0 && (int)s->queue.size() < s->d.max_batch && !s->stop) {
       const double deadline = s->reqs[s->queue.front()].t_arrival + s->d.max_wait_us;
       while (!s->stop && (int)s->queue.size() < s->d.max_batch && now_us() < deadline)
@@ -389,14 +411,21 @@ void loop_main(gw_server* s) {
       q = s->queue.erase(q);
     }
     t.n = (int)t.reqs.size();
-    t.bucket = s->buckets[bucket_index(s, t.n)];
+    t.bi = bucket_index(s, t.n);
+    t.bucket = s->buckets[t.bi];
+    {
+      const double now = now_us();
+      const double start = s->inflight.empty() ? now : std::max(now, s->inflight.back().t_expect);
+      t.t_launch = now;
+      t.t_expect = start + s->dur_us[t.bi];
+    }
     proto.resize((size_t)s->d.n_det * t.n);
     for (int r = 0; r < t.n; ++r) {
       Req& rq = s->reqs[t.reqs[r]];
       Stream& sm = s->streams[rq.stream];
       const int64_t k = sm.k_sched++;
       const int64_t S = sm.S;
-      const int64_t me = m_end((k + 1) * S - s->d.agg_delay, s->Kf);
+      const int64_t me = m_end((k + 1) * S - s->d.agg_delay - s->geom.post_c, s->Kf);
       const int64_t ne = me - (s->Kh - 1) / 2;
       for (int det = 0; det < s->d.n_det; ++det) {
         ServeItem& it = proto[(size_t)det * t.n + r];
@@ -413,6 +442,7 @@ void loop_main(gw_server* s) {
         it.clean = sm.clean[det];
         it.dec = sm.dec[det];
         it.white = sm.white[det];
+        it.pring = sm.pring[det];
         it.in = rq.in_dev + (size_t)det * (s->d.n_witness + 1) * S;
         it.out = rq.out_dev + (size_t)det * S;
         it.score = det == 0 ? rq.out_dev + (size_t)s->d.n_det * s->d.max_stride : nullptr;
@@ -472,6 +502,14 @@ void done_main(gw_server* s) {
     // their tickets until released below
     lk.unlock();
     const double t_now = now_us();
+    {
+      // device time of the tick: from its launch, or from the previous
+      // tick's completion when it had to wait for it
+      const double d_us = t_now - std::max(done.t_launch, s->t_prev_done);
+      double& e = s->dur_us[done.bi];
+      e = e > 0 ? 0.8 * e + 0.2 * d_us : d_us;
+      s->t_prev_done = t_now;
+    }
     for (int rid : done.reqs) {
       Req& rq = s->reqs[rid];
       const int S = s->streams[rq.stream].S;
@@ -627,6 +665,7 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
   GW_CHECK_ARG(d->bbh_len >= 16 && d->bbh_len % 16 == 0, "bbh_len must be a positive multiple of 16");
   GW_CHECK_ARG(d->max_wait_us >= 0, "max_wait_us must be >= 0");
   GW_CHECK_ARG(d->max_inflight >= 1 && d->max_inflight <= kMaxInflight, "max_inflight must be 1..4");
+  GW_CHECK_ARG(d->form_lead_us >= 0, "form_lead_us must be >= 0");
   for (int i = 0; i < d->n_det; ++i) {
     GW_CHECK_ARG(deepclean[i] && deepclean[i]->kind == GW_MODEL_DEEPCLEAN, "need one DeepClean model per detector");
     GW_CHECK_ARG(deepclean[i]->n_in == d->n_witness, "DeepClean n_in != n_witness");
@@ -640,6 +679,8 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
                  "FP8 BBHnet needs activation scales (act_scales or gw_model_calibrate)");
   }
   GW_CHECK_ARG((decimator->ntaps & 1) && (whitening->ntaps & 1), "FIR tap counts must be odd");
+  GW_CHECK_ARG(!d->post || (d->post->precision == GW_FP32 && (d->post->ntaps & 1) && d->post->ntaps <= 16385),
+               "post-processing FIR must be FP32 with an odd number of taps (<= 16385)");
   GW_CUDA(cudaSetDevice(ctx->device));
   s = new gw_server();
   try {
@@ -649,6 +690,7 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
     s->bbh = bbhnet;
     s->fdec = decimator;
     s->fwht = whitening;
+    s->fpost = d->post;
     s->prec = deepclean[0]->precision;
     s->Kf = decimator->ntaps;
     s->Kh = whitening->ntaps;
@@ -661,7 +703,11 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
     g.G = (d->n_witness + 7) / 8;
     g.P = s->prec == GW_FP32 ? 1 : s->dc[0]->layers[0].pin;
     g.W = d->window;
-    g.R = round_up(d->window, 64);
+    // with post-processing the strain ring also serves outputs c samples older
+    g.post = d->post ? 1 : 0;
+    g.post_c = d->post ? (d->post->ntaps - 1) / 2 : 0;
+    g.R = round_up(d->window + g.post_c, 64);
+    g.Rp = d->post ? round_up(d->max_stride + 2 * g.post_c + 64, 64) : 0;
     GW_CHECK_ARG(g.R % g.P == 0 && d->window % g.P == 0, "window must be a multiple of the first layer's phase count");
     g.Rc = round_up(d->max_stride + 2 * s->Kf + 64, 64);
     g.Rd = round_up(d->max_stride / 2 + 2 * s->Kh + 64, 64);
@@ -672,6 +718,7 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
     for (int b : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024})
       if (b < d->max_batch) s->buckets.push_back(b);
     s->buckets.push_back(d->max_batch);
+    s->dur_us.assign(s->buckets.size(), 0.0);
 
     // device workspace
     const int Bmax = d->max_batch, nd = d->n_det, W = d->window;
@@ -803,6 +850,8 @@ int gw_server_open(gw_server_t s, int stride, int* stream_id) {
     sm.dec[det] = (float*)p;
     p += L.dec;
     sm.white[det] = (float*)p;
+    p += L.white;
+    sm.pring[det] = L.pring ? (float*)p : nullptr;
   }
   sm.open = true;
   *stream_id = sid;
@@ -943,6 +992,7 @@ int gw_scored_stream_create(gw_ctx_t ctx, const gw_model_t* deepclean, gw_model_
   d.max_wait_us = 0;
   d.max_inflight = 2;
   d.use_graphs = 1;
+  d.form_lead_us = 0;
   ss = new gw_scored_stream();
   int rc = gw_server_create(ctx, &d, deepclean, bbhnet, decimator, whitening, &ss->srv);
   if (rc == GW_OK) {

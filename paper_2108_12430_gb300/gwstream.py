@@ -71,7 +71,7 @@ class gw_stream_desc(C.Structure):
 class gw_server_desc(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("n_det", "n_witness", "window", "max_stride", "max_streams", "max_batch",
                                         "max_pending", "agg_mode", "agg_delay", "bbh_len", "max_wait_us",
-                                        "max_inflight", "use_graphs")]
+                                        "max_inflight", "use_graphs", "form_lead_us")] + [("post", C.c_void_p)]
 
 
 class gw_server_stats(C.Structure):
@@ -354,10 +354,10 @@ def gw_stream_status(s, stream=0):
 
 def gw_server_create(ctx, deepclean, bbhnet, decimator, whitening, *, n_det, n_witness, window, max_stride,
                      max_streams, max_batch, max_pending=0, agg_mode=GW_AGG_AVERAGE, agg_delay=0, bbh_len=2048,
-                     max_wait_us=0, max_inflight=2, use_graphs=1):
+                     max_wait_us=0, max_inflight=2, use_graphs=1, form_lead_us=0, post=None):
     d = gw_server_desc(n_det, n_witness, window, max_stride, max_streams, max_batch,
                        max_pending or 4 * max_batch, agg_mode, agg_delay, bbh_len, max_wait_us, max_inflight,
-                       use_graphs)
+                       use_graphs, form_lead_us, post)
     arr = (P * 2)(*(list(deepclean) + [None] * (2 - len(deepclean))))
     h = P()
     _check(lib().gw_server_create(ctx, C.byref(d), arr, bbhnet, decimator, whitening, C.byref(h)))

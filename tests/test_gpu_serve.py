@@ -61,7 +61,7 @@ def dc_params(d, out_scale):
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_stream(seed, S, n, mode, delta, W, Lb, Kh, nfft, out_scale):
+def oracle_stream(seed, S, n, mode, delta, W, Lb, Kh, nfft, out_scale, post_k=0):
     wit, strn = stream_inputs(seed, S, n)
     fwd = []
     for d in range(2):
@@ -75,17 +75,25 @@ def oracle_stream(seed, S, n, mode, delta, W, Lb, Kh, nfft, out_scale):
     params, head = synth.bbhnet_params(BBH_SEED)
     cl, logits = pipeline.run_pipeline([wit[d].astype(np.float64) for d in range(2)],
                                        [strn[d].astype(np.float64) for d in range(2)], W, S, n, mode, delta, fwd,
-                                       f_dec, h, params, head, synth.bbhnet_layers(), Lb=Lb)
+                                       f_dec, h, params, head, synth.bbhnet_layers(), Lb=Lb,
+                                       post=post_taps(post_k) if post_k else None)
     return cl, logits
+
+
+def post_taps(K):
+    """The 55-65 Hz post-processing band-pass, designed by the oracle and
+    rounded to float32 as the library stores its taps."""
+    return ofir.bandpass_fir(FS, 8192, K).astype(np.float32).astype(np.float64)
 
 
 class Rig:
     """Models, FIRs and a server on one context."""
 
     def __init__(self, ctx, prec, *, W=2048, max_stride=512, max_streams=8, max_batch=8, mode=G.GW_AGG_AVERAGE,
-                 delta=512, Lb=512, Kh=257, nfft=512, bbh_prec=None, out_scale=1.0, **kw):
+                 delta=512, Lb=512, Kh=257, nfft=512, bbh_prec=None, out_scale=1.0, post_k=0, **kw):
         self.ctx, self.W, self.mode, self.delta, self.Lb, self.Kh, self.nfft = ctx, W, mode, delta, Lb, Kh, nfft
-        self.prec, self.out_scale = prec, out_scale
+        self.prec, self.out_scale, self.post_k = prec, out_scale, post_k
+        self.c = (post_k - 1) // 2 if post_k else 0
         self.dc = []
         for d in range(2):
             mean, std = standardisation(d)
@@ -102,6 +110,10 @@ class Rig:
         self.kw = dict(n_det=2, n_witness=C, window=W, max_stride=max_stride, max_streams=max_streams,
                        max_batch=max_batch, agg_mode=mode, agg_delay=delta, bbh_len=Lb)
         self.kw.update(kw)
+        if post_k:
+            self.fpost = G.gw_fir_create_bandpass(ctx.h, FS, 8192, post_k)
+            ctx.objs.append((G.gw_fir_destroy, self.fpost))
+            self.kw["post"] = self.fpost
         self.s = G.gw_server_create(ctx.h, self.dc, self.bbh, self.fdec, self.fw, **self.kw)
         ctx.objs.append((G.gw_server_destroy, self.s))
 
@@ -130,7 +142,8 @@ class Rig:
         return [(o[0].transpose(1, 0, 2), o[1][:, 0]) for o in outs]
 
     def oracle(self, seed, S, n):
-        return oracle_stream(seed, S, n, self.mode, self.delta, self.W, self.Lb, self.Kh, self.nfft, self.out_scale)
+        return oracle_stream(seed, S, n, self.mode, self.delta, self.W, self.Lb, self.Kh, self.nfft, self.out_scale,
+                             self.post_k)
 
 
 def interleaved(streams, seed=0):
@@ -140,11 +153,11 @@ def interleaved(streams, seed=0):
     return order
 
 
-def strain_emitted(seed, S, n, delta):
+def strain_emitted(seed, S, n, delta, c=0):
     _, strn = stream_inputs(seed, S, n)
     out = np.zeros((2, n, S))
     for k in range(n):
-        t = ostream.emit_times(k, S, delta)
+        t = ostream.emit_times(k, S, delta) - c
         ok = t >= 0
         out[:, k, ok] = strn[:, t[ok]]
     return out
@@ -153,7 +166,7 @@ def strain_emitted(seed, S, n, delta):
 def check(rig, streams, got, tol, logit_check):
     for (seed, S, n), (cl, lg) in zip(streams, got):
         ref_cl, ref_lg = rig.oracle(seed, S, n)
-        st = strain_emitted(seed, S, n, rig.delta)
+        st = strain_emitted(seed, S, n, rig.delta, rig.c)
         err = rel_l2(cl - st, ref_cl - st)
         print(f"stream seed={seed} S={S}: noise rel-L2 {err:.2e}, logit max abs err {np.abs(lg - ref_lg).max():.2e}"
               f" (|logit| <= {np.abs(ref_lg).max():.2f})")
@@ -199,6 +212,25 @@ def test_server_bf16_unscaled_network(ctx):
     rig = Rig(ctx, G.GW_BF16)
     got = rig.run(STREAMS, interleaved(STREAMS, 4))
     check(rig, STREAMS, got, TOL16, lambda g, r: None)
+
+
+POST_STREAMS = [(110, 256, 16), (310, 512, 10)]
+
+
+def test_server_post_processing_fp32(ctx):
+    # the 55-65 Hz band-pass of the aggregated prediction before subtraction
+    # (2049 taps: c = 1024 samples of delay), against the oracle pipeline with
+    # the same post-processing
+    rig = Rig(ctx, G.GW_FP32, post_k=2049)
+    got = rig.run(POST_STREAMS, interleaved(POST_STREAMS, 5))
+    check(rig, POST_STREAMS, got, TOL32,
+          lambda g, r: rel_l2(g, r) <= TOL32 or pytest.fail(f"logit rel-L2 {rel_l2(g, r)}"))
+
+
+def test_server_post_processing_bf16(ctx):
+    rig = Rig(ctx, G.GW_BF16, out_scale=1e-2, post_k=2049)
+    got = rig.run(POST_STREAMS, interleaved(POST_STREAMS, 6))
+    check(rig, POST_STREAMS, got, TOL16, lambda g, r: np.abs(g - r).max() <= LOGIT16 or pytest.fail("logits"))
 
 
 @pytest.mark.parametrize("prec", [G.GW_FP32, G.GW_BF16])
