@@ -569,8 +569,19 @@ def extra_configs(G, torch, dev_index, flush, steps=10, warmup=3):
             ms = time_call(torch, lambda: G.gw_deepclean_forward(m, x1d.data_ptr(), 4096, 0, 1, 4096, y1.data_ptr()),
                            steps, warmup)
             err = float(np.linalg.norm(y1.cpu().numpy()[0] - ref1) / np.linalg.norm(ref1))
+            # the same forward captured once into a CUDA graph and replayed
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                G.gw_deepclean_forward(m, x1d.data_ptr(), 4096, 0, 1, 4096, y1.data_ptr(),
+                                       torch.cuda.current_stream().cuda_stream)
+            ms_g = time_call(torch, graph.replay, steps, warmup)
+            err_g = float(np.linalg.norm(y1.cpu().numpy()[0] - ref1) / np.linalg.norm(ref1))
+            del graph
             out[f"config1_{name}"] = {"workload": "DeepClean forward 1x21x4096", "p50_us": float(np.median(ms) * 1e3),
-                                      "p99_us": float(np.percentile(ms, 99) * 1e3), "rel_l2_vs_fp64_oracle": err}
+                                      "p99_us": float(np.percentile(ms, 99) * 1e3), "rel_l2_vs_fp64_oracle": err,
+                                      "graph_replay_p50_us": float(np.median(ms_g) * 1e3),
+                                      "graph_replay_p99_us": float(np.percentile(ms_g, 99) * 1e3),
+                                      "graph_replay_rel_l2_vs_fp64_oracle": err_g}
             G.gw_model_destroy(m)
         # config 3: whitening (2049 taps) + BBHnet, batch 256
         Bc, Lr = 256, 4096
@@ -684,7 +695,8 @@ def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
     forward with tape, band-limited PSD-weighted loss (2049-tap weight FIR,
     55-65 Hz), its backward, the hand-written network backward and an Adam
     update of the FP32 master parameters - timed with CUDA events, with and
-    without per-block activation checkpointing."""
+    without per-block activation checkpointing, and with the weight gradients
+    on the tensor cores (BF16 operands, FP32 accumulation)."""
     from paper_2108_12430_gb300 import synth
     Bt, Lt = 32, 8192
     out = {}
@@ -696,8 +708,9 @@ def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
                              .astype(np.float32)).cuda()
         s = torch.from_numpy((np.random.default_rng(9).standard_normal((Bt, Lt)) * 0.3).astype(np.float32)).cuda()
         st = torch.cuda.current_stream().cuda_stream
-        for ck in (0, 1):
-            t = G.gw_trainer_create(ctx, C, Bt, Lt, ck)
+        for ck, prec, name in ((0, G.GW_FP32, "config4_fp32"), (1, G.GW_FP32, "config4_fp32_checkpoint"),
+                               (0, G.GW_BF16, "config4_bf16_wgrad")):
+            t = G.gw_trainer_create(ctx, C, Bt, Lt, ck, precision=prec)
             p = torch.from_numpy(synth.flatten_params(synth.deepclean_params(1234))).cuda()
             m, v, dp = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
             y, dy = torch.empty(Bt, Lt, device="cuda"), torch.empty(Bt, Lt, device="cuda")
@@ -725,8 +738,10 @@ def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
             G.gw_profile_enable(False)
             fwd = dc_flops_per_window(Lt) * Bt
             flops = 3 * fwd + (fwd // 2 if ck else 0) + 2 * 2 * 2049 * Bt * (Lt - 2048)
-            out[f"config4_fp32{'_checkpoint' if ck else ''}"] = {
+            G.gw_trainer_status(t, st)
+            out[name] = {
                 "workload": "DeepClean training step, 32 x 21 x 8192, band loss 2049 taps, Adam",
+                "weight_gradients": "tensor cores, BF16 operands" if prec == G.GW_BF16 else "FP32 SIMT",
                 "ms_per_step": float(np.mean(ms)), "p50_ms": float(np.median(ms)),
                 "windows_per_s": Bt / (np.mean(ms) / 1e3), "tflops": flops / (np.mean(ms) / 1e3) / 1e12,
                 "flops_per_step": flops, "loss": float(loss.item()), "kernels_per_step": launches,

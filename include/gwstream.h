@@ -442,19 +442,25 @@ int gw_partition_streams(int n, const int* stride, const int64_t* bytes, int n_d
  * where g is designed by gw_fir_create_band_loss.  BatchNorm uses its running
  * statistics, so it folds into the weights; the trained parameters are every
  * layer's raw w, b, gamma, beta in the canonical order of gw_model_create
- * (running mean / var get gradient 0).  All training calls are FP32 (SIMT
- * FMA) and stream-ordered on device pointers. */
+ * (running mean / var get gradient 0).  Training calls are stream-ordered on
+ * device pointers; the arithmetic is FP32 (SIMT FMA), except that with
+ * precision GW_BF16 the weight gradients of every layer run on the tensor
+ * cores (operands rounded to BF16, FP32 accumulation). */
 typedef struct gw_trainer* gw_trainer_t;
 typedef struct gw_trainer_desc {
   int n_in;        /* witness channels */
   int max_batch;   /* largest B of a forward */
   int length;      /* window length L (multiple of 8) */
   int checkpoint;  /* 1: keep only the four block inputs and recompute inside the backward */
+  int precision;   /* GW_FP32, or GW_BF16: weight gradients on the tensor cores (sm_103a) */
 } gw_trainer_desc;
 /* in_mean / in_std: host [n_in] input standardisation (may be NULL). */
 int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_mean, const float* in_std,
                       gw_trainer_t* out);
 int gw_trainer_destroy(gw_trainer_t t);
+/* GW_ETIMEOUT if a tensor-core kernel of this trainer gave up a bounded wait
+ * (synchronises cuda_stream), else GW_OK. */
+int gw_trainer_status(gw_trainer_t t, void* cuda_stream);
 /* Length of the flat raw parameter vector (= gw_model_param_count). */
 int64_t gw_trainer_param_count(gw_trainer_t t);
 int64_t gw_trainer_bytes(gw_trainer_t t);

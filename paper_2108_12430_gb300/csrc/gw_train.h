@@ -38,6 +38,12 @@ size_t wgrad_smem(const WgradArgs& w);
 // w.partial must hold B * w.chunks_per_b * NA * NC * K floats; out gets NA * NC * K.
 void launch_wgrad_partial(const WgradArgs& w, int B, cudaStream_t st);
 void launch_wgrad_reduce(const WgradArgs& w, int B, float* out, cudaStream_t st);
+// The same weight gradient on the tensor cores (BF16 operands, FP32
+// accumulation; k_wgrad_tc.cu): out gets NA * NC * K floats; partial must hold
+// wgrad_tc_partial_floats(w, B); err receives a bounded wait's give-up.
+bool wgrad_tc_supported(const WgradArgs& w);
+size_t wgrad_tc_partial_floats(const WgradArgs& w, int B);
+void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int* err, cudaStream_t st);
 // out[n] = sum_{b, t} G[b][n][t]; part holds B * N floats.
 void launch_bias_grad(const float* G, int64_t gb, int64_t gn, int B, int N, int L, float* part, float* out,
                       cudaStream_t st);

@@ -1,0 +1,279 @@
+// Weight gradient of a conv / transposed-conv layer on the tensor cores (BF16
+// operands, FP32 accumulation in TMEM), for the training step's backward.
+//
+// The weight gradient is one contraction over all (item, position) pairs:
+//   dW[a][c][k] = sum_{b, t} A[b][a][t] Bm[b][c][s t + k - p]
+// (conv: A = the output gradient, Bm = the layer input; transposed conv: A =
+// the layer input, Bm = the output gradient), zero outside [0, LB).  As a
+// GEMM, D[a][n] = sum_t A[a][t] B[n][t] with n = k NC + c and
+// B[n][t] = Bm[c][s t + k - p]: M = the A channels (zero-padded to 128 MMA
+// rows), N = K NC columns, and the reduction runs over positions, which is
+// the dimension the tensor core's K steps walk.
+//
+// Each CTA takes chunks of 64 positions of one item in turn.  All its threads
+// stage a chunk: FP32 values are read from global memory (the shifted, strided
+// B rows gathered directly), rounded to BF16 and stored in the canonical
+// K-major layout (core matrices of 8 rows x 16 bytes); one thread then issues
+// the chunk's four MMAs into the CTA's TMEM accumulator.  Two stages let the
+// threads fill one while the MMAs read the other.  At the end the
+// accumulator (D, NA x N) goes to the CTA's partial slot, and a second
+// kernel sums the partials in CTA order (deterministic).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "gw_internal.h"
+#include "gw_train.h"
+#include "tc_ptx.h"
+
+namespace gw {
+
+namespace {
+
+using namespace ptx;
+
+constexpr int kWgChunk = 64;     // positions per chunk (four MMA K steps)
+constexpr int kWgThreads = 256;
+constexpr int kWgRowsA = 128;    // MMA M: the A channels, zero-padded
+constexpr int kWgGroup = 4;      // 16-byte segments a thread loads before storing them
+constexpr int kWgMaxCtasPerSm = 2;
+
+struct WgTcParams {
+  const float* A;
+  int64_t ab, aa;  // A[b][a][t] at A + b ab + a aa + t, t < LA
+  int NA, LA;
+  const float* Bm;
+  int64_t bb, bc;  // Bm[b][c][u] at Bm + b bb + c bc + u, u < LB
+  int NC, LB;
+  int K, s, p;
+  int N, Npad;     // N = K NC columns n = k NC + c; Npad: N rounded up to 32
+  int chunks_per_b, n_chunks;
+  float* partial;  // [gridDim.x][NA][Npad]
+  int* err;
+};
+
+// Byte offset of 16-byte segment q (K elements 8q .. 8q + 7) of row r in a
+// K-major tile of R rows: core matrices of 8 rows x 16 bytes, K-adjacent core
+// matrices R / 8 x 128 bytes apart (the descriptor's LBO), row-adjacent ones
+// 128 bytes apart (SBO).
+__device__ __forceinline__ uint32_t seg_off(int r, int q, int R) {
+  return (uint32_t)((((q * (R >> 3)) + (r >> 3)) << 7) + ((r & 7) << 4));
+}
+
+// Stages chunk cid (item b, positions t0 .. t0 + 63) into the tiles at a_smem
+// (128 rows) and b_smem (Npad rows): task = (row, segment); each thread loads
+// kWgGroup tasks' 8 values before it rounds and stores them.
+__device__ __forceinline__ void stage_chunk(const WgTcParams& p, int cid, uint8_t* a_smem, uint8_t* b_smem) {
+  const int b = cid / p.chunks_per_b;
+  const int t0 = (cid - b * p.chunks_per_b) * kWgChunk;
+  const int n_tasks = (p.NA + p.N) * (kWgChunk / 8);
+  const float* Ab = p.A + (int64_t)b * p.ab;
+  const float* Bb = p.Bm + (int64_t)b * p.bb;
+  for (int g0 = threadIdx.x; g0 < n_tasks; g0 += kWgThreads * kWgGroup) {
+    float v[kWgGroup][8];
+#pragma unroll
+    for (int gi = 0; gi < kWgGroup; ++gi) {
+      const int task = g0 + gi * kWgThreads;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[gi][e] = 0.f;
+      if (task >= n_tasks) continue;
+      const int row = task >> 3, q = task & 7;
+      const int t = t0 + 8 * q;
+      if (row < p.NA) {
+        const float* src = Ab + (int64_t)row * p.aa;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (t + e < p.LA) v[gi][e] = src[t + e];
+      } else {
+        const int n = row - p.NA, k = n / p.NC, c = n - k * p.NC;
+        const float* src = Bb + (int64_t)c * p.bc;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int u = p.s * (t + e) + k - p.p;
+          if (u >= 0 && u < p.LB) v[gi][e] = src[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int gi = 0; gi < kWgGroup; ++gi) {
+      const int task = g0 + gi * kWgThreads;
+      if (task >= n_tasks) continue;
+      const int row = task >> 3, q = task & 7;
+      __nv_bfloat162 h[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[gi][2 * e], v[gi][2 * e + 1]);
+      uint8_t* dst = row < p.NA ? a_smem + seg_off(row, q, kWgRowsA) : b_smem + seg_off(row - p.NA, q, p.Npad);
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const WgTcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t base = smem_u32(smem);
+  const uint32_t a_bytes = kWgRowsA * kWgChunk * 2, b_bytes = (uint32_t)p.Npad * kWgChunk * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);  // [0..1] stage MMAs done, [2] all done
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 3);
+  uint32_t* tslot = (uint32_t*)(abort_flag + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // both stages start at zero: the A rows >= NA and B rows >= N are never
+  // written and contribute zeros
+  {
+    uint4* z = reinterpret_cast<uint4*>(smem);
+    for (uint32_t i = tid; i < 2 * stage_bytes / 16; i += kWgThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(smem_u32(&bars[i]), 1);
+    *abort_flag = 0u;
+    fence_barrier_init();
+  }
+  fence_proxy_async_smem();
+  const uint32_t tcols = p.Npad <= 128 ? 128u : 256u;
+  if (warp == 0) tmem_alloc(smem_u32(tslot), tcols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  // D = F32, A = B = BF16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.Npad >> 3) << 17) |
+                         ((uint32_t)(kWgRowsA >> 4) << 24);
+  const uint32_t lbo_a = (kWgRowsA / 8) * 128, lbo_b = (uint32_t)(p.Npad / 8) * 128;
+
+  int i = 0;
+  for (int cid = blockIdx.x; cid < p.n_chunks; cid += gridDim.x, ++i) {
+    const int st = i & 1;
+    bool ok = true;
+    // the stage's previous MMAs (chunk i - 2) have read it
+    if (i >= 2) ok = mbar_wait(smem_u32(&bars[st]), (uint32_t)((i - 2) >> 1) & 1u, abort_flag, p.err, 1);
+    if (!__syncthreads_and(ok)) break;
+    uint8_t* a_s = smem + st * stage_bytes;
+    stage_chunk(p, cid, a_s, a_s + a_bytes);
+    fence_proxy_async_smem();  // the stores above are read by the tensor core (async proxy)
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = base + st * stage_bytes, b0 = a0 + a_bytes;
+#pragma unroll
+      for (int j = 0; j < kWgChunk / 16; ++j)
+        mma_f16(tmem, make_desc(a0 + 2 * j * lbo_a, lbo_a, 128), make_desc(b0 + 2 * j * lbo_b, lbo_b, 128), idesc,
+                (i > 0 || j > 0) ? 1u : 0u);
+      mma_commit(smem_u32(&bars[st]));
+    }
+  }
+  // every MMA of this CTA has completed before the accumulator is read
+  if (tid == 0) mma_commit(smem_u32(&bars[2]));
+  mbar_wait_landed(smem_u32(&bars[2]), 0u, p.err, 2);
+  tc_fence_after();
+  if (warp < 4) {
+    const int r = warp * 32 + lane;  // TMEM lane = MMA row = A channel
+    float* dst = p.partial + ((int64_t)blockIdx.x * p.NA + r) * p.Npad;
+    for (int c0 = 0; c0 < p.Npad; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (r < p.NA) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) dst[c0 + q] = i > 0 ? v[q] : 0.f;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tcols);
+}
+
+// out[a][c][k] = sum over CTAs g of partial[g][a][k NC + c].  A block takes
+// 32 consecutive (a, n) columns of the partials; warp w sums g = w, w + 8, ...
+// in order (lanes on consecutive n: coalesced), then the eight warp sums are
+// added in warp order, so the result does not depend on the schedule.
+constexpr int kWgRedWarps = 8;
+__global__ void __launch_bounds__(32 * kWgRedWarps) wgrad_tc_reduce_kernel(const float* __restrict__ partial, int G,
+                                                                          int NA, int NC, int K, int Npad,
+                                                                          float* __restrict__ out) {
+  __shared__ float red[kWgRedWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;  // index into [NA][Npad]
+  const int64_t stride = (int64_t)NA * Npad;
+  float acc = 0.f;
+  if (e < stride) {
+    const float* src = partial + e;
+    int g = warp;
+    for (; g + 3 * kWgRedWarps < G; g += 4 * kWgRedWarps) {
+      const float v0 = src[(int64_t)g * stride], v1 = src[(int64_t)(g + kWgRedWarps) * stride];
+      const float v2 = src[(int64_t)(g + 2 * kWgRedWarps) * stride], v3 = src[(int64_t)(g + 3 * kWgRedWarps) * stride];
+      acc += v0;
+      acc += v1;
+      acc += v2;
+      acc += v3;
+    }
+    for (; g < G; g += kWgRedWarps) acc += src[(int64_t)g * stride];
+  }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && e < stride) {
+    float t = 0.f;
+    for (int w = 0; w < kWgRedWarps; ++w) t += red[w][lane];
+    const int a = (int)(e / Npad), n = (int)(e - (int64_t)a * Npad);
+    if (n < NC * K) {
+      const int k = n / NC, c = n - k * NC;
+      out[((int64_t)a * NC + c) * K + k] = t;
+    }
+  }
+}
+
+int wgrad_tc_grid(const WgradArgs& w, int B) {
+  const int chunks = B * ((w.LA + kWgChunk - 1) / kWgChunk);
+  return std::max(1, std::min(chunks, kWgMaxCtasPerSm * current_sm_count()));
+}
+
+}  // namespace
+
+bool wgrad_tc_supported(const WgradArgs& w) {
+  return tc_supported() && w.NA >= 1 && w.NA <= kWgRowsA && w.NC >= 1 && w.K * w.NC <= 256;
+}
+
+size_t wgrad_tc_partial_floats(const WgradArgs& w, int B) {
+  const int Npad = (w.K * w.NC + 31) / 32 * 32;
+  return (size_t)wgrad_tc_grid(w, B) * w.NA * Npad;
+}
+
+void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int* err, cudaStream_t st) {
+  GW_CHECK_ARG(wgrad_tc_supported(w), "layer shape outside the tensor-core weight-gradient kernel");
+  WgTcParams p{};
+  p.A = w.A;
+  p.ab = w.ab;
+  p.aa = w.aa;
+  p.NA = w.NA;
+  p.LA = w.LA;
+  p.Bm = w.Bm;
+  p.bb = w.bb;
+  p.bc = w.bc;
+  p.NC = w.NC;
+  p.LB = w.LB;
+  p.K = w.K;
+  p.s = w.s;
+  p.p = w.p;
+  p.N = w.K * w.NC;
+  p.Npad = (p.N + 31) / 32 * 32;
+  p.chunks_per_b = (w.LA + kWgChunk - 1) / kWgChunk;
+  p.n_chunks = B * p.chunks_per_b;
+  p.partial = partial;
+  p.err = err;
+  const int grid = wgrad_tc_grid(w, B);
+  // at least 80 KB of shared memory per CTA, so that at most two CTAs share an
+  // SM and their TMEM allocations (up to 256 columns each) always fit
+  const size_t smem = std::max<size_t>(80 * 1024, 1024 + 2 * (size_t)(kWgRowsA + p.Npad) * kWgChunk * 2 + 3 * 8 + 8);
+  // the limit is set once per device, for the widest layer the kernel takes (N = 256)
+  set_smem_limit_once(wgrad_tc_kernel,
+                      (int)std::max<size_t>(80 * 1024, 1024 + 2 * (size_t)(kWgRowsA + 256) * kWgChunk * 2 + 3 * 8 + 8));
+  wgrad_tc_kernel<<<grid, kWgThreads, smem, st>>>(p);
+  GW_LAUNCH_CHECK();
+  const int64_t cols = (int64_t)w.NA * p.Npad;
+  wgrad_tc_reduce_kernel<<<(unsigned)((cols + 31) / 32), 32 * kWgRedWarps, 0, st>>>(partial, grid, w.NA, w.NC, w.K,
+                                                                                  p.Npad, out);
+  GW_LAUNCH_CHECK();
+}
+
+}  // namespace gw

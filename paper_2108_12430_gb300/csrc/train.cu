@@ -16,6 +16,9 @@
 //   dW' = wgrad(input, dv), db' = sum dv      (fixed-order reductions)
 //   raw: dw = dW' sc, db = db' sc, dbeta = db', dgamma = a (sum w dW' + db' (b - mean))
 //   d input = conv-transpose of dv with W'^T (conv) / conv of dv with W'^T (transposed conv)
+// Weight gradients: FP32 (SIMT FMA, fixed-order reductions) or, with
+// precision GW_BF16, on the tensor cores (BF16 operands, FP32 accumulation in
+// TMEM, per-CTA partials summed in a fixed order; k_wgrad_tc.cu).
 // Activation checkpointing: with `checkpoint`, only the inputs of the four
 // blocks (enc1-enc2, enc3-enc4, dec1-dec2, dec3-out) are kept and the first
 // layer's output of each block is recomputed during the backward.
@@ -35,7 +38,8 @@ struct TrainLayer {
 
 struct gw_trainer {
   gw_ctx* ctx = nullptr;
-  int n_in = 0, max_batch = 0, L = 0, checkpoint = 0;
+  int n_in = 0, max_batch = 0, L = 0, checkpoint = 0, wgrad_tc = 0;
+  int* err = nullptr;  // device: a tensor-core kernel gave up a bounded wait
   size_t n_params = 0;
   std::vector<gw::TrainLayer> layers;
   float* in_mean = nullptr;
@@ -76,6 +80,9 @@ void trainer_free(gw_trainer* t) {
 
 const char* kWgradNames[8] = {"train.wgrad.enc1", "train.wgrad.enc2", "train.wgrad.enc3", "train.wgrad.enc4",
                               "train.wgrad.dec1", "train.wgrad.dec2", "train.wgrad.dec3", "train.wgrad.out"};
+const char* kWgradTcNames[8] = {"train.wgrad_tc.enc1", "train.wgrad_tc.enc2", "train.wgrad_tc.enc3",
+                                "train.wgrad_tc.enc4", "train.wgrad_tc.dec1", "train.wgrad_tc.dec2",
+                                "train.wgrad_tc.dec3", "train.wgrad_tc.out"};
 
 bool recomputed(const gw_trainer* t, int l) { return t->checkpoint && (l % 2 == 0) && l + 1 < (int)t->layers.size(); }
 
@@ -118,6 +125,8 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
   GW_CHECK_ARG(d->max_batch >= 1 && d->max_batch <= 4096, "max_batch out of range");
   GW_CHECK_ARG(d->length >= 16 && d->length % 8 == 0, "length must be a multiple of 8, >= 16");
   GW_CHECK_ARG(d->checkpoint == 0 || d->checkpoint == 1, "checkpoint must be 0 or 1");
+  GW_CHECK_ARG(d->precision == GW_FP32 || d->precision == GW_BF16, "trainer precision must be FP32 or BF16");
+  GW_CHECK_ARG(d->precision == GW_FP32 || tc_supported(), "BF16 weight gradients need the sm_103a tensor cores");
   GW_CUDA(cudaSetDevice(ctx->device));
   t = new gw_trainer();
   try {
@@ -126,6 +135,7 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
     t->max_batch = d->max_batch;
     t->L = d->length;
     t->checkpoint = d->checkpoint;
+    t->wgrad_tc = d->precision == GW_BF16;
     const auto specs = deepclean_specs(d->n_in);
     int64_t off = 0;
     int lin = d->length;
@@ -160,6 +170,8 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
       const WgradArgs w = s.transposed ? plan_wgrad(s.cin, s.cout, s.k, s.stride, T.lin)
                                        : plan_wgrad(s.cout, s.cin, s.k, s.stride, T.lout);
       max_partial = std::max(max_partial, (size_t)d->max_batch * w.chunks_per_b * nw);
+      if (d->precision == GW_BF16 && wgrad_tc_supported(w))
+        max_partial = std::max(max_partial, wgrad_tc_partial_floats(w, d->max_batch));
       t->layers.push_back(T);
       lin = T.lout;
     }
@@ -198,11 +210,22 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
     t->dbf = talloc<float>(t, max_c);
     t->bpart = talloc<float>(t, (size_t)Bm * max_c);
     t->zero_bias = talloc<float>(t, max_c);
+    t->err = talloc<int>(t, 1);
   } catch (...) {
     trainer_free(t);
     throw;
   }
   *out = t;
+  GW_API_END
+}
+
+int gw_trainer_status(gw_trainer_t t, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(t, "trainer is NULL");
+  int h = 0;
+  GW_CUDA(cudaMemcpyAsync(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream));
+  GW_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  if (h) throw Error(GW_ETIMEOUT, "a tensor-core kernel gave up a bounded wait (flag " + std::to_string(h) + ")");
   GW_API_END
 }
 
@@ -283,13 +306,18 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
     }
     w.p = s.pad_l;
     w.partial = t->partial;
-    {
-      Prof p(l < 8 ? kWgradNames[l] : "train.wgrad", st);
-      launch_wgrad_partial(w, B, st);
-    }
-    {
-      Prof p("train.wgrad_reduce", st);
-      launch_wgrad_reduce(w, B, t->dWf, st);
+    if (t->wgrad_tc && wgrad_tc_supported(w)) {
+      Prof p(l < 8 ? kWgradTcNames[l] : "train.wgrad_tc", st);
+      launch_wgrad_tc(w, B, t->partial, t->dWf, t->err, st);
+    } else {
+      {
+        Prof p(l < 8 ? kWgradNames[l] : "train.wgrad", st);
+        launch_wgrad_partial(w, B, st);
+      }
+      {
+        Prof p("train.wgrad_reduce", st);
+        launch_wgrad_reduce(w, B, t->dWf, st);
+      }
     }
     {
       Prof p("train.bgrad", st);

@@ -42,7 +42,7 @@ EXPORTS = (
     "gw_model_status", "gw_tc_inspect", "gw_fir_create_lowpass",
     "gw_server_create", "gw_server_open", "gw_server_close", "gw_server_stream_bytes", "gw_server_submit",
     "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
-    "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
+    "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_status", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
     "gw_trainer_backward", "gw_fir_create_band_loss", "gw_band_loss", "gw_band_loss_backward", "gw_fir_backward",
     "gw_adam_step", "gw_model_calibrate", "gw_model_test_wait_timeout", "gw_fir_create_bandpass",
     "gw_scored_stream_create", "gw_scored_stream_push", "gw_scored_stream_wait", "gw_scored_stream_destroy",
@@ -81,7 +81,8 @@ class gw_server_stats(C.Structure):
 
 
 class gw_trainer_desc(C.Structure):
-    _fields_ = [("n_in", C.c_int), ("max_batch", C.c_int), ("length", C.c_int), ("checkpoint", C.c_int)]
+    _fields_ = [("n_in", C.c_int), ("max_batch", C.c_int), ("length", C.c_int), ("checkpoint", C.c_int),
+                ("precision", C.c_int)]
 
 
 _lib = None
@@ -136,6 +137,7 @@ def _declare(lib):
         "gw_server_destroy": (I, [P]),
         "gw_trainer_create": (I, [P, C.POINTER(gw_trainer_desc), P, P, C.POINTER(P)]),
         "gw_trainer_destroy": (I, [P]),
+        "gw_trainer_status": (I, [P, P]),
         "gw_trainer_param_count": (I64, [P]),
         "gw_trainer_bytes": (I64, [P]),
         "gw_trainer_forward": (I, [P, P, P, I, P, P]),
@@ -463,8 +465,8 @@ def gw_server_destroy(s):
     _check(lib().gw_server_destroy(s))
 
 
-def gw_trainer_create(ctx, n_in, max_batch, length, checkpoint=0, in_mean=None, in_std=None):
-    d = gw_trainer_desc(n_in, max_batch, length, checkpoint)
+def gw_trainer_create(ctx, n_in, max_batch, length, checkpoint=0, in_mean=None, in_std=None, precision=GW_FP32):
+    d = gw_trainer_desc(n_in, max_batch, length, checkpoint, precision)
     m = None if in_mean is None else np.ascontiguousarray(in_mean, np.float32)
     s = None if in_std is None else np.ascontiguousarray(in_std, np.float32)
     h = P()
@@ -475,6 +477,10 @@ def gw_trainer_create(ctx, n_in, max_batch, length, checkpoint=0, in_mean=None, 
 
 def gw_trainer_destroy(t):
     _check(lib().gw_trainer_destroy(t))
+
+
+def gw_trainer_status(t, stream=0):
+    _check(lib().gw_trainer_status(t, stream or None))
 
 
 def gw_trainer_param_count(t):

@@ -98,10 +98,10 @@ def groups(params):
 class Run:
     """A trainer, a loss FIR and device buffers for one case."""
 
-    def __init__(self, ctx, params, x, s, mean, std, psd, ntaps, nfft, checkpoint=0, B_max=None):
+    def __init__(self, ctx, params, x, s, mean, std, psd, ntaps, nfft, checkpoint=0, B_max=None, precision=G.GW_FP32):
         B, _, L = x.shape
         self.B, self.L = B, L
-        self.t = G.gw_trainer_create(ctx.h, C, B_max or B, L, checkpoint, mean, std)
+        self.t = G.gw_trainer_create(ctx.h, C, B_max or B, L, checkpoint, mean, std, precision=precision)
         ctx.objs.append((G.gw_trainer_destroy, self.t))
         self.g = G.gw_fir_create_band_loss(ctx.h, psd, 4096.0, ntaps)
         ctx.objs.append((G.gw_fir_destroy, self.g))
@@ -173,6 +173,29 @@ def test_gradient_matches_finite_differences(ctx):
     err = rel_l2(an, fd)
     print("sampled gradient vs finite differences rel-L2", err)
     assert err <= 1e-4
+
+
+# BF16 weight gradients: rounding both operands of every product to BF16
+# bounds its relative error by about 2^-8 = 3.9e-3; sums whose terms partly
+# cancel can exceed that by a small factor, hence 1e-2 (the data gradients,
+# bias gradients and the loss stay FP32).
+TOL_WG16 = 1e-2
+
+
+@pytest.mark.parametrize("B,L,ntaps,nfft", [(2, 512, 129, 2048), (2, 8192, 2049, 8192)])
+def test_tensor_core_weight_gradients_match_oracle(ctx, B, L, ntaps, nfft):
+    c = case(B, L, ntaps=ntaps, nfft=nfft)
+    loss_ref, y_ref, grads_ref = oracle(*c)
+    run = Run(ctx, *c, precision=G.GW_BF16)
+    loss, y, dp = run.step()
+    G.gw_trainer_status(run.t)
+    assert abs(loss - loss_ref) <= TOL32 * abs(loss_ref)
+    assert rel_l2(y, y_ref) <= TOL32
+    worst = check_grads(dp, flat_grads(grads_ref), c[0], tol=TOL_WG16)
+    print("BF16 weight gradients: worst rel-L2", worst)
+    # the FP32 trainer on the same case stays within the same bound of it
+    _, _, dp32 = Run(ctx, *c).step()
+    assert rel_l2(dp, dp32) <= TOL_WG16
 
 
 def test_full_length_gradient_and_batch_mean_property(ctx):
@@ -248,9 +271,10 @@ def test_adam_step(ctx):
     assert np.abs(p.cpu().numpy() - pp).max() <= 1e-6
 
 
-def test_training_reduces_the_loss(ctx):
+@pytest.mark.parametrize("precision", [G.GW_FP32, G.GW_BF16])
+def test_training_reduces_the_loss(ctx, precision):
     c = case(4, 1024)
-    run = Run(ctx, *c)
+    run = Run(ctx, *c, precision=precision)
     m = torch.zeros_like(run.p)
     v = torch.zeros_like(run.p)
     losses = []
