@@ -78,7 +78,8 @@ struct Tick {
   int slot = 0, n = 0, bucket = 0, bi = 0;
   int64_t kernels = 0;
   double t_launch = 0;  // host time of the launch
-  double t_expect = 0;  // expected completion (launch or the previous tick's expected end, + estimated duration)
+  double t_a_end = 0;   // expected end of the first stage (it starts after the previous tick's first stage)
+  double t_expect = 0;  // expected completion (its second stage starts after the previous tick's)
   std::vector<int> reqs;
 };
 
@@ -119,10 +120,13 @@ struct gw_server {
   float* req_out = nullptr;
   size_t req_in_elems = 0, req_out_elems = 0;
 
-  cudaStream_t st = nullptr, side = nullptr;
+  cudaStream_t st = nullptr, side = nullptr, st2 = nullptr;  // st2: the ticks' second stage
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaEvent_t done_ev[gw::kMaxInflight] = {};
-  std::vector<cudaGraphExec_t> graphs;  // [bucket][slot]
+  // per slot: first stage starts / ends, second stage starts (done_ev: ends)
+  cudaEvent_t start_ev[gw::kMaxInflight] = {}, mid_ev[gw::kMaxInflight] = {}, bstart_ev[gw::kMaxInflight] = {};
+  std::vector<cudaGraphExec_t> graphs;    // [bucket][slot]: first stage
+  std::vector<cudaGraphExec_t> graphs_b;  // [bucket][slot]: second stage
   std::vector<int64_t> graph_kernels;   // per bucket
 
   // host state (guarded by mu)
@@ -136,7 +140,8 @@ struct gw_server {
   uint64_t next_ticket = 1;
   std::deque<gw::Tick> inflight;
   int64_t tick_seq = 0;
-  std::vector<double> dur_us;  // per bucket: running estimate of a tick's device time (0 = none yet)
+  std::vector<double> dur_us;    // per bucket: running estimate of a tick's first-stage device time (0 = none yet)
+  std::vector<double> dur_b_us;  // ... and of its second stage
   double t_prev_done = 0;      // completion time of the last completed tick
   bool stop = false, loop_done = false;
   int sticky = 0;
@@ -212,9 +217,11 @@ void* window_ptr(const gw_server* s, void* ring, int64_t p0) {
   return (float*)ring + p0;
 }
 
-// Enqueues the kernels of one tick of bucket Bb using table slot `slot` on
-// streams a (main) and b (second detector's branch).
-void record_tick(gw_server* s, int Bb, int slot, cudaStream_t a, cudaStream_t b) {
+// Enqueues the first stage of one tick of bucket Bb using table slot `slot`
+// (the tick table upload and both detectors' branches: ring update,
+// DeepClean, subtraction, resampling, whitening) on streams a (main) and b
+// (second detector's branch, joined back into a).
+void record_tick_a(gw_server* s, int Bb, int slot, cudaStream_t a, cudaStream_t b) {
   const ServeGeom& g = s->geom;
   const int nd = s->d.n_det, Bmax = s->d.max_batch, W = s->d.window;
   ServeItem* items = s->d_items[slot];
@@ -268,6 +275,16 @@ void record_tick(gw_server* s, int Bb, int slot, cudaStream_t a, cudaStream_t b)
     GW_CUDA(cudaEventRecord(s->join_ev, b));
     GW_CUDA(cudaStreamWaitEvent(a, s->join_ev, 0));
   }
+}
+
+// Enqueues the second stage of the tick (BBHnet on the newest whitened
+// samples and the scores) on stream a.  It reads only the whitened rings' last
+// bbh_len samples and the slot's table, so the next tick's first stage (which
+// writes newer whitened samples) may run beside it.
+void record_tick_b(gw_server* s, int Bb, int slot, cudaStream_t a) {
+  const ServeGeom& g = s->geom;
+  const int nd = s->d.n_det;
+  ServeItem* items = s->d_items[slot];
   if (s->bbh) {
     {
       Prof p("serve_gather", a);
@@ -302,6 +319,7 @@ int64_t graph_kernel_count(cudaGraph_t g) {
 void capture_graphs(gw_server* s) {
   const int nb = (int)s->buckets.size();
   s->graphs.assign((size_t)nb * s->n_slots, nullptr);
+  s->graphs_b.assign((size_t)nb * s->n_slots, nullptr);
   s->graph_kernels.assign(nb, 0);
   cudaStream_t cs = nullptr, cb = nullptr;
   GW_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -314,28 +332,33 @@ void capture_graphs(gw_server* s) {
       cudaStreamDestroy(b);
     }
   } guard{cs, cb};
-  for (int bi = 0; bi < nb; ++bi)
-    for (int slot = 0; slot < s->n_slots; ++slot) {
-      cudaGraph_t graph = nullptr;
-      prof_set_capturing(true);
-      GW_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      try {
-        record_tick(s, s->buckets[bi], slot, cs, cb);
-      } catch (...) {
-        cudaStreamEndCapture(cs, &graph);
-        if (graph) cudaGraphDestroy(graph);
-        throw;
-      }
-      GW_CUDA(cudaStreamEndCapture(cs, &graph));
-      prof_set_capturing(false);
-      cudaGraphExec_t exec = nullptr;
-      const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-      const int64_t kern = e == cudaSuccess ? graph_kernel_count(graph) : 0;
-      cudaGraphDestroy(graph);
-      GW_CUDA(e);
-      s->graphs[(size_t)bi * s->n_slots + slot] = exec;
-      s->graph_kernels[bi] = kern;
+  auto capture = [&](int bi, int slot, bool second) {
+    cudaGraph_t graph = nullptr;
+    prof_set_capturing(true);
+    GW_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+      if (second)
+        record_tick_b(s, s->buckets[bi], slot, cs);
+      else
+        record_tick_a(s, s->buckets[bi], slot, cs, cb);
+    } catch (...) {
+      cudaStreamEndCapture(cs, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
     }
+    GW_CUDA(cudaStreamEndCapture(cs, &graph));
+    prof_set_capturing(false);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    const int64_t kern = e == cudaSuccess ? graph_kernel_count(graph) : 0;
+    cudaGraphDestroy(graph);
+    GW_CUDA(e);
+    (second ? s->graphs_b : s->graphs)[(size_t)bi * s->n_slots + slot] = exec;
+    return kern;
+  };
+  for (int bi = 0; bi < nb; ++bi)
+    for (int slot = 0; slot < s->n_slots; ++slot)  // every slot's graphs hold the same kernels
+      s->graph_kernels[bi] = capture(bi, slot, false) + capture(bi, slot, true);
 }
 
 int bucket_index(const gw_server* s, int n) {
@@ -380,12 +403,16 @@ void loop_main(gw_server* s) {
              (!s->queue.empty() && (int)s->inflight.size() < s->n_slots);
     });
     if (s->queue.empty()) break;  // stopping and drained
-    // just-in-time formation: while a tick runs, wait until it is expected to
-    // end within form_lead_us (or a full batch is queued), so that snapshots
+    // just-in-time formation: while a tick runs, wait until the next one can
+    // start within form_lead_us - its first stage once the running tick's
+    // first stage has ended, timed so that it ends when the running tick's
+    // second stage does - (or a full batch is queued), so that snapshots
     // arriving meanwhile join the next tick instead of the one after it
     if (s->d.form_lead_us > 0) {
       while (!s->stop && !s->inflight.empty() && (int)s->queue.size() < s->d.max_batch) {
-        const double ready = s->inflight.back().t_expect - s->d.form_lead_us, now = now_us();
+        const Tick& last = s->inflight.back();
+        const double ready = std::max(last.t_a_end, last.t_expect - s->dur_us[last.bi]) - s->d.form_lead_us;
+        const double now = now_us();
         if (now >= ready) break;
         s->cv_loop.wait_for(lk, std::chrono::microseconds((int64_t)std::max(1.0, ready - now)));
       }
@@ -415,9 +442,11 @@ void loop_main(gw_server* s) {
     t.bucket = s->buckets[t.bi];
     {
       const double now = now_us();
-      const double start = s->inflight.empty() ? now : std::max(now, s->inflight.back().t_expect);
+      const double a_start = s->inflight.empty() ? now : std::max(now, s->inflight.back().t_a_end);
       t.t_launch = now;
-      t.t_expect = start + s->dur_us[t.bi];
+      t.t_a_end = a_start + s->dur_us[t.bi];
+      t.t_expect = (s->inflight.empty() ? t.t_a_end : std::max(t.t_a_end, s->inflight.back().t_expect)) +
+                   s->dur_b_us[t.bi];
     }
     proto.resize((size_t)s->d.n_det * t.n);
     for (int r = 0; r < t.n; ++r) {
@@ -459,16 +488,26 @@ void loop_main(gw_server* s) {
     try {
       fill_table(s, t, proto);
       const int bi = bucket_index(s, t.n);
-      if (s->d.use_graphs) {
+      // first stage on st, second stage on st2 after it: the next tick's
+      // first stage runs beside this tick's second stage
+      GW_CUDA(cudaEventRecord(s->start_ev[t.slot], s->st));
+      const int64_t before = gw_launch_count();
+      if (s->d.use_graphs)
         GW_CUDA(cudaGraphLaunch(s->graphs[(size_t)bi * s->n_slots + t.slot], s->st));
+      else
+        record_tick_a(s, t.bucket, t.slot, s->st, s->side);
+      GW_CUDA(cudaEventRecord(s->mid_ev[t.slot], s->st));
+      GW_CUDA(cudaStreamWaitEvent(s->st2, s->mid_ev[t.slot], 0));
+      GW_CUDA(cudaEventRecord(s->bstart_ev[t.slot], s->st2));
+      if (s->d.use_graphs) {
+        GW_CUDA(cudaGraphLaunch(s->graphs_b[(size_t)bi * s->n_slots + t.slot], s->st2));
         add_launches(s->graph_kernels[bi]);
         t.kernels = s->graph_kernels[bi];
       } else {
-        const int64_t before = gw_launch_count();
-        record_tick(s, t.bucket, t.slot, s->st, s->side);
+        record_tick_b(s, t.bucket, t.slot, s->st2);
         t.kernels = gw_launch_count() - before;
       }
-      GW_CUDA(cudaEventRecord(s->done_ev[t.slot], s->st));
+      GW_CUDA(cudaEventRecord(s->done_ev[t.slot], s->st2));
     } catch (const std::exception& e) {
       ok = false;
       err = e.what();
@@ -492,6 +531,11 @@ void done_main(gw_server* s) {
     const int slot = t.slot;
     lk.unlock();
     const cudaError_t e = cudaEventSynchronize(s->done_ev[slot]);
+    // the slot's stage timings, read before the slot can be reused
+    float a_ms = 0.f, b_ms = 0.f;
+    const bool timed = e == cudaSuccess &&
+                       cudaEventElapsedTime(&a_ms, s->start_ev[slot], s->mid_ev[slot]) == cudaSuccess &&
+                       cudaEventElapsedTime(&b_ms, s->bstart_ev[slot], s->done_ev[slot]) == cudaSuccess;
     const int dev_status = s->h_status[slot];
     lk.lock();
     if (e != cudaSuccess) fail_all_locked(s, GW_ECUDA, std::string("tick failed: ") + cudaGetErrorString(e));
@@ -503,11 +547,13 @@ void done_main(gw_server* s) {
     lk.unlock();
     const double t_now = now_us();
     {
-      // device time of the tick: from its launch, or from the previous
-      // tick's completion when it had to wait for it
-      const double d_us = t_now - std::max(done.t_launch, s->t_prev_done);
-      double& e = s->dur_us[done.bi];
-      e = e > 0 ? 0.8 * e + 0.2 * d_us : d_us;
+      // device time of the tick's two stages (events around each stage)
+      if (timed) {
+        double& ea = s->dur_us[done.bi];
+        double& eb = s->dur_b_us[done.bi];
+        ea = ea > 0 ? 0.8 * ea + 0.2 * 1e3 * a_ms : 1e3 * a_ms;
+        eb = eb > 0 ? 0.8 * eb + 0.2 * 1e3 * b_ms : 1e3 * b_ms;
+      }
       s->t_prev_done = t_now;
     }
     for (int rid : done.reqs) {
@@ -556,6 +602,8 @@ void server_free(gw_server* s) {
   s->cv_complete.notify_all();
   if (s->done_th.joinable()) s->done_th.join();
   if (s->st) cudaStreamSynchronize(s->st);
+  for (auto g : s->graphs_b)
+    if (g) cudaGraphExecDestroy(g);
   for (auto g : s->graphs)
     if (g) cudaGraphExecDestroy(g);
   for (auto& sm : s->streams)
@@ -563,11 +611,13 @@ void server_free(gw_server* s) {
   for (auto& a : s->allocs) dev_free(s->ctx, a.first, a.second, nullptr);
   for (void* p : s->host_allocs) cudaFreeHost(p);
   for (int i = 0; i < kMaxInflight; ++i)
-    if (s->done_ev[i]) cudaEventDestroy(s->done_ev[i]);
+    for (cudaEvent_t ev : {s->done_ev[i], s->start_ev[i], s->mid_ev[i], s->bstart_ev[i]})
+      if (ev) cudaEventDestroy(ev);
   if (s->fork_ev) cudaEventDestroy(s->fork_ev);
   if (s->join_ev) cudaEventDestroy(s->join_ev);
   if (s->st) cudaStreamDestroy(s->st);
   if (s->side) cudaStreamDestroy(s->side);
+  if (s->st2) cudaStreamDestroy(s->st2);
   delete s;
 }
 
@@ -719,6 +769,7 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
       if (b < d->max_batch) s->buckets.push_back(b);
     s->buckets.push_back(d->max_batch);
     s->dur_us.assign(s->buckets.size(), 0.0);
+    s->dur_b_us.assign(s->buckets.size(), 0.0);
 
     // device workspace
     const int Bmax = d->max_batch, nd = d->n_det, W = d->window;
@@ -762,7 +813,13 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
     GW_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     GW_CUDA(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
     GW_CUDA(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
-    for (int i = 0; i < kMaxInflight; ++i) GW_CUDA(cudaEventCreateWithFlags(&s->done_ev[i], cudaEventDisableTiming));
+    GW_CUDA(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking));
+    for (int i = 0; i < kMaxInflight; ++i) {
+      GW_CUDA(cudaEventCreate(&s->done_ev[i]));
+      GW_CUDA(cudaEventCreate(&s->start_ev[i]));
+      GW_CUDA(cudaEventCreate(&s->mid_ev[i]));
+      GW_CUDA(cudaEventCreate(&s->bstart_ev[i]));
+    }
     GW_CUDA(cudaDeviceSynchronize());
     // one eager all-padding tick of the largest bucket sets the kernels' lazy
     // attributes before capture
@@ -772,7 +829,8 @@ int gw_server_create(gw_ctx_t ctx, const gw_server_desc* d, const gw_model_t* de
       t.n = 0;
       t.bucket = s->buckets.back();
       fill_table(s, t, {});
-      record_tick(s, t.bucket, 0, s->st, s->side);
+      record_tick_a(s, t.bucket, 0, s->st, s->side);
+      record_tick_b(s, t.bucket, 0, s->st);
       GW_CUDA(cudaStreamSynchronize(s->st));
       int e = 0;
       GW_CUDA(cudaMemcpy(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
