@@ -708,9 +708,9 @@ def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
                              .astype(np.float32)).cuda()
         s = torch.from_numpy((np.random.default_rng(9).standard_normal((Bt, Lt)) * 0.3).astype(np.float32)).cuda()
         st = torch.cuda.current_stream().cuda_stream
-        for ck, prec, name in ((0, G.GW_FP32, "config4_fp32"), (1, G.GW_FP32, "config4_fp32_checkpoint"),
-                               (0, G.GW_BF16, "config4_bf16_wgrad")):
-            t = G.gw_trainer_create(ctx, C, Bt, Lt, ck, precision=prec)
+        for ck, prec, tcd, name in ((0, G.GW_FP32, 0, "config4_fp32"), (1, G.GW_FP32, 0, "config4_fp32_checkpoint"),
+                                    (0, G.GW_BF16, 0, "config4_bf16_wgrad"), (0, G.GW_BF16, 1, "config4_bf16")):
+            t = G.gw_trainer_create(ctx, C, Bt, Lt, ck, precision=prec, tc_data=tcd)
             p = torch.from_numpy(synth.flatten_params(synth.deepclean_params(1234))).cuda()
             m, v, dp = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
             y, dy = torch.empty(Bt, Lt, device="cuda"), torch.empty(Bt, Lt, device="cuda")
@@ -742,6 +742,7 @@ def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
             out[name] = {
                 "workload": "DeepClean training step, 32 x 21 x 8192, band loss 2049 taps, Adam",
                 "weight_gradients": "tensor cores, BF16 operands" if prec == G.GW_BF16 else "FP32 SIMT",
+                "forward_and_data_gradients": "tensor cores, BF16 operands" if tcd else "FP32 SIMT",
                 "ms_per_step": float(np.mean(ms)), "p50_ms": float(np.median(ms)),
                 "windows_per_s": Bt / (np.mean(ms) / 1e3), "tflops": flops / (np.mean(ms) / 1e3) / 1e12,
                 "flops_per_step": flops, "loss": float(loss.item()), "kernels_per_step": launches,

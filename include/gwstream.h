@@ -445,7 +445,10 @@ int gw_partition_streams(int n, const int* stride, const int64_t* bytes, int n_d
  * (running mean / var get gradient 0).  Training calls are stream-ordered on
  * device pointers; the arithmetic is FP32 (SIMT FMA), except that with
  * precision GW_BF16 the weight gradients of every layer run on the tensor
- * cores (operands rounded to BF16, FP32 accumulation). */
+ * cores (operands rounded to BF16, FP32 accumulation), and with tc_data also
+ * every layer's forward conv and data gradient (the layer inputs and output
+ * gradients are rounded to BF16 for the MMAs; activations and gradients are
+ * kept in FP32 between layers). */
 typedef struct gw_trainer* gw_trainer_t;
 typedef struct gw_trainer_desc {
   int n_in;        /* witness channels */
@@ -453,6 +456,8 @@ typedef struct gw_trainer_desc {
   int length;      /* window length L (multiple of 8) */
   int checkpoint;  /* 1: keep only the four block inputs and recompute inside the backward */
   int precision;   /* GW_FP32, or GW_BF16: weight gradients on the tensor cores (sm_103a) */
+  int tc_data;     /* with GW_BF16: 1 = the forward convs and the data gradients on the tensor cores too
+                      (BF16 operands, FP32 activations and gradients between layers) */
 } gw_trainer_desc;
 /* in_mean / in_std: host [n_in] input standardisation (may be NULL). */
 int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_mean, const float* in_std,

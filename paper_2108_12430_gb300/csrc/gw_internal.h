@@ -278,6 +278,13 @@ struct TcOut {
   int rP;
   int fp8_out;           // write e4m3 (scaled by out_scale) instead of bf16
   int fp32_d2s;          // 8-channel layer: write FP32 [B][bstride], channel o of position u at 8 u + o
+  // FP32 [B][C][L] output (training): channel o of position u at p + b bstride + o gstride + u (floats),
+  // optionally times the derivative of an activation whose output is gy (same layout, strides gy_b,
+  // gy_c): 1 - gy^2 (tanh) or gy > 0 (ReLU)
+  int fp32_full;
+  const float* gy;
+  int64_t gy_b, gy_c;
+  int gact;
 };
 // Blocked output of `cout` channels x `lout` positions in P planes, and its view
 // as the next layer's input (api.cu).
@@ -306,6 +313,14 @@ void tc_lower_layer(LayerDev& L, const std::vector<double>& wf, std::vector<uint
 // Byte offset of slice `code` in a buffer of P planes per channel group and
 // `rows` 16-byte rows per plane.
 uint32_t tc_slice_offset(uint32_t code, int P, int rows);
+// Tensor-core layer whose weights change on the device (training): the
+// lowering's operand image is allocated on the device and refilled by
+// launch_tc_pack from FP32 weights; src_of maps a weight in the layer's own
+// [C_out][C_in][K] order to its index in the array given to launch_tc_pack.
+// Returns the device map (image element -> weight index, or -1) and its length.
+void tc_prepare_trainable(LayerDev& L, gw_ctx* ctx, size_t* counter, std::vector<void*>& allocs,
+                          const std::vector<int32_t>& src_of, const int32_t** d_map, int64_t* n_map);
+void launch_tc_pack(const float* w, const int32_t* map, int64_t n, void* img, cudaStream_t st);
 
 // ---- fused DeepClean (k_fused.cu) ------------------------------------------------
 struct FusedPlan;

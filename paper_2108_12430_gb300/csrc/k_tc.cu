@@ -109,6 +109,10 @@ struct TcParams {
   int coutp_log, out_P_log, res_P_log;  // power-of-two shifts for the epilogue addressing
   int min_plen;                          // rows of the shortest input plane
   int fp32_d2s;                          // write the 8 channels of position u as FP32 samples 8u..8u+7
+  int fp32_full;                         // FP32 [B][C][L] output (out_g: bytes per channel)
+  const float* gy;                       // with fp32_full: multiply by the derivative of an activation
+  int64_t gy_b, gy_c;                    // whose output is gy (floats)
+  int gact;
   const char* const* item_ptr;           // optional per-item input addresses (window start)
   int per_sm;                            // resident CTAs per SM the plan is sized for
   // Per K-step A operand, packed (start offset >> 4) | (LBO >> 4) << 16 relative
@@ -162,6 +166,9 @@ __host__ __device__ __forceinline__ uint32_t slice_off(uint32_t code, int P, int
   return ((g * (uint32_t)P + phi) * (uint32_t)rows + dd) * 16u;
 }
 
+// kFull: the FP32 [B][C][L] output mode of the training path is compiled only
+// into its own instantiation, so the inference kernel's epilogue is unchanged.
+template <bool kFull>
 __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -450,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
     const int quarter = warp & 3;          // TMEM lanes this warp may access
     const int col_half = (warp - 2) >> 2;  // first 32-column chunk it drains (then every kEpiWarps / 4-th)
     const int row = quarter * 32 + lane;
-    const bool plain = !p.fp32_single && !p.fp32_d2s && !p.fp8_out && !p.res && !p.wscale;
+    const bool plain = !kFull && !p.fp32_single && !p.fp32_d2s && !p.fp8_out && !p.res && !p.wscale;
     griddep_wait();  // outputs and residuals are shared with the previous kernels
     int i = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x, ++i) {
@@ -499,6 +506,25 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
                            (int64_t)(u >> p.out_P_log) * 16;
                 *reinterpret_cast<uint4*>(op) = *reinterpret_cast<const uint4*>(o16);
               }
+            }
+            continue;
+          }
+          if (kFull) {
+            // FP32 [B][C][L] (training): bias, activation, optionally times the
+            // derivative of the activation whose output is gy
+            const float* gyb = p.gy ? p.gy + (int64_t)b * p.gy_b : nullptr;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int n = jg * 32 + e;
+              const int sg = n >> p.coutp_log, o = n & (p.coutp - 1);
+              const int u = p.Q * m + sg;
+              if (sg >= p.Q || o >= p.cout || u >= p.lout) continue;
+              float val = act_fn(v[e] + s_bias[o], p.act);
+              if (gyb) {
+                const float a = gyb[(int64_t)o * p.gy_c + u];
+                val *= p.gact == ACT_TANH ? 1.f - a * a : (a > 0.f ? 1.f : 0.f);
+              }
+              reinterpret_cast<float*>(outb + (int64_t)o * p.out_g)[u] = val;
             }
             continue;
           }
@@ -734,8 +760,11 @@ static int choose_j(const LayerSpec& s) {
 
 // Lowers one folded layer: K slices, K-steps and the packed B image (per step
 // [2 K-halves][npad rows][16 bytes]: LBO = npad * 16 bytes, SBO = 128 bytes).
+// map (optional, BF16 only): for every bf16 element of the image, the index
+// (o C_in + c) K + k of the weight it holds, or -1; wf may then be empty.
 static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, std::vector<uint8_t>& img,
-                        std::vector<uint32_t>& table, std::vector<float>& wscale) {
+                        std::vector<uint32_t>& table, std::vector<float>& wscale,
+                        std::vector<int32_t>* map = nullptr) {
   const LayerSpec& s = L.s;
   const int cg = fp8 ? 16 : 8;
   const int G = (s.cin + cg - 1) / cg;
@@ -799,6 +828,8 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
   const size_t step_bytes = 32 * (size_t)npad;
   img.assign(n_steps * step_bytes, 0);
   table.assign(2 * n_steps, 0u);
+  GW_CHECK_ARG(!map || !fp8, "weight maps are for BF16 images");
+  if (map) map->assign(img.size() / 2, -1);
   // FP8: per-output-channel weight scale so that max |w| maps to 448
   wscale.assign(s.cout, 1.f);
   if (fp8) {
@@ -825,7 +856,9 @@ static void lower_layer(LayerDev& L, const std::vector<double>& wf, bool fp8, st
         for (int kk = 0; kk < cg; ++kk) {
           const int c = sl.g * cg + kk;
           if (c >= s.cin) continue;
-          const double v = wf[((size_t)o * s.cin + c) * s.k + k];
+          const size_t wi = ((size_t)o * s.cin + c) * s.k + k;
+          if (map) (*map)[((size_t)(dst - img.data()) >> 1) + kk] = (int32_t)wi;
+          const double v = wf.empty() ? 0.0 : wf[wi];
           if (fp8) {
             __nv_fp8_e4m3 q((float)(v / wscale[o]));
             memcpy(dst + kk, &q, 1);
@@ -860,6 +893,50 @@ void tc_lower_layer(LayerDev& L, const std::vector<double>& wf, std::vector<uint
 }
 
 uint32_t tc_slice_offset(uint32_t code, int P, int rows) { return slice_off(code, P, rows); }
+
+namespace {
+__global__ void tc_pack_kernel(const float* __restrict__ w, const int32_t* __restrict__ map, int64_t n,
+                               __nv_bfloat16* __restrict__ img) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = map[e];
+    img[e] = __float2bfloat16_rn(i >= 0 ? w[i] : 0.f);
+  }
+}
+}  // namespace
+
+void tc_prepare_trainable(LayerDev& L, gw_ctx* ctx, size_t* counter, std::vector<void*>& allocs,
+                          const std::vector<int32_t>& src_of, const int32_t** d_map, int64_t* n_map) {
+  std::vector<uint8_t> img;
+  std::vector<uint32_t> table;
+  std::vector<float> wscale;
+  std::vector<int32_t> map;
+  lower_layer(L, {}, false, img, table, wscale, &map);
+  for (auto& m : map)
+    if (m >= 0) {
+      GW_CHECK_ARG((size_t)m < src_of.size(), "weight map out of range");
+      m = src_of[m];
+    }
+  void* d_img = dev_alloc(ctx, img.size(), counter);
+  allocs.push_back(d_img);
+  GW_CUDA(cudaMemset(d_img, 0, img.size()));
+  uint32_t* d_tab = (uint32_t*)dev_alloc(ctx, table.size() * 4, counter);
+  allocs.push_back(d_tab);
+  GW_CUDA(cudaMemcpy(d_tab, table.data(), table.size() * 4, cudaMemcpyHostToDevice));
+  int32_t* dm = (int32_t*)dev_alloc(ctx, map.size() * 4, counter);
+  allocs.push_back(dm);
+  GW_CUDA(cudaMemcpy(dm, map.data(), map.size() * 4, cudaMemcpyHostToDevice));
+  L.wq = d_img;
+  L.table = d_tab;
+  L.table_h = table;
+  *d_map = dm;
+  *n_map = (int64_t)map.size();
+}
+
+void launch_tc_pack(const float* w, const int32_t* map, int64_t n, void* img, cudaStream_t st) {
+  tc_pack_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(w, map, n,
+                                                                                  (__nv_bfloat16*)img);
+  GW_LAUNCH_CHECK();
+}
 
 void tc_pack_layer(LayerDev& L, const std::vector<double>& wf, int precision, gw_ctx* ctx, size_t* counter,
                    std::vector<void*>& allocs, std::vector<float>* wscale_out) {
@@ -1035,7 +1112,14 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.out = (char*)out.p;
   GW_CHECK_ARG(!out.fp32_d2s || s.cout == 8, "depth-to-space output needs 8 channels");
   q.fp32_d2s = out.fp32_d2s;
-  const int oesz = (out.fp32_single || out.fp32_d2s) ? 4 : (out.fp8_out ? 1 : 2);
+  GW_CHECK_ARG(!out.fp32_full || (!fp8 && !out.res && !out.fp32_d2s && !out.fp32_single && s.cout > 1),
+               "FP32 [B][C][L] output: BF16 layer, no residual");
+  q.fp32_full = out.fp32_full;
+  q.gy = out.gy;
+  q.gy_b = out.gy_b;
+  q.gy_c = out.gy_c;
+  q.gact = out.gact;
+  const int oesz = (out.fp32_single || out.fp32_d2s || out.fp32_full) ? 4 : (out.fp8_out ? 1 : 2);
   q.out_b = out.bstride * oesz;
   q.out_g = out.gstride * oesz;
   q.out_p = out.pstride * oesz;
@@ -1097,7 +1181,8 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
   dim3 grid;
   plan_conv_tc(q, L, L.wscale != nullptr, in, lout, out, err, &smem, &grid, B, current_sm_count());
   q.stall_test = tc_take_stall_test() ? 1 : 0;
-  set_smem_limit_once(conv_tc_kernel, 227 * 1024);
+  set_smem_limit_once(conv_tc_kernel<false>, 227 * 1024);
+  set_smem_limit_once(conv_tc_kernel<true>, 227 * 1024);
   // programmatic stream serialisation: this launch may begin (set-up, weight
   // loads) while the previous kernel in the stream runs; the kernel waits on
   // griddepcontrol before touching the previous kernels' data
@@ -1111,7 +1196,10 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  GW_CUDA(cudaLaunchKernelEx(&cfg, conv_tc_kernel, q));
+  if (q.fp32_full)
+    GW_CUDA(cudaLaunchKernelEx(&cfg, conv_tc_kernel<true>, q));
+  else
+    GW_CUDA(cudaLaunchKernelEx(&cfg, conv_tc_kernel<false>, q));
 }
 
 void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,

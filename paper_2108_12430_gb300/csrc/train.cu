@@ -31,6 +31,14 @@ struct TrainLayer {
   LayerSpec s;
   int lin = 0, lout = 0;
   FoldArgs f{};
+  // tensor-core forward / data gradient (tc_data): the layer and the layer
+  // that maps its output gradient to its input gradient, with operand images
+  // refilled from the folded weights at every forward (maps: image element ->
+  // index into wf / wT)
+  LayerDev tf, td;
+  const int32_t* map_f = nullptr;
+  const int32_t* map_d = nullptr;
+  int64_t n_f = 0, n_d = 0;
 };
 
 }  // namespace
@@ -38,7 +46,10 @@ struct TrainLayer {
 
 struct gw_trainer {
   gw_ctx* ctx = nullptr;
-  int n_in = 0, max_batch = 0, L = 0, checkpoint = 0, wgrad_tc = 0;
+  int n_in = 0, max_batch = 0, L = 0, checkpoint = 0, wgrad_tc = 0, tc_data = 0;
+  char* blk = nullptr;  // tc_data: blocked BF16 input of the current tensor-core conv
+  std::vector<void*> tc_allocs;  // operand images, slice tables and weight maps of the tensor-core layers
+  size_t tc_bytes = 0;
   int* err = nullptr;  // device: a tensor-core kernel gave up a bounded wait
   size_t n_params = 0;
   std::vector<gw::TrainLayer> layers;
@@ -75,6 +86,11 @@ void trainer_free(gw_trainer* t) {
   if (!t) return;
   cudaDeviceSynchronize();
   for (auto& a : t->allocs) dev_free(t->ctx, a.first, a.second, nullptr);
+  bool first = true;  // the tensor-core layers' bytes are returned to the budget with the first of their buffers
+  for (void* p : t->tc_allocs) {
+    dev_free(t->ctx, p, first ? t->tc_bytes : 0, nullptr);
+    first = false;
+  }
   delete t;
 }
 
@@ -89,6 +105,27 @@ bool recomputed(const gw_trainer* t, int l) { return t->checkpoint && (l % 2 == 
 // Forward of layer l from `in` into `out` (out strides: item cout*lout, channel lout).
 void layer_forward(gw_trainer* t, int l, const float* in, float* out, int64_t yb, int64_t yc, int B, cudaStream_t st) {
   const TrainLayer& T = t->layers[l];
+  if (t->tc_data) {
+    // the layer input to the blocked BF16 layout, then the tensor-core conv
+    // writing FP32 [B][C][L] (the output layer: FP32 [B][L])
+    const TcOut blk = blocked_out(t->blk, T.s.cin, T.lin, T.tf.pin);
+    {
+      Prof p("train.to_blocked", st);
+      launch_to_blocked(in, (int64_t)T.s.cin * T.lin, T.lin, B, T.s.cin, T.lin, nullptr, nullptr, 1.f, blk, 0, st);
+    }
+    TcOut o{};
+    o.p = out;
+    o.bstride = yb;
+    o.gstride = yc;
+    o.P = 1;
+    if (T.s.cout == 1)
+      o.fp32_single = 1;
+    else
+      o.fp32_full = 1;
+    Prof p("train.conv_fwd_tc", st);
+    launch_conv_tc(T.tf, as_input(blk, T.lin), T.lout, o, B, t->err, st);
+    return;
+  }
   ConvF32Args a{};
   a.x = in;
   a.xb = (int64_t)T.s.cin * T.lin;
@@ -127,6 +164,8 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
   GW_CHECK_ARG(d->checkpoint == 0 || d->checkpoint == 1, "checkpoint must be 0 or 1");
   GW_CHECK_ARG(d->precision == GW_FP32 || d->precision == GW_BF16, "trainer precision must be FP32 or BF16");
   GW_CHECK_ARG(d->precision == GW_FP32 || tc_supported(), "BF16 weight gradients need the sm_103a tensor cores");
+  GW_CHECK_ARG(d->tc_data == 0 || (d->tc_data == 1 && d->precision == GW_BF16),
+               "tc_data (forward and data gradients on the tensor cores) needs precision GW_BF16");
   GW_CUDA(cudaSetDevice(ctx->device));
   t = new gw_trainer();
   try {
@@ -136,6 +175,7 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
     t->L = d->length;
     t->checkpoint = d->checkpoint;
     t->wgrad_tc = d->precision == GW_BF16;
+    t->tc_data = d->tc_data;
     const auto specs = deepclean_specs(d->n_in);
     int64_t off = 0;
     int lin = d->length;
@@ -211,6 +251,52 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
     t->bpart = talloc<float>(t, (size_t)Bm * max_c);
     t->zero_bias = talloc<float>(t, max_c);
     t->err = talloc<int>(t, 1);
+    if (t->tc_data) {
+      // per layer: the forward conv (weights: wf, as stored) and the conv that
+      // maps its output gradient to its input gradient (weights: wT; a
+      // stride-2 conv's is a transposed conv and vice versa, a stride-1 conv's
+      // is a stride-1 conv with the taps reversed and padding K - 1 - p)
+      size_t max_blk = 0;
+      for (int l = 0; l < nl; ++l) {
+        TrainLayer& T = t->layers[l];
+        const LayerSpec& s = T.s;
+        const size_t nw = (size_t)s.cin * s.cout * s.k;
+        std::vector<int32_t> src(nw);
+        for (size_t i = 0; i < nw; ++i) src[i] = (int32_t)i;
+        T.tf.s = s;
+        T.tf.b = T.f.bf;
+        tc_prepare_trainable(T.tf, ctx, &t->tc_bytes, t->tc_allocs, src, &T.map_f, &T.n_f);
+        max_blk = std::max(max_blk, (size_t)blocked_out(nullptr, s.cin, T.lin, T.tf.pin).bstride);
+        if (l == 0) continue;  // the network input needs no gradient
+        LayerSpec ds{};
+        ds.cin = s.cout;
+        ds.cout = s.cin;
+        ds.k = s.k;
+        ds.out_pad = 0;
+        ds.bn = false;
+        ds.act = ACT_NONE;
+        if (s.stride == 2) {
+          ds.transposed = !s.transposed;
+          ds.stride = 2;
+          ds.pad_l = s.pad_l;
+          ds.pad_r = s.pad_r;
+        } else {
+          GW_CHECK_ARG(!s.transposed && s.stride == 1, "unsupported layer for the tensor-core data gradient");
+          ds.transposed = false;
+          ds.stride = 1;
+          ds.pad_l = ds.pad_r = s.k - 1 - s.pad_l;
+          for (int c = 0; c < s.cin; ++c)
+            for (int o = 0; o < s.cout; ++o)
+              for (int k = 0; k < s.k; ++k)
+                src[((size_t)c * s.cout + o) * s.k + k] = (int32_t)(((size_t)c * s.cout + o) * s.k + (s.k - 1 - k));
+        }
+        T.td.s = ds;
+        T.td.b = t->zero_bias;
+        tc_prepare_trainable(T.td, ctx, &t->tc_bytes, t->tc_allocs, src, &T.map_d, &T.n_d);
+        max_blk = std::max(max_blk, (size_t)blocked_out(nullptr, s.cout, T.lout, T.td.pin).bstride);
+      }
+      t->blk = talloc<char>(t, (size_t)Bm * max_blk * 2);
+    }
   } catch (...) {
     trainer_free(t);
     throw;
@@ -249,8 +335,16 @@ int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int 
   t->B = B;
   for (auto& T : t->layers) {
     T.f.p = params;
-    Prof p("train.fold", st);
-    launch_fold(T.f, st);
+    {
+      Prof p("train.fold", st);
+      launch_fold(T.f, st);
+    }
+    if (t->tc_data) {
+      // this step's folded weights into the tensor-core operand images
+      Prof p("train.pack", st);
+      launch_tc_pack(T.f.wf, T.map_f, T.n_f, T.tf.wq, st);
+      if (T.map_d) launch_tc_pack(T.f.wT, T.map_d, T.n_d, T.td.wq, st);
+    }
   }
   {
     Prof p("train.standardise", st);
@@ -330,6 +424,33 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
     if (l == 0) break;
     // data gradient, times the derivative of layer l-1's activation (whose
     // output is this layer's input)
+    if (t->tc_data) {
+      float* dst = t->dv[cur];
+      const TcOut gblk = blocked_out(t->blk, s.cout, T.lout, T.td.pin);
+      {
+        Prof p("train.to_blocked", st);
+        launch_to_blocked(g, gb, gn, B, s.cout, T.lout, nullptr, nullptr, 1.f, gblk, 0, st);
+      }
+      TcOut o{};
+      o.p = dst;
+      o.bstride = xb;
+      o.gstride = xc;
+      o.P = 1;
+      o.fp32_full = 1;
+      o.gy = xin;
+      o.gy_b = xb;
+      o.gy_c = xc;
+      o.gact = t->layers[l - 1].s.act;
+      {
+        Prof p("train.dgrad_tc", st);
+        launch_conv_tc(T.td, as_input(gblk, T.lout), T.lin, o, B, t->err, st);
+      }
+      g = dst;
+      gb = xb;
+      gn = xc;
+      cur ^= 1;
+      continue;
+    }
     ConvF32Args a{};
     a.x = g;
     a.xb = gb;

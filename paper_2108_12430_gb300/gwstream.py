@@ -82,7 +82,7 @@ class gw_server_stats(C.Structure):
 
 class gw_trainer_desc(C.Structure):
     _fields_ = [("n_in", C.c_int), ("max_batch", C.c_int), ("length", C.c_int), ("checkpoint", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("tc_data", C.c_int)]
 
 
 _lib = None
@@ -465,8 +465,9 @@ def gw_server_destroy(s):
     _check(lib().gw_server_destroy(s))
 
 
-def gw_trainer_create(ctx, n_in, max_batch, length, checkpoint=0, in_mean=None, in_std=None, precision=GW_FP32):
-    d = gw_trainer_desc(n_in, max_batch, length, checkpoint, precision)
+def gw_trainer_create(ctx, n_in, max_batch, length, checkpoint=0, in_mean=None, in_std=None, precision=GW_FP32,
+                      tc_data=0):
+    d = gw_trainer_desc(n_in, max_batch, length, checkpoint, precision, tc_data)
     m = None if in_mean is None else np.ascontiguousarray(in_mean, np.float32)
     s = None if in_std is None else np.ascontiguousarray(in_std, np.float32)
     h = P()

@@ -98,10 +98,12 @@ def groups(params):
 class Run:
     """A trainer, a loss FIR and device buffers for one case."""
 
-    def __init__(self, ctx, params, x, s, mean, std, psd, ntaps, nfft, checkpoint=0, B_max=None, precision=G.GW_FP32):
+    def __init__(self, ctx, params, x, s, mean, std, psd, ntaps, nfft, checkpoint=0, B_max=None, precision=G.GW_FP32,
+                 tc_data=0):
         B, _, L = x.shape
         self.B, self.L = B, L
-        self.t = G.gw_trainer_create(ctx.h, C, B_max or B, L, checkpoint, mean, std, precision=precision)
+        self.t = G.gw_trainer_create(ctx.h, C, B_max or B, L, checkpoint, mean, std, precision=precision,
+                                     tc_data=tc_data)
         ctx.objs.append((G.gw_trainer_destroy, self.t))
         self.g = G.gw_fir_create_band_loss(ctx.h, psd, 4096.0, ntaps)
         ctx.objs.append((G.gw_fir_destroy, self.g))
@@ -198,6 +200,29 @@ def test_tensor_core_weight_gradients_match_oracle(ctx, B, L, ntaps, nfft):
     assert rel_l2(dp, dp32) <= TOL_WG16
 
 
+# Forward convs and data gradients on the tensor cores too: the prediction
+# carries the BF16 path's error (bound 2e-2, as for inference); a gradient
+# combines that forward error with the BF16 rounding of the backward operands,
+# so its bound is twice that, 4e-2.
+TOL_TC16_Y, TOL_TC16_G = 2e-2, 4e-2
+
+
+@pytest.mark.parametrize("B,L,ntaps,nfft", [(2, 512, 129, 2048), (2, 8192, 2049, 8192)])
+def test_tensor_core_training_step_matches_oracle(ctx, B, L, ntaps, nfft):
+    c = case(B, L, ntaps=ntaps, nfft=nfft)
+    loss_ref, y_ref, grads_ref = oracle(*c)
+    run = Run(ctx, *c, precision=G.GW_BF16, tc_data=1)
+    loss, y, dp = run.step()
+    G.gw_trainer_status(run.t)
+    print(f"tensor-core step: loss rel err {abs(loss - loss_ref) / abs(loss_ref):.2e}, y rel-L2 {rel_l2(y, y_ref):.2e}")
+    assert abs(loss - loss_ref) <= TOL_TC16_Y * abs(loss_ref)
+    assert rel_l2(y, y_ref) <= TOL_TC16_Y
+    print("worst gradient rel-L2", check_grads(dp, flat_grads(grads_ref), c[0], tol=TOL_TC16_G))
+    # checkpointing recomputes through the same kernels: identical bits
+    b = Run(ctx, *c, precision=G.GW_BF16, tc_data=1, checkpoint=1).step()
+    assert b[0] == loss and np.array_equal(b[1], y) and np.array_equal(b[2], dp)
+
+
 def test_full_length_gradient_and_batch_mean_property(ctx):
     # Windows of the training configuration's length (8192): a batch of 2
     # against the oracle, then a batch of 8 equals the mean of its four
@@ -271,10 +296,10 @@ def test_adam_step(ctx):
     assert np.abs(p.cpu().numpy() - pp).max() <= 1e-6
 
 
-@pytest.mark.parametrize("precision", [G.GW_FP32, G.GW_BF16])
-def test_training_reduces_the_loss(ctx, precision):
+@pytest.mark.parametrize("precision,tc_data", [(G.GW_FP32, 0), (G.GW_BF16, 0), (G.GW_BF16, 1)])
+def test_training_reduces_the_loss(ctx, precision, tc_data):
     c = case(4, 1024)
-    run = Run(ctx, *c, precision=precision)
+    run = Run(ctx, *c, precision=precision, tc_data=tc_data)
     m = torch.zeros_like(run.p)
     v = torch.zeros_like(run.p)
     losses = []
