@@ -285,6 +285,11 @@ struct TcOut {
   const float* gy;
   int64_t gy_b, gy_c;
   int gact;
+  // with fp32_full, optionally the same values also in a blocked BF16 layout
+  // (the next conv's input: blk_P phase planes, strides in elements)
+  void* blk;
+  int64_t blk_b, blk_g, blk_p;
+  int blk_P;
 };
 // Blocked output of `cout` channels x `lout` positions in P planes, and its view
 // as the next layer's input (api.cu).
@@ -321,6 +326,15 @@ uint32_t tc_slice_offset(uint32_t code, int P, int rows);
 void tc_prepare_trainable(LayerDev& L, gw_ctx* ctx, size_t* counter, std::vector<void*>& allocs,
                           const std::vector<int32_t>& src_of, const int32_t** d_map, int64_t* n_map);
 void launch_tc_pack(const float* w, const int32_t* map, int64_t n, void* img, cudaStream_t st);
+// Several packs in one launch (at most kTcPackMax).
+struct TcPackSeg {
+  const float* w;
+  const int32_t* map;
+  int64_t n;
+  void* img;
+};
+constexpr int kTcPackMax = 24;
+void launch_tc_pack_many(const TcPackSeg* segs, int n_segs, cudaStream_t st);
 
 // ---- fused DeepClean (k_fused.cu) ------------------------------------------------
 struct FusedPlan;

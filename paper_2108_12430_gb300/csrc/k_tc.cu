@@ -113,6 +113,9 @@ struct TcParams {
   const float* gy;                       // with fp32_full: multiply by the derivative of an activation
   int64_t gy_b, gy_c;                    // whose output is gy (floats)
   int gact;
+  char* blk;                             // with fp32_full: a blocked BF16 copy (bytes strides below)
+  int64_t blk_b, blk_g, blk_p;
+  int blk_P_log;
   const char* const* item_ptr;           // optional per-item input addresses (window start)
   int per_sm;                            // resident CTAs per SM the plan is sized for
   // Per K-step A operand, packed (start offset >> 4) | (LBO >> 4) << 16 relative
@@ -525,6 +528,11 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
                 val *= p.gact == ACT_TANH ? 1.f - a * a : (a > 0.f ? 1.f : 0.f);
               }
               reinterpret_cast<float*>(outb + (int64_t)o * p.out_g)[u] = val;
+              if (p.blk)
+                *reinterpret_cast<__nv_bfloat16*>(p.blk + (int64_t)b * p.blk_b + (int64_t)(o >> 3) * p.blk_g +
+                                                  (int64_t)(u & ((1 << p.blk_P_log) - 1)) * p.blk_p +
+                                                  (int64_t)(u >> p.blk_P_log) * 16 + (o & 7) * 2) =
+                    __float2bfloat16_rn(val);
             }
             continue;
           }
@@ -902,7 +910,31 @@ __global__ void tc_pack_kernel(const float* __restrict__ w, const int32_t* __res
     img[e] = __float2bfloat16_rn(i >= 0 ? w[i] : 0.f);
   }
 }
+struct TcPackList {
+  TcPackSeg s[kTcPackMax];
+};
+__global__ void tc_pack_many_kernel(const __grid_constant__ TcPackList l) {
+  const TcPackSeg& g = l.s[blockIdx.y];
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  __nv_bfloat16* img = (__nv_bfloat16*)g.img;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = g.map[e];
+    img[e] = i >= 0 ? __float2bfloat16_rn(g.w[i]) : zero;
+  }
+}
 }  // namespace
+
+void launch_tc_pack_many(const TcPackSeg* segs, int n_segs, cudaStream_t st) {
+  GW_CHECK_ARG(n_segs >= 1 && n_segs <= kTcPackMax, "pack list size");
+  TcPackList l{};
+  int64_t mx = 0;
+  for (int i = 0; i < n_segs; ++i) {
+    l.s[i] = segs[i];
+    mx = std::max(mx, segs[i].n);
+  }
+  tc_pack_many_kernel<<<dim3((unsigned)std::min<int64_t>((mx + 255) / 256, 512), n_segs), 256, 0, st>>>(l);
+  GW_LAUNCH_CHECK();
+}
 
 void tc_prepare_trainable(LayerDev& L, gw_ctx* ctx, size_t* counter, std::vector<void*>& allocs,
                           const std::vector<int32_t>& src_of, const int32_t** d_map, int64_t* n_map) {
@@ -1119,6 +1151,16 @@ static void plan_conv_tc(TcParams& q, const LayerDev& L, bool fp8, const TcIn& i
   q.gy_b = out.gy_b;
   q.gy_c = out.gy_c;
   q.gact = out.gact;
+  q.blk = (char*)out.blk;
+  q.blk_b = out.blk_b * 2;
+  q.blk_g = out.blk_g * 2;
+  q.blk_p = out.blk_p * 2;
+  {
+    int lg = 0;
+    while ((1 << lg) < std::max(1, out.blk_P)) ++lg;
+    GW_CHECK_ARG(!out.blk || (1 << lg) == out.blk_P, "blocked copy: phase count must be a power of two");
+    q.blk_P_log = lg;
+  }
   const int oesz = (out.fp32_single || out.fp32_d2s || out.fp32_full) ? 4 : (out.fp8_out ? 1 : 2);
   q.out_b = out.bstride * oesz;
   q.out_g = out.gstride * oesz;

@@ -47,7 +47,10 @@ struct TrainLayer {
 struct gw_trainer {
   gw_ctx* ctx = nullptr;
   int n_in = 0, max_batch = 0, L = 0, checkpoint = 0, wgrad_tc = 0, tc_data = 0;
-  char* blk = nullptr;  // tc_data: blocked BF16 input of the current tensor-core conv
+  // tc_data: blocked BF16 inputs of the tensor-core convs; [0] and [1] alternate
+  // along the forward and along the backward (each conv writes its successor's
+  // input beside its FP32 output), [2] serves the recomputed layers
+  char* blk[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> tc_allocs;  // operand images, slice tables and weight maps of the tensor-core layers
   size_t tc_bytes = 0;
   int* err = nullptr;  // device: a tensor-core kernel gave up a bounded wait
@@ -103,27 +106,46 @@ const char* kWgradTcNames[8] = {"train.wgrad_tc.enc1", "train.wgrad_tc.enc2", "t
 bool recomputed(const gw_trainer* t, int l) { return t->checkpoint && (l % 2 == 0) && l + 1 < (int)t->layers.size(); }
 
 // Forward of layer l from `in` into `out` (out strides: item cout*lout, channel lout).
+// Tensor-core forward of layer l (tc_data): its input in the blocked BF16
+// layout is at in_blk (converted from `in` into t->blk[2] when null); writes
+// FP32 [B][C][L] (the output layer: FP32 [B][L]) and, when out_blk is given,
+// the same values blocked for the next layer.
+void layer_forward_tc(gw_trainer* t, int l, const float* in, const TcOut* in_blk, float* out, int64_t yb, int64_t yc,
+                      const TcOut* out_blk, int B, cudaStream_t st) {
+  const TrainLayer& T = t->layers[l];
+  TcOut blk;
+  if (in_blk) {
+    blk = *in_blk;
+  } else {
+    blk = blocked_out(t->blk[2], T.s.cin, T.lin, T.tf.pin);
+    Prof p("train.to_blocked", st);
+    launch_to_blocked(in, (int64_t)T.s.cin * T.lin, T.lin, B, T.s.cin, T.lin, nullptr, nullptr, 1.f, blk, 0, st);
+  }
+  TcOut o{};
+  o.p = out;
+  o.bstride = yb;
+  o.gstride = yc;
+  o.P = 1;
+  if (T.s.cout == 1) {
+    o.fp32_single = 1;
+  } else {
+    o.fp32_full = 1;
+    if (out_blk) {
+      o.blk = out_blk->p;
+      o.blk_b = out_blk->bstride;
+      o.blk_g = out_blk->gstride;
+      o.blk_p = out_blk->pstride;
+      o.blk_P = out_blk->P;
+    }
+  }
+  Prof p("train.conv_fwd_tc", st);
+  launch_conv_tc(T.tf, as_input(blk, T.lin), T.lout, o, B, t->err, st);
+}
+
 void layer_forward(gw_trainer* t, int l, const float* in, float* out, int64_t yb, int64_t yc, int B, cudaStream_t st) {
   const TrainLayer& T = t->layers[l];
   if (t->tc_data) {
-    // the layer input to the blocked BF16 layout, then the tensor-core conv
-    // writing FP32 [B][C][L] (the output layer: FP32 [B][L])
-    const TcOut blk = blocked_out(t->blk, T.s.cin, T.lin, T.tf.pin);
-    {
-      Prof p("train.to_blocked", st);
-      launch_to_blocked(in, (int64_t)T.s.cin * T.lin, T.lin, B, T.s.cin, T.lin, nullptr, nullptr, 1.f, blk, 0, st);
-    }
-    TcOut o{};
-    o.p = out;
-    o.bstride = yb;
-    o.gstride = yc;
-    o.P = 1;
-    if (T.s.cout == 1)
-      o.fp32_single = 1;
-    else
-      o.fp32_full = 1;
-    Prof p("train.conv_fwd_tc", st);
-    launch_conv_tc(T.tf, as_input(blk, T.lin), T.lout, o, B, t->err, st);
+    layer_forward_tc(t, l, in, nullptr, out, yb, yc, nullptr, B, st);
     return;
   }
   ConvF32Args a{};
@@ -295,7 +317,7 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
         tc_prepare_trainable(T.td, ctx, &t->tc_bytes, t->tc_allocs, src, &T.map_d, &T.n_d);
         max_blk = std::max(max_blk, (size_t)blocked_out(nullptr, s.cout, T.lout, T.td.pin).bstride);
       }
-      t->blk = talloc<char>(t, (size_t)Bm * max_blk * 2);
+      for (int i = 0; i < 3; ++i) t->blk[i] = talloc<char>(t, (size_t)Bm * max_blk * 2);
     }
   } catch (...) {
     trainer_free(t);
@@ -333,6 +355,7 @@ int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int 
   cudaStream_t st = (cudaStream_t)cuda_stream;
   t->params = params;
   t->B = B;
+  std::vector<TcPackSeg> packs;
   for (auto& T : t->layers) {
     T.f.p = params;
     {
@@ -340,11 +363,14 @@ int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int 
       launch_fold(T.f, st);
     }
     if (t->tc_data) {
-      // this step's folded weights into the tensor-core operand images
-      Prof p("train.pack", st);
-      launch_tc_pack(T.f.wf, T.map_f, T.n_f, T.tf.wq, st);
-      if (T.map_d) launch_tc_pack(T.f.wT, T.map_d, T.n_d, T.td.wq, st);
+      packs.push_back({T.f.wf, T.map_f, T.n_f, T.tf.wq});
+      if (T.map_d) packs.push_back({T.f.wT, T.map_d, T.n_d, T.td.wq});
     }
+  }
+  if (!packs.empty()) {
+    // this step's folded weights into the tensor-core operand images
+    Prof p("train.pack", st);
+    launch_tc_pack_many(packs.data(), (int)packs.size(), st);
   }
   {
     Prof p("train.standardise", st);
@@ -352,6 +378,13 @@ int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int 
   }
   const int nl = (int)t->layers.size();
   const float* in = t->x_std;
+  TcOut cur{};
+  if (t->tc_data) {
+    const TrainLayer& T0 = t->layers[0];
+    cur = blocked_out(t->blk[0], T0.s.cin, T0.lin, T0.tf.pin);
+    Prof p("train.to_blocked", st);
+    launch_to_blocked(in, (int64_t)T0.s.cin * T0.lin, T0.lin, B, T0.s.cin, T0.lin, nullptr, nullptr, 1.f, cur, 0, st);
+  }
   for (int l = 0; l < nl; ++l) {
     const TrainLayer& T = t->layers[l];
     float* out;
@@ -363,7 +396,14 @@ int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int 
     } else {
       out = t->act[l] ? t->act[l] : t->scratch;
     }
-    layer_forward(t, l, in, out, yb, yc, B, st);
+    if (t->tc_data) {
+      TcOut next{};
+      if (l + 1 < nl) next = blocked_out(t->blk[(l + 1) & 1], T.s.cout, T.lout, t->layers[l + 1].tf.pin);
+      layer_forward_tc(t, l, in, &cur, out, yb, yc, l + 1 < nl ? &next : nullptr, B, st);
+      cur = next;
+    } else {
+      layer_forward(t, l, in, out, yb, yc, B, st);
+    }
     in = out;
   }
   GW_API_END
@@ -378,6 +418,7 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
   const float* g = dy_hat;  // gradient w.r.t. the current layer's (pre-activation) output
   int64_t gb = t->L, gn = t->L;
   int cur = 0;
+  TcOut gnext{};  // tc_data: the next data gradient's input, blocked by the previous one
   for (int l = nl - 1; l >= 0; --l) {
     const TrainLayer& T = t->layers[l];
     const LayerSpec& s = T.s;
@@ -426,11 +467,16 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
     // output is this layer's input)
     if (t->tc_data) {
       float* dst = t->dv[cur];
-      const TcOut gblk = blocked_out(t->blk, s.cout, T.lout, T.td.pin);
-      {
+      TcOut gblk;
+      if (l == nl - 1) {
+        // the loss gradient, blocked once; later layers' come with their FP32 copies
+        gblk = blocked_out(t->blk[0], s.cout, T.lout, T.td.pin);
         Prof p("train.to_blocked", st);
         launch_to_blocked(g, gb, gn, B, s.cout, T.lout, nullptr, nullptr, 1.f, gblk, 0, st);
+      } else {
+        gblk = gnext;
       }
+      if (l - 1 >= 1) gnext = blocked_out(t->blk[(gblk.p == t->blk[0]) ? 1 : 0], s.cin, T.lin, t->layers[l - 1].td.pin);
       TcOut o{};
       o.p = dst;
       o.bstride = xb;
@@ -441,6 +487,13 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
       o.gy_b = xb;
       o.gy_c = xc;
       o.gact = t->layers[l - 1].s.act;
+      if (l - 1 >= 1) {
+        o.blk = gnext.p;
+        o.blk_b = gnext.bstride;
+        o.blk_g = gnext.gstride;
+        o.blk_p = gnext.pstride;
+        o.blk_P = gnext.P;
+      }
       {
         Prof p("train.dgrad_tc", st);
         launch_conv_tc(T.td, as_input(gblk, T.lout), T.lin, o, B, t->err, st);
