@@ -30,6 +30,9 @@ struct WgradArgs {
 };
 
 void launch_fold(const FoldArgs& f, cudaStream_t st);
+// Several layers' folds in one launch (at most kFoldMax).
+constexpr int kFoldMax = 16;
+void launch_fold_many(const FoldArgs* f, int n, cudaStream_t st);
 // dw_in_major: dWf is [C_in][C_out][K] (transposed conv) instead of [C_out][C_in][K].
 void launch_unfold(const FoldArgs& f, const float* dWf, int dw_in_major, const float* dbf, float* dp,
                    cudaStream_t st);

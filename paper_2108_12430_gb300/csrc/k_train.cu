@@ -32,7 +32,7 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 // the same values transposed to [C_in][C_out][K] (wT, the data-gradient
 // kernel's weights) and the folded bias (bf):
 //   sc[o] = gamma[o] / sqrt(var[o] + eps),  w' = w sc[o],  b' = (b - mean) sc + beta.
-__global__ void fold_kernel(FoldArgs f) {
+__device__ __forceinline__ void fold_body(const FoldArgs& f) {
   const int n = f.cout * f.cin * f.K;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int k = e % f.K, oi = e / f.K, i = oi % f.cin, o = oi / f.cin;
@@ -53,6 +53,12 @@ __global__ void fold_kernel(FoldArgs f) {
     }
   }
 }
+__global__ void fold_kernel(FoldArgs f) { fold_body(f); }
+// Every layer's fold in one launch (blockIdx.y = layer).
+struct FoldList {
+  FoldArgs f[kFoldMax];
+};
+__global__ void fold_many_kernel(const __grid_constant__ FoldList l) { fold_body(l.f[blockIdx.y]); }
 
 // Chain rule from the folded parameters' gradients (dWf in the layer's
 // gradient layout, dbf) to the raw ones; one CTA per output channel o:
@@ -227,6 +233,18 @@ int grid_for(int64_t n) {
 
 void launch_fold(const FoldArgs& f, cudaStream_t st) {
   fold_kernel<<<grid_for((int64_t)f.cout * f.cin * f.K), kThreads, 0, st>>>(f);
+  GW_LAUNCH_CHECK();
+}
+
+void launch_fold_many(const FoldArgs* f, int n, cudaStream_t st) {
+  GW_CHECK_ARG(n >= 1 && n <= kFoldMax, "fold list size");
+  FoldList l{};
+  int64_t mx = 0;
+  for (int i = 0; i < n; ++i) {
+    l.f[i] = f[i];
+    mx = std::max<int64_t>(mx, (int64_t)f[i].cout * f[i].cin * f[i].K);
+  }
+  fold_many_kernel<<<dim3(grid_for(mx), n), kThreads, 0, st>>>(l);
   GW_LAUNCH_CHECK();
 }
 

@@ -356,12 +356,16 @@ int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int 
   t->params = params;
   t->B = B;
   std::vector<TcPackSeg> packs;
+  std::vector<FoldArgs> folds;
   for (auto& T : t->layers) {
     T.f.p = params;
-    {
-      Prof p("train.fold", st);
-      launch_fold(T.f, st);
-    }
+    folds.push_back(T.f);
+  }
+  {
+    Prof p("train.fold", st);
+    launch_fold_many(folds.data(), (int)folds.size(), st);
+  }
+  for (auto& T : t->layers) {
     if (t->tc_data) {
       packs.push_back({T.f.wf, T.map_f, T.n_f, T.tf.wq});
       if (T.map_d) packs.push_back({T.f.wT, T.map_d, T.n_d, T.td.wq});
