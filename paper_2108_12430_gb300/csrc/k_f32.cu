@@ -10,8 +10,6 @@ namespace gw {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCPT = 8;  // output channels per thread
-constexpr int kPPT = 4;  // output positions per thread (strided by the thread count)
 
 __device__ __forceinline__ int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 
@@ -21,97 +19,158 @@ __device__ __forceinline__ float apply_act(float v, int act) {
   return v;
 }
 
-// One CTA: TL output positions x CB output channels of one batch item.
 // Conv:  y[o,u] = b[o] + sum_{i,k} w[o,i,k] x[i, s u + k - p]
 // ConvT: y[o,u] = b[o] + sum_{i,k : s | (u + p - k)} w[o,i,k] x[i, (u + p - k) / s]
-__global__ void __launch_bounds__(kThreads) conv_f32_kernel(ConvF32Args a, int CB, int CI) {
-  extern __shared__ float smem[];
+// (w here in [C_out][C_in][K] for both; the host passes a transposed conv's
+// weights rearranged to that layout).
+//
+// Register-blocked FP32 conv for the shapes of DeepClean and BBHnet (K taps,
+// stride S, transposed or not, known at compile time).  A thread computes CPT
+// output channels x 4 consecutive positions.  For each input channel it loads
+// the x values that its 4 positions and K taps read once, as 16- or 8-byte
+// vectors from shared memory, and per tap its CPT weights as float4 vectors
+// (weights staged [ci][k][CB]), so that every loaded value feeds several FMAs.
+// A transposed conv of stride 1 is the conv with the taps reversed and the
+// padding K - 1 - p.  Every output is an FP32 FMA chain over (ci, k), input
+// channels in order and taps in order within each.
+template <int K, int CPT>
+__device__ __forceinline__ void rb_load_w(const float* wr, int CB, int k, float (&wv)[CPT]) {
+  if constexpr (CPT % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < CPT / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(wr + k * CB)[q];
+      wv[4 * q] = v.x;
+      wv[4 * q + 1] = v.y;
+      wv[4 * q + 2] = v.z;
+      wv[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) wv[c] = wr[k * CB + c];
+  }
+}
+
+// Transposed stride 2: output u = t0 + 4 pt + j takes tap k when
+// u + p - k is even; with A = t0 + p - (K - 1), lo = floor(A / 2), par = A & 1
+// and d = j - k + K - 1, that is when d + par is even, and it reads
+// x[lo + 2 pt + (d + par) / 2].
+template <int K, int CPT, int PAR>
+__device__ __forceinline__ void rb_accum_tr2(const float* xr, const float* wr, int CB, int pt,
+                                             float (&acc)[CPT][4]) {
+  constexpr int NV2 = ((K + 3) / 2 + 2) / 2;
+  float xv[NV2 * 2];
+  const float2* x2 = reinterpret_cast<const float2*>(xr + 2 * pt);
+#pragma unroll
+  for (int q = 0; q < NV2; ++q) {
+    const float2 v = x2[q];
+    xv[2 * q] = v.x;
+    xv[2 * q + 1] = v.y;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float wv[CPT];
+    rb_load_w<K, CPT>(wr, CB, k, wv);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int d = j - k + K - 1;
+      if (((d + PAR) & 1) == 0) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[c][j] = fmaf(wv[c], xv[(d + PAR) >> 1], acc[c][j]);
+      }
+    }
+  }
+}
+
+template <int K, int S, bool TR, int CPT>
+__global__ void __launch_bounds__(kThreads) conv_f32_rb_kernel(ConvF32Args a, int CB, int CI, int spanp) {
+  static_assert(!TR || S == 1 || S == 2, "transposed convs of stride 1 or 2");
+  constexpr bool kTr2 = TR && S == 2;   // transposed, stride 2
+  constexpr bool kFlip = TR && S == 1;  // transposed, stride 1: reversed taps
+  extern __shared__ __align__(16) float smem[];
   const LayerSpec& s = a.s;
-  const int ng = CB / kCPT, np = kThreads / ng, TL = np * kPPT;
+  const int ng = CB / CPT, np = kThreads / ng, TL = np * 4;
   const int tid = threadIdx.x, cg = tid / np, pt = tid % np;
   const int t0 = blockIdx.x * TL, co0 = blockIdx.y * CB, b = blockIdx.z;
-  const int K = s.k, st = s.stride, pad = s.pad_l;
-
+  const int pad = kFlip ? K - 1 - s.pad_l : s.pad_l;
   int lo, span;
-  if (!s.transposed) {
-    lo = t0 * st - pad;
-    span = (TL - 1) * st + K;
+  if constexpr (!kTr2) {
+    lo = t0 * S - pad;
+    span = (TL - 1) * S + K;
   } else {
-    lo = floordiv(t0 + pad - (K - 1), st);
-    span = floordiv(t0 + TL - 1 + pad, st) - lo + 1;
+    lo = floordiv(t0 + pad - (K - 1), 2);
+    span = floordiv(t0 + TL - 1 + pad, 2) - lo + 1;
   }
-  float* xs = smem;                 // [CI][span]
-  float* ws = smem + CI * span;     // [CB][CI][K]
-
-  float acc[kCPT][kPPT];
+  const int par = (t0 + pad - (K - 1)) & 1;  // used by kTr2 only
+  float* xs = smem;               // [CI][spanp]
+  float* ws = smem + CI * spanp;  // [CI][K][CB]
+  float acc[CPT][4];
 #pragma unroll
-  for (int c = 0; c < kCPT; ++c)
+  for (int c = 0; c < CPT; ++c)
 #pragma unroll
-    for (int j = 0; j < kPPT; ++j) acc[c][j] = 0.f;
-
+    for (int j = 0; j < 4; ++j) acc[c][j] = 0.f;
   const float* xb = a.item_ptr ? a.item_ptr[b] : a.x + (int64_t)b * a.xb;
   for (int ci0 = 0; ci0 < s.cin; ci0 += CI) {
     __syncthreads();
-    for (int e = tid; e < CI * span; e += kThreads) {
-      int ci = e / span, j = e % span, t = lo + j, c = ci0 + ci;
+    for (int e = tid; e < CI * spanp; e += kThreads) {
+      const int ci = e / spanp, j = e - ci * spanp, t = lo + j, c = ci0 + ci;
       float v = 0.f;
-      if (c < s.cin && t >= 0 && t < a.lin) {
+      if (c < s.cin && j < span && t >= 0 && t < a.lin) {
         v = xb[(int64_t)c * a.xc + t];
         if (a.in_mean) v = (v - a.in_mean[c]) * a.in_istd[c];
       }
       xs[e] = v;
     }
-    for (int e = tid; e < CB * CI * K; e += kThreads) {
-      int co = e / (CI * K), r = e % (CI * K), ci = r / K, k = r % K;
-      int o = co0 + co, c = ci0 + ci;
-      ws[e] = (o < s.cout && c < s.cin) ? a.w[((int64_t)o * s.cin + c) * K + k] : 0.f;
+    for (int e = tid; e < CI * K * CB; e += kThreads) {
+      const int co = e % CB, r = e / CB, k = r % K, ci = r / K;
+      const int o = co0 + co, c = ci0 + ci, kk = kFlip ? K - 1 - k : k;
+      ws[e] = (o < s.cout && c < s.cin) ? a.w[((int64_t)o * s.cin + c) * K + kk] : 0.f;
     }
     __syncthreads();
-    const float* wrow = ws + (cg * kCPT) * CI * K;
-    if (!s.transposed) {
-      for (int ci = 0; ci < CI; ++ci) {
-        const float* xr = xs + ci * span;
+    for (int ci = 0; ci < CI; ++ci) {
+      const float* xr = xs + ci * spanp;
+      const float* wr = ws + ci * K * CB + cg * CPT;
+      if constexpr (!kTr2) {
+        // output u = t0 + 4 pt + j reads x[lo + (4 pt + j) S + k]
+        constexpr int NV = (3 * S + K + 3) / 4 * 4;
+        float xv[NV];
+        const float4* x4 = reinterpret_cast<const float4*>(xr + 4 * pt * S);
+#pragma unroll
+        for (int q = 0; q < NV / 4; ++q) {
+          const float4 v = x4[q];
+          xv[4 * q] = v.x;
+          xv[4 * q + 1] = v.y;
+          xv[4 * q + 2] = v.z;
+          xv[4 * q + 3] = v.w;
+        }
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-          float xv[kPPT];
+          float wv[CPT];
+          rb_load_w<K, CPT>(wr, CB, k, wv);
 #pragma unroll
-          for (int j = 0; j < kPPT; ++j) xv[j] = xr[(pt + j * np) * st + k];
+          for (int c = 0; c < CPT; ++c)
 #pragma unroll
-          for (int c = 0; c < kCPT; ++c) {
-            float wv = wrow[(c * CI + ci) * K + k];
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) acc[c][j] = fmaf(wv, xv[j], acc[c][j]);
-          }
+            for (int j = 0; j < 4; ++j) acc[c][j] = fmaf(wv[c], xv[j * S + k], acc[c][j]);
         }
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kPPT; ++j) {
-        const int u = t0 + pt + j * np;
-        const int k0 = (u + pad) % st;
-        for (int k = k0; k < K; k += st) {
-          const int tt = (u + pad - k) / st - lo;
-          for (int ci = 0; ci < CI; ++ci) {
-            float xv = xs[ci * span + tt];
-#pragma unroll
-            for (int c = 0; c < kCPT; ++c) acc[c][j] = fmaf(wrow[(c * CI + ci) * K + k], xv, acc[c][j]);
-          }
-        }
+      } else {
+        if (par == 0)
+          rb_accum_tr2<K, CPT, 0>(xr, wr, CB, pt, acc);
+        else
+          rb_accum_tr2<K, CPT, 1>(xr, wr, CB, pt, acc);
       }
     }
   }
 #pragma unroll
-  for (int c = 0; c < kCPT; ++c) {
-    const int o = co0 + cg * kCPT + c;
+  for (int c = 0; c < CPT; ++c) {
+    const int o = co0 + cg * CPT + c;
     if (o >= s.cout) continue;
     const float bias = a.bias[o];
 #pragma unroll
-    for (int j = 0; j < kPPT; ++j) {
-      const int u = t0 + pt + j * np;
+    for (int j = 0; j < 4; ++j) {
+      const int u = t0 + 4 * pt + j;
       if (u >= a.lout) continue;
       float v = acc[c][j] + bias;
       if (a.res) v += a.res[(int64_t)b * a.rb + (int64_t)o * a.rc + u];
       if (a.gy) {
-        // backward: times the derivative of the activation whose output is gy
         const float yv = a.gy[(int64_t)b * a.gyb + (int64_t)o * a.gyc + u];
         v *= a.gact == ACT_TANH ? 1.f - yv * yv : (a.gact == ACT_RELU ? (yv > 0.f ? 1.f : 0.f) : 1.f);
       }
@@ -208,19 +267,53 @@ void launch_absmax(const float* x, int64_t n, float* amax, cudaStream_t st) {
   GW_LAUNCH_CHECK();
 }
 
+// Geometry of one register-blocked launch: CB channels x TL positions per CTA,
+// CI input channels per shared-memory chunk, x rows padded to spanp floats (a
+// multiple of 4, wide enough for the vector loads past the last position).
+template <int K, int S, bool TR, int CPT>
+bool launch_conv_f32_rb(const ConvF32Args& a, cudaStream_t st) {
+  const LayerSpec& s = a.s;
+  const int CB = CPT == 1 ? 1 : std::min(64, (s.cout + CPT - 1) / CPT * CPT);
+  const int ng = CB / CPT, np = kThreads / ng, TL = np * 4;
+  int span_max, need;
+  if (TR && S == 2) {
+    span_max = TL / 2 + K / 2 + 3;
+    need = 2 * (np - 1) + ((K + 3) / 2 + 2) / 2 * 2;
+  } else {
+    span_max = (TL - 1) * S + K;
+    need = 4 * (np - 1) * S + (3 * S + K + 3) / 4 * 4;
+  }
+  const int spanp = (std::max(span_max, need) + 3) / 4 * 4;
+  int CI = 16;
+  while (CI > 1 && (size_t)CI * (spanp + K * CB) * 4 > 96 * 1024) CI /= 2;
+  const int chunks = (s.cin + CI - 1) / CI;
+  CI = (s.cin + chunks - 1) / chunks;
+  const size_t smem = (size_t)CI * (spanp + K * CB) * 4;
+  if (smem > 96 * 1024) return false;
+  set_smem_limit_once(conv_f32_rb_kernel<K, S, TR, CPT>, 96 * 1024);
+  dim3 grid((a.lout + TL - 1) / TL, (s.cout + CB - 1) / CB, a.B);
+  conv_f32_rb_kernel<K, S, TR, CPT><<<grid, kThreads, smem, st>>>(a, CB, CI, spanp);
+  GW_LAUNCH_CHECK();
+  return true;
+}
+
 void launch_conv_f32(const ConvF32Args& a, cudaStream_t st) {
   const LayerSpec& s = a.s;
-  const int CB = std::min(64, (s.cout + 7) / 8 * 8);
-  const int ng = CB / kCPT, np = kThreads / ng, TL = np * kPPT;
-  const int span_max = s.transposed ? TL / s.stride + s.k / s.stride + 3 : (TL - 1) * s.stride + s.k;
-  int CI = 16;
-  while (CI > 1 && (size_t)(CI * span_max + CB * CI * s.k) * 4 > 96 * 1024) CI /= 2;
-  if (CI > s.cin) CI = s.cin;
-  const size_t smem = (size_t)(CI * span_max + CB * CI * s.k) * 4;
-  set_smem_limit_once(conv_f32_kernel, 96 * 1024);
-  dim3 grid((a.lout + TL - 1) / TL, (s.cout + CB - 1) / CB, a.B);
-  conv_f32_kernel<<<grid, kThreads, smem, st>>>(a, CB, CI);
-  GW_LAUNCH_CHECK();
+  const bool tr = s.transposed;
+  bool done = false;
+  if (s.k == 7 && s.stride == 1 && !tr)
+    done = s.cout == 1 ? launch_conv_f32_rb<7, 1, false, 1>(a, st) : launch_conv_f32_rb<7, 1, false, 8>(a, st);
+  else if (s.k == 7 && s.stride == 1 && tr)
+    done = s.cout == 1 ? launch_conv_f32_rb<7, 1, true, 1>(a, st) : launch_conv_f32_rb<7, 1, true, 8>(a, st);
+  else if (s.k == 7 && s.stride == 2 && !tr)
+    done = launch_conv_f32_rb<7, 2, false, 8>(a, st);
+  else if (s.k == 7 && s.stride == 2 && tr)
+    done = launch_conv_f32_rb<7, 2, true, 8>(a, st);
+  else if (s.k == 16 && s.stride == 1 && !tr)
+    done = launch_conv_f32_rb<16, 1, false, 8>(a, st);
+  else if (s.k == 1 && s.stride == 2 && !tr)
+    done = launch_conv_f32_rb<1, 2, false, 8>(a, st);
+  GW_CHECK_ARG(done, "layer shape has no FP32 conv kernel (DeepClean and BBHnet shapes only)");
 }
 
 void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int rows, const float* taps,
