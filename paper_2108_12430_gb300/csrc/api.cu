@@ -413,11 +413,11 @@ int64_t deepclean_tc_act_elems(int L) { return 8LL * L + 2048; }
 // DeepClean on B windows through the tensor-core kernels.  `in` is the
 // blocked BF16 input (ring windows or a converted batch); y gets FP32 [B][y_ld].
 void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1,
-                         int* err, cudaStream_t st) {
+                         int* err, cudaStream_t st, int fresh_x0, int fresh_dx) {
   if (fused_supported(m, L)) {
     // the whole network in one launch, activations in shared memory
     Prof p("deepclean_fused", st);
-    launch_deepclean_fused(m, in, B, L, y, y_ld, err, st);
+    launch_deepclean_fused(m, in, B, L, y, y_ld, err, st, fresh_x0, fresh_dx);
     return;
   }
   const auto& Ls = m->layers;
@@ -1329,7 +1329,9 @@ static void stream_compute(gw_stream* s, int n_snap, const float* wit, const flo
       in.pstride = (2 * R / P) * 8;
       in.P = P;
       in.L = W;
-      deepclean_tc(m, in, n_snap, W, s->pred, W, s->act0, s->act1, s->err, st);
+      // the ring update before this launch writes the batch's newest n samples:
+      // positions x >= W - (j+1) S of window j
+      deepclean_tc(m, in, n_snap, W, s->pred, W, s->act0, s->act1, s->err, st, W - S, S);
     }
     {
       Prof p("sub_ola", st);

@@ -298,9 +298,10 @@ TcIn as_input(const TcOut& o, int lout);
 int64_t deepclean_tc_act_elems(int L);
 // DeepClean on B windows through the tensor-core kernels: `in` is the first
 // layer's blocked input, y gets FP32 [B][y_ld]; buf0/buf1 hold
-// B * deepclean_tc_act_elems(L) elements each.
+// B * deepclean_tc_act_elems(L) elements each; fresh_x0, fresh_dx as for
+// launch_deepclean_fused.
 void deepclean_tc(gw_model* m, TcIn in, int B, int L, float* y, int64_t y_ld, void* buf0, void* buf1, int* err,
-                  cudaStream_t st);
+                  cudaStream_t st, int fresh_x0 = 0, int fresh_dx = 0);
 // BBHnet on B items of FP32 [2][L]; ws holds bbhnet_tc_ws_bytes(B, L).
 void bbhnet_tc(gw_model* m, const float* x, int B, int L, float* logits, char* ws, cudaStream_t st);
 // The same on e4m3 operands with the model's static activation scales.
@@ -349,8 +350,11 @@ bool fused_supported(gw_model* m, int L);
 // DeepClean on B windows of L samples: `in` is the first layer's blocked
 // input (ring windows, a converted batch, or per-window addresses in
 // in.item_ptr), y gets FP32 [B][y_ld].
+// fresh_x0 > 0: the previous kernel on the stream writes only positions
+// x >= fresh_x0 - b fresh_dx of window b (a stream's ring update); tiles that
+// read none of them start before it ends (else every tile waits for it).
 void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y, int64_t y_ld, int* err,
-                            cudaStream_t st);
+                            cudaStream_t st, int fresh_x0 = 0, int fresh_dx = 0);
 
 // max |x| over n floats, combined into *amax (atomic max of non-negative floats).
 void launch_absmax(const float* x, int64_t n, float* amax, cudaStream_t st);

@@ -131,7 +131,12 @@ struct FParams {
   const char* const* item_ptr;
   float* y;
   int64_t y_ld;
-  int Lw, T, tiles, n_items;
+  // items run tile-major: item i is tile i / nb of window i % nb
+  int Lw, T, tiles, nb, n_items;
+  // early: the previous kernel (the stream's ring update) writes only the
+  // newest samples, window positions x >= fresh_x0 - b fresh_dx of window b;
+  // items whose input ends before them start without waiting for it
+  int early, fresh_x0, fresh_dx;
   uint32_t in_bytes, act_bytes;
   int* err;
   // test of the bounded waits: CTA 0 never arms the input of its first item,
@@ -420,7 +425,10 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
     // ---------------- input producer: the first layer's buffer of each item ----------------
     using L0 = fz::L0;
     constexpr int planes = L0::G * L0::P;
-    griddep_wait();  // the input is written by the previous kernel (ring update)
+    // the input is written by the previous kernel (ring update): wait for it
+    // before the first item that reads what it writes
+    bool waited = !p.early;
+    if (waited) griddep_wait();
     // per slot: whether an input phase was armed, and the parity of the last one
     uint32_t armed_any = 0u, armed_par = 0u;
     for (int j = 0; j < my_items; ++j) {
@@ -429,10 +437,14 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
         break;
       if (p.stall_test && blockIdx.x == 0 && j == 0) continue;  // no arrival and no copy: nothing in flight
       const int item = (int)blockIdx.x + j * G;
-      const int b = item / p.tiles, t = item - b * p.tiles;
+      const int t = item / p.nb, b = item - t * p.nb;
       int rm0[kLayers];
       fused_tile_rows(p.T, p.Lw, t, rm0, nullptr, nullptr);
       const int rin0 = rm0[0] + L0::dmin;  // first input row of every plane
+      if (!waited && min((rin0 + L0::rows) * L0::P, p.Lw) > p.fresh_x0 - b * p.fresh_dx) {
+        griddep_wait();
+        waited = true;
+      }
       const char* src0 = p.item_ptr ? p.item_ptr[b] + (int64_t)rin0 * 16
                                     : p.in + p.in_off0 + (int64_t)b * p.in_b + ((int64_t)rin0 + (int64_t)b * p.in_boff) * 16;
       const int slot = j % kSlots;
@@ -516,14 +528,14 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
     const int quarter = warp & 3;                  // TMEM lanes this warp may access
     const bool poller = quarter == 0;              // the slot's first epilogue warp polls the accumulator
     int acc_ph = 0;
-    griddep_wait();  // the prediction buffer may be read by the kernels before this one
+    bool waited = false;
     for (int k = 0; k < n_rounds; ++k) {
       const int j = k * kSlots + s;
       if (j >= my_items) break;
       EpiItem e;
       const int item = (int)blockIdx.x + j * G;
-      e.b = item / p.tiles;
-      e.t = item - e.b * p.tiles;
+      e.t = item / p.nb;
+      e.b = item - e.t * p.nb;
       fused_tile_rows(p.T, p.Lw, e.t, e.rm0, nullptr, nullptr);
       if (!epi_layer<0>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
           !epi_layer<1>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
@@ -531,9 +543,14 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
           !epi_layer<3>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
           !epi_layer<4>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
           !epi_layer<5>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<6>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias) ||
-          !epi_layer<7>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias))
+          !epi_layer<6>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias))
         break;
+      if (!waited) {
+        // the prediction buffer may still be read by the kernels before this one
+        griddep_wait();
+        waited = true;
+      }
+      if (!epi_layer<7>(p, sm, tmem, quarter, lane, s, poller, e, acc_ph, s_bias)) break;
     }
   }
   tc_fence_before();
@@ -712,7 +729,7 @@ bool fused_supported(gw_model* m, int L) {
 }
 
 void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y, int64_t y_ld, int* err,
-                            cudaStream_t st) {
+                            cudaStream_t st, int fresh_x0, int fresh_dx) {
   FusedPlan* f = m->fused;
   GW_CHECK_ARG(f && fused_supported(m, L), "fused DeepClean does not support this window length");
   GW_CHECK_ARG(in.P == fz::L0::P, "fused DeepClean: unexpected input layout");
@@ -730,7 +747,11 @@ void launch_deepclean_fused(gw_model* m, const TcIn& in, int B, int L, float* y,
   q.Lw = L;
   q.T = kTileT;
   q.tiles = (L + kTileT - 1) / kTileT;
+  q.nb = B;
   q.n_items = q.tiles * B;
+  q.early = fresh_x0 > 0 ? 1 : 0;
+  q.fresh_x0 = fresh_x0;
+  q.fresh_dx = fresh_dx;
   q.err = err;
   q.stall_test = tc_take_stall_test() ? 1 : 0;
   const int sms = current_sm_count();

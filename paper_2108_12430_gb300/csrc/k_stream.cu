@@ -210,14 +210,19 @@ __global__ void sub_ola_kernel(const float* __restrict__ pred, int64_t pred_ld, 
 }
 
 // AVERAGE aggregation with the windows of a batch split over the 8 warps of
-// a block: the block handles 32 consecutive times (one per lane); warp q sums,
+// a block: the block handles 32 V consecutive times (V per lane); warp q sums,
 // in window order, its contiguous block of windows [q b, q b + b), b =
 // ceil(n / 8), and keeps its running sum at the emitting window.  Warp 0 then
 // adds, per time, the accumulator (earlier batches) and the eight block sums
 // in block order: the emitted value is the sum up to the emitting window, the
-// accumulator keeps the full sum.  Every load of a warp reads 32 consecutive
-// floats of one window's prediction.
+// accumulator keeps the full sum (warp v does this for the lanes' times
+// tau + v).  Every load of a warp reads 32 V consecutive floats of one
+// window's prediction.  V = 4 (16-byte loads) needs S, W, delta,
+// head, R and the prediction stride to be multiples of 4, so that a lane's four
+// times share their window range and emitting snapshot; the sums are the same
+// (same order) for either V.
 constexpr int kOlaWarps = 8;
+template <int V>
 __global__ void __launch_bounds__(32 * kOlaWarps) sub_ola_avg_kernel(
     const float* __restrict__ pred, int64_t pred_ld, int n, int S, int W, int64_t R, int64_t head, int delta,
     float* __restrict__ acc, const float* __restrict__ strain_ring, float* __restrict__ out, const int* skip,
@@ -226,10 +231,10 @@ __global__ void __launch_bounds__(32 * kOlaWarps) sub_ola_avg_kernel(
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (skip_copy && blockIdx.x == 0 && threadIdx.x == 0) *skip_copy = skip ? *skip : 0;
   if (skip && *skip) return;
-  __shared__ float part[kOlaWarps][33], upto[kOlaWarps][33];
+  __shared__ float part[kOlaWarps][32 * V + 1], upto[kOlaWarps][32 * V + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
-  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t e = ((int64_t)blockIdx.x * 32 + lane) * V;
   const bool valid = e < count;
   const int64_t tau = head + S - W + e, r = tau - head;
   const int64_t k_emit = floordiv64(tau + delta, S);
@@ -239,45 +244,72 @@ __global__ void __launch_bounds__(32 * kOlaWarps) sub_ola_avg_kernel(
   const int jhi = (int)imin64(n - 1, floordiv64(r + W, S) - 1);
   const int blk = (n + kOlaWarps - 1) / kOlaWarps;
   const int ja = max(jlo, warp * blk), jb = valid ? min(jhi, warp * blk + blk - 1) : -1;
-  // window j holds tau at offset tau - (head + (j+1) S - W) of its prediction
-  const float* pj = pred + (tau - head - S + W);
-  float sum = 0.f, at_emit = 0.f;
+  // window j holds tau at offset tau - (head + (j+1) S - W) = e - j S of its prediction
+  const float* pj = pred + e;
+  const int64_t wstep = pred_ld - S;
+  float sum[V], at_emit[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) sum[v] = at_emit[v] = 0.f;
+  auto load = [&](int jj, float (&x)[V]) {
+    if constexpr (V == 4) {
+      const float4 q4 = *reinterpret_cast<const float4*>(pj + (int64_t)jj * wstep);
+      x[0] = q4.x;
+      x[1] = q4.y;
+      x[2] = q4.z;
+      x[3] = q4.w;
+    } else {
+      x[0] = pj[(int64_t)jj * wstep];
+    }
+  };
   int j = ja;
   for (; j + 7 <= jb; j += 8) {
-    float val[8];
+    float val[8][V];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) val[q] = pj[(int64_t)(j + q) * (pred_ld - S)];
+    for (int q = 0; q < 8; ++q) load(j + q, val[q]);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      sum += val[q];
-      if (j + q == j_emit) at_emit = sum;
-    }
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        sum[v] += val[q][v];
+        if (j + q == j_emit) at_emit[v] = sum[v];
+      }
   }
   for (; j <= jb; ++j) {
-    sum += pj[(int64_t)j * (pred_ld - S)];
-    if (j == j_emit) at_emit = sum;
-  }
-  part[warp][lane] = sum;
-  upto[warp][lane] = at_emit;
-  __syncthreads();
-  if (warp != 0 || !valid) return;
-  float total = (tau < head) ? acc[pmod(tau, R)] : 0.f, value = 0.f;
-  const int q_emit = j_emit >= 0 ? j_emit / blk : -1;
+    float val[V];
+    load(j, val);
 #pragma unroll
-  for (int q = 0; q < kOlaWarps; ++q) {
-    if (q == q_emit) value = total + upto[q][lane];
-    total += part[q][lane];
-  }
-  if (emits) {
-    const int64_t first = imax64(0, floordiv64(tau, S));
-    value /= (float)(k_emit - first + 1);
-    if (pring) {
-      if (tau >= 0) pring[pmod(tau, Rp)] = value;
-    } else {
-      out[tau - head + delta] = ((tau >= 0) ? strain_ring[pmod(tau, R)] : 0.f) - value;
+    for (int v = 0; v < V; ++v) {
+      sum[v] += val[v];
+      if (j == j_emit) at_emit[v] = sum[v];
     }
   }
-  acc[pmod(tau, R)] = total;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    part[warp][lane * V + v] = sum[v];
+    upto[warp][lane * V + v] = at_emit[v];
+  }
+  __syncthreads();
+  // warp v < V finishes time tau + v of every lane
+  if (warp >= V || !valid) return;
+  const int v = warp;
+  const int q_emit = j_emit >= 0 ? j_emit / blk : -1;
+  const int64_t first = imax64(0, floordiv64(tau, S));
+  const int64_t tv = tau + v;
+  float total = (tv < head) ? acc[pmod(tv, R)] : 0.f, value = 0.f;
+#pragma unroll
+  for (int q = 0; q < kOlaWarps; ++q) {
+    if (q == q_emit) value = total + upto[q][lane * V + v];
+    total += part[q][lane * V + v];
+  }
+  if (emits) {
+    value /= (float)(k_emit - first + 1);
+    if (pring) {
+      if (tv >= 0) pring[pmod(tv, Rp)] = value;
+    } else {
+      out[tv - head + delta] = ((tv >= 0) ? strain_ring[pmod(tv, R)] : 0.f) - value;
+    }
+  }
+  acc[pmod(tv, R)] = total;
 }
 
 int grid_for(int64_t n) {
@@ -436,8 +468,14 @@ void launch_sub_ola(const float* pred, int64_t pred_ld, int n, int S, int W, int
   GW_CHECK_ARG(!pring || Rp >= (int64_t)n * S, "prediction ring too small");
   const int64_t count = (int64_t)W + (int64_t)(n - 1) * S;
   if (mode == GW_AGG_AVERAGE) {
-    launch_pdl(sub_ola_avg_kernel, dim3((unsigned)((count + 31) / 32)), dim3(32 * kOlaWarps), st, pred, pred_ld, n,
-               S, W, R, head, delta, acc, strain_ring, out, skip, pring, Rp, skip_copy);
+    const bool vec = S % 4 == 0 && W % 4 == 0 && delta % 4 == 0 && head % 4 == 0 && R % 4 == 0 && pred_ld % 4 == 0 &&
+                     ((uintptr_t)pred & 15) == 0;
+    if (vec)
+      launch_pdl(sub_ola_avg_kernel<4>, dim3((unsigned)((count + 127) / 128)), dim3(32 * kOlaWarps), st, pred,
+                 pred_ld, n, S, W, R, head, delta, acc, strain_ring, out, skip, pring, Rp, skip_copy);
+    else
+      launch_pdl(sub_ola_avg_kernel<1>, dim3((unsigned)((count + 31) / 32)), dim3(32 * kOlaWarps), st, pred,
+                 pred_ld, n, S, W, R, head, delta, acc, strain_ring, out, skip, pring, Rp, skip_copy);
     return;
   }
   launch_pdl(sub_ola_kernel, dim3(grid_for(count)), dim3(kThreads), st, pred, pred_ld, n, S, W, R, head, mode, delta,
