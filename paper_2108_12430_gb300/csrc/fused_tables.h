@@ -12,10 +12,10 @@ namespace fz {
 struct L0 {
   static constexpr int transposed = 0, cin = 21, cout = 8, K = 7, stride = 1, pad = 3;
   static constexpr int J = 8, Q = 8, lgQ = 3, coutp = 8, lgcoutp = 3, npad = 64;
-  static constexpr int G = 3, P = 8, lgP = 3, rows = 136, dmin = -1;
+  static constexpr int G = 3, P = 8, lgP = 3, rows = 130, dmin = -1;
   static constexpr int n_steps = 21, step_bytes = 2048, sps = 6, n_chunks = 4, chunk0 = 0;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[21] = {71303169, 71303170, 71303305, 71303306, 71303441, 71303442, 71303577, 71303713, 71303848, 71303849, 71303984, 71303985, 71304120, 71304121, 67713, 67849, 67985, 8915481, 68392, 68528, 68664};
+    constexpr uint32_t t[21] = {68157441, 68157442, 68157571, 68157572, 68157701, 68157702, 68157831, 68157961, 68158090, 68158091, 68158220, 68158221, 68158350, 68158351, 67617, 67747, 67877, 8522151, 68266, 68396, 68526};
     return t[i];
   }
 };
@@ -23,10 +23,10 @@ struct L0 {
 struct L1 {
   static constexpr int transposed = 0, cin = 8, cout = 16, K = 7, stride = 2, pad = 3;
   static constexpr int J = 4, Q = 4, lgQ = 2, coutp = 16, lgcoutp = 4, npad = 64;
-  static constexpr int G = 1, P = 8, lgP = 3, rows = 136, dmin = -1;
+  static constexpr int G = 1, P = 8, lgP = 3, rows = 130, dmin = -1;
   static constexpr int n_steps = 7, step_bytes = 2048, sps = 6, n_chunks = 2, chunk0 = 4;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[7] = {65537, 65673, 8913169, 8847905, 8848041, 8848177, 953};
+    constexpr uint32_t t[7] = {65537, 65667, 8519941, 8454665, 8454795, 8454925, 911};
     return t[i];
   }
 };
@@ -34,10 +34,10 @@ struct L1 {
 struct L2 {
   static constexpr int transposed = 0, cin = 16, cout = 32, K = 7, stride = 2, pad = 3;
   static constexpr int J = 2, Q = 2, lgQ = 1, coutp = 32, lgcoutp = 5, npad = 64;
-  static constexpr int G = 2, P = 4, lgP = 2, rows = 136, dmin = -1;
+  static constexpr int G = 2, P = 4, lgP = 2, rows = 130, dmin = -1;
   static constexpr int n_steps = 9, step_bytes = 2048, sps = 6, n_chunks = 2, chunk0 = 6;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[9] = {35651585, 35651586, 35651720, 35651721, 35651722, 35651856, 35651857, 35651992, 35651993};
+    constexpr uint32_t t[9] = {34078721, 34078722, 34078850, 34078851, 34078852, 34078980, 34078981, 34079110, 34079111};
     return t[i];
   }
 };
@@ -45,10 +45,10 @@ struct L2 {
 struct L3 {
   static constexpr int transposed = 0, cin = 32, cout = 64, K = 7, stride = 2, pad = 3;
   static constexpr int J = 1, Q = 1, lgQ = 0, coutp = 64, lgcoutp = 6, npad = 64;
-  static constexpr int G = 4, P = 2, lgP = 1, rows = 136, dmin = -2;
+  static constexpr int G = 4, P = 2, lgP = 1, rows = 131, dmin = -2;
   static constexpr int n_steps = 14, step_bytes = 2048, sps = 6, n_chunks = 3, chunk0 = 8;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[14] = {17825793, 17826337, 17825794, 17826338, 17825795, 17826339, 17825928, 17826472, 17825929, 17826473, 17825930, 17826474, 17825931, 17826475};
+    constexpr uint32_t t[14] = {17170433, 17170957, 17170434, 17170958, 17170435, 17170959, 17170563, 17171087, 17170564, 17171088, 17170565, 17171089, 17170566, 17171090};
     return t[i];
   }
 };
@@ -56,10 +56,10 @@ struct L3 {
 struct L4 {
   static constexpr int transposed = 1, cin = 64, cout = 32, K = 7, stride = 2, pad = 3;
   static constexpr int J = 1, Q = 2, lgQ = 1, coutp = 32, lgcoutp = 5, npad = 64;
-  static constexpr int G = 8, P = 1, lgP = 0, rows = 136, dmin = -1;
+  static constexpr int G = 8, P = 1, lgP = 0, rows = 131, dmin = -1;
   static constexpr int n_steps = 16, step_bytes = 2048, sps = 6, n_chunks = 3, chunk0 = 11;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[16] = {8912896, 8913168, 8913440, 8913712, 8912897, 8913169, 8913441, 8913713, 8912898, 8913170, 8913442, 8913714, 8912899, 8913171, 8913443, 8913715};
+    constexpr uint32_t t[16] = {8585216, 8585478, 8585740, 8586002, 8585217, 8585479, 8585741, 8586003, 8585218, 8585480, 8585742, 8586004, 8585219, 8585481, 8585743, 8586005};
     return t[i];
   }
 };
@@ -67,10 +67,10 @@ struct L4 {
 struct L5 {
   static constexpr int transposed = 1, cin = 32, cout = 16, K = 7, stride = 2, pad = 3;
   static constexpr int J = 2, Q = 4, lgQ = 2, coutp = 16, lgcoutp = 4, npad = 64;
-  static constexpr int G = 4, P = 2, lgP = 1, rows = 136, dmin = -1;
+  static constexpr int G = 4, P = 2, lgP = 1, rows = 130, dmin = -1;
   static constexpr int n_steps = 10, step_bytes = 2048, sps = 6, n_chunks = 2, chunk0 = 14;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[10] = {17825793, 17826337, 17825794, 17826338, 17825928, 17826472, 17825929, 17826473, 17825930, 17826474};
+    constexpr uint32_t t[10] = {17039361, 17039881, 17039362, 17039882, 17039490, 17040010, 17039491, 17040011, 17039492, 17040012};
     return t[i];
   }
 };
@@ -78,10 +78,10 @@ struct L5 {
 struct L6 {
   static constexpr int transposed = 1, cin = 16, cout = 8, K = 7, stride = 2, pad = 3;
   static constexpr int J = 4, Q = 8, lgQ = 3, coutp = 8, lgcoutp = 3, npad = 64;
-  static constexpr int G = 2, P = 4, lgP = 2, rows = 136, dmin = -1;
+  static constexpr int G = 2, P = 4, lgP = 2, rows = 130, dmin = -1;
   static constexpr int n_steps = 7, step_bytes = 2048, sps = 6, n_chunks = 2, chunk0 = 16;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[7] = {35651585, 35651586, 35651721, 35651722, 35651857, 35651992, 35651993};
+    constexpr uint32_t t[7] = {34078721, 34078722, 34078851, 34078852, 34078981, 34079110, 34079111};
     return t[i];
   }
 };
@@ -89,10 +89,10 @@ struct L6 {
 struct L7 {
   static constexpr int transposed = 0, cin = 8, cout = 1, K = 7, stride = 1, pad = 3;
   static constexpr int J = 8, Q = 8, lgQ = 3, coutp = 1, lgcoutp = 0, npad = 32;
-  static constexpr int G = 1, P = 8, lgP = 3, rows = 136, dmin = -1;
+  static constexpr int G = 1, P = 8, lgP = 3, rows = 130, dmin = -1;
   static constexpr int n_steps = 7, step_bytes = 1024, sps = 12, n_chunks = 1, chunk0 = 18;
   __host__ __device__ static constexpr uint32_t apack(int i) {
-    constexpr uint32_t t[7] = {65537, 65673, 65809, 8913305, 66216, 66352, 66488};
+    constexpr uint32_t t[7] = {65537, 65667, 65797, 8520071, 66186, 66316, 66446};
     return t[i];
   }
 };

@@ -58,7 +58,7 @@ using namespace ptx;
 constexpr int kLayers = 8;
 constexpr int kTileT = 864;        // output samples per item
 constexpr int kRowsM = 128;        // MMA rows per layer and item
-constexpr int kWStages = 4;        // weight ring
+constexpr int kWStages = 5;        // weight ring
 constexpr int kWChunk = 12288;     // bytes per weight chunk (whole K-steps of one layer)
 #ifndef GW_FUSED_SLOTS
 #define GW_FUSED_SLOTS 4
@@ -619,7 +619,7 @@ FusedPlan* fused_plan_create(gw_model* m, const std::vector<std::vector<double>>
     std::vector<uint32_t> table;
     tc_lower_layer(Ld, wfold[l], img, table);
     const LayerSpec& s = Ld.s;
-    const int rows = (kRowsM + Ld.dspan + 7) / 8 * 8;
+    const int rows = kRowsM + Ld.dspan;  // a plane's rows: the MMA rows and the layer's row shifts
     const bool same = lay_field(l, fNSteps) == Ld.n_steps && lay_field(l, fNpad) == Ld.npad &&
                       lay_field(l, fG) == Ld.gin && lay_field(l, fP) == Ld.pin && lay_field(l, fRows) == rows &&
                       lay_field(l, fDmin) == Ld.dmin && lay_field(l, fQ) == Ld.n_chains &&

@@ -71,7 +71,7 @@ def lower(tr, cin, cout, k, s, pad, J):
     for i in range(0, len(left), 2):
         steps.append((left[i], left[i + 1] if i + 1 < len(left) else left[i]))
     steps = [(b, a) if key(b) < key(a) else (a, b) for a, b in steps]
-    rows = (ROWS_M + (dmax - dmin) + 7) // 8 * 8
+    rows = ROWS_M + (dmax - dmin)  # 16-byte rows; planes need no further alignment
     off = lambda a: ((a[0] * P + a[1]) * rows + a[2]) * 16
     apack = []
     for a, b in steps:
