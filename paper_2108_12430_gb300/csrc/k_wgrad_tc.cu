@@ -11,11 +11,12 @@
 // the dimension the tensor core's K steps walk.
 //
 // Each CTA takes chunks of 64 positions of one item in turn.  All its threads
-// stage a chunk: FP32 values are read from global memory (the shifted, strided
-// B rows gathered directly), rounded to BF16 and stored in the canonical
-// K-major layout (core matrices of 8 rows x 16 bytes); one thread then issues
-// the chunk's four MMAs into the CTA's TMEM accumulator.  Two stages let the
-// threads fill one while the MMAs read the other.  At the end the
+// stage a chunk: FP32 values are read from global memory once (the A rows and
+// each B channel's raw span), rounded to BF16, and the shifted, strided tap
+// rows of B are built from shared memory, all in the canonical K-major layout
+// (core matrices of 8 rows x 16 bytes); one thread then issues the chunk's
+// four MMAs into the CTA's TMEM accumulator.  Two stages let the threads fill
+// one while the MMAs read the other.  At the end the
 // accumulator (D, NA x N) goes to the CTA's partial slot, and a second
 // kernel sums the partials in CTA order (deterministic).
 #include <cuda_bf16.h>
@@ -35,7 +36,7 @@ using namespace ptx;
 constexpr int kWgChunk = 64;     // positions per chunk (four MMA K steps)
 constexpr int kWgThreads = 256;
 constexpr int kWgRowsA = 128;    // MMA M: the A channels, zero-padded
-constexpr int kWgGroup = 4;      // 16-byte segments a thread loads before storing them
+constexpr int kWgGroup = 6;      // a thread's 16-byte segments of a chunk (all its pass-1 tasks)
 constexpr int kWgMaxCtasPerSm = 2;
 
 struct WgTcParams {
@@ -47,6 +48,8 @@ struct WgTcParams {
   int NC, LB;
   int K, s, p;
   int N, Npad;     // N = K NC columns n = k NC + c; Npad: N rounded up to 32
+  int span_pad;    // raw B row of a chunk: 63 s + K values, rounded up to 8
+  int a_vec;       // A rows 16-byte aligned at every chunk start
   int chunks_per_b, n_chunks;
   float* partial;  // [gridDim.x][NA][Npad]
   int* err;
@@ -60,55 +63,119 @@ __device__ __forceinline__ uint32_t seg_off(int r, int q, int R) {
   return (uint32_t)((((q * (R >> 3)) + (r >> 3)) << 7) + ((r & 7) << 4));
 }
 
-// Stages chunk cid (item b, positions t0 .. t0 + 63) into the tiles at a_smem
-// (128 rows) and b_smem (Npad rows): task = (row, segment); each thread loads
-// kWgGroup tasks' 8 values before it rounds and stores them.
-__device__ __forceinline__ void stage_chunk(const WgTcParams& p, int cid, uint8_t* a_smem, uint8_t* b_smem) {
+// A chunk cid (item b, positions t0 .. t0 + 63) is staged in two passes.
+// Pass 1 reads global memory once per value: the A rows (task = row, 16-byte
+// segment; 16-byte loads when the row is aligned) and, for every B channel c,
+// the raw span u0 .. u0 + span - 1 (u0 = s t0 - p, span = 63 s + K) of Bm[c].
+// Each thread holds its (at most kWgGroup) tasks' 8 values in registers: the
+// loads of chunk i + 1 are issued right after chunk i's values are stored, so
+// that they are in flight while chunk i's tap rows are built and its MMAs
+// issued.  The stores round to BF16 into the A tile and raw[c][.].  Pass 2
+// builds each tap row B[k NC + c][t] = raw[c][s (t - t0) + k] from shared
+// memory.  A task's addresses relative to the chunk are the same for every
+// chunk: each thread works them out once (Pass1Task, tap_task).
+struct Pass1Task {
+  int goff;       // element offset from the chunk's row start (A: row aa + 8 q; B: c bc + j0)
+  int pos;        // position offset: 8 q (A) or j0 (B); -1: no task
+  uint32_t soff;  // A: byte offset in the A tile; B: byte offset in raw
+  bool is_b;
+};
+
+__device__ __forceinline__ Pass1Task pass1_task(const WgTcParams& p, int task) {
+  Pass1Task t{0, -1, 0u, false};
+  const int span8 = p.span_pad / 8;
+  const int n_a = p.NA * (kWgChunk / 8), n_tasks = n_a + p.NC * span8;
+  if (task >= n_tasks) return t;
+  if (task < n_a) {
+    const int row = task >> 3, q = task & 7;
+    t.goff = row * (int)p.aa + 8 * q;
+    t.pos = 8 * q;
+    t.soff = seg_off(row, q, kWgRowsA);
+  } else {
+    const int r = task - n_a, c = r / span8, j0 = (r - c * span8) * 8;
+    t.goff = c * (int)p.bc + j0;
+    t.pos = j0;
+    t.soff = (uint32_t)(c * p.span_pad + j0) * 2u;
+    t.is_b = true;
+  }
+  return t;
+}
+
+__device__ __forceinline__ void load_chunk(const WgTcParams& p, int cid, const Pass1Task (&tk)[kWgGroup],
+                                           float (&v)[kWgGroup][8]) {
   const int b = cid / p.chunks_per_b;
   const int t0 = (cid - b * p.chunks_per_b) * kWgChunk;
-  const int n_tasks = (p.NA + p.N) * (kWgChunk / 8);
-  const float* Ab = p.A + (int64_t)b * p.ab;
-  const float* Bb = p.Bm + (int64_t)b * p.bb;
-  for (int g0 = threadIdx.x; g0 < n_tasks; g0 += kWgThreads * kWgGroup) {
-    float v[kWgGroup][8];
+  const int u0 = p.s * t0 - p.p;
+  const float* Ab = p.A + (int64_t)b * p.ab + t0;
+  const float* Bb = p.Bm + (int64_t)b * p.bb + u0;
 #pragma unroll
-    for (int gi = 0; gi < kWgGroup; ++gi) {
-      const int task = g0 + gi * kWgThreads;
+  for (int gi = 0; gi < kWgGroup; ++gi) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[gi][e] = 0.f;
-      if (task >= n_tasks) continue;
-      const int row = task >> 3, q = task & 7;
-      const int t = t0 + 8 * q;
-      if (row < p.NA) {
-        const float* src = Ab + (int64_t)row * p.aa;
+    for (int e = 0; e < 8; ++e) v[gi][e] = 0.f;
+    if (tk[gi].pos < 0) continue;
+    if (!tk[gi].is_b) {
+      const int t = t0 + tk[gi].pos;
+      const float* src = Ab + tk[gi].goff;
+      if (p.a_vec && t + 8 <= p.LA) {
+        const float4 x0 = reinterpret_cast<const float4*>(src)[0], x1 = reinterpret_cast<const float4*>(src)[1];
+        v[gi][0] = x0.x, v[gi][1] = x0.y, v[gi][2] = x0.z, v[gi][3] = x0.w;
+        v[gi][4] = x1.x, v[gi][5] = x1.y, v[gi][6] = x1.z, v[gi][7] = x1.w;
+      } else {
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-          if (t + e < p.LA) v[gi][e] = src[t + e];
-      } else {
-        const int n = row - p.NA, k = n / p.NC, c = n - k * p.NC;
-        const float* src = Bb + (int64_t)c * p.bc;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int u = p.s * (t + e) + k - p.p;
-          if (u >= 0 && u < p.LB) v[gi][e] = src[u];
-        }
+          if (t + e < p.LA) v[gi][e] = src[e];
       }
-    }
+    } else {
+      const int u = u0 + tk[gi].pos;
+      const float* src = Bb + tk[gi].goff;
+      if (u >= 0 && u + 8 <= p.LB) {
 #pragma unroll
-    for (int gi = 0; gi < kWgGroup; ++gi) {
-      const int task = g0 + gi * kWgThreads;
-      if (task >= n_tasks) continue;
-      const int row = task >> 3, q = task & 7;
-      __nv_bfloat162 h[4];
+        for (int e = 0; e < 8; ++e) v[gi][e] = src[e];
+      } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[gi][2 * e], v[gi][2 * e + 1]);
-      uint8_t* dst = row < p.NA ? a_smem + seg_off(row, q, kWgRowsA) : b_smem + seg_off(row - p.NA, q, p.Npad);
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+        for (int e = 0; e < 8; ++e)
+          if (u + e >= 0 && u + e < p.LB) v[gi][e] = src[e];
+      }
     }
   }
 }
 
-__global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const WgTcParams p) {
+__device__ __forceinline__ void store_chunk(const Pass1Task (&tk)[kWgGroup], const float (&v)[kWgGroup][8],
+                                            uint8_t* a_smem, uint8_t* raw) {
+#pragma unroll
+  for (int gi = 0; gi < kWgGroup; ++gi) {
+    if (tk[gi].pos < 0) continue;
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[gi][2 * e], v[gi][2 * e + 1]);
+    uint8_t* dst = (tk[gi].is_b ? raw : a_smem) + tk[gi].soff;
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+  }
+}
+
+// Pass 2 task (tap row n = k NC + c, segment q): source element offset in raw
+// (low 16 bits) and byte offset in the B tile (high 16 bits); ~0u: no task.
+constexpr int kWgTaps = 8;  // 256 rows x 8 segments / 256 threads
+__device__ __forceinline__ uint32_t tap_task(const WgTcParams& p, int task) {
+  if (task >= p.N * (kWgChunk / 8)) return ~0u;
+  const int n = task >> 3, q = task & 7, k = n / p.NC, c = n - k * p.NC;
+  return (uint32_t)(c * p.span_pad + p.s * 8 * q + k) | (seg_off(n, q, p.Npad) << 16);
+}
+
+__device__ __forceinline__ void build_taps(const WgTcParams& p, const uint32_t (&tt)[kWgTaps], uint8_t* b_smem,
+                                           const __nv_bfloat16* raw) {
+#pragma unroll
+  for (int it = 0; it < kWgTaps; ++it) {
+    if (tt[it] == ~0u) continue;
+    const __nv_bfloat16* src = raw + (tt[it] & 0xffffu);
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) h[e] = src[p.s * e];
+    *reinterpret_cast<uint4*>(b_smem + (tt[it] >> 16)) = *reinterpret_cast<const uint4*>(h);
+  }
+}
+
+__global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(const WgTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t base = smem_u32(smem);
@@ -117,6 +184,7 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const WgTcParams p
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);  // [0..1] stage MMAs done, [2] all done
   volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 3);
   uint32_t* tslot = (uint32_t*)(abort_flag + 1);
+  __nv_bfloat16* raw = reinterpret_cast<__nv_bfloat16*>(smem + 2 * stage_bytes + 64);  // [NC][span_pad]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // both stages start at zero: the A rows >= NA and B rows >= N are never
@@ -143,6 +211,14 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const WgTcParams p
   const uint32_t lbo_a = (kWgRowsA / 8) * 128, lbo_b = (uint32_t)(p.Npad / 8) * 128;
 
   int i = 0;
+  Pass1Task tk[kWgGroup];
+#pragma unroll
+  for (int gi = 0; gi < kWgGroup; ++gi) tk[gi] = pass1_task(p, tid + gi * kWgThreads);
+  uint32_t tt[kWgTaps];
+#pragma unroll
+  for (int it = 0; it < kWgTaps; ++it) tt[it] = tap_task(p, tid + it * kWgThreads);
+  float v[kWgGroup][8];
+  if ((int)blockIdx.x < p.n_chunks) load_chunk(p, blockIdx.x, tk, v);
   for (int cid = blockIdx.x; cid < p.n_chunks; cid += gridDim.x, ++i) {
     const int st = i & 1;
     bool ok = true;
@@ -150,7 +226,10 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const WgTcParams p
     if (i >= 2) ok = mbar_wait(smem_u32(&bars[st]), (uint32_t)((i - 2) >> 1) & 1u, abort_flag, p.err, 1);
     if (!__syncthreads_and(ok)) break;
     uint8_t* a_s = smem + st * stage_bytes;
-    stage_chunk(p, cid, a_s, a_s + a_bytes);
+    store_chunk(tk, v, a_s, reinterpret_cast<uint8_t*>(raw));
+    if (cid + (int)gridDim.x < p.n_chunks) load_chunk(p, cid + gridDim.x, tk, v);
+    __syncthreads();  // the raw rows are complete
+    build_taps(p, tt, a_s + a_bytes, raw);
     fence_proxy_async_smem();  // the stores above are read by the tensor core (async proxy)
     __syncthreads();
     if (tid == 0) {
@@ -231,7 +310,10 @@ int wgrad_tc_grid(const WgradArgs& w, int B) {
 }  // namespace
 
 bool wgrad_tc_supported(const WgradArgs& w) {
-  return tc_supported() && w.NA >= 1 && w.NA <= kWgRowsA && w.NC >= 1 && w.K * w.NC <= 256;
+  const int span_pad = ((kWgChunk - 1) * w.s + w.K + 7) / 8 * 8;
+  return tc_supported() && w.NA >= 1 && w.NA <= kWgRowsA && w.NC >= 1 && w.K * w.NC <= 256 &&
+         w.NA * (kWgChunk / 8) + w.NC * (span_pad / 8) <= kWgThreads * kWgGroup &&
+         (int64_t)w.NA * w.aa < (1LL << 31) && (int64_t)w.NC * w.bc < (1LL << 31);
 }
 
 size_t wgrad_tc_partial_floats(const WgradArgs& w, int B) {
@@ -257,6 +339,8 @@ void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int*
   p.p = w.p;
   p.N = w.K * w.NC;
   p.Npad = (p.N + 31) / 32 * 32;
+  p.span_pad = ((kWgChunk - 1) * w.s + w.K + 7) / 8 * 8;
+  p.a_vec = (w.aa % 4 == 0 && w.ab % 4 == 0 && ((uintptr_t)w.A & 15) == 0) ? 1 : 0;
   p.chunks_per_b = (w.LA + kWgChunk - 1) / kWgChunk;
   p.n_chunks = B * p.chunks_per_b;
   p.partial = partial;
@@ -264,10 +348,11 @@ void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int*
   const int grid = wgrad_tc_grid(w, B);
   // at least 80 KB of shared memory per CTA, so that at most two CTAs share an
   // SM and their TMEM allocations (up to 256 columns each) always fit
-  const size_t smem = std::max<size_t>(80 * 1024, 1024 + 2 * (size_t)(kWgRowsA + p.Npad) * kWgChunk * 2 + 3 * 8 + 8);
-  // the limit is set once per device, for the widest layer the kernel takes (N = 256)
-  set_smem_limit_once(wgrad_tc_kernel,
-                      (int)std::max<size_t>(80 * 1024, 1024 + 2 * (size_t)(kWgRowsA + 256) * kWgChunk * 2 + 3 * 8 + 8));
+  const size_t raw_bytes = (size_t)w.NC * p.span_pad * 2;
+  const size_t smem = std::max<size_t>(80 * 1024, 1024 + 2 * (size_t)(kWgRowsA + p.Npad) * kWgChunk * 2 + 64 + raw_bytes);
+  GW_CHECK_ARG(smem <= 200 * 1024, "weight-gradient tile exceeds shared memory");
+  // the limit is set once per device, to the most any layer may ask for
+  set_smem_limit_once(wgrad_tc_kernel, 200 * 1024);
   wgrad_tc_kernel<<<grid, kWgThreads, smem, st>>>(p);
   GW_LAUNCH_CHECK();
   const int64_t cols = (int64_t)w.NA * p.Npad;
