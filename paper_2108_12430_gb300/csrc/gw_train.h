@@ -27,6 +27,10 @@ struct WgradArgs {
   int K, s, p;
   int AB, T, chunks_per_b, nj;
   float* partial;
+  // tensor-core kernel only: also the bias gradient, 1 = sum_t A[a][t] (conv:
+  // A is the output gradient), 2 = sum_u Bm[c][u] (transposed conv: Bm is the
+  // output gradient; needs LB = s LA and p + s <= K)
+  int bias = 0;
 };
 
 void launch_fold(const FoldArgs& f, cudaStream_t st);
@@ -36,17 +40,26 @@ void launch_fold_many(const FoldArgs* f, int n, cudaStream_t st);
 // dw_in_major: dWf is [C_in][C_out][K] (transposed conv) instead of [C_out][C_in][K].
 void launch_unfold(const FoldArgs& f, const float* dWf, int dw_in_major, const float* dbf, float* dp,
                    cudaStream_t st);
+// Several layers' unfolds in one launch (at most kFoldMax).
+struct UnfoldItem {
+  FoldArgs f;
+  const float* dWf;
+  int dw_in_major;
+  const float* dbf;
+};
+void launch_unfold_many(const UnfoldItem* u, int n, float* dp, cudaStream_t st);
 WgradArgs plan_wgrad(int NA, int NC, int K, int s, int LA);
 size_t wgrad_smem(const WgradArgs& w);
 // w.partial must hold B * w.chunks_per_b * NA * NC * K floats; out gets NA * NC * K.
 void launch_wgrad_partial(const WgradArgs& w, int B, cudaStream_t st);
 void launch_wgrad_reduce(const WgradArgs& w, int B, float* out, cudaStream_t st);
 // The same weight gradient on the tensor cores (BF16 operands, FP32
-// accumulation; k_wgrad_tc.cu): out gets NA * NC * K floats; partial must hold
-// wgrad_tc_partial_floats(w, B); err receives a bounded wait's give-up.
+// accumulation; k_wgrad_tc.cu): out gets NA * NC * K floats and, with
+// w.bias, db the bias gradient (NA floats for bias 1, NC for bias 2); partial
+// must hold wgrad_tc_partial_floats(w, B); err receives a bounded wait's give-up.
 bool wgrad_tc_supported(const WgradArgs& w);
 size_t wgrad_tc_partial_floats(const WgradArgs& w, int B);
-void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int* err, cudaStream_t st);
+void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, float* db, int* err, cudaStream_t st);
 // out[n] = sum_{b, t} G[b][n][t]; part holds B * N floats.
 void launch_bias_grad(const float* G, int64_t gb, int64_t gn, int B, int N, int L, float* part, float* out,
                       cudaStream_t st);

@@ -65,10 +65,9 @@ __global__ void fold_many_kernel(const __grid_constant__ FoldList l) { fold_body
 //   dw = dWf sc,  db = dbf sc,  dbeta = dbf,
 //   dgamma = a (sum_{i,k} w dWf + dbf (b - mean)),  a = 1 / sqrt(var + eps);
 // running mean and variance are not trained (gradient 0).
-__global__ void unfold_kernel(FoldArgs f, const float* __restrict__ dWf, int dw_in_major,
-                              const float* __restrict__ dbf, float* __restrict__ dp) {
+__device__ __forceinline__ void unfold_body(const FoldArgs& f, const float* __restrict__ dWf, int dw_in_major,
+                                            const float* __restrict__ dbf, float* __restrict__ dp, int o) {
   __shared__ float red[kThreads / 32];
-  const int o = blockIdx.x;
   const double a = f.bn ? 1.0 / sqrt((double)f.p[f.off_var + o] + (double)kBnEps) : 1.0;
   const double sc = f.bn ? (double)f.p[f.off_g + o] * a : 1.0;
   float dot = 0.f;
@@ -91,6 +90,22 @@ __global__ void unfold_kernel(FoldArgs f, const float* __restrict__ dWf, int dw_
       dp[f.off_var + o] = 0.f;
     }
   }
+}
+
+__global__ void unfold_kernel(FoldArgs f, const float* __restrict__ dWf, int dw_in_major,
+                              const float* __restrict__ dbf, float* __restrict__ dp) {
+  unfold_body(f, dWf, dw_in_major, dbf, dp, blockIdx.x);
+}
+
+// Several layers' unfolds in one launch: block (o, i) is output channel o of
+// layer i.
+struct UnfoldList {
+  UnfoldItem u[kFoldMax];
+};
+__global__ void unfold_many_kernel(const __grid_constant__ UnfoldList l, float* __restrict__ dp) {
+  const UnfoldItem& u = l.u[blockIdx.y];
+  if ((int)blockIdx.x >= u.f.cout) return;
+  unfold_body(u.f, u.dWf, u.dw_in_major, u.dbf, dp, blockIdx.x);
 }
 
 // Weight-gradient partials of one chunk of (item, positions):
@@ -250,6 +265,18 @@ void launch_fold_many(const FoldArgs* f, int n, cudaStream_t st) {
 
 void launch_unfold(const FoldArgs& f, const float* dWf, int dw_in_major, const float* dbf, float* dp, cudaStream_t st) {
   unfold_kernel<<<f.cout, kThreads, 0, st>>>(f, dWf, dw_in_major, dbf, dp);
+  GW_LAUNCH_CHECK();
+}
+
+void launch_unfold_many(const UnfoldItem* u, int n, float* dp, cudaStream_t st) {
+  GW_CHECK_ARG(n >= 1 && n <= kFoldMax, "unfold list size");
+  UnfoldList l{};
+  int mx = 1;
+  for (int i = 0; i < n; ++i) {
+    l.u[i] = u[i];
+    mx = std::max(mx, u[i].f.cout);
+  }
+  unfold_many_kernel<<<dim3(mx, n), kThreads, 0, st>>>(l, dp);
   GW_LAUNCH_CHECK();
 }
 

@@ -47,11 +47,13 @@ struct WgTcParams {
   int64_t bb, bc;  // Bm[b][c][u] at Bm + b bb + c bc + u, u < LB
   int NC, LB;
   int K, s, p;
-  int N, Npad;     // N = K NC columns n = k NC + c; Npad: N rounded up to 32
+  int N, Npad;     // N = K NC columns n = k NC + c; Npad: the D columns (N, + 1 for bias 1) rounded up to 32
+  int bias;        // 1: B row N all ones (D[a][N] = sum_t A[a][t]); 2: A row NA all ones
+  int NAr;         // D rows kept: NA, + 1 for bias 2
   int span_pad;    // raw B row of a chunk: 63 s + K values, rounded up to 8
   int a_vec;       // A rows 16-byte aligned at every chunk start
   int chunks_per_b, n_chunks;
-  float* partial;  // [gridDim.x][NA][Npad]
+  float* partial;  // [gridDim.x][NAr][Npad]
   int* err;
 };
 
@@ -198,6 +200,16 @@ __global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(c
     *abort_flag = 0u;
     fence_barrier_init();
   }
+  __syncthreads();
+  if (p.bias) {
+    // the bias row of ones (BF16 1.0) in both stages: staging never writes it
+    const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    if (tid < 16) {
+      const int st = tid >> 3, q = tid & 7;
+      uint8_t* tile = smem + st * stage_bytes + (p.bias == 1 ? a_bytes : 0u);
+      *reinterpret_cast<uint4*>(tile + (p.bias == 1 ? seg_off(p.N, q, p.Npad) : seg_off(p.NA, q, kWgRowsA))) = ones;
+    }
+  }
   fence_proxy_async_smem();
   const uint32_t tcols = p.Npad <= 128 ? 128u : 256u;
   if (warp == 0) tmem_alloc(smem_u32(tslot), tcols);
@@ -248,11 +260,11 @@ __global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(c
   tc_fence_after();
   if (warp < 4) {
     const int r = warp * 32 + lane;  // TMEM lane = MMA row = A channel
-    float* dst = p.partial + ((int64_t)blockIdx.x * p.NA + r) * p.Npad;
+    float* dst = p.partial + ((int64_t)blockIdx.x * p.NAr + r) * p.Npad;
     for (int c0 = 0; c0 < p.Npad; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (r < p.NA) {
+      if (r < p.NAr) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) dst[c0 + q] = i > 0 ? v[q] : 0.f;
       }
@@ -266,20 +278,37 @@ __global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(c
 // out[a][c][k] = sum over CTAs g of partial[g][a][k NC + c].  A block takes
 // 32 consecutive (a, n) columns of the partials; warp w sums g = w, w + 8, ...
 // in order (lanes on consecutive n: coalesced), then the eight warp sums are
-// added in warp order, so the result does not depend on the schedule.
+// added in warp order, so the result does not depend on the schedule.  The
+// bias gradient: bias 1, db[a] = the sum of column N; bias 2, db[c] = the
+// sum of row NA's columns k NC + c for k = p .. p + s - 1 (the taps that put
+// every output position u = s t + k - p of channel c in exactly one (t, k)).
 constexpr int kWgRedWarps = 8;
-__global__ void __launch_bounds__(32 * kWgRedWarps) wgrad_tc_reduce_kernel(const float* __restrict__ partial, int G,
-                                                                          int NA, int NC, int K, int Npad,
-                                                                          float* __restrict__ out) {
+struct WgRedParams {
+  const float* partial;
+  int G, NA, NAr, NC, K, N, Npad, bias, s, p;
+  float* out;
+  float* db;
+};
+__global__ void __launch_bounds__(32 * kWgRedWarps) wgrad_tc_reduce_kernel(const WgRedParams q) {
   __shared__ float red[kWgRedWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t e = (int64_t)blockIdx.x * 32 + lane;  // index into [NA][Npad]
-  const int64_t stride = (int64_t)NA * Npad;
-  float acc = 0.f;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;  // index into [NAr][Npad]
+  const int64_t stride = (int64_t)q.NAr * q.Npad;
+  const int a = (int)(e / q.Npad), n = (int)(e - (int64_t)a * q.Npad);
+  // the partial columns this lane adds (cnt of them, NC apart)
+  int cnt = 0;
   if (e < stride) {
-    const float* src = partial + e;
+    if (a < q.NA)
+      cnt = (n < q.N || (q.bias == 1 && n == q.N)) ? 1 : 0;
+    else if (n < q.N && n / q.NC == q.p)
+      cnt = q.s;
+  }
+  float acc = 0.f;
+  for (int j = 0; j < cnt; ++j) {
+    // four CTAs' partials in flight per step
+    const float* src = q.partial + e + j * q.NC;
     int g = warp;
-    for (; g + 3 * kWgRedWarps < G; g += 4 * kWgRedWarps) {
+    for (; g + 3 * kWgRedWarps < q.G; g += 4 * kWgRedWarps) {
       const float v0 = src[(int64_t)g * stride], v1 = src[(int64_t)(g + kWgRedWarps) * stride];
       const float v2 = src[(int64_t)(g + 2 * kWgRedWarps) * stride], v3 = src[(int64_t)(g + 3 * kWgRedWarps) * stride];
       acc += v0;
@@ -287,17 +316,20 @@ __global__ void __launch_bounds__(32 * kWgRedWarps) wgrad_tc_reduce_kernel(const
       acc += v2;
       acc += v3;
     }
-    for (; g < G; g += kWgRedWarps) acc += src[(int64_t)g * stride];
+    for (; g < q.G; g += kWgRedWarps) acc += src[(int64_t)g * stride];
   }
   red[warp][lane] = acc;
   __syncthreads();
-  if (warp == 0 && e < stride) {
+  if (warp == 0 && cnt > 0) {
     float t = 0.f;
     for (int w = 0; w < kWgRedWarps; ++w) t += red[w][lane];
-    const int a = (int)(e / Npad), n = (int)(e - (int64_t)a * Npad);
-    if (n < NC * K) {
-      const int k = n / NC, c = n - k * NC;
-      out[((int64_t)a * NC + c) * K + k] = t;
+    if (a < q.NA && n < q.N) {
+      const int k = n / q.NC, c = n - k * q.NC;
+      q.out[((int64_t)a * q.NC + c) * q.K + k] = t;
+    } else if (a < q.NA) {
+      q.db[a] = t;
+    } else {
+      q.db[n - q.p * q.NC] = t;
     }
   }
 }
@@ -309,20 +341,30 @@ int wgrad_tc_grid(const WgradArgs& w, int B) {
 
 }  // namespace
 
+namespace {
+// D's columns (N, + 1 for the ones row of bias 1) rounded up to 32, and rows
+// (NA, + 1 for bias 2).
+int wg_npad(const WgradArgs& w) { return (w.K * w.NC + (w.bias == 1 ? 1 : 0) + 31) / 32 * 32; }
+int wg_rows(const WgradArgs& w) { return w.NA + (w.bias == 2 ? 1 : 0); }
+}  // namespace
+
 bool wgrad_tc_supported(const WgradArgs& w) {
   const int span_pad = ((kWgChunk - 1) * w.s + w.K + 7) / 8 * 8;
-  return tc_supported() && w.NA >= 1 && w.NA <= kWgRowsA && w.NC >= 1 && w.K * w.NC <= 256 &&
+  // bias 2 sums taps p .. p + s - 1 of every t < LA: each output position
+  // u < LB exactly once when LB = s LA
+  const bool bias_ok = w.bias == 0 || w.bias == 1 || (w.bias == 2 && w.LB == w.s * w.LA && w.p + w.s <= w.K);
+  return tc_supported() && bias_ok && w.NA >= 1 && wg_rows(w) <= kWgRowsA && w.NC >= 1 && wg_npad(w) <= 256 &&
          w.NA * (kWgChunk / 8) + w.NC * (span_pad / 8) <= kWgThreads * kWgGroup &&
          (int64_t)w.NA * w.aa < (1LL << 31) && (int64_t)w.NC * w.bc < (1LL << 31);
 }
 
 size_t wgrad_tc_partial_floats(const WgradArgs& w, int B) {
-  const int Npad = (w.K * w.NC + 31) / 32 * 32;
-  return (size_t)wgrad_tc_grid(w, B) * w.NA * Npad;
+  return (size_t)wgrad_tc_grid(w, B) * wg_rows(w) * wg_npad(w);
 }
 
-void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int* err, cudaStream_t st) {
+void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, float* db, int* err, cudaStream_t st) {
   GW_CHECK_ARG(wgrad_tc_supported(w), "layer shape outside the tensor-core weight-gradient kernel");
+  GW_CHECK_ARG(!w.bias || db, "bias gradient requested without an output");
   WgTcParams p{};
   p.A = w.A;
   p.ab = w.ab;
@@ -338,7 +380,9 @@ void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int*
   p.s = w.s;
   p.p = w.p;
   p.N = w.K * w.NC;
-  p.Npad = (p.N + 31) / 32 * 32;
+  p.Npad = wg_npad(w);
+  p.bias = w.bias;
+  p.NAr = wg_rows(w);
   p.span_pad = ((kWgChunk - 1) * w.s + w.K + 7) / 8 * 8;
   p.a_vec = (w.aa % 4 == 0 && w.ab % 4 == 0 && ((uintptr_t)w.A & 15) == 0) ? 1 : 0;
   p.chunks_per_b = (w.LA + kWgChunk - 1) / kWgChunk;
@@ -355,9 +399,9 @@ void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, int*
   set_smem_limit_once(wgrad_tc_kernel, 200 * 1024);
   wgrad_tc_kernel<<<grid, kWgThreads, smem, st>>>(p);
   GW_LAUNCH_CHECK();
-  const int64_t cols = (int64_t)w.NA * p.Npad;
-  wgrad_tc_reduce_kernel<<<(unsigned)((cols + 31) / 32), 32 * kWgRedWarps, 0, st>>>(partial, grid, w.NA, w.NC, w.K,
-                                                                                  p.Npad, out);
+  WgRedParams q{partial, grid, w.NA, p.NAr, w.NC, w.K, p.N, p.Npad, w.bias, w.s, w.p, out, db};
+  const int64_t cols = (int64_t)p.NAr * p.Npad;
+  wgrad_tc_reduce_kernel<<<(unsigned)((cols + 31) / 32), 32 * kWgRedWarps, 0, st>>>(q);
   GW_LAUNCH_CHECK();
 }
 

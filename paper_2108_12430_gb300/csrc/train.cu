@@ -41,6 +41,21 @@ struct TrainLayer {
   int64_t n_f = 0, n_d = 0;
 };
 
+// The weight-gradient contraction of a layer (operand pointers left to the
+// caller): conv, A = the output gradient and Bm = the input; transposed conv,
+// A = the input and Bm = the output gradient.  The tensor-core kernel also
+// gives the bias gradient (bias 1: conv, 2: transposed conv).
+WgradArgs wgrad_plan(const TrainLayer& T) {
+  const LayerSpec& s = T.s;
+  WgradArgs w = s.transposed ? plan_wgrad(s.cin, s.cout, s.k, s.stride, T.lin)
+                             : plan_wgrad(s.cout, s.cin, s.k, s.stride, T.lout);
+  w.LB = s.transposed ? T.lout : T.lin;
+  w.p = s.pad_l;
+  w.bias = s.transposed ? 2 : 1;
+  if (!wgrad_tc_supported(w)) w.bias = 0;
+  return w;
+}
+
 }  // namespace
 }  // namespace gw
 
@@ -63,8 +78,8 @@ struct gw_trainer {
   float* scratch = nullptr; // recomputed activation
   float* dv[2] = {nullptr, nullptr};
   float* partial = nullptr;
-  float* dWf = nullptr;
-  float* dbf = nullptr;
+  // per layer: the folded parameters' gradients, unfolded after the backward
+  std::vector<float*> dWf, dbf;
   float* bpart = nullptr;
   float* zero_bias = nullptr;
   const float* params = nullptr;  // raw parameters of the last forward
@@ -201,7 +216,7 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
     const auto specs = deepclean_specs(d->n_in);
     int64_t off = 0;
     int lin = d->length;
-    size_t max_act = 0, max_partial = 0, max_w = 0;
+    size_t max_act = 0, max_partial = 0;
     int max_c = 0;
     for (const auto& s : specs) {
       TrainLayer T;
@@ -227,10 +242,8 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
       }
       max_act = std::max(max_act, (size_t)std::max(s.cin * T.lin, s.cout * T.lout));
       const size_t nw = (size_t)s.cin * s.cout * s.k;
-      max_w = std::max(max_w, nw);
       max_c = std::max(max_c, std::max(s.cin, s.cout));
-      const WgradArgs w = s.transposed ? plan_wgrad(s.cin, s.cout, s.k, s.stride, T.lin)
-                                       : plan_wgrad(s.cout, s.cin, s.k, s.stride, T.lout);
+      const WgradArgs w = wgrad_plan(T);
       max_partial = std::max(max_partial, (size_t)d->max_batch * w.chunks_per_b * nw);
       if (d->precision == GW_BF16 && wgrad_tc_supported(w))
         max_partial = std::max(max_partial, wgrad_tc_partial_floats(w, d->max_batch));
@@ -268,8 +281,10 @@ int gw_trainer_create(gw_ctx_t ctx, const gw_trainer_desc* d, const float* in_me
     t->dv[0] = talloc<float>(t, (size_t)Bm * max_act);
     t->dv[1] = talloc<float>(t, (size_t)Bm * max_act);
     t->partial = talloc<float>(t, max_partial);
-    t->dWf = talloc<float>(t, max_w);
-    t->dbf = talloc<float>(t, max_c);
+    for (const TrainLayer& T : t->layers) {
+      t->dWf.push_back(talloc<float>(t, (size_t)T.s.cin * T.s.cout * T.s.k));
+      t->dbf.push_back(talloc<float>(t, T.s.cout));
+    }
     t->bpart = talloc<float>(t, (size_t)Bm * max_c);
     t->zero_bias = talloc<float>(t, max_c);
     t->err = talloc<int>(t, 1);
@@ -433,38 +448,35 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
     }
     const float* xin = layer_input(t, l);
     const int64_t xb = (int64_t)s.cin * T.lin, xc = T.lin;
-    WgradArgs w;
+    WgradArgs w = wgrad_plan(T);
     if (!s.transposed) {
-      w = plan_wgrad(s.cout, s.cin, s.k, s.stride, T.lout);
       w.A = g; w.ab = gb; w.aa = gn;
-      w.Bm = xin; w.bb = xb; w.bc = xc; w.LB = T.lin;
+      w.Bm = xin; w.bb = xb; w.bc = xc;
     } else {
-      w = plan_wgrad(s.cin, s.cout, s.k, s.stride, T.lin);
       w.A = xin; w.ab = xb; w.aa = xc;
-      w.Bm = g; w.bb = gb; w.bc = gn; w.LB = T.lout;
+      w.Bm = g; w.bb = gb; w.bc = gn;
     }
-    w.p = s.pad_l;
     w.partial = t->partial;
+    bool db_done = false;
     if (t->wgrad_tc && wgrad_tc_supported(w)) {
+      // the bias gradient comes with the weight gradient (a row of ones in the GEMM)
       Prof p(l < 8 ? kWgradTcNames[l] : "train.wgrad_tc", st);
-      launch_wgrad_tc(w, B, t->partial, t->dWf, t->err, st);
+      launch_wgrad_tc(w, B, t->partial, t->dWf[l], w.bias ? t->dbf[l] : nullptr, t->err, st);
+      db_done = w.bias != 0;
     } else {
+      w.bias = 0;
       {
         Prof p(l < 8 ? kWgradNames[l] : "train.wgrad", st);
         launch_wgrad_partial(w, B, st);
       }
       {
         Prof p("train.wgrad_reduce", st);
-        launch_wgrad_reduce(w, B, t->dWf, st);
+        launch_wgrad_reduce(w, B, t->dWf[l], st);
       }
     }
-    {
+    if (!db_done) {
       Prof p("train.bgrad", st);
-      launch_bias_grad(g, gb, gn, B, s.cout, T.lout, t->bpart, t->dbf, st);
-    }
-    {
-      Prof p("train.unfold", st);
-      launch_unfold(T.f, t->dWf, s.transposed ? 1 : 0, t->dbf, dparams, st);
+      launch_bias_grad(g, gb, gn, B, s.cout, T.lout, t->bpart, t->dbf[l], st);
     }
     if (l == 0) break;
     // data gradient, times the derivative of layer l-1's activation (whose
@@ -545,6 +557,14 @@ int gw_trainer_backward(gw_trainer_t t, const float* dy_hat, float* dparams, voi
     gb = xb;
     gn = xc;
     cur ^= 1;
+  }
+  {
+    // every layer's chain rule from the folded to the raw parameters, one launch
+    std::vector<UnfoldItem> u;
+    for (int l = 0; l < nl; ++l)
+      u.push_back({t->layers[l].f, t->dWf[l], t->layers[l].s.transposed ? 1 : 0, t->dbf[l]});
+    Prof p("train.unfold", st);
+    for (int i = 0; i < nl; i += kFoldMax) launch_unfold_many(u.data() + i, std::min(kFoldMax, nl - i), dparams, st);
   }
   GW_API_END
 }
