@@ -179,39 +179,55 @@ __global__ void __launch_bounds__(kThreads) conv_f32_rb_kernel(ConvF32Args a, in
   }
 }
 
-// FIR over one row, CTA = 1024 outputs:
+// FIR over one row:
 //   y[r][n] = scale * sum_k h'[k] x[r][n + k + x_off],  x zero outside [0, x_len),
 // h' = h (rev = 0) or h reversed (rev = 1).  Valid mode: x_off = 0,
 // x_len = lout + ntaps - 1.  Its adjoint (dx[m] = sum_k h[k] dy[m - k]) is
 // x_off = -(ntaps - 1), rev = 1.
-constexpr int kFirTile = 1024;
-__global__ void __launch_bounds__(kThreads) fir_f32_kernel(const float* __restrict__ x, int64_t x_row,
-                                                           float* __restrict__ y, int64_t y_row,
-                                                           const float* __restrict__ h, int ntaps, int lout,
-                                                           int x_off, int x_len, int rev, float scale) {
-  extern __shared__ float smem[];
-  float* hs = smem;
-  float* xs = smem + ntaps;
+// CTA: kFirTile outputs, kFirThreads threads of kFirOut consecutive outputs
+// each.  Taps go in blocks of 8 (zero-padded): per block a thread loads the 8
+// taps and the 16 inputs its outputs read as float4 vectors from shared
+// memory, so that every loaded value feeds 4-8 FMAs.  Each output's sum runs
+// over the taps in order.
+constexpr int kFirThreads = 128, kFirOut = 8, kFirTile = kFirThreads * kFirOut;
+__global__ void __launch_bounds__(kFirThreads) fir_f32_kernel(const float* __restrict__ x, int64_t x_row,
+                                                              float* __restrict__ y, int64_t y_row,
+                                                              const float* __restrict__ h, int ntaps, int lout,
+                                                              int x_off, int x_len, int rev, float scale) {
+  extern __shared__ __align__(16) float smem[];
+  const int npad = (ntaps + 7) / 8 * 8;
+  float* hs = smem;         // [npad]
+  float* xs = smem + npad;  // [kFirTile + npad + 8]
   const int r = blockIdx.y, n0 = blockIdx.x * kFirTile;
   const float* xr = x + (int64_t)r * x_row;
-  const int span = kFirTile + ntaps - 1;
-  for (int e = threadIdx.x; e < ntaps; e += kThreads) hs[e] = h[rev ? ntaps - 1 - e : e];
-  for (int e = threadIdx.x; e < span; e += kThreads) {
+  const int span = kFirTile + npad + 8;
+  for (int e = threadIdx.x; e < npad; e += kFirThreads) hs[e] = e < ntaps ? h[rev ? ntaps - 1 - e : e] : 0.f;
+  for (int e = threadIdx.x; e < span; e += kFirThreads) {
     const int q = n0 + e + x_off;
     xs[e] = (q >= 0 && q < x_len) ? xr[q] : 0.f;
   }
   __syncthreads();
-  float acc[kFirTile / kThreads];
+  float acc[kFirOut];
 #pragma unroll
-  for (int j = 0; j < kFirTile / kThreads; ++j) acc[j] = 0.f;
-  for (int k = 0; k < ntaps; ++k) {
-    const float hv = hs[k];
+  for (int j = 0; j < kFirOut; ++j) acc[j] = 0.f;
+  const float* xt = xs + threadIdx.x * kFirOut;
+  for (int kb = 0; kb < npad; kb += 8) {
+    float hv[8], xv[16];
+    const float4 h0 = *reinterpret_cast<const float4*>(hs + kb), h1 = *reinterpret_cast<const float4*>(hs + kb + 4);
+    hv[0] = h0.x, hv[1] = h0.y, hv[2] = h0.z, hv[3] = h0.w, hv[4] = h1.x, hv[5] = h1.y, hv[6] = h1.z, hv[7] = h1.w;
 #pragma unroll
-    for (int j = 0; j < kFirTile / kThreads; ++j) acc[j] = fmaf(hv, xs[threadIdx.x + j * kThreads + k], acc[j]);
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(xt + kb + 4 * q);
+      xv[4 * q] = v.x, xv[4 * q + 1] = v.y, xv[4 * q + 2] = v.z, xv[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+      for (int j = 0; j < kFirOut; ++j) acc[j] = fmaf(hv[kk], xv[j + kk], acc[j]);
   }
 #pragma unroll
-  for (int j = 0; j < kFirTile / kThreads; ++j) {
-    const int n = n0 + threadIdx.x + j * kThreads;
+  for (int j = 0; j < kFirOut; ++j) {
+    const int n = n0 + threadIdx.x * kFirOut + j;
     if (n < lout) y[(int64_t)r * y_row + n] = scale * acc[j];
   }
 }
@@ -319,11 +335,12 @@ void launch_conv_f32(const ConvF32Args& a, cudaStream_t st) {
 void launch_fir_f32(const float* x, int64_t x_row, float* y, int64_t y_row, int rows, const float* taps,
                     int ntaps, int lout, cudaStream_t st, int x_off, int x_len, int rev, float scale) {
   if (x_len < 0) x_len = lout + ntaps - 1;
-  const size_t smem = (size_t)(ntaps + kFirTile + ntaps - 1) * 4;
+  const int npad = (ntaps + 7) / 8 * 8;
+  const size_t smem = (size_t)(npad + kFirTile + npad + 8) * 4;
   GW_CHECK_ARG(smem <= 200 * 1024, "FIR too long for the FP32 kernel");
   set_smem_limit_once(fir_f32_kernel, 200 * 1024);
   dim3 grid((lout + kFirTile - 1) / kFirTile, rows);
-  fir_f32_kernel<<<grid, kThreads, smem, st>>>(x, x_row, y, y_row, taps, ntaps, lout, x_off, x_len, rev, scale);
+  fir_f32_kernel<<<grid, kFirThreads, smem, st>>>(x, x_row, y, y_row, taps, ntaps, lout, x_off, x_len, rev, scale);
   GW_LAUNCH_CHECK();
 }
 
