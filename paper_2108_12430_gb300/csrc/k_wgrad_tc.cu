@@ -10,13 +10,14 @@
 // rows), N = K NC columns, and the reduction runs over positions, which is
 // the dimension the tensor core's K steps walk.
 //
-// Each CTA takes chunks of 64 positions of one item in turn.  All its threads
-// stage a chunk: FP32 values are read from global memory once (the A rows and
-// each B channel's raw span), rounded to BF16, and the shifted, strided tap
-// rows of B are built from shared memory, all in the canonical K-major layout
-// (core matrices of 8 rows x 16 bytes); one thread then issues the chunk's
-// four MMAs into the CTA's TMEM accumulator.  Two stages let the threads fill
-// one while the MMAs read the other.  At the end the
+// Each CTA (512 threads, one per SM) takes chunks of 128 positions of one
+// item in turn.  All its threads stage a chunk: FP32 values are read from
+// global memory once (the A rows and each B channel's raw span), rounded to
+// BF16, and the shifted, strided tap rows of B are built from shared memory,
+// all in the canonical K-major layout (core matrices of 8 rows x 16 bytes);
+// one thread then issues the chunk's eight MMAs into the CTA's TMEM
+// accumulator.  Two stages let the threads fill one while the MMAs read the
+// other.  At the end the
 // accumulator (D, NA x N) goes to the CTA's partial slot, and a second
 // kernel sums the partials in CTA order (deterministic).
 #include <cuda_bf16.h>
@@ -33,11 +34,13 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kWgChunk = 64;     // positions per chunk (four MMA K steps)
-constexpr int kWgThreads = 256;
+constexpr int kWgChunk = 128;    // positions per chunk (eight MMA K steps)
+constexpr int kWgSegs = kWgChunk / 8, kWgLgSegs = 4;  // 16-byte segments of a chunk row
+static_assert((1 << kWgLgSegs) == kWgSegs, "segments per row");
+constexpr int kWgThreads = 512;
 constexpr int kWgRowsA = 128;    // MMA M: the A channels, zero-padded
 constexpr int kWgGroup = 6;      // a thread's 16-byte segments of a chunk (all its pass-1 tasks)
-constexpr int kWgMaxCtasPerSm = 2;
+constexpr int kWgMaxCtasPerSm = 1;
 
 struct WgTcParams {
   const float* A;
@@ -86,10 +89,10 @@ struct Pass1Task {
 __device__ __forceinline__ Pass1Task pass1_task(const WgTcParams& p, int task) {
   Pass1Task t{0, -1, 0u, false};
   const int span8 = p.span_pad / 8;
-  const int n_a = p.NA * (kWgChunk / 8), n_tasks = n_a + p.NC * span8;
+  const int n_a = p.NA * kWgSegs, n_tasks = n_a + p.NC * span8;
   if (task >= n_tasks) return t;
   if (task < n_a) {
-    const int row = task >> 3, q = task & 7;
+    const int row = task >> kWgLgSegs, q = task & (kWgSegs - 1);
     t.goff = row * (int)p.aa + 8 * q;
     t.pos = 8 * q;
     t.soff = seg_off(row, q, kWgRowsA);
@@ -156,12 +159,13 @@ __device__ __forceinline__ void store_chunk(const Pass1Task (&tk)[kWgGroup], con
 }
 
 // Pass 2 task (tap row n = k NC + c, segment q): source element offset in raw
-// (low 16 bits) and byte offset in the B tile (high 16 bits); ~0u: no task.
-constexpr int kWgTaps = 8;  // 256 rows x 8 segments / 256 threads
+// (low 16 bits) and offset in the B tile in 16-byte units (high 16 bits); ~0u:
+// no task.
+constexpr int kWgTaps = 256 * kWgSegs / kWgThreads;  // at most 256 rows
 __device__ __forceinline__ uint32_t tap_task(const WgTcParams& p, int task) {
-  if (task >= p.N * (kWgChunk / 8)) return ~0u;
-  const int n = task >> 3, q = task & 7, k = n / p.NC, c = n - k * p.NC;
-  return (uint32_t)(c * p.span_pad + p.s * 8 * q + k) | (seg_off(n, q, p.Npad) << 16);
+  if (task >= p.N * kWgSegs) return ~0u;
+  const int n = task >> kWgLgSegs, q = task & (kWgSegs - 1), k = n / p.NC, c = n - k * p.NC;
+  return (uint32_t)(c * p.span_pad + p.s * 8 * q + k) | ((seg_off(n, q, p.Npad) >> 4) << 16);
 }
 
 __device__ __forceinline__ void build_taps(const WgTcParams& p, const uint32_t (&tt)[kWgTaps], uint8_t* b_smem,
@@ -173,7 +177,7 @@ __device__ __forceinline__ void build_taps(const WgTcParams& p, const uint32_t (
     __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) h[e] = src[p.s * e];
-    *reinterpret_cast<uint4*>(b_smem + (tt[it] >> 16)) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(b_smem + ((tt[it] >> 16) << 4)) = *reinterpret_cast<const uint4*>(h);
   }
 }
 
@@ -204,8 +208,8 @@ __global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(c
   if (p.bias) {
     // the bias row of ones (BF16 1.0) in both stages: staging never writes it
     const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
-    if (tid < 16) {
-      const int st = tid >> 3, q = tid & 7;
+    if (tid < 2 * kWgSegs) {
+      const int st = tid >> kWgLgSegs, q = tid & (kWgSegs - 1);
       uint8_t* tile = smem + st * stage_bytes + (p.bias == 1 ? a_bytes : 0u);
       *reinterpret_cast<uint4*>(tile + (p.bias == 1 ? seg_off(p.N, q, p.Npad) : seg_off(p.NA, q, kWgRowsA))) = ones;
     }
@@ -354,7 +358,7 @@ bool wgrad_tc_supported(const WgradArgs& w) {
   // u < LB exactly once when LB = s LA
   const bool bias_ok = w.bias == 0 || w.bias == 1 || (w.bias == 2 && w.LB == w.s * w.LA && w.p + w.s <= w.K);
   return tc_supported() && bias_ok && w.NA >= 1 && wg_rows(w) <= kWgRowsA && w.NC >= 1 && wg_npad(w) <= 256 &&
-         w.NA * (kWgChunk / 8) + w.NC * (span_pad / 8) <= kWgThreads * kWgGroup &&
+         w.NA * kWgSegs + w.NC * (span_pad / 8) <= kWgThreads * kWgGroup && w.NC * span_pad < 65536 &&
          (int64_t)w.NA * w.aa < (1LL << 31) && (int64_t)w.NC * w.bc < (1LL << 31);
 }
 
@@ -393,10 +397,11 @@ void launch_wgrad_tc(const WgradArgs& w, int B, float* partial, float* out, floa
   // at least 80 KB of shared memory per CTA, so that at most two CTAs share an
   // SM and their TMEM allocations (up to 256 columns each) always fit
   const size_t raw_bytes = (size_t)w.NC * p.span_pad * 2;
-  const size_t smem = std::max<size_t>(80 * 1024, 1024 + 2 * (size_t)(kWgRowsA + p.Npad) * kWgChunk * 2 + 64 + raw_bytes);
-  GW_CHECK_ARG(smem <= 200 * 1024, "weight-gradient tile exceeds shared memory");
+  const size_t smem = std::max<size_t>(kWgMaxCtasPerSm == 2 ? 80 * 1024 : 0,
+                                       1024 + 2 * (size_t)(kWgRowsA + p.Npad) * kWgChunk * 2 + 64 + raw_bytes);
+  GW_CHECK_ARG(smem <= 227 * 1024, "weight-gradient tile exceeds shared memory");
   // the limit is set once per device, to the most any layer may ask for
-  set_smem_limit_once(wgrad_tc_kernel, 200 * 1024);
+  set_smem_limit_once(wgrad_tc_kernel, 227 * 1024);
   wgrad_tc_kernel<<<grid, kWgThreads, smem, st>>>(p);
   GW_LAUNCH_CHECK();
   WgRedParams q{partial, grid, w.NA, p.NAr, w.NC, w.K, p.N, p.Npad, w.bias, w.s, w.p, out, db};
