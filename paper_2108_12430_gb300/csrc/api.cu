@@ -535,16 +535,20 @@ void bbhnet_fp8(gw_model* m, const float* x, int B, int L, float* logits, char* 
   const int64_t per = (int64_t)B * 32 * L;  // bytes of the largest activation (and then some)
   void* in0 = ws;
   void* buf[3] = {ws + (size_t)B * 16 * L, ws + (size_t)B * 16 * L + per, ws + (size_t)B * 16 * L + 2 * per};
-  TcOut xin = blocked_out(in0, m->n_in, L, Ls[0].pin, true);
+  // the stem on BF16 operands (when built), its output in e4m3 at the first block's scale
+  const LayerDev& stem = m->has_stem16 ? m->stem16 : Ls[0];
+  const int in_fp8 = m->has_stem16 ? 0 : 1;
+  TcOut xin = blocked_out(in0, m->n_in, L, stem.pin, in_fp8 != 0);
   {
     Prof p("to_blocked", st);
-    launch_to_blocked(x, (int64_t)m->n_in * L, L, B, m->n_in, L, nullptr, nullptr, Ls[0].act_scale, xin, 1, st);
+    launch_to_blocked(x, (int64_t)m->n_in * L, L, B, m->n_in, L, nullptr, nullptr, in_fp8 ? Ls[0].act_scale : 1.f,
+                      xin, in_fp8, st);
   }
   int l = Ls[0].s.lout(L);
   TcOut h = blocked_out(buf[0], Ls[0].s.cout, l, Ls[1].pin, true);
   {
     Prof p(kBbhNames[1][0], st);
-    launch_conv_tc(Ls[0], as_input(xin, L), l, h, B, m->err, st);
+    launch_conv_tc(stem, as_input(xin, L), l, h, B, m->err, st);
   }
   int hi = 0;
   for (int blk = 0; blk < 4; ++blk) {
@@ -616,6 +620,7 @@ static void set_fp8_scales(gw_model* m, const std::vector<float>& s) {
     for (int o = 0; o < L.s.cout; ++o) deq[o] = m->fp8_wscale[li][o] / L.act_scale;
     GW_CUDA(cudaMemcpy(L.wscale, deq.data(), deq.size() * 4, cudaMemcpyHostToDevice));
   }
+  if (m->has_stem16) m->stem16.out_scale = Ls[0].out_scale;
   m->fp8_final_scale = s[n];
   m->fp8_scaled = true;
 }
@@ -823,6 +828,15 @@ int gw_model_create(gw_ctx_t ctx, const gw_model_desc* d, gw_model_t* out) {
       std::vector<float> wscale;
       tc_pack_layer(L, wf, d->precision, ctx, &m->bytes, m->allocs, &wscale);
       if (d->precision == GW_FP8) m->fp8_wscale.push_back(wscale);
+      if (d->kind == GW_MODEL_BBHNET && d->precision == GW_FP8 && li == 0) {
+        LayerDev S;
+        S.s = s;
+        S.w = L.w;
+        S.b = L.b;
+        tc_pack_layer(S, wf, GW_BF16, ctx, &m->bytes, m->allocs);
+        m->stem16 = S;
+        m->has_stem16 = true;
+      }
     }
     m->layers.push_back(L);
   }

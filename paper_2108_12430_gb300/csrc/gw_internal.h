@@ -120,6 +120,10 @@ struct gw_model {
   std::vector<std::vector<float>> fp8_wscale;
   float fp8_final_scale = 1.f;
   bool fp8_scaled = false;
+  // FP8 BBHnet: the stem (2 input channels) on BF16 operands, writing the
+  // first block's e4m3 input; an e4m3 K step would pad its 2 channels to 32
+  gw::LayerDev stem16;
+  bool has_stem16 = false;
   // BF16 DeepClean: the whole-network tensor-core kernel's plan (or null)
   gw::FusedPlan* fused = nullptr;
   // tensor-core BBHnet: a second stream on which each residual block's
