@@ -37,7 +37,7 @@ using namespace ptx;
 constexpr int kWgChunk = 128;    // positions per chunk (eight MMA K steps)
 constexpr int kWgSegs = kWgChunk / 8, kWgLgSegs = 4;  // 16-byte segments of a chunk row
 static_assert((1 << kWgLgSegs) == kWgSegs, "segments per row");
-constexpr int kWgThreads = 512;
+constexpr int kWgThreads = 512, kWgWarps = kWgThreads / 32;
 constexpr int kWgRowsA = 128;    // MMA M: the A channels, zero-padded
 constexpr int kWgGroup = 6;      // a thread's 16-byte segments of a chunk (all its pass-1 tasks)
 constexpr int kWgMaxCtasPerSm = 1;
@@ -68,17 +68,20 @@ __device__ __forceinline__ uint32_t seg_off(int r, int q, int R) {
   return (uint32_t)((((q * (R >> 3)) + (r >> 3)) << 7) + ((r & 7) << 4));
 }
 
-// A chunk cid (item b, positions t0 .. t0 + 63) is staged in two passes.
-// Pass 1 reads global memory once per value: the A rows (task = row, 16-byte
-// segment; 16-byte loads when the row is aligned) and, for every B channel c,
-// the raw span u0 .. u0 + span - 1 (u0 = s t0 - p, span = 63 s + K) of Bm[c].
-// Each thread holds its (at most kWgGroup) tasks' 8 values in registers: the
-// loads of chunk i + 1 are issued right after chunk i's values are stored, so
-// that they are in flight while chunk i's tap rows are built and its MMAs
-// issued.  The stores round to BF16 into the A tile and raw[c][.].  Pass 2
-// builds each tap row B[k NC + c][t] = raw[c][s (t - t0) + k] from shared
-// memory.  A task's addresses relative to the chunk are the same for every
-// chunk: each thread works them out once (Pass1Task, tap_task).
+// A chunk cid (item b, positions t0 .. t0 + kWgChunk - 1) is staged by the
+// CTA's warps, each owning the A rows a = w, w + 16, ... and the B channels
+// c = w, w + 16, ... (w its warp index), in two passes that need no
+// synchronisation beyond the warp.  Pass 1 reads global memory once per value:
+// the warp's A rows (task = row, 16-byte segment; 16-byte loads when the row
+// is aligned) and, for each of its B channels c, the raw span u0 .. u0 +
+// span - 1 (u0 = s t0 - p, span = (kWgChunk - 1) s + K) of Bm[c].  Each thread
+// holds its (at most kWgGroup) tasks' 8 values in registers: the loads of
+// chunk i + 1 are issued right after chunk i's values are stored, so that
+// they are in flight while chunk i's tap rows are built and its MMAs issued.
+// The stores round to BF16 into the A tile and raw[c][.].  Pass 2 builds the
+// warp's tap rows B[k NC + c][t] = raw[c][s (t - t0) + k] from shared memory.
+// A task's addresses relative to the chunk are the same for every chunk: each
+// thread works them out once (Pass1Task, tap_task).
 struct Pass1Task {
   int goff;       // element offset from the chunk's row start (A: row aa + 8 q; B: c bc + j0)
   int pos;        // position offset: 8 q (A) or j0 (B); -1: no task
@@ -86,18 +89,21 @@ struct Pass1Task {
   bool is_b;
 };
 
-__device__ __forceinline__ Pass1Task pass1_task(const WgTcParams& p, int task) {
+// Rows (or channels) r < n with r = w (mod kWgWarps): how many.
+__host__ __device__ __forceinline__ int owned(int n, int w) { return n > w ? (n - w + kWgWarps - 1) / kWgWarps : 0; }
+
+__device__ __forceinline__ Pass1Task pass1_task(const WgTcParams& p, int w, int task) {
   Pass1Task t{0, -1, 0u, false};
   const int span8 = p.span_pad / 8;
-  const int n_a = p.NA * kWgSegs, n_tasks = n_a + p.NC * span8;
+  const int n_a = owned(p.NA, w) * kWgSegs, n_tasks = n_a + owned(p.NC, w) * span8;
   if (task >= n_tasks) return t;
   if (task < n_a) {
-    const int row = task >> kWgLgSegs, q = task & (kWgSegs - 1);
+    const int row = w + kWgWarps * (task >> kWgLgSegs), q = task & (kWgSegs - 1);
     t.goff = row * (int)p.aa + 8 * q;
     t.pos = 8 * q;
     t.soff = seg_off(row, q, kWgRowsA);
   } else {
-    const int r = task - n_a, c = r / span8, j0 = (r - c * span8) * 8;
+    const int r = task - n_a, m = r / span8, j0 = (r - m * span8) * 8, c = w + kWgWarps * m;
     t.goff = c * (int)p.bc + j0;
     t.pos = j0;
     t.soff = (uint32_t)(c * p.span_pad + j0) * 2u;
@@ -158,13 +164,15 @@ __device__ __forceinline__ void store_chunk(const Pass1Task (&tk)[kWgGroup], con
   }
 }
 
-// Pass 2 task (tap row n = k NC + c, segment q): source element offset in raw
-// (low 16 bits) and offset in the B tile in 16-byte units (high 16 bits); ~0u:
-// no task.
-constexpr int kWgTaps = 256 * kWgSegs / kWgThreads;  // at most 256 rows
-__device__ __forceinline__ uint32_t tap_task(const WgTcParams& p, int task) {
-  if (task >= p.N * kWgSegs) return ~0u;
-  const int n = task >> kWgLgSegs, q = task & (kWgSegs - 1), k = n / p.NC, c = n - k * p.NC;
+// Pass 2 task (tap row n = k NC + c of one of the warp's channels c, segment
+// q): source element offset in raw (low 16 bits) and offset in the B tile in
+// 16-byte units (high 16 bits); ~0u: no task.
+constexpr int kWgTaps = 12;
+__device__ __forceinline__ uint32_t tap_task(const WgTcParams& p, int w, int task) {
+  const int per_c = p.K * kWgSegs;
+  if (task >= owned(p.NC, w) * per_c) return ~0u;
+  const int m = task / per_c, r = task - m * per_c, k = r >> kWgLgSegs, q = r & (kWgSegs - 1);
+  const int c = w + kWgWarps * m, n = k * p.NC + c;
   return (uint32_t)(c * p.span_pad + p.s * 8 * q + k) | ((seg_off(n, q, p.Npad) >> 4) << 16);
 }
 
@@ -187,8 +195,9 @@ __global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(c
   const uint32_t base = smem_u32(smem);
   const uint32_t a_bytes = kWgRowsA * kWgChunk * 2, b_bytes = (uint32_t)p.Npad * kWgChunk * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);  // [0..1] stage MMAs done, [2] all done
-  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 3);
+  // [0..1] stage free (its MMAs done), [2] all MMAs done, [3..4] stage staged (one arrival per warp)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(bars + 5);
   uint32_t* tslot = (uint32_t*)(abort_flag + 1);
   __nv_bfloat16* raw = reinterpret_cast<__nv_bfloat16*>(smem + 2 * stage_bytes + 64);  // [NC][span_pad]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -201,6 +210,7 @@ __global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(c
   }
   if (tid == 0) {
     for (int i = 0; i < 3; ++i) mbar_init(smem_u32(&bars[i]), 1);
+    for (int i = 3; i < 5; ++i) mbar_init(smem_u32(&bars[i]), kWgWarps);
     *abort_flag = 0u;
     fence_barrier_init();
   }
@@ -229,35 +239,42 @@ __global__ void __launch_bounds__(kWgThreads, kWgMaxCtasPerSm) wgrad_tc_kernel(c
   int i = 0;
   Pass1Task tk[kWgGroup];
 #pragma unroll
-  for (int gi = 0; gi < kWgGroup; ++gi) tk[gi] = pass1_task(p, tid + gi * kWgThreads);
+  for (int gi = 0; gi < kWgGroup; ++gi) tk[gi] = pass1_task(p, warp, lane + 32 * gi);
   uint32_t tt[kWgTaps];
 #pragma unroll
-  for (int it = 0; it < kWgTaps; ++it) tt[it] = tap_task(p, tid + it * kWgThreads);
+  for (int it = 0; it < kWgTaps; ++it) tt[it] = tap_task(p, warp, lane + 32 * it);
   float v[kWgGroup][8];
   if ((int)blockIdx.x < p.n_chunks) load_chunk(p, blockIdx.x, tk, v);
   for (int cid = blockIdx.x; cid < p.n_chunks; cid += gridDim.x, ++i) {
     const int st = i & 1;
-    bool ok = true;
     // the stage's previous MMAs (chunk i - 2) have read it
-    if (i >= 2) ok = mbar_wait(smem_u32(&bars[st]), (uint32_t)((i - 2) >> 1) & 1u, abort_flag, p.err, 1);
-    if (!__syncthreads_and(ok)) break;
+    bool ok = true;
+    if (i >= 2 && lane == 0) ok = mbar_wait(smem_u32(&bars[st]), (uint32_t)((i - 2) >> 1) & 1u, abort_flag, p.err, 1);
+    if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
     uint8_t* a_s = smem + st * stage_bytes;
     store_chunk(tk, v, a_s, reinterpret_cast<uint8_t*>(raw));
     if (cid + (int)gridDim.x < p.n_chunks) load_chunk(p, cid + gridDim.x, tk, v);
-    __syncthreads();  // the raw rows are complete
+    __syncwarp();  // the warp's raw rows are complete
     build_taps(p, tt, a_s + a_bytes, raw);
     fence_proxy_async_smem();  // the stores above are read by the tensor core (async proxy)
-    __syncthreads();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&bars[3 + st]));
     if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = base + st * stage_bytes, b0 = a0 + a_bytes;
+      // every warp has staged its part of the chunk
+      ok = mbar_wait(smem_u32(&bars[3 + st]), (uint32_t)(i >> 1) & 1u, abort_flag, p.err, 4);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t a0 = base + st * stage_bytes, b0 = a0 + a_bytes;
 #pragma unroll
-      for (int j = 0; j < kWgChunk / 16; ++j)
-        mma_f16(tmem, make_desc(a0 + 2 * j * lbo_a, lbo_a, 128), make_desc(b0 + 2 * j * lbo_b, lbo_b, 128), idesc,
-                (i > 0 || j > 0) ? 1u : 0u);
-      mma_commit(smem_u32(&bars[st]));
+        for (int j = 0; j < kWgChunk / 16; ++j)
+          mma_f16(tmem, make_desc(a0 + 2 * j * lbo_a, lbo_a, 128), make_desc(b0 + 2 * j * lbo_b, lbo_b, 128), idesc,
+                  (i > 0 || j > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&bars[st]));
+      }
     }
+    if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
   }
+  __syncthreads();
   // every MMA of this CTA has completed before the accumulator is read
   if (tid == 0) mma_commit(smem_u32(&bars[2]));
   mbar_wait_landed(smem_u32(&bars[2]), 0u, p.err, 2);
@@ -358,7 +375,8 @@ bool wgrad_tc_supported(const WgradArgs& w) {
   // u < LB exactly once when LB = s LA
   const bool bias_ok = w.bias == 0 || w.bias == 1 || (w.bias == 2 && w.LB == w.s * w.LA && w.p + w.s <= w.K);
   return tc_supported() && bias_ok && w.NA >= 1 && wg_rows(w) <= kWgRowsA && w.NC >= 1 && wg_npad(w) <= 256 &&
-         w.NA * kWgSegs + w.NC * (span_pad / 8) <= kWgThreads * kWgGroup && w.NC * span_pad < 65536 &&
+         owned(w.NA, 0) * kWgSegs + owned(w.NC, 0) * (span_pad / 8) <= 32 * kWgGroup &&
+         owned(w.NC, 0) * w.K * kWgSegs <= 32 * kWgTaps && w.NC * span_pad < 65536 &&
          (int64_t)w.NA * w.aa < (1LL << 31) && (int64_t)w.NC * w.bc < (1LL << 31);
 }
 
