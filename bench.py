@@ -912,7 +912,11 @@ def tick_profile(G, ctx, dcs, bbh, fdec, fw, pools, n_ticks=20):
             res[f"batch{batch}"] = {"sum_kernel_ms_per_tick": tot,
                                     "kernels": {k: round(v[0] / n_ticks * 1e3, 2) for k, v in
                                                 sorted(prof.items(), key=lambda kv: -kv[1][0])},
-                                    "unit": "us per tick (both detector branches summed)"}
+                                    "unit": "us per tick (both detector branches summed)",
+                                    "note": "event intervals per kernel; the two detectors' branches run on two "
+                                            "streams at once, so a kernel's interval includes time queued behind "
+                                            "the other branch (the second detector's ring update waits for SMs "
+                                            "held by the first one's network kernel)"}
         for sid in sids:
             G.gw_server_close(srv, sid)
     finally:
