@@ -739,12 +739,33 @@ def train_config(G, torch, dev_index, flush, steps=10, warmup=3):
             fwd = dc_flops_per_window(Lt) * Bt
             flops = 3 * fwd + (fwd // 2 if ck else 0) + 2 * 2 * 2049 * Bt * (Lt - 2048)
             G.gw_trainer_status(t, st)
+            # the same step captured once as a CUDA graph and replayed (Adam
+            # reads its step count from device memory)
+            step_t = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+            def step_dev(s_):
+                G.gw_trainer_forward(t, p.data_ptr(), x.data_ptr(), Bt, y.data_ptr(), s_)
+                G.gw_band_loss(g, s.data_ptr(), y.data_ptr(), Bt, Lt, loss.data_ptr(), r.data_ptr(), s_)
+                G.gw_band_loss_backward(g, r.data_ptr(), Bt, Lt, 0, dy.data_ptr(), s_)
+                G.gw_trainer_backward(t, dy.data_ptr(), dp.data_ptr(), s_)
+                G.gw_adam_step_dev(p.data_ptr(), dp.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(),
+                                   step_t.data_ptr(), 1e-4, stream=s_)
+
+            step_dev(st)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                step_dev(torch.cuda.current_stream().cuda_stream)
+            gms = time_call(torch, graph.replay, steps, warmup, flush)
+            G.gw_trainer_status(t, st)
             out[name] = {
                 "workload": "DeepClean training step, 32 x 21 x 8192, band loss 2049 taps, Adam",
                 "weight_gradients": "tensor cores, BF16 operands" if prec == G.GW_BF16 else "FP32 SIMT",
                 "forward_and_data_gradients": "tensor cores, BF16 operands" if tcd else "FP32 SIMT",
                 "ms_per_step": float(np.mean(ms)), "p50_ms": float(np.median(ms)),
                 "windows_per_s": Bt / (np.mean(ms) / 1e3), "tflops": flops / (np.mean(ms) / 1e3) / 1e12,
+                "graph_replay_ms_per_step": float(np.mean(gms)),
+                "graph_replay_windows_per_s": Bt / (np.mean(gms) / 1e3),
                 "flops_per_step": flops, "loss": float(loss.item()), "kernels_per_step": launches,
                 "state_bytes": G.gw_trainer_bytes(t),
                 "kernels_ms": {k: round(vv[0] / 3, 4) for k, vv in sorted(prof.items(), key=lambda kv: -kv[1][0])}}

@@ -507,6 +507,12 @@ int gw_fir_backward(gw_fir_t f, const float* dy, int B, int C, int L_in, float* 
  * step counts from 1. */
 int gw_adam_step(float* params, const float* grads, float* m, float* v, int64_t n, int step, float lr, float beta1,
                  float beta2, float eps, void* cuda_stream);
+/* The same update with the step count in device memory: *step (a device int,
+ * the number of steps taken so far) is incremented on the device before the
+ * update, which then uses the new value, so a CUDA graph that captured a
+ * training step replays successive Adam steps.  Two launches on the stream. */
+int gw_adam_step_dev(float* params, const float* grads, float* m, float* v, int64_t n, int* step, float lr,
+                     float beta1, float beta2, float eps, void* cuda_stream);
 
 /* ---- instrumentation ---------------------------------------------------------
  * Process-wide, for benchmarks.  gw_profile_enable(1) clears the record and

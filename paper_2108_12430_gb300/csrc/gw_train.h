@@ -74,5 +74,8 @@ void launch_band_loss_backward(const float* r, int B, int L, const float* taps, 
                                float* dy_hat, cudaStream_t st);
 void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr, float b1, float b2,
                  float eps, cudaStream_t st);
+// Adam with the step count in device memory (incremented by the first of two launches).
+void launch_adam_dev(float* p, const float* g, float* m, float* v, int64_t n, int* step, float lr, float b1,
+                     float b2, float eps, cudaStream_t st);
 
 }  // namespace gw

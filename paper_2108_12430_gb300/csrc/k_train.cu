@@ -239,6 +239,25 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   }
 }
 
+// The same update with the step count t read from device memory (bias
+// corrections 1 - b1^t, 1 - b2^t worked out per thread), after
+// adam_count_kernel has incremented it.
+__global__ void adam_dev_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                                float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                                const int* __restrict__ step) {
+  const float t = (float)*step;
+  const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+__global__ void adam_count_kernel(int* step) { *step += 1; }
+
 int grid_for(int64_t n) {
   const int64_t b = (n + kThreads - 1) / kThreads;
   return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 1216);
@@ -376,6 +395,14 @@ void launch_band_loss_backward(const float* r, int B, int L, const float* taps, 
     scale_by_kernel<<<grid_for(n), kThreads, 0, st>>>(dy_hat, n, dloss);
     GW_LAUNCH_CHECK();
   }
+}
+
+void launch_adam_dev(float* p, const float* g, float* m, float* v, int64_t n, int* step, float lr, float b1,
+                     float b2, float eps, cudaStream_t st) {
+  adam_count_kernel<<<1, 1, 0, st>>>(step);
+  GW_LAUNCH_CHECK();
+  adam_dev_kernel<<<grid_for(n), kThreads, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, step);
+  GW_LAUNCH_CHECK();
 }
 
 void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr, float b1, float b2,

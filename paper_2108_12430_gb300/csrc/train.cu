@@ -621,4 +621,16 @@ int gw_adam_step(float* params, const float* grads, float* m, float* v, int64_t 
   GW_API_END
 }
 
+int gw_adam_step_dev(float* params, const float* grads, float* m, float* v, int64_t n, int* step, float lr,
+                     float beta1, float beta2, float eps, void* cuda_stream) {
+  GW_API_BEGIN
+  GW_CHECK_ARG(params && grads && m && v && step, "NULL argument");
+  GW_CHECK_ARG(n >= 1, "need n >= 1");
+  GW_CHECK_ARG(beta1 >= 0 && beta1 < 1 && beta2 >= 0 && beta2 < 1 && eps > 0 && lr >= 0, "bad Adam hyper-parameters");
+  Prof p("adam", (cudaStream_t)cuda_stream);
+  add_launches(1);  // the step counter's kernel
+  launch_adam_dev(params, grads, m, v, n, step, lr, beta1, beta2, eps, (cudaStream_t)cuda_stream);
+  GW_API_END
+}
+
 }  // extern "C"

@@ -44,7 +44,7 @@ EXPORTS = (
     "gw_server_wait", "gw_server_stats_read", "gw_server_replay", "gw_server_destroy",
     "gw_trainer_create", "gw_trainer_destroy", "gw_trainer_status", "gw_trainer_param_count", "gw_trainer_bytes", "gw_trainer_forward",
     "gw_trainer_backward", "gw_fir_create_band_loss", "gw_band_loss", "gw_band_loss_backward", "gw_fir_backward",
-    "gw_adam_step", "gw_model_calibrate", "gw_model_test_wait_timeout", "gw_fir_create_bandpass",
+    "gw_adam_step", "gw_adam_step_dev", "gw_model_calibrate", "gw_model_test_wait_timeout", "gw_fir_create_bandpass",
     "gw_scored_stream_create", "gw_scored_stream_push", "gw_scored_stream_wait", "gw_scored_stream_destroy",
     "gw_partition_streams",
 )
@@ -149,6 +149,7 @@ def _declare(lib):
         "gw_band_loss_backward": (I, [P, P, I, I, P, P, P]),
         "gw_fir_backward": (I, [P, P, I, I, I, P, P]),
         "gw_adam_step": (I, [P, P, P, P, I64, I, C.c_float, C.c_float, C.c_float, C.c_float, P]),
+        "gw_adam_step_dev": (I, [P, P, P, P, I64, P, C.c_float, C.c_float, C.c_float, C.c_float, P]),
         "gw_model_calibrate": (I, [P, P, I, I, C.c_float, P, P]),
         "gw_scored_stream_create": (I, [P, C.POINTER(P), P, P, P, I, I, I, I, I, I, I, I, C.POINTER(P)]),
         "gw_scored_stream_push": (I, [P, P, P, P, P, C.POINTER(C.c_uint64)]),
@@ -528,6 +529,11 @@ def gw_fir_backward(f, dy_ptr, B, Cc, L_in, dx_ptr, stream=0):
 
 def gw_adam_step(p_ptr, g_ptr, m_ptr, v_ptr, n, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
     _check(lib().gw_adam_step(p_ptr, g_ptr, m_ptr, v_ptr, n, step, lr, beta1, beta2, eps, stream or None))
+
+
+def gw_adam_step_dev(p_ptr, g_ptr, m_ptr, v_ptr, n, step_ptr, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    """Adam with the step count in device memory (int32 at step_ptr, incremented on the device)."""
+    _check(lib().gw_adam_step_dev(p_ptr, g_ptr, m_ptr, v_ptr, n, step_ptr, lr, beta1, beta2, eps, stream or None))
 
 
 def gw_profile_enable(on=True):

@@ -296,6 +296,75 @@ def test_adam_step(ctx):
     assert np.abs(p.cpu().numpy() - pp).max() <= 1e-6
 
 
+def test_adam_step_with_device_step_count(ctx):
+    # three updates with the count on the device against three with the count from the host
+    r = np.random.default_rng(5)
+    n = 4099
+    p0, m0 = r.standard_normal(n).astype(np.float32), (r.standard_normal(n) * 0.1).astype(np.float32)
+    v0 = np.abs(r.standard_normal(n) * 0.1).astype(np.float32)
+    grads = [dev(r.standard_normal(n).astype(np.float32)) for _ in range(3)]
+    a = [dev(p0), dev(m0), dev(v0)]
+    b = [dev(p0), dev(m0), dev(v0)]
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for it, gd in enumerate(grads, 1):
+        G.gw_adam_step(a[0].data_ptr(), gd.data_ptr(), a[1].data_ptr(), a[2].data_ptr(), n, it, 1e-3)
+        G.gw_adam_step_dev(b[0].data_ptr(), gd.data_ptr(), b[1].data_ptr(), b[2].data_ptr(), n, step.data_ptr(), 1e-3)
+    torch.cuda.synchronize()
+    assert int(step.item()) == 3
+    for x, y in zip(a, b):
+        # the bias corrections come from the device's powf instead of the host's
+        assert rel_l2(y.cpu().numpy(), x.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("precision,tc_data", [(G.GW_FP32, 0), (G.GW_BF16, 1)])
+def test_training_step_replays_as_a_cuda_graph(ctx, precision, tc_data):
+    # forward, loss, backward and Adam (device step count) captured once and
+    # replayed: two replays give the parameters of two eager steps exactly
+    c = case(2, 1024)
+    runs = [Run(ctx, *c, precision=precision, tc_data=tc_data) for _ in range(2)]
+    bufs = []
+    for run in runs:
+        B, L, K = run.B, run.L, run.K
+        bufs.append(dict(y=torch.empty(B, L, device="cuda"), loss=torch.empty(1, device="cuda"),
+                         r=torch.empty(B, L - K + 1, device="cuda"), dy=torch.empty(B, L, device="cuda"),
+                         dp=torch.empty_like(run.p), m=torch.zeros_like(run.p), v=torch.zeros_like(run.p),
+                         step=torch.zeros(1, dtype=torch.int32, device="cuda")))
+
+    def step(run, b, st):
+        G.gw_trainer_forward(run.t, run.p.data_ptr(), run.x.data_ptr(), run.B, b["y"].data_ptr(), st)
+        G.gw_band_loss(run.g, run.s.data_ptr(), b["y"].data_ptr(), run.B, run.L, b["loss"].data_ptr(),
+                       b["r"].data_ptr(), st)
+        G.gw_band_loss_backward(run.g, b["r"].data_ptr(), run.B, run.L, 0, b["dy"].data_ptr(), st)
+        G.gw_trainer_backward(run.t, b["dy"].data_ptr(), b["dp"].data_ptr(), st)
+        G.gw_adam_step_dev(run.p.data_ptr(), b["dp"].data_ptr(), b["m"].data_ptr(), b["v"].data_ptr(),
+                           run.p.numel(), b["step"].data_ptr(), 1e-3, stream=st)
+
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            step(runs[0], bufs[0], side.cuda_stream)
+    side.synchronize()
+    # a warm-up eager step on the graph run's own buffers first (lazy set-up
+    # happens outside the capture), then its parameters and moments reset
+    p_init = runs[1].p.clone()
+    with torch.cuda.stream(side):
+        step(runs[1], bufs[1], side.cuda_stream)
+    side.synchronize()
+    runs[1].p.copy_(p_init)
+    for k in ("m", "v", "step"):
+        bufs[1][k].zero_()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step(runs[1], bufs[1], torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert int(bufs[1]["step"].item()) == 2
+    assert torch.equal(runs[0].p, runs[1].p)
+    assert torch.equal(bufs[0]["m"], bufs[1]["m"]) and torch.equal(bufs[0]["v"], bufs[1]["v"])
+
+
 @pytest.mark.parametrize("precision,tc_data", [(G.GW_FP32, 0), (G.GW_BF16, 0), (G.GW_BF16, 1)])
 def test_training_reduces_the_loss(ctx, precision, tc_data):
     c = case(4, 1024)
