@@ -371,9 +371,10 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
                     cudaStream_t st);
 // FP32 element (b, c, t) at x + b*xb + c*xc + t*ts -> blocked bf16 / e4m3,
 // optionally standardised (ts = 8, xc = 1: space-to-depth of one signal).
+// y (optional): the (standardised) FP32 values also written to y[b yb + c yc + t].
 void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,
                        const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st,
-                       int64_t ts = 1);
+                       int64_t ts = 1, float* y = nullptr, int64_t yb = 0, int64_t yc = 0);
 // Global average pool over a blocked activation + linear head -> FP32 logits.
 void launch_gap_linear_blocked(const TcIn& in, int C, int fp8, float in_scale, const float* w,
                                const float* b, float* out, int B, cudaStream_t st);

@@ -624,10 +624,12 @@ __global__ void __launch_bounds__(kThreads, kMaxCtasPerSm) conv_tc_kernel(const 
 
 // FP32 element (b, c, t) at x[b xb + c xc + t ts] -> blocked layout (bf16 rows
 // of 8 channels, or e4m3 rows of 16).  ts = 8, xc = 1 turns one signal into 8
-// "channels" of consecutive samples (space-to-depth).
+// "channels" of consecutive samples (space-to-depth).  Optionally the
+// (standardised) FP32 values also go to y[b yb + c yc + t].
 __global__ void to_blocked_kernel(const float* __restrict__ x, int64_t xb, int64_t xc, int64_t ts, int B, int C,
                                   int L, const float* __restrict__ mean, const float* __restrict__ istd, float scale,
-                                  char* __restrict__ out, int64_t ob, int64_t og, int64_t op, int P, int fp8) {
+                                  char* __restrict__ out, int64_t ob, int64_t og, int64_t op, int P, int fp8,
+                                  float* __restrict__ y, int64_t yb, int64_t yc) {
   const int cg = fp8 ? 16 : 8;
   const int G = (C + cg - 1) / cg;
   const int64_t total = (int64_t)B * G * L;
@@ -643,6 +645,7 @@ __global__ void to_blocked_kernel(const float* __restrict__ x, int64_t xb, int64
       if (i < cg && c < C) {
         a = x[(int64_t)b * xb + (int64_t)c * xc + (int64_t)t * ts];
         if (mean) a = (a - mean[c]) * istd[c];
+        if (y) y[(int64_t)b * yb + (int64_t)c * yc + t] = a;
       }
       v[i] = a;
     }
@@ -1245,13 +1248,14 @@ void launch_conv_tc(const LayerDev& L, const TcIn& in, int lout, const TcOut& ou
 }
 
 void launch_to_blocked(const float* x, int64_t xb, int64_t xc, int B, int C, int L, const float* mean,
-                       const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st, int64_t ts) {
+                       const float* istd, float scale, const TcOut& out, int fp8, cudaStream_t st, int64_t ts,
+                       float* y, int64_t yb, int64_t yc) {
   const int esz = fp8 ? 1 : 2;
   const int cg = fp8 ? 16 : 8;
   const int64_t total = (int64_t)B * ((C + cg - 1) / cg) * L;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
   to_blocked_kernel<<<grid, 256, 0, st>>>(x, xb, xc, ts, B, C, L, mean, istd, scale, (char*)out.p, out.bstride * esz,
-                                          out.gstride * esz, out.pstride * esz, out.P, fp8);
+                                          out.gstride * esz, out.pstride * esz, out.P, fp8, y, yb, yc);
   GW_LAUNCH_CHECK();
 }
 

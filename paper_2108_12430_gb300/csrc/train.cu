@@ -391,18 +391,20 @@ int gw_trainer_forward(gw_trainer_t t, const float* params, const float* x, int 
     Prof p("train.pack", st);
     launch_tc_pack_many(packs.data(), (int)packs.size(), st);
   }
-  {
-    Prof p("train.standardise", st);
-    launch_standardise(x, B, t->n_in, t->L, t->in_mean, t->in_istd, t->x_std, st);
-  }
   const int nl = (int)t->layers.size();
   const float* in = t->x_std;
   TcOut cur{};
   if (t->tc_data) {
+    // one pass: the standardised input in FP32 (the tape) and blocked BF16 (the first conv's operand)
     const TrainLayer& T0 = t->layers[0];
     cur = blocked_out(t->blk[0], T0.s.cin, T0.lin, T0.tf.pin);
-    Prof p("train.to_blocked", st);
-    launch_to_blocked(in, (int64_t)T0.s.cin * T0.lin, T0.lin, B, T0.s.cin, T0.lin, nullptr, nullptr, 1.f, cur, 0, st);
+    Prof p("train.standardise", st);
+    const int64_t xb = (int64_t)T0.s.cin * T0.lin;
+    launch_to_blocked(x, xb, T0.lin, B, T0.s.cin, T0.lin, t->in_mean, t->in_istd, 1.f, cur, 0, st, 1, t->x_std, xb,
+                      T0.lin);
+  } else {
+    Prof p("train.standardise", st);
+    launch_standardise(x, B, t->n_in, t->L, t->in_mean, t->in_istd, t->x_std, st);
   }
   for (int l = 0; l < nl; ++l) {
     const TrainLayer& T = t->layers[l];
