@@ -71,9 +71,12 @@ constexpr int kEpiW = 4;           // epilogue warps per slot, one per TMEM lane
 // issue of slots 2 .. kSlots - 1
 constexpr int kWarpIn = 0, kWarpWeights = 1, kWarpEpi0 = 4, kWarpMmaHi = kWarpEpi0 + kSlots * kEpiW;
 constexpr int kThreads = 32 * (kWarpMmaHi + kSlots - 2);
-constexpr int kAccCols = 64;       // TMEM columns per item accumulator
-constexpr int kTmemCols = kSlots * kAccCols <= 128 ? 128 : 256;
-static_assert(kSlots >= 2 && kSlots * kAccCols <= 256, "slots");
+constexpr int kAccCols = 64;       // TMEM columns per accumulator
+// two accumulators per slot, for even and odd layers: a layer's first MMAs
+// may run while the previous layer's epilogue still reads its accumulator
+constexpr int kTmemCols = 2 * kSlots * kAccCols <= 256 ? 256 : 512;
+static_assert(kSlots >= 2 && 2 * kSlots * kAccCols <= 512, "slots");
+__device__ __forceinline__ uint32_t acc_col(int s, int l) { return (uint32_t)((2 * s + (l & 1)) * kAccCols); }
 static_assert(kWarpEpi0 % 4 == 0 && kEpiW == 4, "an epilogue warp's TMEM lane quarter is its warp index mod 4");
 constexpr int kZeroRowsF = 256;
 // Copies of the weight image in global memory: every CTA streams the same
@@ -213,7 +216,7 @@ struct Smem {
 // buffer (only the producer waits on those, in order).
 enum { kInFull = 0, kInEmpty = kInFull + kSlots, kWFull = kInEmpty + kInBufs, kWEmpty = kWFull + kWStages,
        kAccFull = kWEmpty + kWStages, kActReady = kAccFull + kSlots, kDrain = kActReady + kSlots,
-       kNBars = kDrain + kSlots };
+       kActHalf = kDrain + kSlots, kNBars = kActHalf + kSlots };
 
 
 // Descriptor words: low = start address >> 4 (14 bits) | LBO >> 4 << 16, high
@@ -227,9 +230,11 @@ constexpr uint32_t kDescHi = (128u >> 4) | (1u << 14);
 // slice of the input buffer at a_addr, the B operand the step's rows of the
 // weight chunk in the ring.  Every chunk is released by all slots' threads
 // (its empty barrier counts kSlots arrivals), each committing after its last
-// MMA on the chunk.
+// MMA on the chunk.  For l > 0 the first F::split steps read only what the
+// first half of the previous layer's epilogue wrote (the caller waited for
+// that half); before the rest, the whole epilogue (act_ready).
 template <int l>
-__device__ __forceinline__ bool issue_layer(const Smem& sm, uint32_t d, int k, uint32_t a_addr) {
+__device__ __forceinline__ bool issue_layer(const Smem& sm, uint32_t d, int k, uint32_t a_addr, int s, int& act_ph) {
   using F = typename Lay<l>::T;
   constexpr uint32_t b_lbo = (((uint32_t)F::npad * 16u) >> 4) << 16;
   constexpr uint32_t idesc = idesc_for(F::npad);
@@ -243,29 +248,46 @@ __device__ __forceinline__ bool issue_layer(const Smem& sm, uint32_t d, int k, u
     tc_fence_after();
     const uint32_t b_base = ((sm.w + (uint32_t)st * kWChunk) >> 4) | b_lbo;
 #pragma unroll
-    for (int i = c * F::sps; i < (c + 1) * F::sps && i < F::n_steps; ++i)
+    for (int i = c * F::sps; i < (c + 1) * F::sps && i < F::n_steps; ++i) {
+      if (l > 0 && i == F::split) {
+        if (!mbar_spin(sm.bar(kActReady + s), (uint32_t)act_ph & 1u, sm.abort_flag, sm.err, kErrAct)) return false;
+        ++act_ph;
+        tc_fence_after();
+      }
       mma_f16(d, hi | (a_base + F::apack(i)), hi | (b_base + (uint32_t)(i - c * F::sps) * b_step), idesc,
               i == 0 ? 0u : 1u);
+    }
     mma_commit(sm.bar(kWEmpty + st));
+  }
+  if (l > 0 && F::split >= F::n_steps) {
+    if (!mbar_spin(sm.bar(kActReady + s), (uint32_t)act_ph & 1u, sm.abort_flag, sm.err, kErrAct)) return false;
+    ++act_ph;
   }
   return true;
 }
 
 // Layer l of the CTA's item j (round k) in slot s.
 template <int l>
-__device__ __forceinline__ bool mma_layer(const Smem& sm, uint32_t tmem, int k, int j, int s, int& act_ph) {
-  // the layer's input is in place, and the slot's accumulator has been
-  // drained by the epilogue (of the previous layer, or of the slot's previous
-  // item's last layer; that epilogue has also finished with the slot's
-  // activation buffer, which the first layer's epilogue rewrites)
+__device__ __forceinline__ bool mma_layer(const Smem& sm, uint32_t tmem, int k, int j, int s, int& act_ph,
+                                          int& half_ph) {
+  // the layer's input (or, for l > 0, the part its first F::split steps read)
+  // is in place, and its accumulator (one of the slot's two, by the layer's
+  // parity) was last read by the epilogue of layer l - 2, which ended before
+  // the previous layer's epilogue began; the first layer also waits for the
+  // previous item's last epilogue (done with the slot's activation buffer,
+  // which the first layer's epilogue rewrites)
   const int ib = j % kInBufs;
   if (l == 0 && !mbar_spin(sm.bar(kInFull + s), (uint32_t)k & 1u, sm.abort_flag, sm.err, kErrIn)) return false;
-  if (l > 0 || k > 0) {
+  if (l == 0 && k > 0) {
     if (!mbar_spin(sm.bar(kActReady + s), (uint32_t)act_ph & 1u, sm.abort_flag, sm.err, kErrAct)) return false;
     ++act_ph;
   }
+  if (l > 0) {
+    if (!mbar_spin(sm.bar(kActHalf + s), (uint32_t)half_ph & 1u, sm.abort_flag, sm.err, kErrAct)) return false;
+    ++half_ph;
+  }
   tc_fence_after();
-  if (!issue_layer<l>(sm, tmem + (uint32_t)(s * kAccCols), k, l == 0 ? sm.input(ib) : sm.act(s))) return false;
+  if (!issue_layer<l>(sm, tmem + acc_col(s, l), k, l == 0 ? sm.input(ib) : sm.act(s), s, act_ph)) return false;
   mma_commit(sm.bar(kAccFull + s));
   if (l == 0) mma_commit(sm.bar(kInEmpty + ib));
   return true;
@@ -340,11 +362,18 @@ __device__ __forceinline__ bool epi_layer(const FParams& p, const Smem& sm, uint
 #pragma unroll
   for (int half = 0; half * 32 < F::npad; ++half) {
     float v[32];
-    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * kAccCols + half * 32), v);
+    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + acc_col(s, l) + (uint32_t)(half * 32), v);
     if constexpr (l + 1 < kLayers) {
       using N = typename Lay<l + 1>::T;
       const int rin0 = e.rm0[l + 1] + N::dmin;
       epi_hidden<l>(v, half, R, rin0, sm.act(s), p.lout[l], s_bias);
+      if (half == 0) {
+        // the next layer's first F::split steps read only what this half wrote
+        static_assert(F::npad == 64, "a hidden layer's epilogue runs in two halves of 32 columns");
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(sm.bar(kActHalf + s));
+      }
     } else {
       // output layer: one channel, Q positions per row -> FP32 prediction
       const int lo = e.t * p.T, hi2 = min(lo + p.T, p.Lw);
@@ -390,6 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
       mbar_init(sm.bar(kAccFull + i), 1);
       mbar_init(sm.bar(kActReady + i), kEpiW);
       mbar_init(sm.bar(kDrain + i), 1);
+      mbar_init(sm.bar(kActHalf + i), kEpiW);
     }
     for (int i = 0; i < kWStages; ++i) {
       mbar_init(sm.bar(kWFull + i), 1);
@@ -495,7 +525,8 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
     // ---------------- MMA issue: one thread per slot ----------------
     const int s = mma_slot;
     if (lane == 0) {
-      int act_ph = 0;  // act_ready phases consumed
+      int act_ph = 0;   // act_ready phases consumed
+      int half_ph = 0;  // act_half phases consumed
       for (int k = 0; k < n_rounds; ++k) {
         const int j = k * kSlots + s;
         if (j >= my_items) {
@@ -511,10 +542,10 @@ __global__ void __launch_bounds__(kThreads, 1) deepclean_fused_kernel(const FPar
           if (!ok) break;
           continue;
         }
-        if (!mma_layer<0>(sm, tmem, k, j, s, act_ph) || !mma_layer<1>(sm, tmem, k, j, s, act_ph) ||
-            !mma_layer<2>(sm, tmem, k, j, s, act_ph) || !mma_layer<3>(sm, tmem, k, j, s, act_ph) ||
-            !mma_layer<4>(sm, tmem, k, j, s, act_ph) || !mma_layer<5>(sm, tmem, k, j, s, act_ph) ||
-            !mma_layer<6>(sm, tmem, k, j, s, act_ph) || !mma_layer<7>(sm, tmem, k, j, s, act_ph))
+        if (!mma_layer<0>(sm, tmem, k, j, s, act_ph, half_ph) || !mma_layer<1>(sm, tmem, k, j, s, act_ph, half_ph) ||
+            !mma_layer<2>(sm, tmem, k, j, s, act_ph, half_ph) || !mma_layer<3>(sm, tmem, k, j, s, act_ph, half_ph) ||
+            !mma_layer<4>(sm, tmem, k, j, s, act_ph, half_ph) || !mma_layer<5>(sm, tmem, k, j, s, act_ph, half_ph) ||
+            !mma_layer<6>(sm, tmem, k, j, s, act_ph, half_ph) || !mma_layer<7>(sm, tmem, k, j, s, act_ph, half_ph))
           break;
       }
       // every MMA issued by this thread completes before TMEM is released
@@ -597,6 +628,18 @@ uint32_t lay_apack(int l, int i) {
     default: return Lay<7>::T::apack(i);
   }
 }
+int lay_order(int l, int i) {
+  switch (l) {
+    case 0: return Lay<0>::T::order(i);
+    case 1: return Lay<1>::T::order(i);
+    case 2: return Lay<2>::T::order(i);
+    case 3: return Lay<3>::T::order(i);
+    case 4: return Lay<4>::T::order(i);
+    case 5: return Lay<5>::T::order(i);
+    case 6: return Lay<6>::T::order(i);
+    default: return Lay<7>::T::order(i);
+  }
+}
 
 }  // namespace
 
@@ -630,8 +673,12 @@ FusedPlan* fused_plan_create(gw_model* m, const std::vector<std::vector<double>>
                       (l + 1 < kLayers ? s.act == ACT_TANH : s.act == ACT_NONE) &&
                       (!s.transposed || s.out_pad == 1);
     if (!same) return nullptr;
+    // step i of the kernel is step order(i) of the host lowering (a permutation)
+    std::vector<int> seen(Ld.n_steps, 0);
     for (int i = 0; i < Ld.n_steps; ++i) {
-      const uint32_t o0 = tc_slice_offset(table[2 * i], Ld.pin, rows), o1 = tc_slice_offset(table[2 * i + 1], Ld.pin, rows);
+      const int h = lay_order(l, i);
+      if (h < 0 || h >= Ld.n_steps || seen[h]++) return nullptr;
+      const uint32_t o0 = tc_slice_offset(table[2 * h], Ld.pin, rows), o1 = tc_slice_offset(table[2 * h + 1], Ld.pin, rows);
       if (o1 < o0 || lay_apack(l, i) != ((o0 >> 4) | (((o1 - o0) >> 4) << 16))) return nullptr;
     }
     const uint32_t buf = (uint32_t)(Ld.gin * Ld.pin * rows * 16);
@@ -644,7 +691,10 @@ FusedPlan* fused_plan_create(gw_model* m, const std::vector<std::vector<double>>
       const int i0 = c * sps, i1 = std::min(Ld.n_steps, i0 + sps);
       q.chunk_off[c0 + c] = (uint32_t)all.size();
       q.chunk_bytes[c0 + c] = (uint32_t)((i1 - i0) * step_bytes);
-      all.insert(all.end(), img.begin() + (size_t)i0 * step_bytes, img.begin() + (size_t)i1 * step_bytes);
+      for (int i = i0; i < i1; ++i) {
+        const size_t h = (size_t)lay_order(l, i);
+        all.insert(all.end(), img.begin() + h * step_bytes, img.begin() + (h + 1) * step_bytes);
+      }
     }
     const int b0 = (l == 0 ? BiasOff<0>::v : l == 1 ? BiasOff<1>::v : l == 2 ? BiasOff<2>::v : l == 3 ? BiasOff<3>::v
                     : l == 4 ? BiasOff<4>::v : l == 5 ? BiasOff<5>::v : l == 6 ? BiasOff<6>::v : BiasOff<7>::v);

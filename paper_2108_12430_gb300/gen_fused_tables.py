@@ -72,12 +72,31 @@ def lower(tr, cin, cout, k, s, pad, J):
         steps.append((left[i], left[i + 1] if i + 1 < len(left) else left[i]))
     steps = [(b, a) if key(b) < key(a) else (a, b) for a, b in steps]
     rows = ROWS_M + (dmax - dmin)  # 16-byte rows; planes need no further alignment
-    off = lambda a: ((a[0] * P + a[1]) * rows + a[2]) * 16
-    apack = []
-    for a, b in steps:
+    return dict(G=G, P=P, Q=Q, coutp=coutp, npad=npad, dmin=dmin, rows=rows, n_steps=len(steps), steps=steps)
+
+
+def half_order(m, prev):
+    """The steps of a layer reordered so that those reading only the outputs of
+    the previous layer's first 32 accumulator columns come first (stable), and
+    their number.  Column n = sigma * coutp + o of the previous layer holds
+    output position offset sigma (this layer's phase plane) of channel o (this
+    layer's channel group o / 8)."""
+    if prev is None:
+        return list(range(m["n_steps"])), 0
+    half = lambda sl: (sl[1] * prev["coutp"] + 8 * sl[0]) // 32
+    dep = [max(half(a), half(b)) for a, b in m["steps"]]
+    first = [i for i in range(m["n_steps"]) if dep[i] == 0]
+    return first + [i for i in range(m["n_steps"]) if dep[i] != 0], len(first)
+
+
+def apack_of(m, order):
+    off = lambda a: ((a[0] * m["P"] + a[1]) * m["rows"] + a[2]) * 16
+    out = []
+    for i in order:
+        a, b = m["steps"][i]
         o0, o1 = off(a), off(b)
-        apack.append((o0 >> 4) | (((o1 - o0) >> 4) << 16))
-    return dict(G=G, P=P, Q=Q, coutp=coutp, npad=npad, dmin=dmin, rows=rows, n_steps=len(steps), apack=apack)
+        out.append((o0 >> 4) | (((o1 - o0) >> 4) << 16))
+    return out
 
 
 def main():
@@ -86,7 +105,10 @@ def main():
         "// Compile-time tables of the fused DeepClean kernel (k_fused.cu): per layer the",
         "// tensor-core lowering (input buffer geometry, K-steps, per-step A-operand",
         "// start and LBO in 16-byte units relative to the input buffer) and the weight",
-        "// chunking.  The host plan checks them against its own lowering.",
+        "// chunking.  Steps are ordered so that the first `split` read only the",
+        "// outputs of the previous layer's first 32 accumulator columns (the MMAs",
+        "// can start once half the previous epilogue is done); order(i) is the host",
+        "// lowering's index of step i.  The host plan checks them against its own lowering.",
         "#pragma once",
         "#include <stdint.h>",
         "",
@@ -95,8 +117,12 @@ def main():
         "",
     ]
     chunk0 = 0
+    prev = None
     for li, (tr, cin, cout, k, s, pad, op, J) in enumerate(LAYERS):
         m = lower(tr, cin, cout, k, s, pad, J)
+        order, split = half_order(m, prev)
+        apack = apack_of(m, order)
+        prev = m
         step_bytes = 32 * m["npad"]
         sps = max(1, W_CHUNK // step_bytes)
         n_chunks = (m["n_steps"] + sps - 1) // sps
@@ -109,9 +135,14 @@ def main():
             f"  static constexpr int G = {m['G']}, P = {m['P']}, lgP = {lg(m['P'])}, rows = {m['rows']}, "
             f"dmin = {m['dmin']};",
             f"  static constexpr int n_steps = {m['n_steps']}, step_bytes = {step_bytes}, sps = {sps}, "
-            f"n_chunks = {n_chunks}, chunk0 = {chunk0};",
+            f"n_chunks = {n_chunks}, chunk0 = {chunk0}, split = {split};",
             f"  __host__ __device__ static constexpr uint32_t apack(int i) {{",
-            f"    constexpr uint32_t t[{m['n_steps']}] = {{{', '.join(str(v) for v in m['apack'])}}};",
+            f"    constexpr uint32_t t[{m['n_steps']}] = {{{', '.join(str(v) for v in apack)}}};",
+            "    return t[i];",
+            "  }",
+            f"  // step i issues the host lowering's step order(i)",
+            f"  __host__ __device__ static constexpr int order(int i) {{",
+            f"    constexpr int t[{m['n_steps']}] = {{{', '.join(str(v) for v in order)}}};",
             "    return t[i];",
             "  }",
             "};",
