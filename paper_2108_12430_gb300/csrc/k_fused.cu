@@ -273,15 +273,14 @@ __device__ __forceinline__ bool mma_layer(const Smem& sm, uint32_t tmem, int k, 
   // the layer's input (or, for l > 0, the part its first F::split steps read)
   // is in place, and its accumulator (one of the slot's two, by the layer's
   // parity) was last read by the epilogue of layer l - 2, which ended before
-  // the previous layer's epilogue began; the first layer also waits for the
-  // previous item's last epilogue (done with the slot's activation buffer,
-  // which the first layer's epilogue rewrites)
+  // the previous layer's epilogue began (for the first layer: the previous
+  // item's layer 6, whose epilogue ended before that item's last layer took
+  // its second part).  The first layer does not wait for the previous item's
+  // last epilogue: its MMAs read only the input buffer, and its own epilogue,
+  // which rewrites the slot's activation buffer, runs on the same warps after
+  // that one and after all of this thread's earlier MMAs have completed.
   const int ib = j % kInBufs;
   if (l == 0 && !mbar_spin(sm.bar(kInFull + s), (uint32_t)k & 1u, sm.abort_flag, sm.err, kErrIn)) return false;
-  if (l == 0 && k > 0) {
-    if (!mbar_spin(sm.bar(kActReady + s), (uint32_t)act_ph & 1u, sm.abort_flag, sm.err, kErrAct)) return false;
-    ++act_ph;
-  }
   if (l > 0) {
     if (!mbar_spin(sm.bar(kActHalf + s), (uint32_t)half_ph & 1u, sm.abort_flag, sm.err, kErrAct)) return false;
     ++half_ph;
@@ -388,9 +387,11 @@ __device__ __forceinline__ bool epi_layer(const FParams& p, const Smem& sm, uint
     }
   }
   tc_fence_before();
-  fence_proxy_async_smem();  // the stores above feed the next layer's MMAs (async proxy)
-  __syncwarp();
-  if (lane == 0) mbar_arrive(sm.bar(kActReady + s));
+  if constexpr (l + 1 < kLayers) {
+    fence_proxy_async_smem();  // the stores above feed the next layer's MMAs (async proxy)
+    __syncwarp();
+    if (lane == 0) mbar_arrive(sm.bar(kActReady + s));
+  }
   return true;
 }
 
