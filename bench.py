@@ -40,7 +40,7 @@ L2_BYTES = 129 * 1024 * 1024
 # the whole-network DeepClean kernel on this workload, from the ncu capture
 # summarised in profiles/deepclean_fused_stream_batch64.md (None when the
 # kernel has changed since that capture)
-FUSED_TRAFFIC_BYTES_PER_LAUNCH = None
+FUSED_TRAFFIC_BYTES_PER_LAUNCH = 5_337_344
 
 
 def dc_flops_per_window(L=W):
