@@ -24,16 +24,21 @@
 // ring: every window is a view), the last layer writes the FP32 prediction.
 //
 // Scheduling.  One persistent CTA per SM keeps kSlots items in flight, one
-// per slot, each with its own TMEM accumulator, MMA-issuing thread and
-// epilogue warps: while one slot's epilogue drains its accumulator of layer
-// l, the other slots' MMAs keep the tensor pipe busy.  An item's activations
-// live in one buffer per slot, rewritten in place layer after layer (a
-// layer's epilogue runs only once all of the layer's MMAs, the buffer's
-// readers, have completed); the first layer's inputs, three times larger,
-// have two buffers that the CTA's items use in turn.  The CTA takes its items
-// in rounds of kSlots, all with the same weights: a layer's B-operand image
-// is streamed from global memory in chunks of whole K-steps through a 4-stage
-// ring, each chunk released once every slot has read it.
+// per slot, each with two TMEM accumulators (even and odd layers), an
+// MMA-issuing thread and epilogue warps: while one slot's epilogue drains its
+// accumulator of layer l, the other slots' MMAs keep the tensor pipe busy.
+// An item's activations live in one buffer per slot, rewritten in place layer
+// after layer (a layer's epilogue runs only once all of the layer's MMAs, the
+// buffer's readers, have completed); the first layer's inputs, three times
+// larger, have two buffers that the CTA's items use in turn.  A hidden
+// layer's epilogue drains its 64 columns in two halves and signals after the
+// first: the next layer's K-steps that read only that half's outputs come
+// first in its step table and are issued then, the rest once the whole
+// epilogue is stored; an item's first layer reads only the input buffer and
+// does not wait for the previous item's last epilogue.  The CTA takes its
+// items in rounds of kSlots, all with the same weights: a layer's B-operand
+// image is streamed from global memory in chunks of whole K-steps through a
+// kWStages-deep ring, each chunk released once every slot has read it.
 //
 // Warps: 0 stages the first-layer input of the next items (bulk copies, zero
 // rows at the window edges), 1 streams the weight chunks, one warp per slot
