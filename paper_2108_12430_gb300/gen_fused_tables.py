@@ -99,7 +99,8 @@ def apack_of(m, order):
     return out
 
 
-def main():
+def render():
+    """The header's text."""
     lines = [
         "// Generated by paper_2108_12430_gb300/gen_fused_tables.py -- do not edit.",
         "// Compile-time tables of the fused DeepClean kernel (k_fused.cu): per layer the",
@@ -150,8 +151,12 @@ def main():
         ]
         chunk0 += n_chunks
     lines += [f"constexpr int kChunks = {chunk0};", "", "}  // namespace fz", "}  // namespace gw", ""]
+    return "\n".join(lines)
+
+
+def main():
     with open(OUT, "w") as f:
-        f.write("\n".join(lines))
+        f.write(render())
     print(OUT)
 
 
