@@ -35,6 +35,9 @@ __device__ __forceinline__ uint32_t wrap(uint32_t b, uint32_t d, uint32_t m) {
 // both copies q and q + R are written, so every window is contiguous.
 __global__ void serve_push_kernel(const ServeItem* __restrict__ items, ServeGeom g, const float* __restrict__ mean,
                                   const float* __restrict__ istd) {
+  // the network kernel after this one may start now: it reads only older
+  // samples of the rings until it waits for this kernel to finish
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const ServeItem it = items[blockIdx.y];
   if (!it.active) return;
   const int S = it.S;

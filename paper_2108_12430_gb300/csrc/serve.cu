@@ -252,7 +252,9 @@ void record_tick_a(gw_server* s, int Bb, int slot, cudaStream_t a, cudaStream_t 
       in.P = g.P;
       in.L = W;
       in.item_ptr = (const void* const*)(ptrs + det * Bb);
-      deepclean_tc(m, in, Bb, W, pred, W, s->act[det][0], s->act[det][1], s->d_err, sd);
+      // the ring update before this launch writes each window's newest S <=
+      // max_stride samples: tiles that read only older ones start under it
+      deepclean_tc(m, in, Bb, W, pred, W, s->act[det][0], s->act[det][1], s->d_err, sd, W - s->d.max_stride, 0);
     }
     {
       Prof p("serve_sub_ola", sd);
