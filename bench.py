@@ -861,7 +861,13 @@ def serve_configs(G, dev_index, seconds=1.5, precisions=None):
                 return {"snapshots": len(ids), "snapshots_per_s": len(ids) / wall, "wall_s": wall,
                         "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
                         "max_us": float(lat.max()), "mean_batch": st["mean_batch"],
-                        "kernels_per_tick": st["kernels"] / max(st["ticks"], 1), "ticks": st["ticks"]}
+                        "kernels_per_tick": st["kernels"] / max(st["ticks"], 1), "ticks": st["ticks"],
+                        # where the slowest request's time went: a tick on the device, the wait
+                        # for a launch, or the load generator queueing late
+                        "max_tick_device_us": st["max_tick_device_us"],
+                        "max_launch_wait_us": st["max_launch_wait_us"],
+                        "max_submit_late_us": st["max_submit_late_us"],
+                        "max_launch_call_us": st["max_launch_call_us"]}
 
             def saturated(n):
                 # every request is due at once: throughput only (its latency

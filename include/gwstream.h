@@ -334,6 +334,15 @@ typedef struct gw_server_stats {
   double mean_batch;      /* snapshots per tick */
   double p50_us, p99_us, mean_us, max_us;  /* submit -> result latency */
   double busy_s;          /* wall time from the first submit to the last completion */
+  /* Where a slow request's time went (maxima since the last reset): the
+   * device time of a tick (both stages, from events around each stage), the
+   * wait from a tick's oldest request's arrival to the tick's launch (the
+   * formation loop, or a backlog of ticks), for gw_server_replay how late the
+   * load generator queued a request after its scheduled time (0 otherwise),
+   * and the host time of one tick's launch calls.  The first stage's start
+   * event is recorded before its launch, so a host pause inside the launch
+   * calls shows in both the tick's device time and max_launch_call_us. */
+  double max_tick_device_us, max_launch_wait_us, max_submit_late_us, max_launch_call_us;
 } gw_server_stats;
 /* deepclean: n_det models (same precision, n_in = n_witness); bbhnet: a
  * BBHnet with n_in = n_det, or NULL to skip scoring (score_out gets NaN);

@@ -151,6 +151,7 @@ struct gw_server {
   size_t lat_next = 0;
   int64_t st_snap = 0, st_ticks = 0, st_kernels = 0;
   double st_batch_sum = 0, t_first = -1, t_last = 0;
+  double st_max_dev = 0, st_max_wait = 0, st_max_late = 0, st_max_call = 0;  // gw_server_stats' maxima
 
   std::thread loop_th, done_th;
 };
@@ -446,6 +447,7 @@ void loop_main(gw_server* s) {
       const double now = now_us();
       const double a_start = s->inflight.empty() ? now : std::max(now, s->inflight.back().t_a_end);
       t.t_launch = now;
+      for (int rid : t.reqs) s->st_max_wait = std::max(s->st_max_wait, now - s->reqs[rid].t_arrival);
       t.t_a_end = a_start + s->dur_us[t.bi];
       t.t_expect = (s->inflight.empty() ? t.t_a_end : std::max(t.t_a_end, s->inflight.back().t_expect)) +
                    s->dur_b_us[t.bi];
@@ -487,6 +489,7 @@ void loop_main(gw_server* s) {
     lk.unlock();
     bool ok = true;
     std::string err;
+    const double t_call0 = now_us();
     try {
       fill_table(s, t, proto);
       const int bi = bucket_index(s, t.n);
@@ -514,7 +517,9 @@ void loop_main(gw_server* s) {
       ok = false;
       err = e.what();
     }
+    const double t_call = now_us() - t_call0;
     lk.lock();
+    s->st_max_call = std::max(s->st_max_call, t_call);
     if (!ok) fail_all_locked(s, GW_ECUDA, "tick launch failed: " + err);
     s->inflight.push_back(std::move(t));
     s->cv_complete.notify_one();
@@ -581,6 +586,7 @@ void done_main(gw_server* s) {
     s->st_snap += done.n;
     s->st_ticks += 1;
     s->st_batch_sum += done.n;
+    if (timed) s->st_max_dev = std::max(s->st_max_dev, 1e3 * ((double)a_ms + (double)b_ms));
     s->st_kernels += done.kernels;
     s->t_last = t_now;
     s->cv_done.notify_all();
@@ -985,12 +991,17 @@ int gw_server_stats_read(gw_server_t s, int reset, gw_server_stats* out) {
     r.max_us = mx;
   }
   r.busy_s = s->t_first >= 0 ? (s->t_last - s->t_first) * 1e-6 : 0.0;
+  r.max_tick_device_us = s->st_max_dev;
+  r.max_launch_wait_us = s->st_max_wait;
+  r.max_submit_late_us = s->st_max_late;
+  r.max_launch_call_us = s->st_max_call;
   *out = r;
   if (reset) {
     s->lat.clear();
     s->lat_next = 0;
     s->st_snap = s->st_ticks = s->st_kernels = 0;
     s->st_batch_sum = 0;
+    s->st_max_dev = s->st_max_wait = s->st_max_late = s->st_max_call = 0;
     s->t_first = -1;
     s->t_last = 0;
   }
@@ -1004,6 +1015,7 @@ int gw_server_replay(gw_server_t s, int n, const int* ids, const double* t_us, c
   for (int i = 1; i < n; ++i) GW_CHECK_ARG(t_us[i] >= t_us[i - 1], "arrival times must be non-decreasing");
   std::vector<uint64_t> tickets(n);
   const double t0 = now_us();
+  double late = 0;
   for (int i = 0; i < n; ++i) {
     const double due = t0 + t_us[i];
     while (now_us() < due) {
@@ -1011,6 +1023,11 @@ int gw_server_replay(gw_server_t s, int n, const int* ids, const double* t_us, c
     }
     submit_impl(s, ids[i], witness[i], strain[i], clean[i], score ? score + i : nullptr, &tickets[i], due,
                 latency_us ? latency_us + i : nullptr);
+    late = std::max(late, now_us() - due);  // queued this long after its time (copy, a full request pool)
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->st_max_late = std::max(s->st_max_late, late);
   }
   for (int i = 0; i < n; ++i) wait_impl(s, tickets[i], 60 * 1000000LL);
   GW_API_END

@@ -77,7 +77,8 @@ class gw_server_desc(C.Structure):
 class gw_server_stats(C.Structure):
     _fields_ = [("snapshots", C.c_int64), ("ticks", C.c_int64), ("kernels", C.c_int64), ("mean_batch", C.c_double),
                 ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double),
-                ("busy_s", C.c_double)]
+                ("busy_s", C.c_double), ("max_tick_device_us", C.c_double), ("max_launch_wait_us", C.c_double),
+                ("max_submit_late_us", C.c_double), ("max_launch_call_us", C.c_double)]
 
 
 class gw_trainer_desc(C.Structure):

@@ -341,7 +341,13 @@ def test_replay_matches_submit_and_reports_latency(ctx):
         assert np.array_equal(clean[j], ref[i][0][:, k]) and score[j] == ref[i][1][k]
     st = G.gw_server_stats_read(rig.s, reset=True)
     assert st["snapshots"] == len(order) and st["p50_us"] <= st["p99_us"]
-    assert G.gw_server_stats_read(rig.s)["snapshots"] == 0
+    # the slowest request's time is bounded by what its parts can add up to:
+    # it waited for a launch, then for at most the in-flight ticks and its own
+    assert 0 < st["max_tick_device_us"] and 0 <= st["max_launch_wait_us"] <= st["max_us"]
+    assert 0 <= st["max_submit_late_us"] < st["busy_s"] * 1e6 and 0 < st["max_launch_call_us"]
+    st0 = G.gw_server_stats_read(rig.s)
+    assert st0["snapshots"] == 0 and st0["max_tick_device_us"] == st0["max_launch_wait_us"] == 0
+    assert st0["max_submit_late_us"] == st0["max_launch_call_us"] == 0
 
 
 def test_non_finite_snapshot_is_refused(ctx):
