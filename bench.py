@@ -894,7 +894,10 @@ def serve_configs(G, dev_index, seconds=1.5, precisions=None):
                 G.gw_server_close(srv, int(sid))
             G.gw_server_destroy(srv)
             objs.pop()
-            ticks = tick_profile(G, ctx, dcs, bbh, fdec, fw, pools)
+            try:
+                ticks = tick_profile(G, ctx, dcs, bbh, fdec, fw, pools)
+            except G.GwError as e:  # a diagnostic breakdown: its failure is reported, the line still printed
+                ticks = {"error": str(e)}
             out[f"config5_{name}"] = {
                 "workload": "serving 64 streams x 2 detectors, strides 128/256/512, DeepClean 21x32768 -> subtract "
                             "-> 2x resample -> whiten 2049 taps -> BBHnet 2x2048, AVERAGE delay W-512",
@@ -904,9 +907,14 @@ def serve_configs(G, dev_index, seconds=1.5, precisions=None):
                 "poisson_realtime": dict(rt, rate_per_s=rt_rate), "tick_kernels_eager": ticks,
                 "launch": "one CUDA graph per tick (batch bucket), inputs read from pinned mapped host slots",
                 "form_lead_us": SERVE_FORM_LEAD_US}
+        except G.GwError as e:  # the error is the configuration's result; the other lines still print
+            out[f"config5_{name}"] = {"error": str(e)}
         finally:
             for fn, o in reversed(objs):
-                fn(o)
+                try:
+                    fn(o)
+                except G.GwError:
+                    pass  # a server left in an error state still frees what it can
             G.gw_ctx_destroy(ctx)
     return out
 
