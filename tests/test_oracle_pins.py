@@ -590,3 +590,23 @@ def test_quant_e4m3_matches_torch_in_range():
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
     np.testing.assert_array_equal(quant.to_e4m3(x.astype(np.float32)), ref)
     assert quant.to_e4m3(1e4) == 448.0 and quant.to_e4m3(-1e4) == -448.0
+
+
+# ----------------------------------------------------------------------------
+# The oracle's process pool: distribution only
+# ----------------------------------------------------------------------------
+
+def test_pool_returns_each_windows_serial_forward_in_order():
+    """Worker processes (spawned, one BLAS thread each) return, in the order
+    asked, what the serial oracle gives for each snapshot window, including a
+    window that starts before t = 0 (zero fill) and repeated indices."""
+    from oracle import pool
+    W, S = 256, 64
+    x = rng.standard_normal((21, W + 7 * S))
+    params = synth.deepclean_params(3)
+    ks = [5, 0, 7, 2, 5, 3]
+    got = pool.deepclean_stream_windows(x, W, S, ks, params, synth.DEEPCLEAN_LAYERS, workers=2, chunk=1)
+    ref = np.stack([nets.deepclean_forward(stream.window(x, W, S, k)[None], params, synth.DEEPCLEAN_LAYERS)[0]
+                    for k in ks])
+    assert got.shape == (len(ks), W)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
