@@ -428,11 +428,18 @@ def gpu_arm(args):
         roofline = {"bound": "alu", "kernel": "conv_f32 (8 launches per step)", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
-    configs = extra_configs(G, torch, dev_index, flush)
-    configs.update(bulk_config(G, torch, dev_index, flush))
-    configs.update(study_config(dev_index))
-    configs.update(train_config(G, torch, dev_index, flush))
-    configs.update(serve_configs(G, dev_index))
+    configs = {}
+    # the other configurations: a library error in one is recorded as its
+    # result and the rest still run, so that the line is always printed
+    for name, run in (("configs_1_3", lambda: extra_configs(G, torch, dev_index, flush)),
+                      ("bulk", lambda: bulk_config(G, torch, dev_index, flush)),
+                      ("study", lambda: study_config(dev_index)),
+                      ("config4", lambda: train_config(G, torch, dev_index, flush)),
+                      ("config5", lambda: serve_configs(G, dev_index))):
+        try:
+            configs.update(run())
+        except G.GwError as e:
+            configs[f"{name}_error"] = str(e)
     cpu = cpu_baseline(budget_s=args.cpu_seconds)
     cpu["one_core"] = cpu_baseline_one_core()
     line = {
