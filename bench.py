@@ -492,8 +492,10 @@ def compact_configs(configs):
     """The configs' numbers for the JSON line: scalars (floats to 4 significant
     digits) and one level of nested dicts of scalars; descriptions, series and
     per-kernel tables are left to the stderr record.  config5_bf16 comes last."""
-    def keep(v):
-        return isinstance(v, (int, float, bool)) or v is None or (isinstance(v, str) and len(v) <= 40)
+    def keep(v, key=""):
+        # short strings, and error messages whole
+        return isinstance(v, (int, float, bool)) or v is None or (isinstance(v, str) and
+                                                                   (len(v) <= 40 or key.endswith("error")))
 
     def rnd(v):
         return float(f"{v:.4g}") if isinstance(v, float) else v
@@ -503,17 +505,17 @@ def compact_configs(configs):
     for k in order:
         v = configs[k]
         if not isinstance(v, dict):
-            out[k] = rnd(v) if keep(v) else None
+            out[k] = rnd(v) if keep(v, k) else None
             continue
         c = {}
         for kk, vv in v.items():
             if "kernel" in kk and kk != "kernels_per_tick":
                 continue
             if isinstance(vv, dict):
-                sub = {a: rnd(b) for a, b in vv.items() if keep(b) and "kernel" not in a}
+                sub = {a: rnd(b) for a, b in vv.items() if keep(b, a) and "kernel" not in a}
                 if sub:
                     c[kk] = sub
-            elif keep(vv):
+            elif keep(vv, kk):
                 c[kk] = rnd(vv)
         out[k] = c
     return out
