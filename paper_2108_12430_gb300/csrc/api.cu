@@ -20,13 +20,16 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 // ---- instrumentation ---------------------------------------------------------
 static std::mutex g_prof_mu;
-static bool g_prof_on = false;
+static std::atomic<bool> g_prof_on{false};  // set by the caller, read by every launching thread
 static std::atomic<int64_t> g_launches{0};
 struct ProfRec {
   std::string name;
   cudaEvent_t a, b;
 };
 static std::vector<ProfRec> g_prof;
+// bumped whenever g_prof is cleared, so that a scope opened before a clear
+// (on another thread) does not touch a slot of the new list
+static int64_t g_prof_gen = 0;
 
 // While a CUDA graph is being captured on this thread, launches are neither
 // counted nor timed here: the graph's kernels are counted at each replay.
@@ -34,10 +37,10 @@ static thread_local bool g_capturing = false;
 void prof_set_capturing(bool on) { g_capturing = on; }
 void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-Prof::Prof(const char* name, cudaStream_t s) : slot(-1), st(s) {
+Prof::Prof(const char* name, cudaStream_t s) : slot(-1), gen(0), st(s) {
   if (g_capturing) return;
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (!g_prof_on) return;
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   ProfRec r;
   r.name = name;
@@ -45,12 +48,13 @@ Prof::Prof(const char* name, cudaStream_t s) : slot(-1), st(s) {
   cudaEventRecord(r.a, st);
   g_prof.push_back(r);
   slot = (int)g_prof.size() - 1;
+  gen = g_prof_gen;
 }
 
 Prof::~Prof() {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  cudaEventRecord(g_prof[slot].b, st);
+  if (gen == g_prof_gen) cudaEventRecord(g_prof[slot].b, st);
 }
 
 static void prof_clear() {
@@ -59,6 +63,7 @@ static void prof_clear() {
     cudaEventDestroy(r.b);
   }
   g_prof.clear();
+  ++g_prof_gen;
 }
 
 // ---- per-device launch state ----------------------------------------------
@@ -713,7 +718,7 @@ int gw_profile_enable(int on) {
   GW_API_BEGIN
   std::lock_guard<std::mutex> lk(g_prof_mu);
   prof_clear();
-  g_prof_on = on != 0;
+  g_prof_on.store(on != 0, std::memory_order_relaxed);
   GW_API_END
 }
 

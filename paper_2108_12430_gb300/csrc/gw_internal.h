@@ -157,6 +157,7 @@ struct Prof {
   Prof(const char* name, cudaStream_t st);
   ~Prof();
   int slot;
+  int64_t gen;  // the record list's generation when the slot was taken
   cudaStream_t st;
 };
 void prof_set_capturing(bool on);  // this thread is capturing a CUDA graph
