@@ -142,7 +142,6 @@ struct gw_server {
   int64_t tick_seq = 0;
   std::vector<double> dur_us;    // per bucket: running estimate of a tick's first-stage device time (0 = none yet)
   std::vector<double> dur_b_us;  // ... and of its second stage
-  double t_prev_done = 0;      // completion time of the last completed tick
   bool stop = false, loop_done = false;
   int sticky = 0;
   std::string sticky_msg;
@@ -553,16 +552,6 @@ void done_main(gw_server* s) {
     // their tickets until released below
     lk.unlock();
     const double t_now = now_us();
-    {
-      // device time of the tick's two stages (events around each stage)
-      if (timed) {
-        double& ea = s->dur_us[done.bi];
-        double& eb = s->dur_b_us[done.bi];
-        ea = ea > 0 ? 0.8 * ea + 0.2 * 1e3 * a_ms : 1e3 * a_ms;
-        eb = eb > 0 ? 0.8 * eb + 0.2 * 1e3 * b_ms : 1e3 * b_ms;
-      }
-      s->t_prev_done = t_now;
-    }
     for (int rid : done.reqs) {
       Req& rq = s->reqs[rid];
       const int S = s->streams[rq.stream].S;
@@ -586,7 +575,15 @@ void done_main(gw_server* s) {
     s->st_snap += done.n;
     s->st_ticks += 1;
     s->st_batch_sum += done.n;
-    if (timed) s->st_max_dev = std::max(s->st_max_dev, 1e3 * ((double)a_ms + (double)b_ms));
+    if (timed) {
+      // running estimates of the bucket's two stage times (events around each
+      // stage), read by the loop's tick formation under the same lock
+      double& ea = s->dur_us[done.bi];
+      double& eb = s->dur_b_us[done.bi];
+      ea = ea > 0 ? 0.8 * ea + 0.2 * 1e3 * a_ms : 1e3 * a_ms;
+      eb = eb > 0 ? 0.8 * eb + 0.2 * 1e3 * b_ms : 1e3 * b_ms;
+      s->st_max_dev = std::max(s->st_max_dev, 1e3 * ((double)a_ms + (double)b_ms));
+    }
     s->st_kernels += done.kernels;
     s->t_last = t_now;
     s->cv_done.notify_all();
