@@ -52,10 +52,10 @@ void set_last_error(const std::string& msg);
 enum Act { ACT_NONE = 0, ACT_TANH = 1, ACT_RELU = 2 };
 
 struct LayerSpec {
-  bool transposed;
-  int cin, cout, k, stride, pad_l, pad_r, out_pad;
-  bool bn;
-  int act;
+  bool transposed = false;
+  int cin = 0, cout = 0, k = 1, stride = 1, pad_l = 0, pad_r = 0, out_pad = 0;
+  bool bn = false;
+  int act = ACT_NONE;
   int lout(int lin) const {
     return transposed ? (lin - 1) * stride - pad_l - pad_r + k + out_pad
                       : (lin + pad_l + pad_r - k) / stride + 1;
