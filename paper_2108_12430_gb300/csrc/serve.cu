@@ -606,7 +606,10 @@ void server_free(gw_server* s) {
   }
   s->cv_complete.notify_all();
   if (s->done_th.joinable()) s->done_th.join();
-  if (s->st) cudaStreamSynchronize(s->st);
+  // nothing of the server may still run on any of its streams before the
+  // graphs, workspace and events go
+  for (cudaStream_t q : {s->st, s->side, s->st2})
+    if (q) cudaStreamSynchronize(q);
   for (auto g : s->graphs_b)
     if (g) cudaGraphExecDestroy(g);
   for (auto g : s->graphs)
