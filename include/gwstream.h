@@ -59,7 +59,12 @@ const char* gw_version(void);
 /* ---- context ------------------------------------------------------------
  * One context per GPU.  `hbm_budget_bytes` caps the device memory of every
  * object created under the context (0 = no cap); a create that would exceed
- * it returns GW_EBUDGET and allocates nothing.
+ * it returns GW_EBUDGET and allocates nothing.  Creates make the context's
+ * device current on the calling thread; every other call launches on the
+ * calling thread's current CUDA device, which must be the one of the objects
+ * it is given (a thread that did not create them selects it first).  The
+ * destroy calls switch to the object's device themselves and give the
+ * caller's back.  A server's own threads select its device.
  */
 int gw_ctx_create(int device, size_t hbm_budget_bytes, gw_ctx_t* out);
 int gw_ctx_destroy(gw_ctx_t ctx);

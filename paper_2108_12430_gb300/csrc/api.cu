@@ -203,6 +203,7 @@ static T* upload(gw_model* m, const std::vector<T>& host) {
 
 static void model_free(gw_model* m) {
   if (!m) return;
+  DeviceGuard dg(m->ctx ? m->ctx->device : -1);
   cudaDeviceSynchronize();
   for (void* p : m->allocs) cudaFree(p);
   if (m->ws) cudaFree(m->ws);
@@ -680,6 +681,7 @@ namespace gw {
 
 static void stream_free(gw_stream* s) {
   if (!s) return;
+  DeviceGuard dg(s->ctx ? s->ctx->device : -1);
   cudaDeviceSynchronize();
   for (void* p : s->allocs) cudaFree(p);
   if (s->reject_h) cudaFreeHost(s->reject_h);
@@ -1134,6 +1136,7 @@ int gw_fir_create_lowpass(gw_ctx_t ctx, double fc, double fs, int ntaps, int pre
 int gw_fir_destroy(gw_fir_t f) {
   GW_API_BEGIN
   GW_CHECK_ARG(f, "fir is NULL");
+  DeviceGuard dg(f->ctx ? f->ctx->device : -1);
   cudaDeviceSynchronize();
   if (f->d_taps) cudaFree(f->d_taps);
   for (void* p : f->allocs) cudaFree(p);

@@ -153,6 +153,25 @@ namespace gw {
 // ---- instrumentation -------------------------------------------------------
 // Every launch site opens a Prof scope: it counts the launch and, when
 // profiling is on, records CUDA events around it on the launching stream.
+// Makes `device` current for a scope (device < 0: leaves it as it is) and
+// gives the caller's device back at its end (object teardown synchronises
+// and frees on the object's device).
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int device) {
+    if (device < 0 || cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      return;
+    }
+    if (prev != device) cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 struct Prof {
   Prof(const char* name, cudaStream_t st);
   ~Prof();

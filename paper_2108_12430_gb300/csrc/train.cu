@@ -102,6 +102,7 @@ T* talloc(gw_trainer* t, size_t count) {
 
 void trainer_free(gw_trainer* t) {
   if (!t) return;
+  DeviceGuard dg(t->ctx ? t->ctx->device : -1);
   cudaDeviceSynchronize();
   for (auto& a : t->allocs) dev_free(t->ctx, a.first, a.second, nullptr);
   bool first = true;  // the tensor-core layers' bytes are returned to the budget with the first of their buffers
