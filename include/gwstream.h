@@ -65,6 +65,8 @@ const char* gw_version(void);
  * it is given (a thread that did not create them selects it first).  The
  * destroy calls switch to the object's device themselves and give the
  * caller's back.  A server's own threads select its device.
+ * gw_ctx_destroy frees the context alone: destroy every object created
+ * under it first (an object destroyed after its context reads freed memory).
  */
 int gw_ctx_create(int device, size_t hbm_budget_bytes, gw_ctx_t* out);
 int gw_ctx_destroy(gw_ctx_t ctx);
