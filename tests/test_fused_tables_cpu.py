@@ -9,9 +9,11 @@ generator writes.
 """
 import os
 
+import numpy as np
 import pytest
 
 from paper_2108_12430_gb300 import gen_fused_tables as gft
+from paper_2108_12430_gb300 import gwstream as G
 
 HEADER = os.path.join(os.path.dirname(gft.__file__), "csrc", "fused_tables.h")
 
@@ -72,3 +74,33 @@ def test_first_layer_keeps_the_host_order():
 def test_committed_header_is_current():
     with open(HEADER) as f:
         assert f.read() == gft.render()
+
+
+def decode(code):
+    """A K-step table word of the host lowering: (channel group, phase plane, row shift)."""
+    return code & 255, (code >> 8) & 63, code >> 14
+
+
+@pytest.mark.parametrize("li", range(len(gft.LAYERS) - 1))
+def test_tables_match_the_libraries_own_lowering(li):
+    """The library lowers each hidden layer itself (gw_tc_inspect, host only;
+    the same lowering the per-layer kernel runs and the model checks the
+    tables against before it uses the whole-network kernel): same geometry,
+    and every kernel step's A-operand start and LBO, computed from the
+    library's slice codes with the whole-network buffers' rows per plane,
+    equal the header's packed value.  (The output layer is lowered there with
+    another folding, so only the model-creation check covers it.)"""
+    tr, cin, cout, k, s, pad, op, J = gft.LAYERS[li]
+    m, order, _ = lowered()[li]
+    _, table, md = G.gw_tc_inspect((tr, cin, cout, k, s, pad, pad, op), G.GW_BF16, np.zeros((cout, cin, k)),
+                                   32768, 0, 1, 64)
+    assert (md["Q"], md["n_steps"], md["npad"], md["in_P"], md["dmin"], md["groups"], md["coutp"]) == \
+        (m["Q"], m["n_steps"], m["npad"], m["P"], m["dmin"], m["G"], m["coutp"])
+    assert 128 + md["dspan"] == m["rows"]
+    rows, P = m["rows"], m["P"]
+    packed = gft.apack_of(m, order)
+    for i, h in enumerate(order):
+        o0, o1 = (((g * P + phi) * rows + dd) * 16 for g, phi, dd in (decode(int(table[2 * h])),
+                                                                       decode(int(table[2 * h + 1]))))
+        assert o1 >= o0
+        assert packed[i] == (o0 >> 4) | (((o1 - o0) >> 4) << 16), (li, i)
