@@ -36,6 +36,26 @@ def test_deepclean_config1_bf16(ctx):
     assert err <= TOL16
 
 
+def test_bf16_deepclean_is_one_whole_network_launch(ctx):
+    """A BF16 DeepClean model runs the whole-network kernel, one launch per
+    forward.  The per-layer kernels give results within the same tolerance,
+    so only the launch list shows a model that fell back to them."""
+    x = synth.witness_channels(1, 21, 4096)
+    m = ctx.deepclean(0, G.GW_BF16)
+    xd = dev(x)
+    y = torch.zeros(1, 4096, device="cuda")
+    G.gw_deepclean_forward(m, xd.data_ptr(), 4096, 0, 1, 4096, y.data_ptr())  # the workspace is made here
+    torch.cuda.synchronize()
+    G.gw_profile_enable(True)
+    try:
+        G.gw_deepclean_forward(m, xd.data_ptr(), 4096, 0, 1, 4096, y.data_ptr())
+        prof = G.gw_profile_read()
+    finally:
+        G.gw_profile_enable(False)
+    assert prof.get("deepclean_fused", (0.0, 0))[1] == 1, prof
+    assert not any(k.startswith("conv_tc") for k in prof), prof
+
+
 @pytest.mark.parametrize("B,L,stride", [(3, 1000, 1000), (5, 2056, 264), (2, 8, 8), (1, 4104, 0)])
 def test_deepclean_ragged_and_views_bf16(ctx, B, L, stride):
     ld = L + (B - 1) * stride
