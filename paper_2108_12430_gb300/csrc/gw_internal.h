@@ -150,9 +150,6 @@ struct gw_fir {
 
 namespace gw {
 
-// ---- instrumentation -------------------------------------------------------
-// Every launch site opens a Prof scope: it counts the launch and, when
-// profiling is on, records CUDA events around it on the launching stream.
 // Makes `device` current for a scope (device < 0: leaves it as it is) and
 // gives the caller's device back at its end (object teardown synchronises
 // and frees on the object's device).
@@ -172,6 +169,9 @@ struct DeviceGuard {
   DeviceGuard& operator=(const DeviceGuard&) = delete;
 };
 
+// ---- instrumentation -------------------------------------------------------
+// Every launch site opens a Prof scope: it counts the launch and, when
+// profiling is on, records CUDA events around it on the launching stream.
 struct Prof {
   Prof(const char* name, cudaStream_t st);
   ~Prof();
